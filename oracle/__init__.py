@@ -89,7 +89,9 @@ def _dptr(a):
 
 
 def _as_c128(a):
-    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    """complex128, C-contiguous, rank preserved (rank-0 stays a scalar)."""
+    a = np.asarray(a, dtype=np.complex128)
+    return a if a.flags.c_contiguous else a.copy(order="C")
 
 
 def _out_shape(sa, sb, axes_a, axes_b):
@@ -174,12 +176,25 @@ def contract(network, path, nthreads=None):
 
 
 def greedy_path(network):
-    """The oracle's own pairwise order: repeatedly join the connected pair with
-    the smallest result (ties: lowest ids); disconnected pieces last."""
+    """The oracle's own pairwise order: repeatedly join the connected pair whose
+    result has the fewest entries, ties to the smaller (result entries - entries
+    of the two operands), then to the lowest ids; disconnected pieces are
+    joined last.  Any order gives the same result up to rounding."""
     labels = {i: list(l) for i, l in enumerate(network.labels)}
+    ext = {}
+    for t, l in zip(network.tensors, network.labels):
+        for x, e in zip(l, np.shape(t)):
+            ext[x] = e
     out = set(network.out_labels)
     nxt = len(labels)
     path = []
+
+    def size(ls):
+        p = 1
+        for x in ls:
+            p *= ext[x]
+        return p
+
     while len(labels) > 1:
         best = None
         ids = sorted(labels)
@@ -193,8 +208,8 @@ def greedy_path(network):
                 if not shared:
                     continue
                 summed = {x for x in shared if x not in out and count[x] == 2}
-                rank = len(labels[i]) + len(labels[j]) - 2 * len(summed)
-                key = (rank, i, j)
+                res = [x for x in labels[i] if x not in summed] + [x for x in labels[j] if x not in summed]
+                key = (size(res), size(res) - size(labels[i]) - size(labels[j]), i, j)
                 if best is None or key < best[0]:
                     best = (key, i, j, summed)
         if best is None:  # disconnected: outer product of the two lowest ids

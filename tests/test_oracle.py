@@ -45,6 +45,9 @@ CASES = [
     ((5,), (5,), [0], [0]),                      # dot
     ((2, 2, 2, 2, 2), (2, 2, 2, 2), [4, 0, 2], [1, 3, 0]),
     ((1, 3, 1), (3, 1, 2), [1, 2], [0, 1]),      # extent-1 axes
+    ((), (3,), [], []),                          # rank-0 operand (scalar times tensor)
+    ((2, 5), (), [], []),
+    ((), (), [], []),
 ]
 
 
