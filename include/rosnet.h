@@ -1,0 +1,277 @@
+/*
+ * rosnet.h -- C ABI of the B300 block tensor library (librosnet.so).
+ *
+ * The library computes the blocked pairwise tensordot of the RosneT paper
+ * (Sanchez-Ramirez et al., "RosneT: A Block Tensor Algebra Library for
+ * Out-of-Core Quantum Computing Simulation"):
+ *
+ *   - a block tensor is a tensor cut into a uniform grid of equally shaped
+ *     blocks (Sec. II-C, "Dimension Extents" layout);
+ *   - the pairwise contraction C[fA, fB] = sum_k A[fA, k] B[k, fB] of Sec. II-A
+ *     is computed per output block as the sum, over the pairs of A and B blocks
+ *     matched on the contracted-index block coordinates, of the local
+ *     contraction of each pair (Sec. II-C steps 1-4); the order of that sum is
+ *     free (Sec. IV-A, commutative reduction);
+ *   - a tensor network (e.g. a quantum circuit, Sec. II-A) is contracted as a
+ *     sequence of such pairwise contractions.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *   * Element types: complex64 (two float32) or complex128 (two float64).
+ *   * Host buffers passed to upload/download are DENSE, ROW-MAJOR and
+ *     INTERLEAVED (re, im, re, im, ...), i.e. numpy's C-order complex arrays.
+ *   * Device storage is owned by the library: block-major (all blocks laid out
+ *     one after another in row-major order of their grid coordinates, each
+ *     block row-major inside) and planar (all real parts, then all imaginary
+ *     parts).  Callers never need to know this layout.
+ *   * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a call is enqueued on that stream; calls
+ *     return without waiting for it unless stated otherwise.  Errors raised by
+ *     kernels after a call has returned are reported by rosnet_sync().
+ *   * Every call returns a rosnet_status (0 = ROSNET_OK, negative = error).
+ *     No C++ exception crosses the ABI.  On error, output handles are set to
+ *     NULL and nothing is leaked.  Handles returned by create / tensordot /
+ *     contract belong to the caller, who must pass them to
+ *     rosnet_btensor_destroy.  Input handles are never modified or freed.
+ *   * The library is for one GPU: it uses the CUDA device that is current on
+ *     the calling thread.
+ */
+#ifndef ROSNET_H
+#define ROSNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------- */
+/* status codes                                                             */
+/* ----------------------------------------------------------------------- */
+typedef int rosnet_status;
+#define ROSNET_OK                  0
+#define ROSNET_ERR_INVALID_ARG    -1  /* NULL handle/pointer, bad axis, bad enum   */
+#define ROSNET_ERR_SHAPE          -2  /* extents of contracted axes differ, bad shape */
+#define ROSNET_ERR_BLOCK_MISMATCH -3  /* block extent does not divide the extent, or
+                                         contracted axes have different block extents */
+#define ROSNET_ERR_DTYPE          -4  /* operands of different element types        */
+#define ROSNET_ERR_ALLOC          -5  /* the allocator returned NULL                 */
+#define ROSNET_ERR_RANK_LIMIT     -6  /* rank > ROSNET_MAX_RANK                       */
+#define ROSNET_ERR_CUDA           -7  /* a CUDA runtime call failed                   */
+#define ROSNET_ERR_TIMEOUT        -8  /* a bounded device-side wait gave up           */
+#define ROSNET_ERR_UNSUPPORTED    -9  /* e.g. a precision mode for the wrong dtype    */
+
+/* Tensors of any rank from 0 to ROSNET_MAX_RANK are accepted (the paper
+ * needs more than numpy's 32 dimensions, Sec. V). */
+#define ROSNET_MAX_RANK 64
+
+typedef enum {
+    ROSNET_C64 = 1,   /* complex64: float32 real and imaginary parts  */
+    ROSNET_C128 = 2   /* complex128: float64 real and imaginary parts */
+} rosnet_dtype;
+
+/* Arithmetic used for the block products (the sum is always accumulated in
+ * at least float32; see each mode). */
+typedef enum {
+    ROSNET_PREC_DEFAULT = 0, /* FP32 CUDA cores for C64, FP64 for C128            */
+    ROSNET_PREC_FP32 = 1,    /* C64 only: float32 products and sums (CUDA cores)  */
+    ROSNET_PREC_TF32 = 2,    /* C64 only: TF32 tensor-core products, FP32 sums    */
+    ROSNET_PREC_BF16X3 = 3,  /* C64 only: each float32 operand split into bf16
+                                hi + lo; hi*hi + hi*lo + lo*hi on tensor cores,
+                                FP32 sums                                         */
+    ROSNET_PREC_FP64 = 4     /* C128 only: float64 products and sums              */
+} rosnet_precision;
+
+typedef struct rosnet_btensor_s *rosnet_btensor;
+
+/* Options of tensordot/contract (pass NULL for defaults: all fields 0). */
+typedef struct {
+    int32_t precision;          /* a rosnet_precision                                */
+    int32_t flags;              /* ROSNET_OPT_* bits                                 */
+    int64_t max_block_entries;  /* contract only: if > 0, every intermediate whose
+                                   block holds more entries is re-blocked by turning
+                                   its slowest-varying axes into grid axes until the
+                                   block fits (0 = blocks inherited from operands)  */
+    int64_t reserved[6];        /* must be 0                                         */
+} rosnet_opts;
+
+#define ROSNET_OPT_GRAPH  0x1   /* contract: capture the step sequence in a CUDA
+                                   graph on first use and replay it afterwards      */
+#define ROSNET_OPT_NOGROUP 0x2  /* contract: one launch per step instead of one
+                                   grouped launch per dependency wave               */
+#define ROSNET_OPT_TIMING 0x4   /* contract: record CUDA events around the plan's
+                                   heaviest launch (most 8*M*N*K flops) on the
+                                   call's stream; read with rosnet_timing_drain    */
+
+/* ----------------------------------------------------------------------- */
+/* memory                                                                   */
+/* ----------------------------------------------------------------------- */
+/*
+ * Replace the device allocator.  alloc(bytes, stream, ctx) must return device
+ * memory usable in stream order on `stream` (or NULL on failure); free(ptr,
+ * stream, ctx) releases it in stream order.  Passing alloc = free = NULL
+ * restores the built-in allocator (cudaMallocAsync / cudaFreeAsync on the
+ * device's default memory pool).  Not thread-safe with concurrent calls.
+ */
+rosnet_status rosnet_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
+                                   void (*free)(void *ptr, void *stream, void *ctx),
+                                   void *ctx);
+
+/* ----------------------------------------------------------------------- */
+/* block tensors (Sec. II-C)                                                */
+/* ----------------------------------------------------------------------- */
+/*
+ * Create an uninitialised block tensor of `rank` axes with extents shape[i]
+ * and block extents block_shape[i] (block_shape may be NULL: one block).
+ * Each block_shape[i] must be >= 1 and divide shape[i]; the grid extent of
+ * axis i is shape[i] / block_shape[i].  Device memory (numel * element size)
+ * comes from the allocator in stream order on `stream`.
+ * Errors: INVALID_ARG (out == NULL, shape == NULL with rank > 0, extent < 0),
+ * RANK_LIMIT, BLOCK_MISMATCH, DTYPE, ALLOC.
+ */
+rosnet_status rosnet_btensor_create(int rank, const int64_t *shape, const int64_t *block_shape,
+                                    rosnet_dtype dtype, void *stream, rosnet_btensor *out);
+
+/* Release a tensor (stream-ordered on the stream it was created or last
+ * written on).  NULL is accepted and ignored. */
+rosnet_status rosnet_btensor_destroy(rosnet_btensor t);
+
+/*
+ * Copy a dense row-major interleaved host array (numel complex values of the
+ * tensor's dtype) into the tensor.  The host buffer may be pageable or pinned;
+ * it is read before the call returns if pageable, or in stream order if it is
+ * pinned (the caller must keep it alive until the stream reaches the copy).
+ */
+rosnet_status rosnet_btensor_upload(rosnet_btensor t, const void *host, void *stream);
+
+/* Copy the tensor into a dense row-major interleaved host array.  Blocks
+ * until the data is on the host (synchronises `stream`). */
+rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream);
+
+/* Shape, block shape (arrays of at least `rank` entries; either may be NULL)
+ * and dtype (may be NULL) of a tensor.  *rank is always written. */
+rosnet_status rosnet_btensor_info(rosnet_btensor t, int *rank, int64_t *shape,
+                                  int64_t *block_shape, rosnet_dtype *dtype);
+
+/* Device addresses of the real and imaginary planes (block-major layout);
+ * for callers that move blocks themselves.  Either output may be NULL. */
+rosnet_status rosnet_btensor_planes(rosnet_btensor t, void **re, void **im);
+
+/* ----------------------------------------------------------------------- */
+/* pairwise blocked tensordot (Sec. II-A, II-C, IV-A)                       */
+/* ----------------------------------------------------------------------- */
+/*
+ * C = tensordot(A, B, axes=(axes_a, axes_b)) with numpy's conventions: axis
+ * axes_a[i] of A is contracted with axis axes_b[i] of B; C's axes are A's free
+ * axes in order followed by B's free axes in order; naxes = 0 is the outer
+ * product; contracting every axis gives a rank-0 tensor (one value).
+ * Block rules (Sec. II-C): contracted pairs must have equal extents (else
+ * SHAPE) and equal block extents (else BLOCK_MISMATCH); C's block extents are
+ * those of the free axes, so an output block is the sum over the B_k matched
+ * block pairs.  A and B must have the same dtype (else DTYPE); opts->precision
+ * must suit it (else UNSUPPORTED).  *out_C is a new tensor owned by the caller.
+ */
+rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes,
+                               const int *axes_a, const int *axes_b,
+                               const rosnet_opts *opts, void *stream, rosnet_btensor *out_C);
+
+/* ----------------------------------------------------------------------- */
+/* networks (Sec. II-A)                                                     */
+/* ----------------------------------------------------------------------- */
+/*
+ * A tensor network: tensor t has ranks[t] axes labelled labels[t][0..ranks[t]).
+ * A label carried by two tensors is a bond and is summed over when they are
+ * joined, unless it appears in out_labels; out_labels (nout entries, each
+ * carried by exactly one tensor) stay open and give the result's axis order.
+ * Labels are arbitrary int64 values; every tensor must share the dtype.
+ */
+typedef struct {
+    int32_t ntensors;
+    const rosnet_btensor *tensors;
+    const int32_t *ranks;
+    const int64_t *const *labels;
+    int32_t nout;
+    const int64_t *out_labels;
+} rosnet_network;
+
+/*
+ * A contraction path in SSA form: step s joins the tensors with ids
+ * pairs[2s] and pairs[2s+1] and creates id ntensors + s.  A full path has
+ * ntensors - 1 steps.
+ */
+typedef struct {
+    int32_t nsteps;
+    const int32_t *pairs;
+} rosnet_path;
+
+/*
+ * A greedy min-size path (the paper takes its paths from an external path
+ * optimiser, Sec. V; this one is the library's own): at each step join the
+ * pair of tensors sharing at least one label whose result is smallest; ties go
+ * to the smaller size(result) - size(a) - size(b), then to the lowest ids;
+ * disconnected pieces are joined last by outer products.  pairs_out must hold
+ * 2 * (ntensors - 1) ints; *nsteps receives ntensors - 1.  Host-only.
+ */
+rosnet_status rosnet_path_greedy(const rosnet_network *net, int32_t *pairs_out, int32_t *nsteps);
+
+/* The same greedy path from labels and extents alone (no tensors, no GPU):
+ * tensor t has ranks[t] axes with labels[t][i] and extents extents[t][i].
+ * Errors: INVALID_ARG, SHAPE (a label with two extents), UNSUPPORTED (a label
+ * on more than two tensors), RANK_LIMIT. */
+rosnet_status rosnet_path_greedy_extents(int32_t ntensors, const int32_t *ranks,
+                                         const int64_t *const *labels,
+                                         const int64_t *const *extents, int32_t nout,
+                                         const int64_t *out_labels, int32_t *pairs_out,
+                                         int32_t *nsteps);
+
+/*
+ * Contract a network along a path; *out is a new tensor whose axes follow
+ * out_labels (rank 0 for a closed network such as one amplitude).
+ * Intermediates live in one device arena sized from their lifetimes.  With
+ * ROSNET_OPT_GRAPH the launch sequence is captured in a CUDA graph, keyed by
+ * the network's structure (shapes, labels, path, options), and replayed on
+ * later calls with the same structure.  Errors as rosnet_tensordot, plus
+ * INVALID_ARG for a malformed path or labels.
+ */
+rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path,
+                              const rosnet_opts *opts, void *stream, rosnet_btensor *out);
+
+/*
+ * Elapsed device time of the heaviest launch of every rosnet_contract call
+ * made with ROSNET_OPT_TIMING since the last drain (oldest first, at most the
+ * newest 4096).  Waits for those events.  ms[i] receives the milliseconds,
+ * flops[i] / bytes[i] (either may be NULL) the launch's algorithmic work:
+ * sum of 8*M*N*K and of (|A| + |B| + |C|) * element size over its problems.
+ * *n receives the number of entries written (<= max_entries).
+ */
+rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t max_entries,
+                                  int32_t *n);
+
+/* Free every cached contraction plan (arena, offset tables, descriptors,
+ * CUDA graph).  Plans are cached by rosnet_contract and kept until this call;
+ * the caller must make sure no contraction is still running. */
+rosnet_status rosnet_release_plans(void);
+
+/* ----------------------------------------------------------------------- */
+/* misc                                                                     */
+/* ----------------------------------------------------------------------- */
+/* Wait for `stream`; returns CUDA if a kernel failed, TIMEOUT if a bounded
+ * device wait of the library gave up. */
+rosnet_status rosnet_sync(void *stream);
+
+/* Static, human-readable description of a status code. */
+const char *rosnet_status_string(rosnet_status s);
+
+/* Message of the last error raised on the calling thread (static storage
+ * owned by the library; valid until the thread's next failing call). */
+const char *rosnet_last_error(void);
+
+/* Number of kernels the library has launched in this process (for
+ * accounting; graph replays count each kernel node). */
+int64_t rosnet_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROSNET_H */

@@ -1,0 +1,453 @@
+"""Python binding of librosnet, the B300 blocked pairwise tensordot library.
+
+Argument marshalling only: every step of a contraction runs in the CUDA
+kernels of ``librosnet.so`` (built from ``csrc/`` by ``build.py``).  There is
+no CPU fallback: importing works without a GPU, but any call that needs the
+device raises ``RosnetError`` if the library or the GPU is missing.
+
+PyTorch provides device memory (its caching allocator is installed as the
+library's allocator) and streams (``torch.cuda.current_stream()`` by
+default).
+
+The C ABI is declared in ``include/rosnet.h``; the names here mirror it:
+
+* ``BTensor`` -- a block tensor handle (Sec. II-C of the RosneT paper),
+  created with ``btensor(array, block_shape)`` or ``empty(...)``;
+* ``tensordot(A, B, axes_a, axes_b, precision=...)`` -- the blocked pairwise
+  contraction (Sec. II-A, II-C);
+* ``path_greedy(...)`` and ``contract(...)`` -- a network contracted along a
+  pairwise path (Sec. II-A).
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
+    "path_greedy_extents", "contract",
+    "sync", "kernel_launches", "release_plans", "lib", "use_torch_allocator",
+    "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
+    "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librosnet.so")
+
+C64, C128 = 1, 2
+PREC_DEFAULT, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_FP64 = 0, 1, 2, 3, 4
+OPT_GRAPH, OPT_NOGROUP, OPT_TIMING = 0x1, 0x2, 0x4
+STATUS = {
+    0: "OK", -1: "INVALID_ARG", -2: "SHAPE", -3: "BLOCK_MISMATCH", -4: "DTYPE", -5: "ALLOC",
+    -6: "RANK_LIMIT", -7: "CUDA", -8: "TIMEOUT", -9: "UNSUPPORTED",
+}
+#: every function the header declares
+EXPORTS = [
+    "rosnet_set_allocator", "rosnet_btensor_create", "rosnet_btensor_destroy",
+    "rosnet_btensor_upload", "rosnet_btensor_download", "rosnet_btensor_info",
+    "rosnet_btensor_planes", "rosnet_tensordot", "rosnet_path_greedy", "rosnet_contract",
+    "rosnet_release_plans", "rosnet_sync", "rosnet_status_string", "rosnet_last_error",
+    "rosnet_kernel_launches", "rosnet_path_greedy_extents", "rosnet_timing_drain",
+]
+
+_lock = threading.Lock()
+_lib = None
+_alloc_cbs = None
+
+
+class RosnetError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        msg = ""
+        if _lib is not None:
+            msg = _lib.rosnet_last_error().decode(errors="replace")
+        super().__init__(f"{where}: ROSNET_ERR_{self.name} ({status}) {msg}".strip())
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("max_block_entries", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
+
+
+class _Network(ctypes.Structure):
+    _fields_ = [("ntensors", ctypes.c_int32), ("tensors", ctypes.POINTER(ctypes.c_void_p)),
+                ("ranks", ctypes.POINTER(ctypes.c_int32)),
+                ("labels", ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))),
+                ("nout", ctypes.c_int32), ("out_labels", ctypes.POINTER(ctypes.c_int64))]
+
+
+class _Path(ctypes.Structure):
+    _fields_ = [("nsteps", ctypes.c_int32), ("pairs", ctypes.POINTER(ctypes.c_int32))]
+
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def lib():
+    """Load librosnet.so (no GPU needed to load it)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RosnetError(-7, f"librosnet.so not built at {LIB_PATH}; run "
+                                      "python -m paper_2201_06620_b300.build")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64p, i32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)
+            L.rosnet_set_allocator.argtypes = [_ALLOC_T, _FREE_T, vp]
+            L.rosnet_btensor_create.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, vp,
+                                                ctypes.POINTER(vp)]
+            L.rosnet_btensor_destroy.argtypes = [vp]
+            L.rosnet_btensor_upload.argtypes = [vp, vp, vp]
+            L.rosnet_btensor_download.argtypes = [vp, vp, vp]
+            L.rosnet_btensor_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i64p, i64p,
+                                              ctypes.POINTER(ctypes.c_int)]
+            L.rosnet_btensor_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+            L.rosnet_tensordot.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_Opts), vp,
+                                           ctypes.POINTER(vp)]
+            L.rosnet_path_greedy.argtypes = [ctypes.POINTER(_Network), i32p, i32p]
+            L.rosnet_path_greedy_extents.argtypes = [
+                ctypes.c_int32, i32p, ctypes.POINTER(i64p), ctypes.POINTER(i64p), ctypes.c_int32,
+                i64p, i32p, i32p]
+            L.rosnet_contract.argtypes = [ctypes.POINTER(_Network), ctypes.POINTER(_Path),
+                                          ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+            L.rosnet_release_plans.argtypes = []
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.rosnet_timing_drain.argtypes = [dp, dp, dp, ctypes.c_int32, i32p]
+            L.rosnet_sync.argtypes = [vp]
+            L.rosnet_status_string.argtypes = [ctypes.c_int]
+            L.rosnet_status_string.restype = ctypes.c_char_p
+            L.rosnet_last_error.argtypes = []
+            L.rosnet_last_error.restype = ctypes.c_char_p
+            L.rosnet_kernel_launches.argtypes = []
+            L.rosnet_kernel_launches.restype = ctypes.c_int64
+            for name in EXPORTS:
+                f = getattr(L, name)
+                if f.restype is ctypes.c_int or name in (
+                        "rosnet_set_allocator", "rosnet_btensor_create", "rosnet_btensor_destroy",
+                        "rosnet_btensor_upload", "rosnet_btensor_download", "rosnet_btensor_info",
+                        "rosnet_btensor_planes", "rosnet_tensordot", "rosnet_path_greedy",
+                        "rosnet_contract", "rosnet_release_plans", "rosnet_sync",
+                        "rosnet_path_greedy_extents", "rosnet_timing_drain"):
+                    f.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != 0:
+        raise RosnetError(status, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _default_stream():
+    torch = _torch()
+    if not torch.cuda.is_available():
+        raise RosnetError(-7, "no CUDA device available (librosnet has no CPU fallback)")
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _stream(stream):
+    if stream is None:
+        return _default_stream()
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def use_torch_allocator(enable=True):
+    """Route the library's device allocations through torch's caching allocator
+    (enable=False restores the built-in cudaMallocAsync pool)."""
+    global _alloc_cbs
+    L = lib()
+    if not enable:
+        _check(L.rosnet_set_allocator(_ALLOC_T(), _FREE_T(), None), "rosnet_set_allocator")
+        _alloc_cbs = None
+        return
+    torch = _torch()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # out of memory -> NULL -> ROSNET_ERR_ALLOC
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _alloc_cbs = (_ALLOC_T(_alloc), _FREE_T(_free))
+    _check(L.rosnet_set_allocator(_alloc_cbs[0], _alloc_cbs[1], None), "rosnet_set_allocator")
+
+
+_init_done = False
+_shutting_down = False
+
+
+def _at_exit():
+    """Free cached plans while the Python allocator callbacks still work, then
+    stop touching device memory from finalisers."""
+    global _shutting_down
+    try:
+        if _lib is not None and _alloc_cbs is not None:
+            _lib.rosnet_release_plans()
+    finally:
+        _shutting_down = True
+
+
+def _init():
+    global _init_done
+    if not _init_done:
+        lib()
+        torch = _torch()
+        if torch.cuda.is_available():
+            torch.cuda.init()
+            use_torch_allocator(True)
+            atexit.register(_at_exit)
+        _init_done = True
+
+
+def _i64arr(seq):
+    seq = [int(x) for x in seq]
+    return (ctypes.c_int64 * max(1, len(seq)))(*seq)
+
+
+def _i32arr(seq):
+    seq = [int(x) for x in seq]
+    return (ctypes.c_int * max(1, len(seq)))(*seq)
+
+
+def _np_dtype(dt):
+    return np.complex64 if dt == C64 else np.complex128
+
+
+class BTensor:
+    """Owning handle of a device block tensor."""
+
+    __slots__ = ("_h", "shape", "block_shape", "dtype", "__weakref__")
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+        L = lib()
+        r = ctypes.c_int()
+        sh = (ctypes.c_int64 * 64)()
+        bl = (ctypes.c_int64 * 64)()
+        dt = ctypes.c_int()
+        _check(L.rosnet_btensor_info(self._h, ctypes.byref(r), sh, bl, ctypes.byref(dt)), "info")
+        self.shape = tuple(sh[i] for i in range(r.value))
+        self.block_shape = tuple(bl[i] for i in range(r.value))
+        self.dtype = dt.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def rank(self):
+        return len(self.shape)
+
+    @property
+    def numel(self):
+        return int(np.prod(self.shape, dtype=np.int64)) if self.shape else 1
+
+    def planes(self):
+        re, im = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().rosnet_btensor_planes(self._h, ctypes.byref(re), ctypes.byref(im)), "planes")
+        return re.value, im.value
+
+    def upload(self, array, stream=None):
+        """Copy a host array (numpy, or a pinned torch CPU tensor) into the tensor."""
+        if hasattr(array, "data_ptr"):  # torch CPU tensor (e.g. pinned)
+            ptr = array.data_ptr()
+            keep = array
+        else:
+            keep = np.asarray(array, dtype=_np_dtype(self.dtype), order="C")
+            if keep.shape != self.shape:
+                raise ValueError(f"shape {keep.shape} != tensor shape {self.shape}")
+            ptr = keep.ctypes.data
+        _check(lib().rosnet_btensor_upload(self._h, ctypes.c_void_p(ptr), _stream(stream)), "upload")
+        return keep
+
+    def download(self, out=None, stream=None):
+        """Dense row-major host copy (numpy); synchronises the stream."""
+        if out is None:
+            out = np.empty(self.shape, dtype=_np_dtype(self.dtype))
+        if hasattr(out, "data_ptr"):
+            ptr = out.data_ptr()
+        else:
+            ptr = out.ctypes.data
+        _check(lib().rosnet_btensor_download(self._h, ctypes.c_void_p(ptr), _stream(stream)),
+               "download")
+        return out
+
+    def destroy(self):
+        if _shutting_down:   # the allocator behind the handle may be gone
+            self._h = None
+            return
+        if self._h is not None and self._h.value:
+            lib().rosnet_btensor_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __repr__(self):
+        return f"BTensor(shape={self.shape}, block_shape={self.block_shape}, dtype={'c64' if self.dtype == C64 else 'c128'})"
+
+
+def empty(shape, block_shape=None, dtype=C64, stream=None):
+    _init()
+    h = ctypes.c_void_p()
+    bl = _i64arr(block_shape) if block_shape is not None else None
+    _check(lib().rosnet_btensor_create(len(shape), _i64arr(shape), bl, int(dtype), _stream(stream),
+                                       ctypes.byref(h)), "rosnet_btensor_create")
+    return BTensor(h.value)
+
+
+def btensor(array, block_shape=None, dtype=None, stream=None):
+    """Create a block tensor from a host array and upload it."""
+    array = np.asarray(array)
+    if dtype is None:
+        dtype = C128 if array.dtype == np.complex128 else C64
+    t = empty(array.shape, block_shape, dtype, stream)
+    t.upload(array, stream)
+    return t
+
+
+def _opts(precision, flags=0, max_block_entries=0):
+    o = _Opts()
+    o.precision = int(precision)
+    o.flags = int(flags)
+    o.max_block_entries = int(max_block_entries)
+    return o
+
+
+def tensordot(A, B, axes_a, axes_b, precision=PREC_DEFAULT, stream=None):
+    """C = tensordot(A, B, axes=(axes_a, axes_b)) on the GPU (numpy conventions)."""
+    _init()
+    h = ctypes.c_void_p()
+    o = _opts(precision)
+    _check(lib().rosnet_tensordot(A.handle, B.handle, len(axes_a), _i32arr(axes_a), _i32arr(axes_b),
+                                  ctypes.byref(o), _stream(stream), ctypes.byref(h)),
+           "rosnet_tensordot")
+    return BTensor(h.value)
+
+
+class Network:
+    """A network prepared for repeated contraction: the ctypes view of its
+    tensors, labels and output labels is built once; ``set_tensor`` swaps a
+    leaf (e.g. the output-bitstring projectors of an amplitude query) without
+    rebuilding it."""
+
+    def __init__(self, tensors, labels, out_labels=()):
+        n = len(tensors)
+        self.tensors = list(tensors)
+        self.labels = [tuple(int(x) for x in l) for l in labels]
+        self.out_labels = [int(x) for x in out_labels]
+        self.handles = (ctypes.c_void_p * max(1, n))(*[t.handle.value for t in tensors])
+        self.ranks = (ctypes.c_int32 * max(1, n))(*[len(l) for l in labels])
+        self._lab = [_i64arr(l) for l in labels]
+        self._labp = (ctypes.POINTER(ctypes.c_int64) * max(1, n))(
+            *[ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)) for a in self._lab])
+        self._out = _i64arr(out_labels)
+        self.net = _Network(n, ctypes.cast(self.handles, ctypes.POINTER(ctypes.c_void_p)),
+                            ctypes.cast(self.ranks, ctypes.POINTER(ctypes.c_int32)),
+                            ctypes.cast(self._labp, ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))),
+                            len(out_labels), ctypes.cast(self._out, ctypes.POINTER(ctypes.c_int64)))
+        self._path = None
+        self._path_key = None
+
+    def set_tensor(self, i, t):
+        self.tensors[i] = t
+        self.handles[i] = t.handle.value
+
+    def greedy_path(self):
+        n = len(self.tensors)
+        pairs = (ctypes.c_int32 * max(1, 2 * (n - 1)))()
+        ns = ctypes.c_int32()
+        _check(lib().rosnet_path_greedy(ctypes.byref(self.net), pairs, ctypes.byref(ns)),
+               "rosnet_path_greedy")
+        return [(pairs[2 * i], pairs[2 * i + 1]) for i in range(ns.value)]
+
+    def _cpath(self, path):
+        key = tuple(tuple(p) for p in path)
+        if key != self._path_key:
+            flat = [int(x) for p in key for x in p]
+            self._parr = (ctypes.c_int32 * max(1, len(flat)))(*flat)
+            self._path = _Path(len(key), ctypes.cast(self._parr, ctypes.POINTER(ctypes.c_int32)))
+            self._path_key = key
+        return self._path
+
+
+def path_greedy(tensors, labels, out_labels=()):
+    """The library's greedy min-size path as a list of SSA pairs."""
+    return Network(tensors, labels, out_labels).greedy_path()
+
+
+def path_greedy_extents(labels, extents, out_labels=()):
+    """Greedy path from labels and extents alone (host-only, no GPU needed)."""
+    n = len(labels)
+    ranks = (ctypes.c_int32 * max(1, n))(*[len(l) for l in labels])
+    lab = [_i64arr(l) for l in labels]
+    ext = [_i64arr(e) for e in extents]
+    P = ctypes.POINTER(ctypes.c_int64)
+    labp = (P * max(1, n))(*[ctypes.cast(a, P) for a in lab])
+    extp = (P * max(1, n))(*[ctypes.cast(a, P) for a in ext])
+    out = _i64arr(out_labels)
+    pairs = (ctypes.c_int32 * max(1, 2 * (n - 1)))()
+    ns = ctypes.c_int32()
+    _check(lib().rosnet_path_greedy_extents(n, ranks, labp, extp, len(out_labels), out, pairs,
+                                            ctypes.byref(ns)), "rosnet_path_greedy_extents")
+    return [(pairs[2 * i], pairs[2 * i + 1]) for i in range(ns.value)]
+
+
+def contract(tensors, labels=None, out_labels=None, path=None, precision=PREC_DEFAULT, flags=0,
+             max_block_entries=0, stream=None):
+    """Contract a network along an SSA path on the GPU.
+
+    ``tensors`` is either a prepared ``Network`` (then ``labels`` and
+    ``out_labels`` are ignored) or a list of BTensors with their labels."""
+    _init()
+    net = tensors if isinstance(tensors, Network) else Network(tensors, labels, out_labels or ())
+    if path is None:
+        path = net.greedy_path()
+    pth = net._cpath(path)
+    o = _opts(precision, flags, max_block_entries)
+    h = ctypes.c_void_p()
+    _check(lib().rosnet_contract(ctypes.byref(net.net), ctypes.byref(pth), ctypes.byref(o),
+                                 _stream(stream), ctypes.byref(h)), "rosnet_contract")
+    return BTensor(h.value)
+
+
+def sync(stream=None):
+    _check(lib().rosnet_sync(_stream(stream)), "rosnet_sync")
+
+
+def kernel_launches():
+    return int(lib().rosnet_kernel_launches())
+
+
+def timing_drain(max_entries=4096):
+    """[(ms, flops, bytes)] of the heaviest launch of each timed contract call."""
+    ms = (ctypes.c_double * max_entries)()
+    fl = (ctypes.c_double * max_entries)()
+    by = (ctypes.c_double * max_entries)()
+    n = ctypes.c_int32()
+    _check(lib().rosnet_timing_drain(ms, fl, by, max_entries, ctypes.byref(n)), "rosnet_timing_drain")
+    return [(ms[i], fl[i], by[i]) for i in range(n.value)]
+
+
+def release_plans():
+    _check(lib().rosnet_release_plans(), "rosnet_release_plans")

@@ -1,0 +1,716 @@
+// Tensor-network contraction along a pairwise path (Sec. II-A: the
+// contraction is a sequence of operations between neighbouring tensors that
+// create intermediates), and the library's greedy path.
+//
+// Execution model.  Every step of the path is one blocked pairwise tensordot
+// (gett.cu).  Steps are grouped into dependency waves (a step's wave is one
+// more than the latest wave of its operands); all steps of a wave that use
+// the same kernel family run in ONE grouped launch whose CTAs look up their
+// problem in a device-side descriptor array.  Intermediates live in one
+// device arena whose offsets are packed by lifetime (first wave written, last
+// wave read).  Plans (offset tables, arena, descriptors and optionally a
+// captured CUDA graph of the launches) are cached by the network's structure,
+// so a later call with the same structure only patches the operand addresses
+// and replays.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace rosnet {
+
+void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axes_a,
+                     const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc);
+int check_precision(const rosnet_opts *opts, int dtype);
+int64_t reduce_ctas(const GettDesc &d);
+
+namespace {
+
+// offsets tables on the host (same contents as build_table_kernel)
+void host_table(const ModeList &ml, int64_t total, int64_t *o0, int64_t *o1) {
+    for (int64_t i = 0; i < total; ++i) {
+        int64_t r = i, a = 0, b = 0;
+        for (int j = ml.n - 1; j >= 0; --j) {
+            int64_t d = r % ml.m[j].ext;
+            r /= ml.m[j].ext;
+            a += d * ml.m[j].s0;
+            b += d * ml.m[j].s1;
+        }
+        o0[i] = a;
+        o1[i] = b;
+    }
+}
+
+struct Step {
+    int ia, ib;          // operand ids (SSA)
+    int naxes;
+    std::vector<int> axa, axb;
+    Layout lay;          // layout of the result
+    int wave;
+    int64_t table_off;   // in int64 entries
+    size_t arena_off;    // for intermediates; SIZE_MAX for the final result
+    GettDesc desc;       // pointers patched per call
+};
+
+struct Plan {
+    int ntensors = 0;
+    int dtype = 0;
+    int precision = 0;
+    int flags = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<Step> steps;
+    std::vector<int> final_perm;   // output axis i = final tensor axis final_perm[i]
+    bool final_direct = true;      // last step writes straight into the output
+    Layout out_lay;
+    size_t arena_bytes = 0;
+    DevBuf arena, tables, descs, partials;
+    // launch list: (kind, first desc, count, total tiles)
+    struct Launch { int kind; int first; int count; int64_t tiles; };
+    std::vector<Launch> launches;
+    std::vector<int> desc_step;    // desc slot -> step index
+    std::vector<GettDesc> slot_desc;  // desc slot -> static descriptor fields
+    // pinned staging ring for descriptor uploads
+    static constexpr int kRing = 4;
+    GettDesc *pinned[kRing] = {nullptr};
+    cudaEvent_t ev[kRing] = {nullptr};
+    int ring = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaGraph_t graph_src = nullptr;           // kept for event-node updates
+    cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+    int graph_nodes = 0;
+    std::vector<GettDesc> mirror;              // descriptor contents last enqueued
+    bool mirror_valid = false;
+    // timing of the heaviest launch (ROSNET_OPT_TIMING)
+    int heavy = -1;
+    double heavy_flops = 0, heavy_bytes = 0;
+    static constexpr int kTimingRing = 4096;
+    std::vector<cudaEvent_t> tev;              // 2 * kTimingRing, created lazily
+    int tpos = 0;
+    size_t final_tmp_off = SIZE_MAX;  // arena offset of the last result if a permute follows
+    ~Plan() {
+        for (int i = 0; i < kRing; ++i) {
+            if (ev[i]) { cudaEventSynchronize(ev[i]); cudaEventDestroy(ev[i]); }
+            if (pinned[i]) cudaFreeHost(pinned[i]);
+        }
+        if (graph) cudaGraphExecDestroy(graph);
+        if (graph_src) cudaGraphDestroy(graph_src);
+        for (cudaEvent_t e : tev) if (e) cudaEventDestroy(e);
+    }
+};
+
+// Cached plans.  Deliberately never destroyed at process exit: by then the
+// CUDA runtime or an injected allocator (e.g. one implemented in Python) may
+// already be gone.  rosnet_release_plans() frees them explicitly.
+std::mutex g_plan_mu;
+auto &g_plans = *new std::unordered_map<std::string, std::unique_ptr<Plan>>();
+// (plan, ring slot) of every timed launch not yet drained
+auto &g_timing_log = *new std::vector<std::pair<Plan *, int>>();
+
+struct NetInfo {
+    std::vector<std::vector<int64_t>> labels;
+};
+
+std::string plan_key(const rosnet_network *net, const rosnet_path *path, int prec, int flags,
+                     int64_t maxblk, cudaStream_t s) {
+    std::string k;
+    k.reserve(64 + net->ntensors * 48 + path->nsteps * 8);
+    auto put = [&k](int64_t v) { k.append((const char *)&v, sizeof(v)); };
+    put(net->ntensors);
+    put(prec);
+    put(flags);
+    put(maxblk);
+    put((int64_t)(intptr_t)s);
+    for (int t = 0; t < net->ntensors; ++t) {
+        rosnet_btensor x = net->tensors[t];
+        put(x->dtype);
+        put(x->lay.rank);
+        for (int i = 0; i < x->lay.rank; ++i) {
+            put(x->lay.shape[i]);
+            put(x->lay.block[i]);
+            put(net->labels[t][i]);
+        }
+    }
+    put(net->nout);
+    for (int i = 0; i < net->nout; ++i) put(net->out_labels[i]);
+    put(path->nsteps);
+    for (int i = 0; i < 2 * path->nsteps; ++i) put(path->pairs[i]);
+    return k;
+}
+
+void validate_network(const rosnet_network *net) {
+    if (!net || net->ntensors < 1 || !net->tensors || !net->ranks || !net->labels)
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed network");
+    if (net->nout < 0 || (net->nout > 0 && !net->out_labels))
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed output labels");
+    if (net->nout > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "output rank > 64");
+    std::unordered_map<int64_t, int> count;
+    int dtype = 0;
+    for (int t = 0; t < net->ntensors; ++t) {
+        rosnet_btensor x = net->tensors[t];
+        if (!x) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL tensor in network");
+        if (net->ranks[t] != x->lay.rank) RN_FAIL(ROSNET_ERR_INVALID_ARG, "rank does not match tensor");
+        if (x->lay.rank > 0 && !net->labels[t]) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL labels");
+        if (t == 0) dtype = x->dtype;
+        else if (x->dtype != dtype) RN_FAIL(ROSNET_ERR_DTYPE, "network tensors differ in dtype");
+        for (int i = 0; i < x->lay.rank; ++i) {
+            for (int j = 0; j < i; ++j)
+                if (net->labels[t][j] == net->labels[t][i])
+                    RN_FAIL(ROSNET_ERR_UNSUPPORTED, "a label repeated on one tensor (trace)");
+            count[net->labels[t][i]]++;
+        }
+    }
+    std::unordered_map<int64_t, int> outc;
+    for (int i = 0; i < net->nout; ++i) {
+        if (outc[net->out_labels[i]]++) RN_FAIL(ROSNET_ERR_INVALID_ARG, "repeated output label");
+        if (count[net->out_labels[i]] != 1)
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "an output label must be carried by exactly one tensor");
+    }
+    for (auto &kv : count) {
+        if (kv.second > 2) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "a label carried by more than two tensors");
+        if (kv.second == 1 && !outc.count(kv.first))
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "an open label is missing from out_labels");
+    }
+}
+
+std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *path, int prec,
+                                 int flags, int64_t maxblk, cudaStream_t s) {
+    const int nt = net->ntensors;
+    if (!path || path->nsteps != nt - 1 || (path->nsteps > 0 && !path->pairs))
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "a path must have ntensors - 1 steps");
+    auto plan = std::make_unique<Plan>();
+    plan->ntensors = nt;
+    plan->dtype = net->tensors[0]->dtype;
+    plan->precision = prec;
+    plan->flags = flags;
+    plan->stream = s;
+    const int total_ids = nt + path->nsteps;
+    std::vector<std::vector<int64_t>> labels(total_ids);
+    std::vector<Layout> lays(total_ids);
+    std::vector<int> wave(total_ids, 0), alive(total_ids, 0), last_use(total_ids, -1);
+    for (int t = 0; t < nt; ++t) {
+        labels[t].assign(net->labels[t], net->labels[t] + net->ranks[t]);
+        lays[t] = net->tensors[t]->lay;
+        alive[t] = 1;
+    }
+    plan->steps.resize(path->nsteps);
+    for (int st = 0; st < path->nsteps; ++st) {
+        int i = path->pairs[2 * st], j = path->pairs[2 * st + 1];
+        if (i < 0 || j < 0 || i >= nt + st || j >= nt + st || i == j || !alive[i] || !alive[j])
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "path step " + std::to_string(st) + " uses a dead or unknown id");
+        alive[i] = alive[j] = 0;
+        Step &S = plan->steps[st];
+        S.ia = i;
+        S.ib = j;
+        // every label shared by the pair is a bond carried by exactly these two
+        std::vector<int64_t> lc;
+        std::vector<int64_t> shc, blc;
+        const Layout &la = lays[i], &lb = lays[j];
+        std::vector<bool> ca(la.rank, false), cb(lb.rank, false);
+        for (int x = 0; x < la.rank; ++x)
+            for (int y = 0; y < lb.rank; ++y)
+                if (labels[i][x] == labels[j][y]) {
+                    if (la.shape[x] != lb.shape[y])
+                        RN_FAIL(ROSNET_ERR_SHAPE, "a bond has different extents on its two tensors");
+                    S.axa.push_back(x);
+                    S.axb.push_back(y);
+                    ca[x] = cb[y] = true;
+                }
+        S.naxes = (int)S.axa.size();
+        for (int x = 0; x < la.rank; ++x)
+            if (!ca[x]) { lc.push_back(labels[i][x]); shc.push_back(la.shape[x]); blc.push_back(la.block[x]); }
+        for (int y = 0; y < lb.rank; ++y)
+            if (!cb[y]) { lc.push_back(labels[j][y]); shc.push_back(lb.shape[y]); blc.push_back(lb.block[y]); }
+        if ((int)lc.size() > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "intermediate rank > 64");
+        if (maxblk > 0) {
+            int64_t bs = 1;
+            for (int64_t b : blc) bs *= b;
+            for (size_t x = 0; x < blc.size() && bs > maxblk; ++x) {
+                bs /= blc[x];
+                blc[x] = 1;
+            }
+        }
+        const int id = nt + st;
+        labels[id] = lc;
+        lays[id].init((int)lc.size(), shc.data(), blc.data());
+        S.lay = lays[id];
+        wave[id] = std::max(wave[i], wave[j]) + 1;
+        S.wave = wave[id];
+        last_use[i] = last_use[j] = S.wave;
+        alive[id] = 1;
+    }
+    const int final_id = nt + path->nsteps - 1;
+    const int last = path->nsteps > 0 ? final_id : 0;
+    // output permutation
+    const std::vector<int64_t> &fl = labels[last];
+    if ((int)fl.size() != net->nout) RN_FAIL(ROSNET_ERR_INVALID_ARG, "path leaves labels open that are not outputs");
+    plan->final_perm.resize(net->nout);
+    bool ident = true;
+    for (int o = 0; o < net->nout; ++o) {
+        int pos = -1;
+        for (int x = 0; x < (int)fl.size(); ++x)
+            if (fl[x] == net->out_labels[o]) pos = x;
+        if (pos < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "output label not produced by the path");
+        plan->final_perm[o] = pos;
+        if (pos != o) ident = false;
+    }
+    {
+        std::vector<int64_t> osh(net->nout), obl(net->nout);
+        for (int o = 0; o < net->nout; ++o) {
+            osh[o] = lays[last].shape[plan->final_perm[o]];
+            obl[o] = lays[last].block[plan->final_perm[o]];
+        }
+        plan->out_lay.init(net->nout, osh.data(), obl.data());
+    }
+    plan->final_direct = ident && path->nsteps > 0;
+
+    // arena: intermediates (and the final result if it must be permuted)
+    struct Slot { size_t off, size; int from, to; };
+    std::vector<Slot> placed;
+    const size_t el2 = 2 * (plan->dtype == ROSNET_C64 ? 4 : 8);
+    for (int st = 0; st < path->nsteps; ++st) {
+        const int id = nt + st;
+        Step &S = plan->steps[st];
+        if (id == final_id && plan->final_direct) {
+            S.arena_off = SIZE_MAX;
+            continue;
+        }
+        size_t bytes = ((size_t)S.lay.numel * el2 + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        int from = S.wave, to = (id == final_id) ? S.wave + 1 : last_use[id];
+        // first fit among slots whose lifetime overlaps
+        std::vector<std::pair<size_t, size_t>> busy;
+        for (auto &p : placed)
+            if (!(p.to < from || p.from > to)) busy.push_back({p.off, p.off + p.size});
+        std::sort(busy.begin(), busy.end());
+        size_t off = 0;
+        for (auto &b : busy) {
+            if (off + bytes <= b.first) break;
+            off = std::max(off, b.second);
+        }
+        placed.push_back({off, bytes, from, to});
+        S.arena_off = off;
+        plan->arena_bytes = std::max(plan->arena_bytes, off + bytes);
+        if (id == final_id) plan->final_tmp_off = off;
+    }
+    // tables (host-built, one upload)
+    std::vector<GettView> views(path->nsteps);
+    int64_t tab_entries = 0;
+    for (int st = 0; st < path->nsteps; ++st) {
+        Step &S = plan->steps[st];
+        views[st] = make_view(lays[S.ia], lays[S.ib], S.lay, S.naxes, S.axa.data(), S.axb.data());
+        S.table_off = tab_entries;
+        tab_entries += (int64_t)table_entries(views[st]);
+    }
+    std::vector<int64_t> htab(std::max<int64_t>(tab_entries, 1));
+    for (int st = 0; st < path->nsteps; ++st) {
+        const GettView &v = views[st];
+        int64_t *t = htab.data() + plan->steps[st].table_off;
+        host_table(v.M, v.Mtot, t, t + v.Mtot);
+        t += 2 * v.Mtot;
+        host_table(v.N, v.Ntot, t, t + v.Ntot);
+        t += 2 * v.Ntot;
+        host_table(v.K, v.Ktot, t, t + v.Ktot);
+    }
+    plan->tables = DevBuf(htab.size() * sizeof(int64_t), s);
+    plan->arena = DevBuf(std::max<size_t>(plan->arena_bytes, 256), s);
+    RN_CHECK_CUDA(cudaMemcpyAsync(plan->tables.p, htab.data(), htab.size() * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, s));
+    // descriptors, grouped by (wave, kind); split-K problems of a wave get a
+    // reduction launch right after their wave's launches
+    const int64_t *dtab = (const int64_t *)plan->tables.p;
+    std::map<std::pair<int, int>, std::vector<int>> groups;
+    std::map<int, std::vector<int>> split_of_wave;
+    for (int st = 0; st < path->nsteps; ++st) {
+        Step &S = plan->steps[st];
+        memset(&S.desc, 0, sizeof(S.desc));
+        fill_desc_tables(S.desc, views[st], dtab + S.table_off);
+        choose_kernel(S.desc, plan->dtype, prec);
+        if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
+        int key_kind = (flags & ROSNET_OPT_NOGROUP) ? st : S.desc.kind;
+        groups[{S.wave, key_kind}].push_back(st);
+        if (S.desc.ksplit > 1) split_of_wave[S.wave].push_back(st);
+    }
+    // split-K partials: one workspace reused by every wave
+    size_t part_bytes = 0;
+    for (auto &w : split_of_wave) {
+        size_t b = 0;
+        for (int st : w.second) b += (desc_part_bytes(plan->steps[st].desc, plan->dtype) + 255) & ~(size_t)255;
+        part_bytes = std::max(part_bytes, b);
+    }
+    if (part_bytes) plan->partials = DevBuf(part_bytes, s);
+    for (auto &w : split_of_wave) {
+        size_t off = 0;
+        for (int st : w.second) {
+            plan->steps[st].desc.part = (char *)plan->partials.p + off;
+            off += (desc_part_bytes(plan->steps[st].desc, plan->dtype) + 255) & ~(size_t)255;
+        }
+    }
+    std::vector<GettDesc> slot_desc;   // per descriptor slot: the static fields
+    auto add_launch = [&](int kind, const std::vector<int> &sts, bool reduce) {
+        Plan::Launch L;
+        L.kind = kind;
+        L.first = (int)plan->desc_step.size();
+        L.count = (int)sts.size();
+        int64_t ctas = 0;
+        for (int st : sts) {
+            GettDesc d = plan->steps[st].desc;
+            d.tile_begin = ctas;
+            ctas += reduce ? reduce_ctas(d) : desc_ctas(d);
+            plan->desc_step.push_back(st);
+            slot_desc.push_back(d);
+        }
+        L.tiles = ctas;
+        plan->launches.push_back(L);
+    };
+    for (auto it = groups.begin(); it != groups.end(); ++it) {
+        const int w = it->first.first;
+        add_launch(plan->steps[it->second[0]].desc.kind, it->second, false);
+        auto nx = std::next(it);
+        if ((nx == groups.end() || nx->first.first != w) && split_of_wave.count(w))
+            add_launch(kKindReduce, split_of_wave[w], true);
+    }
+    plan->slot_desc = std::move(slot_desc);
+    // the launch with the most algorithmic work (8 M N K per complex GEMM)
+    {
+        const double el2d = (double)el2;
+        double best = -1;
+        for (size_t li = 0; li < plan->launches.size(); ++li) {
+            const auto &L = plan->launches[li];
+            double fl = 0, by = 0;
+            if (L.kind == kKindReduce) continue;
+            for (int q = L.first; q < L.first + L.count; ++q) {
+                const GettDesc &d = plan->slot_desc[q];
+                fl += 8.0 * (double)d.M * (double)d.N * (double)d.K;
+                by += el2d * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
+            }
+            if (fl > best) { best = fl; plan->heavy = (int)li; plan->heavy_flops = fl; plan->heavy_bytes = by; }
+        }
+    }
+    const size_t nd = std::max<size_t>(plan->desc_step.size(), 1);
+    plan->descs = DevBuf(nd * sizeof(GettDesc), s);
+    for (int r = 0; r < Plan::kRing; ++r) {
+        RN_CHECK_CUDA(cudaMallocHost((void **)&plan->pinned[r], nd * sizeof(GettDesc)));
+        RN_CHECK_CUDA(cudaEventCreateWithFlags(&plan->ev[r], cudaEventDisableTiming));
+    }
+    return plan;
+}
+
+void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream_t s) {
+    const int nt = P.ntensors;
+    char *arena = (char *)P.arena.p;
+    auto ptr_of = [&](int id) -> void * {
+        if (id < nt) return net->tensors[id]->data;
+        const Step &S = P.steps[id - nt];
+        if (S.arena_off == SIZE_MAX) return out->data;
+        return arena + S.arena_off;
+    };
+    // patch descriptors into the next pinned staging buffer; upload only the
+    // range whose operand addresses changed since the last call
+    const int r = P.ring;
+    P.ring = (P.ring + 1) % Plan::kRing;
+    RN_CHECK_CUDA(cudaEventSynchronize(P.ev[r]));
+    GettDesc *h = P.pinned[r];
+    const size_t nd = P.desc_step.size();
+    if (P.mirror.size() != nd) P.mirror.resize(nd);
+    size_t lo = nd, hi = 0;
+    for (size_t i = 0; i < nd; ++i) {
+        const int st = P.desc_step[i];
+        const Step &S = P.steps[st];
+        GettDesc d = P.slot_desc[i];
+        const Layout &la = S.ia < nt ? net->tensors[S.ia]->lay : P.steps[S.ia - nt].lay;
+        const Layout &lb = S.ib < nt ? net->tensors[S.ib]->lay : P.steps[S.ib - nt].lay;
+        bind_operands(d, ptr_of(S.ia), ptr_of(S.ib), ptr_of(nt + st), la.numel, lb.numel, S.lay.numel);
+        h[i] = d;
+        if (!P.mirror_valid || P.mirror[i].a != d.a || P.mirror[i].b != d.b || P.mirror[i].c != d.c) {
+            lo = std::min(lo, i);
+            hi = i + 1;
+            P.mirror[i] = d;
+        }
+    }
+    P.mirror_valid = true;
+    if (lo < hi)
+        RN_CHECK_CUDA(cudaMemcpyAsync((GettDesc *)P.descs.p + lo, h + lo, (hi - lo) * sizeof(GettDesc),
+                                      cudaMemcpyHostToDevice, s));
+    RN_CHECK_CUDA(cudaEventRecord(P.ev[r], s));
+
+    const bool timing = (P.flags & ROSNET_OPT_TIMING) && P.heavy >= 0;
+    int slot = -1;
+    if (timing) {
+        if (P.tev.empty()) {
+            P.tev.resize(2 * Plan::kTimingRing, nullptr);
+            for (auto &e : P.tev) RN_CHECK_CUDA(cudaEventCreate(&e));
+        }
+        slot = P.tpos;
+        P.tpos = (P.tpos + 1) % Plan::kTimingRing;
+    }
+    const GettDesc *dd = (const GettDesc *)P.descs.p;
+    auto enqueue = [&](bool capturing) {
+        for (size_t li = 0; li < P.launches.size(); ++li) {
+            const auto &L = P.launches[li];
+            const bool th = timing && (int)li == P.heavy;
+            if (th) {
+                cudaEvent_t e0 = P.tev[2 * slot];
+                RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal)
+                                        : cudaEventRecord(e0, s));
+            }
+            launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
+            if (th) {
+                cudaEvent_t e1 = P.tev[2 * slot + 1];
+                RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal)
+                                        : cudaEventRecord(e1, s));
+            }
+        }
+    };
+    const bool use_graph = (P.flags & ROSNET_OPT_GRAPH) && s != nullptr && !P.launches.empty();
+    if (use_graph) {
+        if (!P.graph) {
+            cudaGraph_t gr = nullptr;
+            RN_CHECK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            int64_t before = g_launches.load();
+            try {
+                enqueue(true);
+            } catch (...) {
+                cudaStreamEndCapture(s, &gr);
+                if (gr) cudaGraphDestroy(gr);
+                throw;
+            }
+            P.graph_nodes = (int)(g_launches.load() - before);
+            g_launches -= P.graph_nodes;  // counted at replay
+            RN_CHECK_CUDA(cudaStreamEndCapture(s, &gr));
+            if (timing) {  // find the two event-record nodes
+                size_t nn = 0;
+                RN_CHECK_CUDA(cudaGraphGetNodes(gr, nullptr, &nn));
+                std::vector<cudaGraphNode_t> nodes(nn);
+                RN_CHECK_CUDA(cudaGraphGetNodes(gr, nodes.data(), &nn));
+                int k = 0;
+                for (auto nd_ : nodes) {
+                    cudaGraphNodeType ty;
+                    RN_CHECK_CUDA(cudaGraphNodeGetType(nd_, &ty));
+                    if (ty == cudaGraphNodeTypeEventRecord && k < 2) {
+                        cudaEvent_t e;
+                        RN_CHECK_CUDA(cudaGraphEventRecordNodeGetEvent(nd_, &e));
+                        P.ev_node[e == P.tev[2 * slot] ? 0 : 1] = nd_;
+                        ++k;
+                    }
+                }
+            }
+            cudaError_t e = cudaGraphInstantiate(&P.graph, gr, 0);
+            P.graph_src = gr;
+            RN_CHECK_CUDA(e);
+        } else if (timing && P.ev_node[0] && P.ev_node[1]) {
+            RN_CHECK_CUDA(cudaGraphExecEventRecordNodeSetEvent(P.graph, P.ev_node[0], P.tev[2 * slot]));
+            RN_CHECK_CUDA(cudaGraphExecEventRecordNodeSetEvent(P.graph, P.ev_node[1], P.tev[2 * slot + 1]));
+        }
+        RN_CHECK_CUDA(cudaGraphLaunch(P.graph, s));
+        g_launches += P.graph_nodes;
+    } else {
+        enqueue(false);
+    }
+    if (timing) g_timing_log.push_back({&P, slot});
+    if (!P.final_direct) {
+        const int last = P.steps.empty() ? 0 : nt + (int)P.steps.size() - 1;
+        const Layout &src = P.steps.empty() ? net->tensors[0]->lay : P.steps.back().lay;
+        launch_relayout(src, out->lay, P.final_perm.data(), P.dtype, ptr_of(last), out->data, s);
+    }
+}
+
+}  // namespace
+
+}  // namespace rosnet
+
+using namespace rosnet;
+
+extern "C" {
+
+rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path,
+                              const rosnet_opts *opts, void *stream, rosnet_btensor *out) {
+    if (!out) return ROSNET_ERR_INVALID_ARG;
+    *out = nullptr;
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!net || net->ntensors < 1 || !net->tensors || !net->ranks || !net->labels)
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed network");
+    for (int t = 0; t < net->ntensors; ++t)
+        if (!net->tensors[t] || net->ranks[t] != net->tensors[t]->lay.rank ||
+            (net->ranks[t] > 0 && !net->labels[t]))
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL tensor or rank mismatch in network");
+    if (net->nout < 0 || (net->nout > 0 && !net->out_labels))
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed output labels");
+    if (!path || path->nsteps < 0 || (path->nsteps > 0 && !path->pairs))
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL path");
+    const int prec = check_precision(opts, net->tensors[0]->dtype);
+    const int flags = opts ? opts->flags : 0;
+    const int64_t maxblk = opts ? opts->max_block_entries : 0;
+    if (maxblk < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "negative max_block_entries");
+    std::string key = plan_key(net, path, prec, flags, maxblk, s);
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    Plan *P;
+    if (it == g_plans.end()) {
+        validate_network(net);  // the key encodes everything validated here
+        auto np = build_plan(net, path, prec, flags, maxblk, s);
+        P = np.get();
+        g_plans.emplace(std::move(key), std::move(np));
+    } else {
+        P = it->second.get();
+    }
+    rosnet_btensor C = new_tensor(P->out_lay.rank, P->out_lay.shape, P->out_lay.block, P->dtype, s);
+    try {
+        run_plan(*P, net, C, s);
+    } catch (...) {
+        free_tensor(C);
+        throw;
+    }
+    *out = C;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t max_entries,
+                                  int32_t *n) {
+    if (!n || max_entries < 0 || (max_entries > 0 && !ms)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    int32_t k = 0;
+    // keep only the newest kTimingRing entries per plan (older slots were reused)
+    size_t start = g_timing_log.size() > (size_t)Plan::kTimingRing
+                       ? g_timing_log.size() - Plan::kTimingRing : 0;
+    for (size_t i = start; i < g_timing_log.size() && k < max_entries; ++i) {
+        Plan *P = g_timing_log[i].first;
+        int slot = g_timing_log[i].second;
+        RN_CHECK_CUDA(cudaEventSynchronize(P->tev[2 * slot + 1]));
+        float t = 0;
+        RN_CHECK_CUDA(cudaEventElapsedTime(&t, P->tev[2 * slot], P->tev[2 * slot + 1]));
+        ms[k] = t;
+        if (flops) flops[k] = P->heavy_flops;
+        if (bytes) bytes[k] = P->heavy_bytes;
+        ++k;
+    }
+    g_timing_log.clear();
+    *n = k;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_release_plans(void) {
+    RN_API_BEGIN
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_timing_log.clear();
+    g_plans.clear();
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_path_greedy_extents(int32_t ntensors, const int32_t *ranks,
+                                         const int64_t *const *labels, const int64_t *const *extents,
+                                         int32_t nout, const int64_t *out_labels, int32_t *pairs_out,
+                                         int32_t *nsteps) {
+    if (!pairs_out || !nsteps || ntensors < 1 || !ranks || !labels || !extents ||
+        (nout > 0 && !out_labels) || nout < 0)
+        return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    const int nt = ntensors;
+    std::unordered_map<int64_t, int64_t> ext;  // label -> extent
+    std::vector<std::vector<int64_t>> lab(2 * nt);
+    std::vector<bool> alive(2 * nt, false);
+    std::unordered_map<int64_t, std::vector<int>> holders;  // label -> live ids carrying it
+    for (int t = 0; t < nt; ++t) {
+        if (ranks[t] < 0 || ranks[t] > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "bad rank");
+        if (ranks[t] > 0 && (!labels[t] || !extents[t])) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL labels");
+        lab[t].assign(labels[t], labels[t] + ranks[t]);
+        alive[t] = true;
+        for (int i = 0; i < ranks[t]; ++i) {
+            int64_t e = extents[t][i];
+            auto it = ext.find(lab[t][i]);
+            if (it != ext.end() && it->second != e)
+                RN_FAIL(ROSNET_ERR_SHAPE, "a label has two different extents");
+            ext[lab[t][i]] = e;
+            holders[lab[t][i]].push_back(t);
+        }
+    }
+    for (auto &kv : holders)
+        if (kv.second.size() > 2) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "a label carried by more than two tensors");
+    auto size_of = [&](const std::vector<int64_t> &l) {
+        double s = 1;
+        for (int64_t x : l) s *= (double)ext[x];
+        return s;
+    };
+    auto result_labels = [&](int a, int b) {
+        std::vector<int64_t> r;
+        for (int64_t x : lab[a])
+            if (std::find(lab[b].begin(), lab[b].end(), x) == lab[b].end()) r.push_back(x);
+        for (int64_t x : lab[b])
+            if (std::find(lab[a].begin(), lab[a].end(), x) == lab[a].end()) r.push_back(x);
+        return r;
+    };
+    int next = nt;
+    for (int st = 0; st < nt - 1; ++st) {
+        bool found = false;
+        double best_size = 0, best_delta = 0;
+        int ba = -1, bb = -1;
+        for (auto &kv : holders) {
+            const auto &h = kv.second;
+            if (h.size() != 2) continue;
+            int a = std::min(h[0], h[1]), b = std::max(h[0], h[1]);
+            std::vector<int64_t> r = result_labels(a, b);
+            double sz = size_of(r);
+            double delta = sz - size_of(lab[a]) - size_of(lab[b]);
+            bool better = !found || sz < best_size ||
+                          (sz == best_size && (delta < best_delta ||
+                                               (delta == best_delta && (a < ba || (a == ba && b < bb)))));
+            if (better) {
+                found = true;
+                best_size = sz;
+                best_delta = delta;
+                ba = a;
+                bb = b;
+            }
+        }
+        if (!found) {  // disconnected: outer product of the two lowest live ids
+            for (int i = 0; i < next && bb < 0; ++i)
+                if (alive[i]) { if (ba < 0) ba = i; else bb = i; }
+        }
+        std::vector<int64_t> r = result_labels(ba, bb);
+        for (int64_t x : lab[ba]) {
+            auto &h = holders[x];
+            h.erase(std::remove(h.begin(), h.end(), ba), h.end());
+        }
+        for (int64_t x : lab[bb]) {
+            auto &h = holders[x];
+            h.erase(std::remove(h.begin(), h.end(), bb), h.end());
+        }
+        alive[ba] = alive[bb] = false;
+        lab[next] = r;
+        alive[next] = true;
+        for (int64_t x : r) holders[x].push_back(next);
+        pairs_out[2 * st] = ba;
+        pairs_out[2 * st + 1] = bb;
+        ++next;
+    }
+    *nsteps = nt - 1;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_path_greedy(const rosnet_network *net, int32_t *pairs_out, int32_t *nsteps) {
+    if (!pairs_out || !nsteps) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    validate_network(net);
+    std::vector<const int64_t *> ex(net->ntensors);
+    for (int t = 0; t < net->ntensors; ++t) ex[t] = net->tensors[t]->lay.shape;
+    return rosnet_path_greedy_extents(net->ntensors, net->ranks, net->labels, ex.data(), net->nout,
+                                      net->out_labels, pairs_out, nsteps);
+    RN_API_END
+}
+
+}  // extern "C"

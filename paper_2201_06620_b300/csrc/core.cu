@@ -1,0 +1,398 @@
+// Allocator, block layouts, tensor handles and layout-changing copies.
+//
+// Block tensors (Sec. II-C): a tensor is cut into a uniform grid of blocks;
+// on the device the blocks are stored one after another (row-major over the
+// grid coordinates), each block row-major inside, with all real parts first
+// and all imaginary parts after them (planar complex).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace rosnet {
+
+std::atomic<int64_t> g_launches{0};
+
+static thread_local std::string t_last_error;
+void set_last_error(const std::string &s) { t_last_error = s; }
+const char *last_error_cstr() { return t_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// allocator
+// ---------------------------------------------------------------------------
+static void *(*g_alloc)(size_t, void *, void *) = nullptr;
+static void (*g_free)(void *, void *, void *) = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, (void *)s, g_alloc_ctx);
+        if (!p) RN_FAIL(ROSNET_ERR_ALLOC, "injected allocator returned NULL for " +
+                                              std::to_string(bytes) + " bytes");
+        return p;
+    }
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        RN_FAIL(ROSNET_ERR_ALLOC, "cudaMallocAsync(" + std::to_string(bytes) +
+                                      "): " + cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (!p) return;
+    if (g_free) {
+        g_free(p, (void *)s, g_alloc_ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------------------
+// layouts
+// ---------------------------------------------------------------------------
+void Layout::init(int r, const int64_t *sh, const int64_t *bl) {
+    if (r < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "negative rank");
+    if (r > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "rank " + std::to_string(r) + " > 64");
+    if (r > 0 && !sh) RN_FAIL(ROSNET_ERR_INVALID_ARG, "shape is NULL");
+    rank = r;
+    numel = 1;
+    for (int i = 0; i < r; ++i) {
+        if (sh[i] < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "negative extent");
+        int64_t b = bl ? bl[i] : (sh[i] > 0 ? sh[i] : 1);
+        if (b < 1) RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "block extent < 1");
+        if (sh[i] % b != 0)
+            RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "block extent " + std::to_string(b) +
+                                                   " does not divide extent " +
+                                                   std::to_string(sh[i]) + " of axis " +
+                                                   std::to_string(i));
+        shape[i] = sh[i];
+        block[i] = b;
+        if (sh[i] > 0 && numel > (int64_t(1) << 62) / sh[i])
+            RN_FAIL(ROSNET_ERR_SHAPE, "tensor too large");
+        numel *= sh[i];
+    }
+    int64_t bs = 1;
+    for (int i = r - 1; i >= 0; --i) {
+        lstride[i] = bs;
+        bs *= block[i];
+    }
+    int64_t g = bs;
+    for (int i = r - 1; i >= 0; --i) {
+        gstride[i] = g;
+        g *= shape[i] / block[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// strided copies between layouts
+// ---------------------------------------------------------------------------
+// Modes of a copy, innermost last: element e (enumerated row-major over the
+// modes) is read at sum d_j*ss_j and written at sum d_j*ds_j.
+struct CopyModes {
+    int n;
+    int pow2;                 // all extents are powers of two
+    int64_t ext[kMaxModes];
+    int64_t ss[kMaxModes];
+    int64_t ds[kMaxModes];
+};
+
+static void push_mode(CopyModes &cm, int64_t ext, int64_t ss, int64_t ds) {
+    if (ext == 1) return;
+    if (cm.n > 0) {  // fuse with the previous (outer) mode when contiguous in both
+        int j = cm.n - 1;
+        if (cm.ss[j] == ss * ext && cm.ds[j] == ds * ext) {
+            cm.ext[j] *= ext;
+            cm.ss[j] = ss;
+            cm.ds[j] = ds;
+            return;
+        }
+    }
+    if (cm.n >= kMaxModes) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "too many modes");
+    cm.ext[cm.n] = ext;
+    cm.ss[cm.n] = ss;
+    cm.ds[cm.n] = ds;
+    cm.n++;
+}
+
+static void finish_modes(CopyModes &cm) {
+    cm.pow2 = 1;
+    for (int i = 0; i < cm.n; ++i)
+        if (cm.ext[i] & (cm.ext[i] - 1)) cm.pow2 = 0;
+}
+
+// The digits of one logical axis of extent s under the two block extents
+// b_src and b_dst (one must divide the other): modes from outer to inner with
+// their strides in both layouts.
+static void axis_modes(CopyModes &cm, int64_t s, int64_t b1, int64_t g1, int64_t l1,
+                       int64_t b2, int64_t g2, int64_t l2) {
+    int64_t lo = b1 < b2 ? b1 : b2, hi = b1 < b2 ? b2 : b1;
+    if (hi % lo) RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "block extents are not nested");
+    // levels (units): hi, lo, 1 ; a digit with unit u has stride
+    // (u >= b ? g * (u / b) : l * u) in a layout with block b
+    auto st = [](int64_t u, int64_t b, int64_t g, int64_t l) { return u >= b ? g * (u / b) : l * u; };
+    push_mode(cm, s / hi, st(hi, b1, g1, l1), st(hi, b2, g2, l2));
+    push_mode(cm, hi / lo, st(lo, b1, g1, l1), st(lo, b2, g2, l2));
+    push_mode(cm, lo, st(1, b1, g1, l1), st(1, b2, g2, l2));
+}
+
+template <typename T, int MODE>  // MODE 0: interleaved->planar, 1: planar->interleaved, 2: planar->planar
+__global__ void __launch_bounds__(256) copy_modes_kernel(CopyModes cm, int64_t total,
+                                                         const T *__restrict__ src, int64_t src_plane,
+                                                         T *__restrict__ dst, int64_t dst_plane) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; e < total; e += stride) {
+        int64_t r = e, so = 0, dof = 0;
+        if (cm.pow2) {
+            for (int j = cm.n - 1; j >= 0; --j) {
+                int64_t x = cm.ext[j];
+                int64_t d = r & (x - 1);
+                r >>= __popcll(x - 1);
+                so += d * cm.ss[j];
+                dof += d * cm.ds[j];
+            }
+        } else {
+            for (int j = cm.n - 1; j >= 0; --j) {
+                int64_t d = r % cm.ext[j];
+                r /= cm.ext[j];
+                so += d * cm.ss[j];
+                dof += d * cm.ds[j];
+            }
+        }
+        T re, im;
+        if (MODE == 0) {
+            re = src[2 * so];
+            im = src[2 * so + 1];
+        } else {
+            re = src[so];
+            im = src[so + src_plane];
+        }
+        if (MODE == 1) {
+            dst[2 * dof] = re;
+            dst[2 * dof + 1] = im;
+        } else {
+            dst[dof] = re;
+            dst[dof + dst_plane] = im;
+        }
+    }
+}
+
+static int copy_grid(int64_t total) {
+    int64_t b = (total + 255) / 256;
+    int64_t cap = 148 * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <int MODE>
+static void launch_copy(const CopyModes &cm, int64_t total, int dtype, const void *src,
+                        int64_t src_plane, void *dst, int64_t dst_plane, cudaStream_t s) {
+    if (total == 0) return;
+    if (dtype == ROSNET_C64)
+        copy_modes_kernel<float, MODE><<<copy_grid(total), 256, 0, s>>>(
+            cm, total, (const float *)src, src_plane, (float *)dst, dst_plane);
+    else
+        copy_modes_kernel<double, MODE><<<copy_grid(total), 256, 0, s>>>(
+            cm, total, (const double *)src, src_plane, (double *)dst, dst_plane);
+    g_launches++;
+    RN_CHECK_CUDA(cudaGetLastError());
+}
+
+// Modes of "dense row-major" <-> "block-major" for one layout.  Elements are
+// enumerated in row-major order of the dense tensor.
+static CopyModes dense_block_modes(const Layout &lay) {
+    CopyModes cm{};
+    int64_t rs = 1;
+    int64_t rstride[kMaxRank];
+    for (int i = lay.rank - 1; i >= 0; --i) {
+        rstride[i] = rs;
+        rs *= lay.shape[i];
+    }
+    for (int i = 0; i < lay.rank; ++i) {
+        int64_t s = lay.shape[i], b = lay.block[i];
+        // dense row-major: block "s" (one block); block-major: block b
+        axis_modes(cm, s, s, 0, rstride[i], b, lay.gstride[i], lay.lstride[i]);
+    }
+    finish_modes(cm);
+    return cm;
+}
+
+void launch_pack(const Layout &lay, int dtype, const void *dense, void *planar, cudaStream_t s) {
+    if (lay.numel == 0) return;
+    CopyModes cm = dense_block_modes(lay);
+    launch_copy<0>(cm, lay.numel, dtype, dense, 0, planar, lay.numel, s);
+}
+
+void launch_unpack(const Layout &lay, int dtype, const void *planar, void *dense, cudaStream_t s) {
+    if (lay.numel == 0) return;
+    CopyModes cm = dense_block_modes(lay);
+    // enumerate in dense order: ss = block-major (source), ds = dense (dest)
+    for (int j = 0; j < cm.n; ++j) {
+        int64_t t = cm.ss[j];
+        cm.ss[j] = cm.ds[j];
+        cm.ds[j] = t;
+    }
+    launch_copy<1>(cm, lay.numel, dtype, planar, lay.numel, dense, 0, s);
+}
+
+void launch_relayout(const Layout &src, const Layout &dst, const int *perm, int dtype,
+                     const void *sp, void *dp, cudaStream_t s) {
+    if (dst.numel == 0) return;
+    // enumerate in destination axis order
+    CopyModes cm{};
+    for (int i = 0; i < dst.rank; ++i) {
+        int a = perm[i];
+        if (src.shape[a] != dst.shape[i]) RN_FAIL(ROSNET_ERR_SHAPE, "relayout shape mismatch");
+        axis_modes(cm, dst.shape[i], src.block[a], src.gstride[a], src.lstride[a], dst.block[i],
+                   dst.gstride[i], dst.lstride[i]);
+    }
+    finish_modes(cm);
+    launch_copy<2>(cm, dst.numel, dtype, sp, src.numel, dp, dst.numel, s);
+}
+
+// ---------------------------------------------------------------------------
+// tensors
+// ---------------------------------------------------------------------------
+rosnet_btensor new_tensor(int rank, const int64_t *shape, const int64_t *block, int dtype,
+                          cudaStream_t s) {
+    if (dtype != ROSNET_C64 && dtype != ROSNET_C128) RN_FAIL(ROSNET_ERR_DTYPE, "unknown dtype");
+    rosnet_btensor t = new rosnet_btensor_s();
+    try {
+        t->lay.init(rank, shape, block);
+        t->dtype = dtype;
+        t->elsize = dtype == ROSNET_C64 ? 4 : 8;
+        t->stream = s;
+        t->data = dev_alloc(2 * t->lay.numel * t->elsize, s);
+    } catch (...) {
+        delete t;
+        throw;
+    }
+    return t;
+}
+
+void free_tensor(rosnet_btensor t) {
+    if (!t) return;
+    if (t->owned && t->data) dev_free(t->data, t->stream);
+    delete t;
+}
+
+}  // namespace rosnet
+
+using namespace rosnet;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+rosnet_status rosnet_set_allocator(void *(*alloc)(size_t, void *, void *),
+                                   void (*freef)(void *, void *, void *), void *ctx) {
+    if ((alloc == nullptr) != (freef == nullptr)) return ROSNET_ERR_INVALID_ARG;
+    g_alloc = alloc;
+    g_free = freef;
+    g_alloc_ctx = ctx;
+    return ROSNET_OK;
+}
+
+rosnet_status rosnet_btensor_create(int rank, const int64_t *shape, const int64_t *block_shape,
+                                    rosnet_dtype dtype, void *stream, rosnet_btensor *out) {
+    if (!out) return ROSNET_ERR_INVALID_ARG;
+    *out = nullptr;
+    RN_API_BEGIN
+    *out = new_tensor(rank, shape, block_shape, (int)dtype, (cudaStream_t)stream);
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_destroy(rosnet_btensor t) {
+    RN_API_BEGIN
+    free_tensor(t);
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_upload(rosnet_btensor t, const void *host, void *stream) {
+    if (!t || (!host && t->lay.numel > 0)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = 2 * t->lay.numel * t->elsize;
+    if (bytes == 0) return ROSNET_OK;
+    DevBuf stage(bytes, s);
+    RN_CHECK_CUDA(cudaMemcpyAsync(stage.p, host, bytes, cudaMemcpyHostToDevice, s));
+    launch_pack(t->lay, t->dtype, stage.p, t->data, s);
+    t->stream = s;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream) {
+    if (!t || (!host && t->lay.numel > 0)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = 2 * t->lay.numel * t->elsize;
+    if (bytes == 0) return ROSNET_OK;
+    {
+        DevBuf stage(bytes, s);
+        launch_unpack(t->lay, t->dtype, t->data, stage.p, s);
+        RN_CHECK_CUDA(cudaMemcpyAsync(host, stage.p, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    RN_CHECK_CUDA(cudaStreamSynchronize(s));
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_info(rosnet_btensor t, int *rank, int64_t *shape, int64_t *block_shape,
+                                  rosnet_dtype *dtype) {
+    if (!t || !rank) return ROSNET_ERR_INVALID_ARG;
+    *rank = t->lay.rank;
+    for (int i = 0; i < t->lay.rank; ++i) {
+        if (shape) shape[i] = t->lay.shape[i];
+        if (block_shape) block_shape[i] = t->lay.block[i];
+    }
+    if (dtype) *dtype = (rosnet_dtype)t->dtype;
+    return ROSNET_OK;
+}
+
+rosnet_status rosnet_btensor_planes(rosnet_btensor t, void **re, void **im) {
+    if (!t) return ROSNET_ERR_INVALID_ARG;
+    if (re) *re = t->re();
+    if (im) *im = t->im();
+    return ROSNET_OK;
+}
+
+rosnet_status rosnet_sync(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        rosnet::set_last_error(cudaGetErrorString(e));
+        return ROSNET_ERR_CUDA;
+    }
+    return ROSNET_OK;
+}
+
+const char *rosnet_status_string(rosnet_status s) {
+    switch (s) {
+        case ROSNET_OK: return "ok";
+        case ROSNET_ERR_INVALID_ARG: return "invalid argument";
+        case ROSNET_ERR_SHAPE: return "shape mismatch";
+        case ROSNET_ERR_BLOCK_MISMATCH: return "block shape mismatch";
+        case ROSNET_ERR_DTYPE: return "dtype mismatch";
+        case ROSNET_ERR_ALLOC: return "allocation failed";
+        case ROSNET_ERR_RANK_LIMIT: return "rank limit exceeded";
+        case ROSNET_ERR_CUDA: return "CUDA error";
+        case ROSNET_ERR_TIMEOUT: return "device wait timed out";
+        case ROSNET_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+int64_t rosnet_kernel_launches(void) { return rosnet::g_launches.load(); }
+
+const char *rosnet_last_error(void) { return rosnet::last_error_cstr(); }
+
+}  // extern "C"

@@ -1,0 +1,760 @@
+// The pairwise blocked tensordot on CUDA cores.
+//
+// Sec. II-C computes each output block as the sum over the pairs of A and B
+// blocks matched on the contracted-index block coordinates of the local
+// contraction of each pair.  Here every logical axis of a block tensor
+// contributes two index digits (its block coordinate and its position inside
+// the block), each with its own element stride in the block-major layout.
+// Classifying the digits of all axes as M (free in A), N (free in B) or K
+// (contracted) turns the whole blocked contraction into one GEMM-shaped loop
+// nest C[m, n] = sum_k A[m, k] B[k, n] whose operands are addressed through
+// offset tables.  The K digits include the contracted block coordinates, so
+// the K loop of one output tile walks the matched block pairs (steps 1-2)
+// and the intra-block contraction (step 3), and keeps the partial sums of all
+// pairs in registers (step 4); no transpose pass and no partial block ever
+// reaches memory.  The order of the sum over pairs is free (Sec. IV-A).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace rosnet {
+
+// ---------------------------------------------------------------------------
+// planner: the GEMM view
+// ---------------------------------------------------------------------------
+namespace {
+
+// Digits of one logical axis of extent s carried by two layouts with block
+// extents b0, b1 (nested): outer to inner, each with its stride in both.
+void axis_digits(std::vector<Mode> &out, int64_t s, int64_t b0, int64_t g0, int64_t l0, int64_t b1,
+                 int64_t g1, int64_t l1) {
+    int64_t lo = std::min(b0, b1), hi = std::max(b0, b1);
+    if (lo < 1 || hi % lo) RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "block extents are not nested");
+    auto st = [](int64_t u, int64_t b, int64_t g, int64_t l) { return u >= b ? g * (u / b) : l * u; };
+    const int64_t ext[3] = {s / hi, hi / lo, lo};
+    const int64_t unit[3] = {hi, lo, 1};
+    for (int i = 0; i < 3; ++i)
+        if (ext[i] != 1) out.push_back(Mode{ext[i], st(unit[i], b0, g0, l0), st(unit[i], b1, g1, l1)});
+}
+
+// Order digits outermost-first by the stride in tensor `which` (0 or 1),
+// then fuse neighbours that are contiguous in both tensors.
+void order_and_fuse(std::vector<Mode> &ms, int which, ModeList &out) {
+    std::stable_sort(ms.begin(), ms.end(), [which](const Mode &x, const Mode &y) {
+        int64_t a = which ? x.s1 : x.s0, b = which ? y.s1 : y.s0;
+        return a > b;
+    });
+    out.n = 0;
+    for (const Mode &q : ms) {
+        if (out.n > 0) {
+            Mode &p = out.m[out.n - 1];
+            if (p.s0 == q.s0 * q.ext && p.s1 == q.s1 * q.ext) {
+                p.ext *= q.ext;
+                p.s0 = q.s0;
+                p.s1 = q.s1;
+                continue;
+            }
+        }
+        if (out.n >= kMaxModes) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "too many index digits");
+        out.m[out.n++] = q;
+    }
+}
+
+int64_t min_stride(const std::vector<Mode> &ms, int which) {
+    int64_t m = INT64_MAX;
+    for (const Mode &x : ms) m = std::min(m, which ? x.s1 : x.s0);
+    return m;
+}
+
+}  // namespace
+
+GettView make_view(const Layout &A, const Layout &B, const Layout &C, int naxes, const int *axa,
+                   const int *axb) {
+    bool ca[kMaxRank] = {false}, cb[kMaxRank] = {false};
+    for (int i = 0; i < naxes; ++i) {
+        ca[axa[i]] = true;
+        cb[axb[i]] = true;
+    }
+    std::vector<Mode> mM, mN, mK;
+    int p = 0;  // axis of C
+    for (int i = 0; i < A.rank; ++i) {
+        if (ca[i]) continue;
+        axis_digits(mM, A.shape[i], A.block[i], A.gstride[i], A.lstride[i], C.block[p],
+                    C.gstride[p], C.lstride[p]);
+        ++p;
+    }
+    for (int i = 0; i < B.rank; ++i) {
+        if (cb[i]) continue;
+        axis_digits(mN, B.shape[i], B.block[i], B.gstride[i], B.lstride[i], C.block[p],
+                    C.gstride[p], C.lstride[p]);
+        ++p;
+    }
+    for (int i = 0; i < naxes; ++i) {
+        int x = axa[i], y = axb[i];
+        axis_digits(mK, A.shape[x], A.block[x], A.gstride[x], A.lstride[x], B.block[y], B.gstride[y],
+                    B.lstride[y]);
+    }
+    GettView v;
+    // A's unit-stride digit decides whether A tiles are read along m or k;
+    // likewise B along n or k.
+    v.a_m_fast = !mM.empty() && min_stride(mM, 0) < min_stride(mK, 0);
+    v.b_n_fast = !mN.empty() && min_stride(mN, 0) < min_stride(mK, 1);
+    v.c_n_fast = mM.empty() || (!mN.empty() && min_stride(mN, 1) < min_stride(mM, 1));
+    order_and_fuse(mM, 0, v.M);
+    order_and_fuse(mN, 0, v.N);
+    order_and_fuse(mK, v.a_m_fast ? 1 : 0, v.K);
+    v.Mtot = v.M.total();
+    v.Ntot = v.N.total();
+    v.Ktot = v.K.total();
+    return v;
+}
+
+size_t table_entries(const GettView &v) {
+    return (size_t)(2 * v.Mtot + 2 * v.Ntot + 2 * v.Ktot);
+}
+
+// offsets of every index value of one class in its two tensors
+__global__ void __launch_bounds__(256) build_table_kernel(ModeList ml, int64_t total,
+                                                          int64_t *__restrict__ out0,
+                                                          int64_t *__restrict__ out1) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i, o0 = 0, o1 = 0;
+        for (int j = ml.n - 1; j >= 0; --j) {
+            int64_t x = ml.m[j].ext;
+            int64_t d;
+            if ((x & (x - 1)) == 0) {
+                d = r & (x - 1);
+                r >>= __popcll(x - 1);
+            } else {
+                d = r % x;
+                r /= x;
+            }
+            o0 += d * ml.m[j].s0;
+            o1 += d * ml.m[j].s1;
+        }
+        out0[i] = o0;
+        out1[i] = o1;
+    }
+}
+
+static void launch_table(const ModeList &ml, int64_t total, int64_t *o0, int64_t *o1,
+                         cudaStream_t s) {
+    if (total <= 0) return;
+    int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 8);
+    build_table_kernel<<<(int)blocks, 256, 0, s>>>(ml, total, o0, o1);
+    g_launches++;
+    RN_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_build_tables(const GettView &v, int64_t *t, cudaStream_t s) {
+    launch_table(v.M, v.Mtot, t, t + v.Mtot, s);
+    t += 2 * v.Mtot;
+    launch_table(v.N, v.Ntot, t, t + v.Ntot, s);
+    t += 2 * v.Ntot;
+    launch_table(v.K, v.Ktot, t, t + v.Ktot, s);
+}
+
+void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *t) {
+    d.offAM = t;
+    d.offCM = t + v.Mtot;
+    t += 2 * v.Mtot;
+    d.offBN = t;
+    d.offCN = t + v.Ntot;
+    t += 2 * v.Ntot;
+    d.offAK = t;
+    d.offBK = t + v.Ktot;
+    d.M = v.Mtot;
+    d.N = v.Ntot;
+    d.K = v.Ktot;
+    d.flags = (v.a_m_fast ? kFlagAMFast : 0) | (v.b_n_fast ? kFlagBNFast : 0) |
+              (v.c_n_fast ? kFlagCNFast : 0);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+struct GroupArgs {
+    const GettDesc *descs;  // device array, or NULL to use `single`
+    int ndesc;
+    GettDesc single;
+};
+
+// Locate this CTA's problem (the last one whose tile_begin <= blockIdx.x).
+__device__ __forceinline__ void load_desc(const GroupArgs &g, GettDesc &sd) {
+    if (g.descs == nullptr) {
+        sd = g.single;
+        return;
+    }
+    const int64_t bid = blockIdx.x;
+    int lo = 0, hi = g.ndesc - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g.descs[mid].tile_begin <= bid) lo = mid;
+        else hi = mid - 1;
+    }
+    sd = g.descs[lo];
+}
+
+template <typename T>
+__device__ __forceinline__ void cmac(T &cr, T &ci, T ar, T ai, T br, T bi) {
+    cr = fma(ar, br, cr);
+    cr = fma(-ai, bi, cr);
+    ci = fma(ar, bi, ci);
+    ci = fma(ai, br, ci);
+}
+
+// (m, n) of output o of a thread-per-output kernel: n fastest when B or C
+// are contiguous along n, else m fastest.
+__device__ __forceinline__ void out_coords(const GettDesc &d, int64_t o, int64_t &m, int64_t &n) {
+    if (d.flags & (kFlagBNFast | kFlagCNFast)) {
+        n = o % d.N;
+        m = o / d.N;
+    } else {
+        m = o % d.M;
+        n = o / d.M;
+    }
+}
+
+// One thread per output entry; the (short) K loop runs in registers.
+template <typename T>
+__global__ void __launch_bounds__(256) gett_small_kernel(const __grid_constant__ GroupArgs g) {
+    __shared__ GettDesc sd;
+    if (threadIdx.x == 0) load_desc(g, sd);
+    __syncthreads();
+    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
+    const int64_t o = tile * 256 + threadIdx.x;
+    const int64_t M = sd.M, N = sd.N, K = sd.K;
+    if (o >= M * N) return;
+    int64_t m, n;
+    out_coords(sd, o, m, n);
+    const T *__restrict__ A = (const T *)sd.a;
+    const T *__restrict__ B = (const T *)sd.b;
+    const int64_t *__restrict__ offAK = sd.offAK;
+    const int64_t *__restrict__ offBK = sd.offBK;
+    const int64_t am = sd.offAM[m], bn = sd.offBN[n];
+    const int64_t ap = sd.a_plane, bp = sd.b_plane;
+    T sr = 0, si = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        const int64_t ia = am + offAK[k], ib = bn + offBK[k];
+        cmac(sr, si, A[ia], A[ia + ap], B[ib], B[ib + bp]);
+    }
+    T *C = (T *)sd.c;
+    const int64_t ic = sd.offCM[m] + sd.offCN[n];
+    C[ic] = sr;
+    C[ic + sd.c_plane] = si;
+}
+
+// One warp per output entry; lanes split the K loop, shuffle reduction.
+template <typename T>
+__global__ void __launch_bounds__(256) gett_warpk_kernel(const __grid_constant__ GroupArgs g) {
+    __shared__ GettDesc sd;
+    if (threadIdx.x == 0) load_desc(g, sd);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
+    const int64_t o = tile * 8 + (threadIdx.x >> 5);
+    const int64_t M = sd.M, N = sd.N, K = sd.K;
+    if (o >= M * N) return;
+    int64_t m, n;
+    out_coords(sd, o, m, n);
+    const T *__restrict__ A = (const T *)sd.a;
+    const T *__restrict__ B = (const T *)sd.b;
+    const int64_t am = sd.offAM[m], bn = sd.offBN[n];
+    const int64_t ap = sd.a_plane, bp = sd.b_plane;
+    T sr = 0, si = 0;
+    for (int64_t k = lane; k < K; k += 32) {
+        const int64_t ia = am + sd.offAK[k], ib = bn + sd.offBK[k];
+        cmac(sr, si, A[ia], A[ia + ap], B[ib], B[ib + bp]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+        si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    if (lane == 0) {
+        T *C = (T *)sd.c;
+        const int64_t ic = sd.offCM[m] + sd.offCN[n];
+        C[ic] = sr;
+        C[ic + sd.c_plane] = si;
+    }
+}
+
+// Sum of the split-K partials (in split order: deterministic) into C.
+template <typename T>
+__global__ void __launch_bounds__(256) gett_reduce_kernel(const __grid_constant__ GroupArgs g) {
+    __shared__ GettDesc sd;
+    if (threadIdx.x == 0) load_desc(g, sd);
+    __syncthreads();
+    const int64_t MN = sd.M * sd.N;
+    const int64_t o = ((int64_t)blockIdx.x - sd.tile_begin) * 256 + threadIdx.x;
+    if (o >= MN) return;
+    const T *__restrict__ P = (const T *)sd.part;
+    T sr = 0, si = 0;
+    for (int s = 0; s < sd.ksplit; ++s) {
+        sr += P[(2 * (int64_t)s) * MN + o];
+        si += P[(2 * (int64_t)s + 1) * MN + o];
+    }
+    const int64_t m = o / sd.N, n = o % sd.N;
+    T *C = (T *)sd.c;
+    const int64_t ic = sd.offCM[m] + sd.offCN[n];
+    C[ic] = sr;
+    C[ic + sd.c_plane] = si;
+}
+
+__device__ __forceinline__ void cp_async_el(void *smem, const void *gsrc, int bytes, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? bytes : 0;   // 0 source bytes: the shared word is zero-filled
+    if (bytes == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc), "r"(n));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gsrc), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// BM x BN output tile per CTA, 256 threads (16 x 16) each owning TM x TN
+// complex outputs.  A and B tiles of BK contracted indices are gathered
+// element by element through the offset tables (consecutive threads take
+// consecutive values of A's / B's unit-stride digit, so the gathers
+// coalesce) with cp.async into a STAGES-deep shared-memory ring of planar
+// re/im rows.  The K loop runs over every matched block pair and every
+// intra-block index and keeps all partial sums in registers.  With split-K
+// the CTA covers one contracted range and writes its partial tile to the
+// workspace instead of C (summed by gett_reduce_kernel).
+template <typename T, int BM, int BN, int BK, int STAGES>
+struct TiledCfg {
+    static constexpr int NT = 256;
+    static constexpr int TM = BM / 16, TN = BN / 16;
+    static constexpr int LA = BM * BK / NT, LB = BN * BK / NT;
+    static constexpr int PAD = 16 / sizeof(T);
+    static constexpr int RA = BM + PAD, RB = BN + PAD;    // shared row lengths
+    static constexpr int VA = TM * (int)sizeof(T) / 16;    // 16-byte vectors per row fragment
+    static constexpr int VB = TN * (int)sizeof(T) / 16;
+    static constexpr size_t smem = sizeof(T) * (size_t)STAGES * 2 * BK * (RA + RB);
+};
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+template <typename T, int BM, int BN, int BK, int STAGES>
+__global__ void __launch_bounds__(256, 1) gett_tiled_kernel(const __grid_constant__ GroupArgs g) {
+    using Cfg = TiledCfg<T, BM, BN, BK, STAGES>;
+    using V = typename Vec16<T>::type;
+    constexpr int NT = Cfg::NT, TM = Cfg::TM, TN = Cfg::TN, LA = Cfg::LA, LB = Cfg::LB;
+    constexpr int RA = Cfg::RA, RB = Cfg::RB;
+    constexpr int PA = BK * RA, PB = BK * RB;   // one plane of one stage
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);          // [STAGES][2 planes][BK][RA]
+    T *Bs = As + STAGES * 2 * PA;                       // [STAGES][2 planes][BK][RB]
+    __shared__ GettDesc sd;
+    __shared__ int64_t sCM[BM], sCN[BN];
+
+    const int tid = threadIdx.x;
+    if (tid == 0) load_desc(g, sd);
+    __syncthreads();
+    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
+    const int64_t ntile = sd.tiles_m * sd.tiles_n;
+    const int split = (int)(tile / ntile);
+    const int64_t t2 = tile - (int64_t)split * ntile;
+    const int64_t m0 = (t2 % sd.tiles_m) * BM, n0 = (t2 / sd.tiles_m) * BN;
+    const int64_t M = sd.M, N = sd.N, K = sd.K;
+    const bool amf = sd.flags & kFlagAMFast, bnf = sd.flags & kFlagBNFast;
+    const T *__restrict__ A = (const T *)sd.a;
+    const T *__restrict__ B = (const T *)sd.b;
+    const int64_t *__restrict__ offAK = sd.offAK;
+    const int64_t *__restrict__ offBK = sd.offBK;
+    const int64_t ap = sd.a_plane, bp = sd.b_plane;
+    // contracted range of this CTA, in k-tiles
+    const int64_t nkt_all = (K + BK - 1) / BK;
+    const int64_t kt0 = (int64_t)split * sd.ktiles_per_split;
+    const int64_t kt1 = min(nkt_all, kt0 + (int64_t)sd.ktiles_per_split);
+    const int nkt = kt1 > kt0 ? (int)(kt1 - kt0) : 0;
+
+    if (sd.part == nullptr)
+        for (int i = tid; i < BM + BN; i += NT) {
+            if (i < BM) sCM[i] = (m0 + i < M) ? sd.offCM[m0 + i] : 0;
+            else sCN[i - BM] = (n0 + i - BM < N) ? sd.offCN[n0 + i - BM] : 0;
+        }
+
+    // this thread's share of the A and B tiles
+    int aK[LA], aS[LA], bK[LB], bS[LB];   // k within the tile, shared-row offset
+    int64_t aOff[LA], bOff[LB];
+    bool aOk[LA], bOk[LB];
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+        const int e = tid + i * NT;
+        const int mi = amf ? e % BM : e / BK;
+        aK[i] = amf ? e / BM : e % BK;
+        aS[i] = aK[i] * RA + mi;
+        aOk[i] = m0 + mi < M;
+        aOff[i] = aOk[i] ? sd.offAM[m0 + mi] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+        const int e = tid + i * NT;
+        const int ni = bnf ? e % BN : e / BK;
+        bK[i] = bnf ? e / BN : e % BK;
+        bS[i] = bK[i] * RB + ni;
+        bOk[i] = n0 + ni < N;
+        bOff[i] = bOk[i] ? sd.offBN[n0 + ni] : 0;
+    }
+
+    // offsets of the contracted indices of a k-tile, one tile ahead
+    int64_t kA[LA], kB[LB];
+    auto load_koff = [&](int t) {   // t: local k-tile index
+        const int64_t kb = (kt0 + t) * BK;
+#pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            const int64_t k = kb + aK[i];
+            kA[i] = (t < nkt && k < K) ? __ldg(offAK + k) : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            const int64_t k = kb + bK[i];
+            kB[i] = (t < nkt && k < K) ? __ldg(offBK + k) : -1;
+        }
+    };
+    auto issue = [&](int st) {      // cp.async of the tile whose offsets are in kA/kB
+        T *a0 = As + st * 2 * PA, *b0 = Bs + st * 2 * PB;
+#pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            const bool v = aOk[i] && kA[i] >= 0;
+            const T *src = v ? A + aOff[i] + kA[i] : A;
+            cp_async_el(a0 + aS[i], src, sizeof(T), v);
+            cp_async_el(a0 + PA + aS[i], v ? src + ap : A, sizeof(T), v);
+        }
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            const bool v = bOk[i] && kB[i] >= 0;
+            const T *src = v ? B + bOff[i] + kB[i] : B;
+            cp_async_el(b0 + bS[i], src, sizeof(T), v);
+            cp_async_el(b0 + PB + bS[i], v ? src + bp : B, sizeof(T), v);
+        }
+    };
+
+    const int ty = tid >> 4, tx = tid & 15;
+    T cr[TM][TN], ci[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0;
+
+    // prologue: tiles 0 .. STAGES-2 in flight, offsets of tile STAGES-1 loaded
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        load_koff(s);
+        if (s < nkt) issue(s);
+        cp_async_commit();
+    }
+    load_koff(STAGES - 1);
+
+    for (int kt = 0; kt < nkt; ++kt) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();   // tile kt visible to all; stage of tile kt-1 free
+        if (kt + STAGES - 1 < nkt) issue((kt + STAGES - 1) % STAGES);
+        cp_async_commit();
+        load_koff(kt + STAGES);
+        const int st = kt % STAGES;
+        const T *a0 = As + st * 2 * PA + ty * TM, *a1 = a0 + PA;
+        const T *b0 = Bs + st * 2 * PB + tx * TN, *b1 = b0 + PB;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T xr[TM], xi[TM], yr[TN], yi[TN];
+#pragma unroll
+            for (int v = 0; v < Cfg::VA; ++v) {
+                V r = *reinterpret_cast<const V *>(a0 + kk * RA + v * Vec16<T>::n);
+                V q = *reinterpret_cast<const V *>(a1 + kk * RA + v * Vec16<T>::n);
+                const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
+#pragma unroll
+                for (int u = 0; u < Vec16<T>::n; ++u) {
+                    xr[v * Vec16<T>::n + u] = rr[u];
+                    xi[v * Vec16<T>::n + u] = qq[u];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < Cfg::VB; ++v) {
+                V r = *reinterpret_cast<const V *>(b0 + kk * RB + v * Vec16<T>::n);
+                V q = *reinterpret_cast<const V *>(b1 + kk * RB + v * Vec16<T>::n);
+                const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
+#pragma unroll
+                for (int u = 0; u < Vec16<T>::n; ++u) {
+                    yr[v * Vec16<T>::n + u] = rr[u];
+                    yi[v * Vec16<T>::n + u] = qq[u];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) cmac(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
+        }
+    }
+    cp_async_wait<0>();
+
+    if (sd.part != nullptr) {   // split-K: partial tile to the workspace
+        const int64_t MN = M * N;
+        T *P = (T *)sd.part + (2 * (int64_t)split) * MN;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t m = m0 + ty * TM + i;
+            if (m >= M) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t n = n0 + tx * TN + j;
+                if (n >= N) continue;
+                P[m * N + n] = cr[i][j];
+                P[MN + m * N + n] = ci[i][j];
+            }
+        }
+        return;
+    }
+    T *C = (T *)sd.c;
+    const int64_t cp = sd.c_plane;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int mi = ty * TM + i;
+        if (m0 + mi >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int nj = tx * TN + j;
+            if (n0 + nj >= N) continue;
+            const int64_t o = sCM[mi] + sCN[nj];
+            C[o] = cr[i][j];
+            C[o + cp] = ci[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+// C^T = B^T A^T: exchange the roles of the two operands (no data moves).
+static void swap_operands(GettDesc &d) {
+    std::swap(d.offAM, d.offBN);
+    std::swap(d.offCM, d.offCN);
+    std::swap(d.offAK, d.offBK);
+    std::swap(d.M, d.N);
+    int f = d.flags;
+    d.flags = ((f & kFlagAMFast) ? kFlagBNFast : 0) | ((f & kFlagBNFast) ? kFlagAMFast : 0) |
+              ((f & kFlagCNFast) ? 0 : kFlagCNFast) | ((f & kFlagSwapped) ? 0 : kFlagSwapped);
+}
+
+constexpr int kTiledStages = 3;
+constexpr int kSMs = 148;
+
+void choose_kernel(GettDesc &d, int dtype, int precision) {
+    (void)precision;
+    d.ksplit = 1;
+    d.ktiles_per_split = 0x7fffffff;
+    d.part = nullptr;
+    const int64_t MN = d.M * d.N;
+    const bool tiled_ok = d.K >= 16 && std::min(d.M, d.N) >= 16 && MN >= 2048;
+    if (tiled_ok) {
+        if (d.N > d.M) swap_operands(d);   // the BM side takes the larger extent
+        const bool wide = dtype == ROSNET_C64 && d.M >= 128 && d.N >= 48;
+        const int BM = wide ? 128 : 64, BN = 64, BK = dtype == ROSNET_C64 ? 16 : 8;
+        d.kind = wide ? kKindTiledWide : kKindTiled;
+        d.tiles_m = (d.M + BM - 1) / BM;
+        d.tiles_n = (d.N + BN - 1) / BN;
+        // split the contracted range when the tile grid cannot fill the GPU
+        const int64_t tiles = d.tiles_m * d.tiles_n;
+        const int64_t nkt = (d.K + BK - 1) / BK;
+        if (tiles < kSMs && nkt >= 32) {
+            int64_t want = (2 * kSMs + tiles - 1) / tiles;
+            int64_t cap = nkt / 16;            // at least 16 k-tiles per range
+            int64_t ks = std::max<int64_t>(1, std::min<int64_t>(std::min(want, cap), 64));
+            if (ks > 1) {
+                d.ktiles_per_split = (int)((nkt + ks - 1) / ks);
+                d.ksplit = (int)((nkt + d.ktiles_per_split - 1) / d.ktiles_per_split);
+            }
+        }
+        return;
+    }
+    if (d.K >= 128 && MN <= (int64_t(1) << 16)) {
+        d.kind = kKindWarpK;
+        d.tiles_m = (MN + 7) / 8;
+        d.tiles_n = 1;
+    } else {
+        d.kind = kKindSmall;
+        d.tiles_m = (MN + 255) / 256;
+        d.tiles_n = 1;
+    }
+}
+
+size_t desc_part_bytes(const GettDesc &d, int dtype) {
+    if (d.ksplit <= 1) return 0;
+    return (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * (dtype == ROSNET_C64 ? 4 : 8);
+}
+
+template <typename T, int BM, int BN, int BK>
+static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
+    using Cfg = TiledCfg<T, BM, BN, BK, kTiledStages>;
+    static bool attr_set = false;   // once per process (one device)
+    if (!attr_set) {
+        RN_CHECK_CUDA(cudaFuncSetAttribute(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
+        attr_set = true;
+    }
+    gett_tiled_kernel<T, BM, BN, BK, kTiledStages><<<grid, 256, Cfg::smem, s>>>(ga);
+}
+
+static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t total_ctas,
+                              cudaStream_t s) {
+    if (total_ctas <= 0) return;
+    if (total_ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "too many tiles in one launch");
+    dim3 grid((unsigned)total_ctas);
+    if (dtype == ROSNET_C64) {
+        switch (kind) {
+            case kKindSmall: gett_small_kernel<float><<<grid, 256, 0, s>>>(ga); break;
+            case kKindWarpK: gett_warpk_kernel<float><<<grid, 256, 0, s>>>(ga); break;
+            case kKindReduce: gett_reduce_kernel<float><<<grid, 256, 0, s>>>(ga); break;
+            case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
+            default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
+        }
+    } else {
+        switch (kind) {
+            case kKindSmall: gett_small_kernel<double><<<grid, 256, 0, s>>>(ga); break;
+            case kKindWarpK: gett_warpk_kernel<double><<<grid, 256, 0, s>>>(ga); break;
+            case kKindReduce: gett_reduce_kernel<double><<<grid, 256, 0, s>>>(ga); break;
+            default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
+        }
+    }
+    g_launches++;
+    RN_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_gett_group(int kind, int dtype, const GettDesc *descs, int ndesc, int64_t total_ctas,
+                       cudaStream_t s) {
+    GroupArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.descs = descs;
+    ga.ndesc = ndesc;
+    launch_group_args(kind, dtype, ga, total_ctas, s);
+}
+
+static void launch_gett_single(const GettDesc &d, int kind, int64_t ctas, int dtype, cudaStream_t s) {
+    GroupArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.descs = nullptr;
+    ga.ndesc = 1;
+    ga.single = d;
+    ga.single.tile_begin = 0;
+    launch_group_args(kind, dtype, ga, ctas, s);
+}
+
+// CTAs of the split-K reduction of a problem
+int64_t reduce_ctas(const GettDesc &d) { return (d.M * d.N + 255) / 256; }
+
+// ---------------------------------------------------------------------------
+// one pairwise contraction
+// ---------------------------------------------------------------------------
+void tensordot_into(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa, const int *axb,
+                    rosnet_btensor C, int precision, cudaStream_t s) {
+    GettView v = make_view(A->lay, B->lay, C->lay, naxes, axa, axb);
+    if (v.Mtot * v.Ntot == 0) return;
+    GettDesc d;
+    memset(&d, 0, sizeof(d));
+    DevBuf tab(table_entries(v) * sizeof(int64_t), s);
+    launch_build_tables(v, (int64_t *)tab.p, s);
+    fill_desc_tables(d, v, (const int64_t *)tab.p);
+    choose_kernel(d, A->dtype, precision);
+    bind_operands(d, A->data, B->data, C->data, A->lay.numel, B->lay.numel, C->lay.numel);
+    DevBuf part(desc_part_bytes(d, A->dtype), s);
+    d.part = part.p;
+    launch_gett_single(d, d.kind, desc_ctas(d), A->dtype, s);
+    if (d.part) launch_gett_single(d, kKindReduce, reduce_ctas(d), A->dtype, s);
+}
+
+// Validate a tensordot request and return the shape/blocks of C.
+void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axes_a,
+                     const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc) {
+    if (!A || !B) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL operand");
+    if (naxes < 0 || naxes > A->lay.rank || naxes > B->lay.rank)
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad number of contracted axes");
+    if (naxes > 0 && (!axes_a || !axes_b)) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL axes");
+    if (A->dtype != B->dtype) RN_FAIL(ROSNET_ERR_DTYPE, "operands have different dtypes");
+    bool ua[kMaxRank] = {false}, ub[kMaxRank] = {false};
+    for (int i = 0; i < naxes; ++i) {
+        int x = axes_a[i] < 0 ? axes_a[i] + A->lay.rank : axes_a[i];
+        int y = axes_b[i] < 0 ? axes_b[i] + B->lay.rank : axes_b[i];
+        if (x < 0 || x >= A->lay.rank || y < 0 || y >= B->lay.rank)
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "axis out of range");
+        if (ua[x] || ub[y]) RN_FAIL(ROSNET_ERR_INVALID_ARG, "axis contracted twice");
+        ua[x] = ub[y] = true;
+        if (A->lay.shape[x] != B->lay.shape[y])
+            RN_FAIL(ROSNET_ERR_SHAPE, "contracted axes have different extents");
+        if (A->lay.block[x] != B->lay.block[y])
+            RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "contracted axes have different block extents");
+        axa[i] = x;
+        axb[i] = y;
+    }
+    rc = 0;
+    for (int i = 0; i < A->lay.rank; ++i)
+        if (!ua[i]) {
+            shc[rc] = A->lay.shape[i];
+            blc[rc++] = A->lay.block[i];
+        }
+    for (int i = 0; i < B->lay.rank; ++i)
+        if (!ub[i]) {
+            if (rc >= kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "result rank > 64");
+            shc[rc] = B->lay.shape[i];
+            blc[rc++] = B->lay.block[i];
+        }
+}
+
+int check_precision(const rosnet_opts *opts, int dtype) {
+    if (!opts) return ROSNET_PREC_DEFAULT;
+    for (int i = 0; i < 6; ++i)
+        if (opts->reserved[i] != 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "reserved option fields must be 0");
+    int p = opts->precision;
+    if (p < ROSNET_PREC_DEFAULT || p > ROSNET_PREC_FP64) RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad precision");
+    if (dtype == ROSNET_C128 && p != ROSNET_PREC_DEFAULT && p != ROSNET_PREC_FP64)
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "complex128 supports the FP64 mode only");
+    if (dtype == ROSNET_C64 && p == ROSNET_PREC_FP64)
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "FP64 mode needs complex128 operands");
+    if (p == ROSNET_PREC_TF32 || p == ROSNET_PREC_BF16X3)
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "tensor-core precision modes are not available in this build");
+    return p;
+}
+
+}  // namespace rosnet
+
+using namespace rosnet;
+
+extern "C" rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes,
+                                          const int *axes_a, const int *axes_b,
+                                          const rosnet_opts *opts, void *stream,
+                                          rosnet_btensor *out_C) {
+    if (!out_C) return ROSNET_ERR_INVALID_ARG;
+    *out_C = nullptr;
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    int axa[kMaxRank], axb[kMaxRank], rc = 0;
+    int64_t shc[kMaxRank], blc[kMaxRank];
+    check_tensordot(A, B, naxes, axes_a, axes_b, axa, axb, rc, shc, blc);
+    int prec = check_precision(opts, A->dtype);
+    rosnet_btensor C = new_tensor(rc, shc, blc, A->dtype, s);
+    try {
+        tensordot_into(A, B, naxes, axa, axb, C, prec, s);
+    } catch (...) {
+        free_tensor(C);
+        throw;
+    }
+    *out_C = C;
+    return ROSNET_OK;
+    RN_API_END
+}

@@ -1,0 +1,238 @@
+// Internal declarations of librosnet (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/rosnet.h"
+
+namespace rosnet {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+    rosnet_status code;
+    std::string what;
+};
+
+#define RN_CHECK_CUDA(expr)                                             \
+    do {                                                                \
+        cudaError_t _e = (expr);                                        \
+        if (_e != cudaSuccess) throw ::rosnet::Error{ROSNET_ERR_CUDA,   \
+                                   std::string(#expr) + ": " +         \
+                                   cudaGetErrorString(_e)};             \
+    } while (0)
+
+#define RN_FAIL(code, msg) throw ::rosnet::Error{(code), (msg)}
+
+void set_last_error(const std::string &s);
+const char *last_error_cstr();
+
+#define RN_API_BEGIN try {
+#define RN_API_END                                   \
+    }                                                \
+    catch (const rosnet::Error &e) {                 \
+        rosnet::set_last_error(e.what);              \
+        return e.code;                               \
+    }                                                \
+    catch (const std::bad_alloc &) {                 \
+        rosnet::set_last_error("host out of memory"); \
+        return ROSNET_ERR_ALLOC;                     \
+    }                                                \
+    catch (...) {                                    \
+        rosnet::set_last_error("unknown error");     \
+        return ROSNET_ERR_INVALID_ARG;               \
+    }
+
+
+extern std::atomic<int64_t> g_launches;
+
+// ---------------------------------------------------------------------------
+// memory: the injected (or built-in stream-ordered) allocator
+// ---------------------------------------------------------------------------
+void *dev_alloc(size_t bytes, cudaStream_t s);      // throws ALLOC on failure
+void dev_free(void *p, cudaStream_t s);
+
+// RAII buffer in stream order
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(size_t n, cudaStream_t st) : bytes(n), s(st) { p = n ? dev_alloc(n, st) : nullptr; }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { reset(); p = o.p; bytes = o.bytes; s = o.s; o.p = nullptr; }
+        return *this;
+    }
+    void reset() { if (p) dev_free(p, s); p = nullptr; }
+    ~DevBuf() { reset(); }
+    void *release() { void *q = p; p = nullptr; return q; }
+};
+
+// ---------------------------------------------------------------------------
+// block tensors
+// ---------------------------------------------------------------------------
+constexpr int kMaxRank = ROSNET_MAX_RANK;
+
+struct Layout {
+    int rank = 0;
+    int64_t shape[kMaxRank];
+    int64_t block[kMaxRank];
+    int64_t numel = 1;
+    // element strides (within one plane) of the grid and intra-block index of
+    // every axis in the block-major layout: offset(x) = sum_i (x_i / b_i) *
+    // gstride[i] + (x_i % b_i) * lstride[i]
+    int64_t gstride[kMaxRank];
+    int64_t lstride[kMaxRank];
+    void init(int r, const int64_t *sh, const int64_t *bl);  // validates, throws
+};
+
+}  // namespace rosnet
+
+struct rosnet_btensor_s {
+    rosnet::Layout lay;
+    int dtype = 0;           // ROSNET_C64 / ROSNET_C128
+    size_t elsize = 0;       // bytes of one real component (4 or 8)
+    void *data = nullptr;    // real plane; imaginary plane at data + numel*elsize
+    cudaStream_t stream = nullptr;  // stream of the last write, for ordered free
+    bool owned = true;       // false: a view into a contraction arena
+    void *arena_owner = nullptr;
+    void *re() const { return data; }
+    void *im() const { return (char *)data + lay.numel * elsize; }
+};
+
+namespace rosnet {
+
+// ---------------------------------------------------------------------------
+// the GEMM view of a pairwise contraction (Sec. II-C steps 1-2)
+// ---------------------------------------------------------------------------
+// A fused index mode of one class (M: free in A, N: free in B, K:
+// contracted) with its extent and element strides in the two tensors that
+// carry it (M: A and C; N: B and C; K: A and B).
+struct Mode {
+    int64_t ext;
+    int64_t s0, s1;
+};
+
+constexpr int kMaxModes = 2 * kMaxRank;
+
+struct ModeList {
+    int n = 0;
+    Mode m[kMaxModes];      // outermost first
+    int64_t total() const { int64_t t = 1; for (int i = 0; i < n; ++i) t *= m[i].ext; return t; }
+};
+
+struct GettView {
+    ModeList M, N, K;
+    int64_t Mtot = 1, Ntot = 1, Ktot = 1;
+    bool a_m_fast = false;  // A's unit-stride mode is an M mode (else a K mode)
+    bool b_n_fast = false;  // B's unit-stride mode is an N mode (else a K mode)
+    bool c_n_fast = true;   // C's unit-stride mode is an N mode
+};
+
+// Build the view of C = tensordot(A, B, axes) for the three block layouts.
+// axa/axb: contracted axis pairs; the caller has validated them.
+GettView make_view(const Layout &A, const Layout &B, const Layout &C, int naxes,
+                   const int *axa, const int *axb);
+
+// Device-side problem descriptor of one pairwise contraction.  Offsets are
+// in elements within a plane; the imaginary plane of a tensor starts
+// *_plane elements after its real plane.
+struct GettDesc {
+    const void *a;
+    const void *b;
+    void *c;
+    int64_t a_plane, b_plane, c_plane;
+    const int64_t *offAM, *offCM, *offBN, *offCN, *offAK, *offBK;
+    int64_t M, N, K;
+    int64_t tiles_m, tiles_n;   // output tile grid of the kernel chosen for it
+    int64_t tile_begin;         // first global CTA index of this problem in its launch
+    void *part;                 // split-K partial sums [ksplit][2 planes][M*N], or NULL
+    int32_t ksplit;             // number of contracted-index ranges (1 = no split)
+    int32_t ktiles_per_split;   // k-tiles of each range
+    int32_t flags;              // kFlag* bits
+    int32_t kind;               // kernel family (KernelKind)
+};
+
+// CTAs of one problem in its launch (split-K ranges included)
+inline int64_t desc_ctas(const GettDesc &d) { return d.tiles_m * d.tiles_n * (int64_t)d.ksplit; }
+
+// Point a descriptor at its operands and result (honours kFlagSwapped).
+inline void bind_operands(GettDesc &d, const void *A, const void *B, void *C, int64_t a_numel,
+                          int64_t b_numel, int64_t c_numel);
+
+enum : int32_t {
+    kFlagAMFast = 1,
+    kFlagBNFast = 2,
+    kFlagCNFast = 4,
+    kFlagSwapped = 8,   // roles of A and B exchanged (the kernel computes C^T = B^T A^T)
+};
+
+enum KernelKind : int32_t {
+    kKindSmall = 0,   // one thread per output, full K loop (low arithmetic intensity)
+    kKindWarpK = 1,   // one warp per output, lanes split K, shuffle reduction
+    kKindTiled = 2,   // 64x64 register-blocked tiles staged through shared memory
+    kKindTiledWide = 3,  // 128x64 tiles (complex64 only), 8x4 outputs per thread
+    kKindReduce = 4,     // sum of the split-K partials of a problem into C
+};
+
+inline void bind_operands(GettDesc &d, const void *A, const void *B, void *C, int64_t a_numel,
+                          int64_t b_numel, int64_t c_numel) {
+    if (d.flags & kFlagSwapped) {
+        d.a = B; d.b = A; d.a_plane = b_numel; d.b_plane = a_numel;
+    } else {
+        d.a = A; d.b = B; d.a_plane = a_numel; d.b_plane = b_numel;
+    }
+    d.c = C;
+    d.c_plane = c_numel;
+}
+
+// Bytes of split-K partials a problem needs (0 without split).
+size_t desc_part_bytes(const GettDesc &d, int dtype);
+
+// Offsets tables: 2*M + 2*N + 2*K int64 entries, built on the device.
+size_t table_entries(const GettView &v);
+void launch_build_tables(const GettView &v, int64_t *tables, cudaStream_t s);
+void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tables);
+
+// Choose the kernel family, tile grid and split-K for a problem (may swap
+// the operand roles; call bind_operands afterwards).
+void choose_kernel(GettDesc &d, int dtype, int precision);
+
+// Launch one group of problems of the same kind and dtype.  `descs` is in
+// device memory (ndesc entries, with tile_begin prefix sums); total_tiles is
+// the sum of tiles_m*tiles_n.
+void launch_gett_group(int kind, int dtype, const GettDesc *descs, int ndesc,
+                       int64_t total_tiles, cudaStream_t s);
+
+// Pack/unpack between dense row-major interleaved and block-major planar.
+void launch_pack(const Layout &lay, int dtype, const void *dense_interleaved, void *planar,
+                 cudaStream_t s);
+void launch_unpack(const Layout &lay, int dtype, const void *planar, void *dense_interleaved,
+                   cudaStream_t s);
+
+// Copy src (block-major planar) to dst with a different block shape and/or
+// axis permutation: dst axis i = src axis perm[i].
+void launch_relayout(const Layout &src, const Layout &dst, const int *perm, int dtype,
+                     const void *src_planar, void *dst_planar, cudaStream_t s);
+
+// Create / free tensors.
+rosnet_btensor new_tensor(int rank, const int64_t *shape, const int64_t *block, int dtype,
+                          cudaStream_t s);
+void free_tensor(rosnet_btensor t);
+
+// One pairwise contraction enqueued on s into an existing C (used by both
+// rosnet_tensordot and the network executor).  workspace for the tables is
+// allocated from the allocator.
+void tensordot_into(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa,
+                    const int *axb, rosnet_btensor C, int precision, cudaStream_t s);
+
+}  // namespace rosnet

@@ -1,0 +1,133 @@
+"""GPU parity of rosnet_contract (circuit amplitudes) against the oracle's
+state-vector simulation and closed forms.
+
+Single amplitudes are compared with |a - a_ref| / max(|a_ref|, 2^(-n/2))
+(near-zero amplitudes make the plain relative error unstable); open-output
+networks with the relative Frobenius error.  Bar: 1e-5 for complex64 (FP32),
+1e-12 for complex128 (FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2201_06620_b300 as R
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {R.C64: 1e-5, R.C128: 1e-12}
+NPT = {R.C64: np.complex64, R.C128: np.complex128}
+
+
+def amp_err(a, ref, n):
+    return abs(complex(a) - complex(ref)) / max(abs(ref), 2.0 ** (-n / 2))
+
+
+def gpu_network(net, dtype, max_block_entries=0, flags=0, path=None):
+    ts = [R.btensor(np.asarray(t, dtype=NPT[dtype]), None, dtype) for t in net.tensors]
+    if path is None:
+        path = R.path_greedy(ts, net.labels, net.out_labels)
+    C = R.contract(ts, net.labels, net.out_labels, path, flags=flags,
+                   max_block_entries=max_block_entries)
+    return C.download(), path
+
+
+@pytest.mark.parametrize("dtype", [R.C64, R.C128])
+@pytest.mark.parametrize("n,depth,seed", [(4, 4, 0), (8, 8, 1), (12, 12, 2)])
+def test_random_circuit_amplitude(dtype, n, depth, seed):
+    circ = W.random_circuit(n, depth, seed)
+    ref = oracle.amplitude_sv(circ)
+    for flags in (0, R.OPT_NOGROUP, R.OPT_GRAPH):
+        got, _ = gpu_network(W.circuit_network(circ), dtype, flags=flags)
+        assert got.shape == ()
+        assert amp_err(got, ref, n) <= TOL[dtype], flags
+
+
+def test_ghz_and_hadamard_closed_forms():
+    for n in (5, 16):
+        circ = W.ghz_circuit(n)
+        for bits, want in (([0] * n, 1 / math.sqrt(2)), ([1] * n, 1 / math.sqrt(2)),
+                           ([0] * (n - 1) + [1], 0.0)):
+            got, _ = gpu_network(W.circuit_network(circ, bitstring=bits), R.C128)
+            assert abs(complex(got) - want) <= 1e-12
+        hc = W.hadamard_circuit(n)
+        got, _ = gpu_network(W.circuit_network(hc, bitstring=[1] * n), R.C64)
+        assert abs(complex(got) - 2.0 ** (-n / 2)) <= 1e-5 * 2.0 ** (-n / 2)
+
+
+def test_open_output_state_and_norm():
+    circ = W.random_circuit(10, 8, 4)
+    ref = oracle.statevector(circ)
+    for dtype in (R.C64, R.C128):
+        got, _ = gpu_network(W.circuit_network(circ, open_output=True), dtype)
+        assert got.shape == (2,) * 10
+        assert oracle.rel_frobenius(got.ravel(), ref) <= TOL[dtype]
+        assert abs(np.sum(np.abs(got.astype(np.complex128)) ** 2) - 1) <= 10 * TOL[dtype]
+
+
+def test_out_label_permutation():
+    circ = W.random_circuit(6, 4, 9)
+    net = W.circuit_network(circ, open_output=True)
+    ref = oracle.statevector(circ).reshape((2,) * 6)
+    perm = [3, 0, 5, 1, 4, 2]
+    net.out_labels = [net.out_labels[p] for p in perm]
+    got, _ = gpu_network(net, R.C128)
+    np.testing.assert_allclose(got, np.transpose(ref, perm), atol=1e-13)
+
+
+def test_rqc20_amplitude_full_size():
+    """The 20-qubit 4x5 depth-12 amplitude with the greedy path, complex64,
+    blocks of 2^8 entries on every tensor of rank > 8, in the launch
+    configuration the benchmark times (grouped waves, CUDA graph)."""
+    circ = W.rqc20_config()
+    psi = oracle.statevector(circ)
+    rng = np.random.default_rng(0)
+    bitstrings = [circ.bitstring] + [rng.integers(0, 2, 20) for _ in range(3)]
+    for flags in (R.OPT_GRAPH, 0):
+        for bits in bitstrings:
+            got, _ = gpu_network(W.circuit_network(circ, bitstring=bits), R.C64,
+                                 max_block_entries=256, flags=flags)
+            ref = psi[oracle.bitstring_index(bits)]
+            assert amp_err(got, ref, 20) <= 1e-5
+
+
+def test_graph_replay_determinism_and_reuse():
+    circ = W.random_circuit(12, 10, 8)
+    net = W.circuit_network(circ)
+    a1, path = gpu_network(net, R.C64, flags=R.OPT_GRAPH)
+    a2, _ = gpu_network(net, R.C64, flags=R.OPT_GRAPH, path=path)
+    a3, _ = gpu_network(net, R.C64, flags=0, path=path)
+    assert a1 == a2 == a3   # same kernels, same order of sums
+    # a different bitstring through the same cached plan
+    psi = oracle.statevector(circ)
+    bits = 1 - circ.bitstring
+    got, _ = gpu_network(W.circuit_network(circ, bitstring=bits), R.C64, flags=R.OPT_GRAPH, path=path)
+    assert amp_err(got, psi[oracle.bitstring_index(bits)], 12) <= 1e-5
+
+
+def test_reblocking_keeps_values():
+    circ = W.random_circuit(10, 6, 3)
+    ref = oracle.amplitude_sv(circ)
+    for mb in (4, 16, 256):
+        got, _ = gpu_network(W.circuit_network(circ), R.C128, max_block_entries=mb)
+        assert amp_err(got, ref, 10) <= 1e-12
+
+
+def test_contract_errors():
+    ts = [R.btensor(np.ones(2, dtype=np.complex64)), R.btensor(np.ones(2, dtype=np.complex64))]
+    with pytest.raises(R.RosnetError) as e:
+        R.contract(ts, [(0,), (0,)], [], [(0, 0)])
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(R.RosnetError) as e:
+        R.contract(ts, [(0,), (1,)], [], [(0, 1)])       # open labels not listed
+    assert e.value.name == "INVALID_ARG"
+    t3 = R.btensor(np.ones(3, dtype=np.complex64))
+    with pytest.raises(R.RosnetError) as e:
+        R.contract([ts[0], t3], [(0,), (0,)], [], [(0, 1)])
+    assert e.value.name == "SHAPE"
+    tc = R.btensor(np.ones(2, dtype=np.complex128), None, R.C128)
+    with pytest.raises(R.RosnetError) as e:
+        R.contract([ts[0], tc], [(0,), (0,)], [], [(0, 1)])
+    assert e.value.name == "DTYPE"
