@@ -170,6 +170,7 @@ def run_rosnet(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     wall0 = time.perf_counter()
     for i in range(args.warmup, steps):
         flush.random_(0, 255) if i == args.warmup else flush.fill_(i & 0xff)
@@ -179,6 +180,7 @@ def run_rosnet(args):
         ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -323,13 +325,18 @@ def run_reference(args):
 
 def _profiled_traffic():
     """DRAM bytes per launch of the heaviest kernel from the committed ncu
-    summary, if one exists for the current kernel (else null)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    summary, or None when the kernel source changed since that capture."""
+    import hashlib
     try:
-        with open(p) as f:
-            return json.load(f).get("gett_tiled_rqc20_bytes_per_launch")
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, "paper_2201_06620_b300", "csrc", "gett.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
     except (OSError, ValueError):
         return None
+    if not sha.startswith(rec.get("kernel_source_sha256_prefix", "-")):
+        return None
+    return rec.get("gett_tiled_rqc20_bytes_per_launch")
 
 
 def main():
