@@ -176,6 +176,38 @@ rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes,
                                const int *axes_a, const int *axes_b,
                                const rosnet_opts *opts, void *stream, rosnet_btensor *out_C);
 
+/*
+ * rosnet_tensordot_noalloc -- the same contraction as rosnet_tensordot for
+ * callers that cannot allocate device memory at the call (the paper has no
+ * counterpart: it is an interface convenience of this library).  Callers in
+ * this position include code running inside a framework that owns all device
+ * memory and forbids foreign allocations, real-time or embedded code with a
+ * fixed memory budget committed up front, and paths where an allocation could
+ * block or fail unpredictably.
+ *
+ * The caller passes the operands and an already created output tensor C whose
+ * shape, block shape and dtype are those rosnet_tensordot would give the
+ * result (else SHAPE / BLOCK_MISMATCH / DTYPE); C must not alias A or B.  The
+ * call allocates nothing: the offset tables and split-K partial sums the
+ * kernels need are placed in one fixed device array of
+ * ROSNET_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
+ * loads the library keeps until the process exits.  A problem needing more
+ * scratch is rejected with ROSNET_ERR_UNSUPPORTED before anything is launched
+ * (rosnet_last_error() gives the bytes needed).
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the previous call's
+ * contents; every byte a call reads from it is written earlier by the same
+ * call, so nothing needs clearing, but calls that overlap on the GPU (on
+ * different streams, or from different threads) race on it: serialise them.
+ * Errors as rosnet_tensordot.
+ */
+#define ROSNET_NOALLOC_SCRATCH_BYTES (4u << 20)
+rosnet_status rosnet_tensordot_noalloc(rosnet_btensor A, rosnet_btensor B, int naxes,
+                                       const int *axes_a, const int *axes_b, rosnet_btensor C,
+                                       const rosnet_opts *opts, void *stream);
+
 /* ----------------------------------------------------------------------- */
 /* networks (Sec. II-A)                                                     */
 /* ----------------------------------------------------------------------- */

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
-    "path_greedy_extents", "contract",
+    "path_greedy_extents", "contract", "tensordot_noalloc",
     "sync", "kernel_launches", "release_plans", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
@@ -52,6 +52,7 @@ EXPORTS = [
     "rosnet_btensor_planes", "rosnet_tensordot", "rosnet_path_greedy", "rosnet_contract",
     "rosnet_release_plans", "rosnet_sync", "rosnet_status_string", "rosnet_last_error",
     "rosnet_kernel_launches", "rosnet_path_greedy_extents", "rosnet_timing_drain",
+    "rosnet_tensordot_noalloc",
 ]
 
 _lock = threading.Lock()
@@ -112,6 +113,9 @@ def lib():
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_Opts), vp,
                                            ctypes.POINTER(vp)]
             L.rosnet_path_greedy.argtypes = [ctypes.POINTER(_Network), i32p, i32p]
+            L.rosnet_tensordot_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                   ctypes.POINTER(ctypes.c_int), vp,
+                                                   ctypes.POINTER(_Opts), vp]
             L.rosnet_path_greedy_extents.argtypes = [
                 ctypes.c_int32, i32p, ctypes.POINTER(i64p), ctypes.POINTER(i64p), ctypes.c_int32,
                 i64p, i32p, i32p]
@@ -134,7 +138,8 @@ def lib():
                         "rosnet_btensor_upload", "rosnet_btensor_download", "rosnet_btensor_info",
                         "rosnet_btensor_planes", "rosnet_tensordot", "rosnet_path_greedy",
                         "rosnet_contract", "rosnet_release_plans", "rosnet_sync",
-                        "rosnet_path_greedy_extents", "rosnet_timing_drain"):
+                        "rosnet_path_greedy_extents", "rosnet_timing_drain",
+                        "rosnet_tensordot_noalloc"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -343,6 +348,17 @@ def tensordot(A, B, axes_a, axes_b, precision=PREC_DEFAULT, stream=None):
                                   ctypes.byref(o), _stream(stream), ctypes.byref(h)),
            "rosnet_tensordot")
     return BTensor(h.value)
+
+
+def tensordot_noalloc(A, B, axes_a, axes_b, C, precision=PREC_DEFAULT, stream=None):
+    """tensordot into an existing tensor C without any device allocation (the
+    library's fixed scratch array holds the kernels' workspace)."""
+    _init()
+    o = _opts(precision)
+    _check(lib().rosnet_tensordot_noalloc(A.handle, B.handle, len(axes_a), _i32arr(axes_a),
+                                          _i32arr(axes_b), C.handle, ctypes.byref(o),
+                                          _stream(stream)), "rosnet_tensordot_noalloc")
+    return C
 
 
 class Network:

@@ -679,6 +679,30 @@ void tensordot_into(rosnet_btensor A, rosnet_btensor B, int naxes, const int *ax
     if (d.part) launch_gett_single(d, kKindReduce, reduce_ctas(d), A->dtype, s);
 }
 
+// The same contraction with caller-provided scratch instead of allocations:
+// the offset tables and any split-K partials are placed in `ws` (ws_bytes
+// long, 256-byte aligned).  Returns the scratch bytes the problem needs; if
+// that exceeds ws_bytes nothing is launched.
+size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa,
+                         const int *axb, rosnet_btensor C, int precision, void *ws,
+                         size_t ws_bytes, cudaStream_t s) {
+    GettView v = make_view(A->lay, B->lay, C->lay, naxes, axa, axb);
+    if (v.Mtot * v.Ntot == 0) return 0;
+    GettDesc d;
+    memset(&d, 0, sizeof(d));
+    const size_t tab_bytes = (table_entries(v) * sizeof(int64_t) + 255) & ~(size_t)255;
+    fill_desc_tables(d, v, (const int64_t *)ws);
+    choose_kernel(d, A->dtype, precision);
+    const size_t need = tab_bytes + desc_part_bytes(d, A->dtype);
+    if (need > ws_bytes) return need;
+    launch_build_tables(v, (int64_t *)ws, s);
+    bind_operands(d, A->data, B->data, C->data, A->lay.numel, B->lay.numel, C->lay.numel);
+    d.part = d.ksplit > 1 ? (char *)ws + tab_bytes : nullptr;
+    launch_gett_single(d, d.kind, desc_ctas(d), A->dtype, s);
+    if (d.part) launch_gett_single(d, kKindReduce, reduce_ctas(d), A->dtype, s);
+    return need;
+}
+
 // Validate a tensordot request and return the shape/blocks of C.
 void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axes_a,
                      const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc) {
