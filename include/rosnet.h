@@ -72,15 +72,21 @@ typedef enum {
 } rosnet_dtype;
 
 /* Arithmetic used for the block products (the sum is always accumulated in
- * at least float32; see each mode). */
+ * at least float32; see each mode).  The tensor-core modes apply to block
+ * products large enough to fill a 128 x 128 tile; smaller products of the same
+ * call use the FP32 CUDA-core kernels. */
 typedef enum {
     ROSNET_PREC_DEFAULT = 0, /* FP32 CUDA cores for C64, FP64 for C128            */
     ROSNET_PREC_FP32 = 1,    /* C64 only: float32 products and sums (CUDA cores)  */
-    ROSNET_PREC_TF32 = 2,    /* C64 only: TF32 tensor-core products, FP32 sums    */
+    ROSNET_PREC_TF32 = 2,    /* C64 only: TF32 tensor-core products (operands
+                                rounded to 10-bit mantissas), FP32 sums           */
     ROSNET_PREC_BF16X3 = 3,  /* C64 only: each float32 operand split into bf16
                                 hi + lo; hi*hi + hi*lo + lo*hi on tensor cores,
                                 FP32 sums                                         */
-    ROSNET_PREC_FP64 = 4     /* C128 only: float64 products and sums              */
+    ROSNET_PREC_FP64 = 4,    /* C128 only: float64 products and sums              */
+    ROSNET_PREC_TF32X3 = 5   /* C64 only: each float32 operand split into TF32
+                                big + small; big*big + big*small + small*big on
+                                tensor cores, FP32 sums                           */
 } rosnet_precision;
 
 typedef struct rosnet_btensor_s *rosnet_btensor;

@@ -32,6 +32,7 @@ __all__ = [
     "path_greedy_extents", "contract", "tensordot_noalloc",
     "sync", "kernel_launches", "release_plans", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
+    "PREC_TF32X3",
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
 ]
 
@@ -39,7 +40,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librosnet.so")
 
 C64, C128 = 1, 2
-PREC_DEFAULT, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_FP64 = 0, 1, 2, 3, 4
+PREC_DEFAULT, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_FP64, PREC_TF32X3 = 0, 1, 2, 3, 4, 5
 OPT_GRAPH, OPT_NOGROUP, OPT_TIMING = 0x1, 0x2, 0x4
 STATUS = {
     0: "OK", -1: "INVALID_ARG", -2: "SHAPE", -3: "BLOCK_MISMATCH", -4: "DTYPE", -5: "ALLOC",

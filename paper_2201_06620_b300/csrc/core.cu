@@ -372,7 +372,13 @@ rosnet_status rosnet_sync(void *stream) {
         rosnet::set_last_error(cudaGetErrorString(e));
         return ROSNET_ERR_CUDA;
     }
+    RN_API_BEGIN
+    if (rosnet::take_device_status() != 0) {
+        rosnet::set_last_error("a kernel gave up a bounded wait");
+        return ROSNET_ERR_TIMEOUT;
+    }
     return ROSNET_OK;
+    RN_API_END
 }
 
 const char *rosnet_status_string(rosnet_status s) {

@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "gett_common.cuh"
 
 namespace rosnet {
 
@@ -177,28 +178,6 @@ void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *t) {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-struct GroupArgs {
-    const GettDesc *descs;  // device array, or NULL to use `single`
-    int ndesc;
-    GettDesc single;
-};
-
-// Locate this CTA's problem (the last one whose tile_begin <= blockIdx.x).
-__device__ __forceinline__ void load_desc(const GroupArgs &g, GettDesc &sd) {
-    if (g.descs == nullptr) {
-        sd = g.single;
-        return;
-    }
-    const int64_t bid = blockIdx.x;
-    int lo = 0, hi = g.ndesc - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (g.descs[mid].tile_begin <= bid) lo = mid;
-        else hi = mid - 1;
-    }
-    sd = g.descs[lo];
-}
-
 template <typename T>
 __device__ __forceinline__ void cmac(T &cr, T &ci, T ar, T ai, T br, T bi) {
     cr = fma(ar, br, cr);
@@ -556,12 +535,25 @@ static void swap_operands(GettDesc &d) {
 constexpr int kTiledStages = 3;
 constexpr int kSMs = 148;
 
+bool tc_mode_of(int precision, int *mode);
+void launch_tc_group(int mode, const GroupArgs &ga, int64_t ctas, cudaStream_t s);
+int tc_tile_m();
+int tc_tile_n();
+
 void choose_kernel(GettDesc &d, int dtype, int precision) {
-    (void)precision;
     d.ksplit = 1;
     d.ktiles_per_split = 0x7fffffff;
     d.part = nullptr;
     const int64_t MN = d.M * d.N;
+    int tcmode;
+    if (dtype == ROSNET_C64 && tc_mode_of(precision, &tcmode) && std::max(d.M, d.N) >= 128 &&
+        std::min(d.M, d.N) >= 64 && d.K >= 32) {
+        if (d.N > d.M) swap_operands(d);
+        d.kind = kKindTcTF32 + tcmode;
+        d.tiles_m = (d.M + tc_tile_m() - 1) / tc_tile_m();
+        d.tiles_n = (d.N + tc_tile_n() - 1) / tc_tile_n();
+        return;
+    }
     const bool tiled_ok = d.K >= 16 && std::min(d.M, d.N) >= 16 && MN >= 2048;
     if (tiled_ok) {
         if (d.N > d.M) swap_operands(d);   // the BM side takes the larger extent
@@ -617,6 +609,10 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
     if (total_ctas <= 0) return;
     if (total_ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "too many tiles in one launch");
     dim3 grid((unsigned)total_ctas);
+    if (kind >= kKindTcTF32 && kind <= kKindTcBF16x3) {
+        launch_tc_group(kind - kKindTcTF32, ga, total_ctas, s);
+        return;   // counted and checked by launch_tc_group
+    }
     if (dtype == ROSNET_C64) {
         switch (kind) {
             case kKindSmall: gett_small_kernel<float><<<grid, 256, 0, s>>>(ga); break;
@@ -745,13 +741,11 @@ int check_precision(const rosnet_opts *opts, int dtype) {
     for (int i = 0; i < 6; ++i)
         if (opts->reserved[i] != 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "reserved option fields must be 0");
     int p = opts->precision;
-    if (p < ROSNET_PREC_DEFAULT || p > ROSNET_PREC_FP64) RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad precision");
+    if (p < ROSNET_PREC_DEFAULT || p > ROSNET_PREC_TF32X3) RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad precision");
     if (dtype == ROSNET_C128 && p != ROSNET_PREC_DEFAULT && p != ROSNET_PREC_FP64)
         RN_FAIL(ROSNET_ERR_UNSUPPORTED, "complex128 supports the FP64 mode only");
     if (dtype == ROSNET_C64 && p == ROSNET_PREC_FP64)
         RN_FAIL(ROSNET_ERR_UNSUPPORTED, "FP64 mode needs complex128 operands");
-    if (p == ROSNET_PREC_TF32 || p == ROSNET_PREC_BF16X3)
-        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "tensor-core precision modes are not available in this build");
     return p;
 }
 

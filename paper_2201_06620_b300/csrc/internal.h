@@ -52,6 +52,10 @@ const char *last_error_cstr();
 
 extern std::atomic<int64_t> g_launches;
 
+// Read and clear the device status word written by kernels whose bounded
+// waits gave up (0 = none).
+int32_t take_device_status();
+
 // ---------------------------------------------------------------------------
 // memory: the injected (or built-in stream-ordered) allocator
 // ---------------------------------------------------------------------------
@@ -182,6 +186,9 @@ enum KernelKind : int32_t {
     kKindTiled = 2,   // 64x64 register-blocked tiles staged through shared memory
     kKindTiledWide = 3,  // 128x64 tiles (complex64 only), 8x4 outputs per thread
     kKindReduce = 4,     // sum of the split-K partials of a problem into C
+    kKindTcTF32 = 5,     // tcgen05 tensor cores, TF32 products
+    kKindTcTF32x3 = 6,   // tcgen05, 3 x TF32 split products
+    kKindTcBF16x3 = 7,   // tcgen05, 3 x BF16 split products
 };
 
 inline void bind_operands(GettDesc &d, const void *A, const void *B, void *C, int64_t a_numel,
