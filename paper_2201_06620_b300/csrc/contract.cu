@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "gett_common.cuh"
 
 namespace rosnet {
 
@@ -33,6 +34,9 @@ void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *a
                      const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc);
 int check_precision(const rosnet_opts *opts, int dtype);
 int64_t reduce_ctas(const GettDesc &d);
+bool is_tc_kind(int kind);
+size_t tc_workspace_bytes(const GettDesc &d, int mode);
+void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s);
 
 namespace {
 
@@ -73,9 +77,9 @@ struct Plan {
     bool final_direct = true;      // last step writes straight into the output
     Layout out_lay;
     size_t arena_bytes = 0;
-    DevBuf arena, tables, descs, partials;
+    DevBuf arena, tables, descs, partials, tcws;
     // launch list: (kind, first desc, count, total tiles)
-    struct Launch { int kind; int first; int count; int64_t tiles; };
+    struct Launch { int kind; int first; int count; int64_t tiles; size_t tc_ws_off; };
     std::vector<Launch> launches;
     std::vector<int> desc_step;    // desc slot -> step index
     std::vector<GettDesc> slot_desc;  // desc slot -> static descriptor fields
@@ -336,7 +340,8 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
         fill_desc_tables(S.desc, views[st], dtab + S.table_off);
         choose_kernel(S.desc, plan->dtype, prec);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
-        int key_kind = (flags & ROSNET_OPT_NOGROUP) ? st : S.desc.kind;
+        // tensor-core problems carry their own tensor maps: one launch each
+        int key_kind = ((flags & ROSNET_OPT_NOGROUP) || is_tc_kind(S.desc.kind)) ? 1000 + st : S.desc.kind;
         groups[{S.wave, key_kind}].push_back(st);
         if (S.desc.ksplit > 1) split_of_wave[S.wave].push_back(st);
     }
@@ -356,9 +361,15 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
         }
     }
     std::vector<GettDesc> slot_desc;   // per descriptor slot: the static fields
+    size_t tc_bytes = 0;
     auto add_launch = [&](int kind, const std::vector<int> &sts, bool reduce) {
         Plan::Launch L;
         L.kind = kind;
+        L.tc_ws_off = 0;
+        if (is_tc_kind(kind)) {
+            L.tc_ws_off = tc_bytes;
+            tc_bytes += (tc_workspace_bytes(plan->steps[sts[0]].desc, kind - kKindTcTF32) + 255) & ~(size_t)255;
+        }
         L.first = (int)plan->desc_step.size();
         L.count = (int)sts.size();
         int64_t ctas = 0;
@@ -380,6 +391,7 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
             add_launch(kKindReduce, split_of_wave[w], true);
     }
     plan->slot_desc = std::move(slot_desc);
+    if (tc_bytes) plan->tcws = DevBuf(tc_bytes, s);
     // the launch with the most algorithmic work (8 M N K per complex GEMM)
     {
         const double el2d = (double)el2;
@@ -463,7 +475,16 @@ void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream
                 RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal)
                                         : cudaEventRecord(e0, s));
             }
-            launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
+            if (is_tc_kind(L.kind)) {
+                GroupArgs ga;
+                memset(&ga, 0, sizeof(ga));
+                ga.descs = dd + L.first;
+                ga.ndesc = 1;
+                launch_tc_problem(L.kind - kKindTcTF32, P.slot_desc[L.first], ga,
+                                  (char *)P.tcws.p + L.tc_ws_off, s);
+            } else {
+                launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
+            }
             if (th) {
                 cudaEvent_t e1 = P.tev[2 * slot + 1];
                 RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal)

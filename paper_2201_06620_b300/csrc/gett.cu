@@ -536,9 +536,10 @@ constexpr int kTiledStages = 3;
 constexpr int kSMs = 148;
 
 bool tc_mode_of(int precision, int *mode);
-void launch_tc_group(int mode, const GroupArgs &ga, int64_t ctas, cudaStream_t s);
 int tc_tile_m();
 int tc_tile_n();
+size_t tc_workspace_bytes(const GettDesc &d, int mode);
+void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s);
 
 void choose_kernel(GettDesc &d, int dtype, int precision) {
     d.ksplit = 1;
@@ -609,10 +610,8 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
     if (total_ctas <= 0) return;
     if (total_ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "too many tiles in one launch");
     dim3 grid((unsigned)total_ctas);
-    if (kind >= kKindTcTF32 && kind <= kKindTcBF16x3) {
-        launch_tc_group(kind - kKindTcTF32, ga, total_ctas, s);
-        return;   // counted and checked by launch_tc_group
-    }
+    if (kind >= kKindTcTF32 && kind <= kKindTcBF16x3)
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "tensor-core problems are launched with their workspace");
     if (dtype == ROSNET_C64) {
         switch (kind) {
             case kKindSmall: gett_small_kernel<float><<<grid, 256, 0, s>>>(ga); break;
@@ -669,11 +668,23 @@ void tensordot_into(rosnet_btensor A, rosnet_btensor B, int naxes, const int *ax
     fill_desc_tables(d, v, (const int64_t *)tab.p);
     choose_kernel(d, A->dtype, precision);
     bind_operands(d, A->data, B->data, C->data, A->lay.numel, B->lay.numel, C->lay.numel);
+    if (d.kind >= kKindTcTF32 && d.kind <= kKindTcBF16x3) {
+        const int mode = d.kind - kKindTcTF32;
+        DevBuf ws(tc_workspace_bytes(d, mode), s);
+        GroupArgs ga;
+        memset(&ga, 0, sizeof(ga));
+        ga.ndesc = 1;
+        ga.single = d;
+        launch_tc_problem(mode, d, ga, ws.p, s);
+        return;
+    }
     DevBuf part(desc_part_bytes(d, A->dtype), s);
     d.part = part.p;
     launch_gett_single(d, d.kind, desc_ctas(d), A->dtype, s);
     if (d.part) launch_gett_single(d, kKindReduce, reduce_ctas(d), A->dtype, s);
 }
+
+bool is_tc_kind(int kind) { return kind >= kKindTcTF32 && kind <= kKindTcBF16x3; }
 
 // The same contraction with caller-provided scratch instead of allocations:
 // the offset tables and any split-K partials are placed in `ws` (ws_bytes
@@ -689,10 +700,20 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
     const size_t tab_bytes = (table_entries(v) * sizeof(int64_t) + 255) & ~(size_t)255;
     fill_desc_tables(d, v, (const int64_t *)ws);
     choose_kernel(d, A->dtype, precision);
-    const size_t need = tab_bytes + desc_part_bytes(d, A->dtype);
+    const bool tcp = d.kind >= kKindTcTF32 && d.kind <= kKindTcBF16x3;
+    const size_t extra = tcp ? tc_workspace_bytes(d, d.kind - kKindTcTF32) : desc_part_bytes(d, A->dtype);
+    const size_t need = tab_bytes + extra;
     if (need > ws_bytes) return need;
     launch_build_tables(v, (int64_t *)ws, s);
     bind_operands(d, A->data, B->data, C->data, A->lay.numel, B->lay.numel, C->lay.numel);
+    if (tcp) {
+        GroupArgs ga;
+        memset(&ga, 0, sizeof(ga));
+        ga.ndesc = 1;
+        ga.single = d;
+        launch_tc_problem(d.kind - kKindTcTF32, d, ga, (char *)ws + tab_bytes, s);
+        return need;
+    }
     d.part = d.ksplit > 1 ? (char *)ws + tab_bytes : nullptr;
     launch_gett_single(d, d.kind, desc_ctas(d), A->dtype, s);
     if (d.part) launch_gett_single(d, kKindReduce, reduce_ctas(d), A->dtype, s);

@@ -1,27 +1,42 @@
 // The blocked pairwise tensordot on the 5th-generation tensor cores.
 //
 // Complex64 block products run as real tcgen05 GEMMs with FP32 accumulators
-// in tensor memory (TMEM) that persist across the whole contracted-index loop,
-// i.e. across every matched block pair of the output tile (Sec. II-C steps
-// 3-4: all partial products of an output block are summed in place, in any
-// order, Sec. IV-A).  With planar operands the complex product is four real
-// products:
+// in tensor memory (TMEM).  With planar operands the complex product is four
+// real products:
 //     Cr += Ar*Br + (-Ai)*Bi        (the minus is the MMA's negate-A bit)
 //     Ci += Ar*Bi + Ai*Br
-// Precision modes (each operand element x is converted while it is staged):
+// Precision modes (each operand element x is converted once, when packed):
 //   TF32    x -> tf32(x)                                  1 product per term
 //   TF32X3  x = big + small, both tf32;  big*big + big*small + small*big
 //   BF16X3  x = hi + lo, both bf16;      hi*hi + hi*lo + lo*hi  (kind::f16)
 //
-// CTA = 256 threads: warps 0-3 gather the A and B tiles of each k-stage
-// through the offset tables into the 64-byte-swizzled K-major layout the MMA
-// reads (any axis permutation and blocking); one thread of warp 4 issues the
-// MMAs; warps 4-7 move the accumulators TMEM -> registers -> C.  Stages are
-// handed over with mbarriers.  Every wait is bounded: on timeout the kernel
-// records kDevErrTimeout in a device status word, stops, waits for its own
-// MMAs, frees its TMEM and returns (rosnet_sync reports ROSNET_ERR_TIMEOUT).
+// Two kernels per problem:
+//   1. tc_pack_kernel gathers each operand through its offset tables (any
+//      axis permutation and block layout, coalesced along the operand's
+//      unit-stride digit, transposed through shared memory) and writes the
+//      converted parts as K-major [rows][K] arrays padded to whole tiles.
+//   2. tc_gemm_kernel: one thread streams 128 x (64-byte) boxes of those
+//      arrays into a ring of shared-memory stages with TMA tensor copies
+//      (cp.async.bulk.tensor, 64-byte swizzle = the MMA's K-major layout);
+//      one thread issues the MMAs; eight warps own the output tile.  The
+//      contracted loop (every matched block pair of the tile, Sec. II-C steps
+//      2-4) is accumulated in chunks of 256 k in two alternating TMEM
+//      accumulators; the eight warps add each finished chunk into FP32
+//      registers while the tensor core fills the other one.  The tensor
+//      core's accumulator adds carry a small one-sided error that grows with
+//      the number of terms; chunking caps it at 256 terms.  The sum over
+//      pairs is order-free (Sec. IV-A); the order here is fixed.
+//
+// Every wait is bounded: on timeout the kernel records kDevErrTimeout in a
+// device status word, stops issuing work, waits (bounded) for its own copies
+// and MMAs, frees its TMEM and returns; rosnet_sync reports
+// ROSNET_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "gett_common.cuh"
 
@@ -32,24 +47,32 @@ __device__ int32_t g_dev_status = 0;
 namespace tc {
 
 constexpr int BM = 128, BN = 128;
-constexpr int ROWB = 64;                  // bytes of one K-row of a stage (64B swizzle)
-constexpr int NTHREADS = 256;
-constexpr int NPROD = 128;                // producer threads (warps 0-3)
+constexpr int ROWB = 64;                 // bytes of one K-row of a stage (64B swizzle span)
+constexpr int NTHREADS = 320;            // warp 0 TMA, warp 1 MMA, warps 2-9 accumulators
+constexpr int NACC_WARPS = 8;
+constexpr int CHUNK_K = 256;             // contracted indices per TMEM accumulation chunk
 constexpr long long kWaitBudget = 4000000000LL;   // cycles (~2 s at 2 GHz)
 
 enum Mode : int { kTF32 = 0, kTF32x3 = 1, kBF16x3 = 2 };
 
 template <int MODE>
 struct Cfg {
-    static constexpr int ESZ = MODE == kBF16x3 ? 2 : 4;       // bytes per staged element
-    static constexpr int BK = ROWB / ESZ;                     // k per stage (16 or 32)
-    static constexpr int NARR = MODE == kTF32 ? 2 : 4;        // arrays per operand
-    static constexpr int ARR_A = BM * ROWB, ARR_B = BN * ROWB;  // bytes of one array
+    static constexpr int ESZ = MODE == kBF16x3 ? 2 : 4;        // bytes per packed element
+    static constexpr int BK = ROWB / ESZ;                      // k per stage (16 or 32)
+    static constexpr int NARR = MODE == kTF32 ? 2 : 4;         // arrays per operand
+    static constexpr int ARR_A = BM * ROWB, ARR_B = BN * ROWB;   // bytes of one array's box
     static constexpr int STAGE = NARR * (ARR_A + ARR_B);
     static constexpr int STAGES = MODE == kTF32 ? 6 : 3;
-    static constexpr int KSTEP = 32 / ESZ;                    // k of one MMA (8 tf32 / 16 bf16)
-    static constexpr int KSTEPS = BK / KSTEP;                 // MMAs per product per stage (2)
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;  // + alignment slack
+    static constexpr int KSTEPS = BK / (32 / ESZ);             // MMAs per product per stage
+    static constexpr int CH_STAGES = CHUNK_K / BK;             // stages per chunk
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
+};
+
+struct TcArgs {
+    CUtensorMap mapA[4];   // packed A arrays (re[,re_lo], im[,im_lo]) as [Mpad][Kpad]
+    CUtensorMap mapB[4];
+    GroupArgs g;           // the problem (C pointer, C offset tables, M, N, K, tiles)
+    int32_t nkt;           // k-stages (Kpad / BK)
 };
 
 // ---------------------------------------------------------------------------
@@ -62,6 +85,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
     uint32_t ok;
@@ -91,14 +119,20 @@ __device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile in
     return true;
 }
 
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(su32(bar))
+        : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
@@ -145,8 +179,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *b) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
         "[%16];"
@@ -154,10 +187,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -165,252 +196,244 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-// Byte offset of element (row r, k) of one array (64-byte rows, 64B swizzle).
-__device__ __forceinline__ uint32_t swz(int r, int kbyte) {
-    const int c = kbyte >> 4;
-    return (uint32_t)(r * ROWB + ((c ^ ((r >> 1) & 3)) << 4) + (kbyte & 15));
-}
-
-// Stage one element x of an operand row into its arrays (re planes: arrays
-// 0[,1]; im planes: arrays 1 or 2[,3]).
+// ---------------------------------------------------------------------------
+// 1. pack: gather + convert one operand into K-major [Rpad][Kpad] part arrays
+// ---------------------------------------------------------------------------
+// which = 0: operand A of the problem (rows = M digits), 1: operand B (rows =
+// N digits).  32 x 32 (row, k) tiles, 256 threads, transposed through shared
+// memory so that both the gather and the row-major store coalesce.
 template <int MODE>
-__device__ __forceinline__ void put(unsigned char *arr0, int arr_bytes, int plane, int r, int k, float x) {
-    constexpr int ESZ = Cfg<MODE>::ESZ;
-    const uint32_t off = swz(r, k * ESZ);
-    if (MODE == kTF32) {
-        *reinterpret_cast<uint32_t *>(arr0 + plane * arr_bytes + off) = to_tf32(x);
-    } else if (MODE == kTF32x3) {
-        const uint32_t big = to_tf32(x);
-        const uint32_t small = to_tf32(x - __uint_as_float(big));
-        *reinterpret_cast<uint32_t *>(arr0 + (2 * plane) * arr_bytes + off) = big;
-        *reinterpret_cast<uint32_t *>(arr0 + (2 * plane + 1) * arr_bytes + off) = small;
-    } else {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-        *reinterpret_cast<__nv_bfloat16 *>(arr0 + (2 * plane) * arr_bytes + off) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(arr0 + (2 * plane + 1) * arr_bytes + off) = lo;
+__global__ void __launch_bounds__(256) tc_pack_kernel(const __grid_constant__ GroupArgs g, int which,
+                                                      unsigned char *__restrict__ out, int64_t Rpad,
+                                                      int64_t Kpad) {
+    using C_ = Cfg<MODE>;
+    __shared__ GettDesc sd;
+    __shared__ float tr[2][32][33];
+    if (threadIdx.x == 0) load_desc(g, sd);
+    __syncthreads();
+    const float *__restrict__ src = (const float *)(which ? sd.b : sd.a);
+    const int64_t plane = which ? sd.b_plane : sd.a_plane;
+    const int64_t *__restrict__ offR = which ? sd.offBN : sd.offAM;
+    const int64_t *__restrict__ offK = which ? sd.offBK : sd.offAK;
+    const int64_t R = which ? sd.N : sd.M, K = sd.K;
+    const bool row_fast = which ? (sd.flags & kFlagBNFast) : (sd.flags & kFlagAMFast);
+    const int64_t ktiles = Kpad / 32;
+    const int64_t r0 = ((int64_t)blockIdx.x / ktiles) * 32, k0 = ((int64_t)blockIdx.x % ktiles) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int a = tx, b = ty + 8 * j;
+        const int rr = row_fast ? a : b, kk = row_fast ? b : a;
+        const int64_t r = r0 + rr, k = k0 + kk;
+        float xr = 0.f, xi = 0.f;
+        if (r < R && k < K) {
+            const int64_t o = offR[r] + offK[k];
+            xr = src[o];
+            xi = src[o + plane];
+        }
+        tr[0][kk][rr] = xr;
+        tr[1][kk][rr] = xi;
+    }
+    __syncthreads();
+    const size_t arr = (size_t)Rpad * Kpad * C_::ESZ;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int rr = ty + 8 * j, kk = tx;
+        const size_t e = (size_t)(r0 + rr) * Kpad + (k0 + kk);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float x = tr[p][kk][rr];
+            if (MODE == kTF32) {
+                reinterpret_cast<uint32_t *>(out + p * arr)[e] = to_tf32(x);
+            } else if (MODE == kTF32x3) {
+                const uint32_t big = to_tf32(x);
+                reinterpret_cast<uint32_t *>(out + (2 * p) * arr)[e] = big;
+                reinterpret_cast<uint32_t *>(out + (2 * p + 1) * arr)[e] = to_tf32(x - __uint_as_float(big));
+            } else {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                reinterpret_cast<__nv_bfloat16 *>(out + (2 * p) * arr)[e] = hi;
+                reinterpret_cast<__nv_bfloat16 *>(out + (2 * p + 1) * arr)[e] =
+                    __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
+        }
     }
 }
 
+// ---------------------------------------------------------------------------
+// 2. TMA + tcgen05 GEMM with chunked TMEM accumulation
+// ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_gett_kernel(const __grid_constant__ GroupArgs g) {
+__global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ TcArgs p) {
     using C_ = Cfg<MODE>;
-    constexpr int BK = C_::BK, STAGES = C_::STAGES, NARR = C_::NARR;
+    constexpr int STAGES = C_::STAGES, NARR = C_::NARR, BK = C_::BK;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *dsm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ GettDesc sd;
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf[2], acce[2], fin_bar;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    __shared__ int64_t s_arow[BM], s_brow[BN];   // element offsets of the tile's rows (-1: outside)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        load_desc(g, sd);
+        load_desc(p.g, sd);
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full_bar[s], NPROD);
+            mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&done_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], NACC_WARPS);
+        }
+        mbar_init(&fin_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {   // the MMA warp owns the accumulators: 2 x 128 columns (Cr, Ci)
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+    if (warp == 1) {   // two accumulators of Cr|Ci (2 x 256 columns): all of TMEM
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                          su32(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    __syncthreads();   // descriptor visible
-    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
-    const int64_t m0 = (tile % sd.tiles_m) * BM, n0 = (tile / sd.tiles_m) * BN;
-    const int64_t M = sd.M, N = sd.N, K = sd.K;
-    const int nkt = (int)((K + BK - 1) / BK);
-    if (tid < BM) s_arow[tid] = (m0 + tid < M) ? sd.offAM[m0 + tid] : -1;
-    else if (tid < BM + BN) s_brow[tid - BM] = (n0 + tid - BM < N) ? sd.offBN[n0 + tid - BM] : -1;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
+    const int64_t m0 = (tile % sd.tiles_m) * BM, n0 = (tile / sd.tiles_m) * BN;
+    const int nkt = p.nkt;
+    const int nchunks = (nkt + C_::CH_STAGES - 1) / C_::CH_STAGES;
 
-    if (warp < 4) {
-        // ------------------------------------------------------------ producers
-        const bool amf = sd.flags & kFlagAMFast, bnf = sd.flags & kFlagBNFast;
-        const float *__restrict__ A = (const float *)sd.a;
-        const float *__restrict__ B = (const float *)sd.b;
-        const int64_t ap = sd.a_plane, bp = sd.b_plane;
-        const int pt = tid;   // 0..127
-        // a "fast" operand is read one row per thread over all k of the stage;
-        // otherwise one k per thread over BK rows spaced NPROD/BK apart
-        constexpr int RSTEP = NPROD / BK;
-        for (int kt = 0; kt < nkt; ++kt) {
-            const int s = kt % STAGES;
-            if (!mbar_wait(&empty_bar[s], ((kt / STAGES) & 1) ^ 1, &abort_flag)) break;
-            unsigned char *sa = dsm + (size_t)s * C_::STAGE;
-            unsigned char *sb = sa + NARR * C_::ARR_A;
-            const int64_t k0 = (int64_t)kt * BK;
-            // A tile
-            if (amf) {
-                const int r = pt;
-                const int64_t ro = s_arow[r];
-#pragma unroll 4
-                for (int kk = 0; kk < BK; ++kk) {
-                    const int64_t k = k0 + kk;
-                    float xr = 0.f, xi = 0.f;
-                    if (ro >= 0 && k < K) {
-                        const int64_t o = ro + __ldg(sd.offAK + k);
-                        xr = __ldg(A + o);
-                        xi = __ldg(A + o + ap);
-                    }
-                    put<MODE>(sa, C_::ARR_A, 0, r, kk, xr);
-                    put<MODE>(sa, C_::ARR_A, 1, r, kk, xi);
-                }
-            } else {
-                const int kk = pt % BK;
-                const int64_t k = k0 + kk;
-                const int64_t ko = k < K ? __ldg(sd.offAK + k) : 0;
-#pragma unroll 4
-                for (int j = 0; j < BK; ++j) {
-                    const int r = pt / BK + j * RSTEP;
-                    const int64_t ro = s_arow[r];
-                    float xr = 0.f, xi = 0.f;
-                    if (ro >= 0 && k < K) {
-                        const int64_t o = ro + ko;
-                        xr = __ldg(A + o);
-                        xi = __ldg(A + o + ap);
-                    }
-                    put<MODE>(sa, C_::ARR_A, 0, r, kk, xr);
-                    put<MODE>(sa, C_::ARR_A, 1, r, kk, xi);
-                }
-            }
-            // B tile
-            if (bnf) {
-                const int r = pt;
-                const int64_t ro = s_brow[r];
-#pragma unroll 4
-                for (int kk = 0; kk < BK; ++kk) {
-                    const int64_t k = k0 + kk;
-                    float xr = 0.f, xi = 0.f;
-                    if (ro >= 0 && k < K) {
-                        const int64_t o = ro + __ldg(sd.offBK + k);
-                        xr = __ldg(B + o);
-                        xi = __ldg(B + o + bp);
-                    }
-                    put<MODE>(sb, C_::ARR_B, 0, r, kk, xr);
-                    put<MODE>(sb, C_::ARR_B, 1, r, kk, xi);
-                }
-            } else {
-                const int kk = pt % BK;
-                const int64_t k = k0 + kk;
-                const int64_t ko = k < K ? __ldg(sd.offBK + k) : 0;
-#pragma unroll 4
-                for (int j = 0; j < BK; ++j) {
-                    const int r = pt / BK + j * RSTEP;
-                    const int64_t ro = s_brow[r];
-                    float xr = 0.f, xi = 0.f;
-                    if (ro >= 0 && k < K) {
-                        const int64_t o = ro + ko;
-                        xr = __ldg(B + o);
-                        xi = __ldg(B + o + bp);
-                    }
-                    put<MODE>(sb, C_::ARR_B, 0, r, kk, xr);
-                    put<MODE>(sb, C_::ARR_B, 1, r, kk, xi);
-                }
-            }
-            fence_proxy_async();   // generic-proxy stores -> visible to the MMA (async proxy)
-            mbar_arrive(&full_bar[s]);
-        }
-    } else if (warp == 4) {
-        // ------------------------------------------------------------ MMA issue
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
-            const uint32_t dr = tmem, di = tmem + BN;   // Cr: columns [0,128), Ci: [128,256)
+            int issued = 0;
             for (int kt = 0; kt < nkt; ++kt) {
                 const int s = kt % STAGES;
-                if (!mbar_wait(&full_bar[s], (kt / STAGES) & 1, &abort_flag)) break;
-                tc_fence_after();
+                if (!mbar_wait(&empty_bar[s], ((kt / STAGES) & 1) ^ 1, &abort_flag)) break;
+                mbar_expect_tx(&full_bar[s], C_::STAGE);
                 const uint32_t sa = su32(dsm + (size_t)s * C_::STAGE);
                 const uint32_t sb = sa + NARR * C_::ARR_A;
 #pragma unroll
-                for (int ks = 0; ks < C_::KSTEPS; ++ks) {
-                    const uint32_t kb = ks * 32;   // byte offset of this MMA's K slice
-                    auto A_ = [&](int arr) { return sdesc(sa + arr * C_::ARR_A + kb); };
-                    auto B_ = [&](int arr) { return sdesc(sb + arr * C_::ARR_B + kb); };
-                    const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
-                    if (MODE == kTF32) {
-                        // arrays: 0 = re, 1 = im
-                        mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), first);
-                        mma<MODE>(dr, A_(1), B_(1), idesc<MODE>(true), 1u);
-                        mma<MODE>(di, A_(0), B_(1), idesc<MODE>(false), first);
-                        mma<MODE>(di, A_(1), B_(0), idesc<MODE>(false), 1u);
-                    } else {
-                        // arrays: 0 = re big/hi, 1 = re small/lo, 2 = im big/hi, 3 = im small/lo
-                        // small terms first, then the big*big term
-                        mma<MODE>(dr, A_(0), B_(1), idesc<MODE>(false), first);
-                        mma<MODE>(dr, A_(1), B_(0), idesc<MODE>(false), 1u);
-                        mma<MODE>(dr, A_(2), B_(3), idesc<MODE>(true), 1u);
-                        mma<MODE>(dr, A_(3), B_(2), idesc<MODE>(true), 1u);
-                        mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), 1u);
-                        mma<MODE>(dr, A_(2), B_(2), idesc<MODE>(true), 1u);
-                        mma<MODE>(di, A_(0), B_(3), idesc<MODE>(false), first);
-                        mma<MODE>(di, A_(1), B_(2), idesc<MODE>(false), 1u);
-                        mma<MODE>(di, A_(2), B_(1), idesc<MODE>(false), 1u);
-                        mma<MODE>(di, A_(3), B_(0), idesc<MODE>(false), 1u);
-                        mma<MODE>(di, A_(0), B_(2), idesc<MODE>(false), 1u);
-                        mma<MODE>(di, A_(2), B_(0), idesc<MODE>(false), 1u);
-                    }
+                for (int a = 0; a < NARR; ++a) {
+                    tma_load_2d(sa + a * C_::ARR_A, &p.mapA[a], kt * BK, (int)m0, &full_bar[s]);
+                    tma_load_2d(sb + a * C_::ARR_B, &p.mapB[a], kt * BK, (int)n0, &full_bar[s]);
                 }
-                mma_commit(&empty_bar[s]);   // frees the stage when these MMAs are done
+                issued = kt + 1;
             }
-            mma_commit(&done_bar);           // all MMAs issued by this thread are complete
+            // copies still in flight must land before this CTA can exit
+            for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+                mbar_wait(&full_bar[kt % STAGES], (kt / STAGES) & 1, &abort_flag, false);
         }
-        __syncwarp();
-    }
-
-    if (warp >= 4) {
-        // ------------------------------------------------------------ epilogue
-        // wait for every MMA even after an abort: TMEM must not be freed under them
-        bool ok = mbar_wait(&done_bar, 0, &abort_flag, false);
-        ok = __all_sync(0xffffffffu, ok) && !abort_flag;
-        tc_fence_after();
-        const int q = warp & 3;                 // TMEM lane quarter of this warp
-        const int r = q * 32 + lane;            // output row of this thread
-        const bool rok = ok && (m0 + r < M) && nkt > 0;
-        const int64_t cm = (m0 + r < M) ? sd.offCM[m0 + r] : 0;   // C offset of row r
-        float *__restrict__ C = (float *)sd.c;
-        const int64_t cp = sd.c_plane;
-        if (ok) {
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float vr[16], vi[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c0, vr);
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + BN + c0, vi);
-                if (rok) {
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            int kt = 0;
+            bool go = true;
+            for (int c = 0; c < nchunks && go; ++c) {
+                const int b = c & 1;
+                if (c >= 2 && !mbar_wait(&acce[b], ((c >> 1) - 1) & 1, &abort_flag)) break;
+                tc_fence_after();
+                const uint32_t dr = tmem + b * 2 * BN, di = dr + BN;
+                const int kend = min(nkt, (c + 1) * C_::CH_STAGES);
+                for (; kt < kend; ++kt) {
+                    const int s = kt % STAGES;
+                    if (!mbar_wait(&full_bar[s], (kt / STAGES) & 1, &abort_flag)) {
+                        go = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = su32(dsm + (size_t)s * C_::STAGE);
+                    const uint32_t sb = sa + NARR * C_::ARR_A;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t n = n0 + c0 + j;
-                        if (n < N) {
-                            const int64_t o = cm + __ldg(sd.offCN + n);
-                            C[o] = vr[j];
-                            C[o + cp] = vi[j];
+                    for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                        const uint32_t kb = ks * 32;   // byte offset of this MMA's K slice
+                        auto A_ = [&](int arr) { return sdesc(sa + arr * C_::ARR_A + kb); };
+                        auto B_ = [&](int arr) { return sdesc(sb + arr * C_::ARR_B + kb); };
+                        const uint32_t acc = (kt == c * C_::CH_STAGES && ks == 0) ? 0u : 1u;
+                        if (MODE == kTF32) {
+                            // arrays: 0 = re, 1 = im
+                            mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), acc);
+                            mma<MODE>(dr, A_(1), B_(1), idesc<MODE>(true), 1u);
+                            mma<MODE>(di, A_(0), B_(1), idesc<MODE>(false), acc);
+                            mma<MODE>(di, A_(1), B_(0), idesc<MODE>(false), 1u);
+                        } else {
+                            // arrays: 0 = re big/hi, 1 = re small/lo, 2 = im big/hi, 3 = im small/lo
+                            mma<MODE>(dr, A_(0), B_(1), idesc<MODE>(false), acc);
+                            mma<MODE>(dr, A_(1), B_(0), idesc<MODE>(false), 1u);
+                            mma<MODE>(dr, A_(2), B_(3), idesc<MODE>(true), 1u);
+                            mma<MODE>(dr, A_(3), B_(2), idesc<MODE>(true), 1u);
+                            mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), 1u);
+                            mma<MODE>(dr, A_(2), B_(2), idesc<MODE>(true), 1u);
+                            mma<MODE>(di, A_(0), B_(3), idesc<MODE>(false), acc);
+                            mma<MODE>(di, A_(1), B_(2), idesc<MODE>(false), 1u);
+                            mma<MODE>(di, A_(2), B_(1), idesc<MODE>(false), 1u);
+                            mma<MODE>(di, A_(3), B_(0), idesc<MODE>(false), 1u);
+                            mma<MODE>(di, A_(0), B_(2), idesc<MODE>(false), 1u);
+                            mma<MODE>(di, A_(2), B_(0), idesc<MODE>(false), 1u);
                         }
                     }
+                    mma_commit(&empty_bar[s]);   // frees the stage once these MMAs are done
+                }
+                if (go) mma_commit(&accf[b]);    // chunk c is complete in accumulator b
+            }
+            mma_commit(&fin_bar);                // every MMA of this thread has completed
+            mbar_wait(&fin_bar, 0, &abort_flag, false);
+        }
+    } else {
+        // ---------------------------------------------------------- accumulators
+        const int e = warp - 2;                 // 0..7
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int h = e >> 2;                   // column half of the tile
+        const int r = q * 32 + lane;            // output row of this thread
+        float sr[64], si[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) sr[j] = si[j] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            ok = mbar_wait(&accf[b], (c >> 1) & 1, &abort_flag);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 2 * BN + h * 64;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t vr[16], vi[16];
+                tmem_ld16(base + j * 16, vr);
+                tmem_ld16(base + BN + j * 16, vi);
+                tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    sr[j * 16 + t] += __uint_as_float(vr[t]);
+                    si[j * 16 + t] += __uint_as_float(vi[t]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);   // accumulator b may be overwritten
+        }
+        const int64_t M = sd.M, N = sd.N;
+        if (ok && !abort_flag && m0 + r < M) {
+            float *__restrict__ C = (float *)sd.c;
+            const int64_t cp = sd.c_plane;
+            const int64_t cm = sd.offCM[m0 + r];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int64_t n = n0 + h * 64 + j;
+                if (n < N) {
+                    const int64_t o = cm + __ldg(sd.offCN + n);
+                    C[o] = sr[j];
+                    C[o + cp] = si[j];
                 }
             }
         }
-        // no contracted index at all: the result is zero
-        if (ok && nkt == 0 && m0 + r < M)
-            for (int64_t n = n0; n < n0 + BN && n < N; ++n) {
-                const int64_t o = cm + sd.offCN[n];
-                C[o] = 0.f;
-                C[o + cp] = 0.f;
-            }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -428,33 +451,110 @@ bool tc_mode_of(int precision, int *mode) {
     }
 }
 
+int tc_tile_m() { return tc::BM; }
+int tc_tile_n() { return tc::BN; }
+
+namespace {
+
+struct TcGeom {
+    int esz, bk, narr;
+    int64_t Mpad, Npad, Kpad;
+    size_t arrA, arrB;   // bytes of one packed array
+};
+
+TcGeom tc_geom(const GettDesc &d, int mode) {
+    TcGeom g;
+    g.esz = mode == tc::kBF16x3 ? 2 : 4;
+    g.bk = tc::ROWB / g.esz;
+    g.narr = mode == tc::kTF32 ? 2 : 4;
+    g.Mpad = (d.M + tc::BM - 1) / tc::BM * tc::BM;
+    g.Npad = (d.N + tc::BN - 1) / tc::BN * tc::BN;
+    const int64_t kq = 32;   // the pack kernel's k tile; a multiple of bk
+    g.Kpad = (d.K + kq - 1) / kq * kq;
+    g.arrA = (size_t)g.Mpad * g.Kpad * g.esz;
+    g.arrB = (size_t)g.Npad * g.Kpad * g.esz;
+    return g;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (err == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    if (!fn) RN_FAIL(ROSNET_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    return fn;
+}
+
+// 2-D map over one packed [rows][Kpad] array, boxes of (64 bytes of k) x 128 rows.
+void make_map(CUtensorMap *m, void *base, int64_t rows, int64_t Kpad, int esz) {
+    cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(Kpad * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)(tc::ROWB / esz), 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(m, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                             2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) RN_FAIL(ROSNET_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
 template <int MODE>
-static void launch_tc_mode(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
+void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, cudaStream_t s) {
     using C_ = tc::Cfg<MODE>;
     static bool attr_set = false;
     if (!attr_set) {
-        RN_CHECK_CUDA(cudaFuncSetAttribute(tc::tc_gett_kernel<MODE>,
+        RN_CHECK_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<MODE>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM));
         attr_set = true;
     }
-    tc::tc_gett_kernel<MODE><<<grid, tc::NTHREADS, C_::SMEM, s>>>(ga);
-}
-
-void launch_tc_group(int mode, const GroupArgs &ga, int64_t ctas, cudaStream_t s) {
-    if (ctas <= 0) return;
-    if (ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "too many tiles in one launch");
-    dim3 grid((unsigned)ctas);
-    switch (mode) {
-        case tc::kTF32: launch_tc_mode<tc::kTF32>(grid, ga, s); break;
-        case tc::kTF32x3: launch_tc_mode<tc::kTF32x3>(grid, ga, s); break;
-        default: launch_tc_mode<tc::kBF16x3>(grid, ga, s); break;
+    unsigned char *pa = (unsigned char *)ws;
+    unsigned char *pb = pa + g.narr * g.arrA;
+    const int64_t ca = (g.Mpad / 32) * (g.Kpad / 32), cb = (g.Npad / 32) * (g.Kpad / 32);
+    if (ca > 0x7fffffffLL || cb > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "operand too large to pack");
+    tc::tc_pack_kernel<MODE><<<(unsigned)ca, 256, 0, s>>>(ga, 0, pa, g.Mpad, g.Kpad);
+    tc::tc_pack_kernel<MODE><<<(unsigned)cb, 256, 0, s>>>(ga, 1, pb, g.Npad, g.Kpad);
+    tc::TcArgs args;
+    memset(&args, 0, sizeof(args));
+    for (int a = 0; a < g.narr; ++a) {
+        make_map(&args.mapA[a], pa + a * g.arrA, g.Mpad, g.Kpad, g.esz);
+        make_map(&args.mapB[a], pb + a * g.arrB, g.Npad, g.Kpad, g.esz);
     }
-    g_launches++;
+    args.g = ga;
+    args.nkt = (int)(g.Kpad / g.bk);
+    tc::tc_gemm_kernel<MODE><<<(unsigned)ctas, tc::NTHREADS, C_::SMEM, s>>>(args);
+    g_launches += 3;
     RN_CHECK_CUDA(cudaGetLastError());
 }
 
-int tc_tile_m() { return tc::BM; }
-int tc_tile_n() { return tc::BN; }
+}  // namespace
+
+// Workspace bytes of the packed operands of a tensor-core problem.
+size_t tc_workspace_bytes(const GettDesc &d, int mode) {
+    TcGeom g = tc_geom(d, mode);
+    return g.narr * (g.arrA + g.arrB);
+}
+
+// Enqueue pack + GEMM for one tensor-core problem.  `ga` locates the
+// problem's descriptor (by value or in device memory); ws holds
+// tc_workspace_bytes(d, mode) bytes, 256-byte aligned.
+void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s) {
+    const TcGeom g = tc_geom(d, mode);
+    const int64_t ctas = d.tiles_m * d.tiles_n;
+    if (ctas <= 0) return;
+    if (ctas > 0x7fffffffLL || g.Kpad / g.bk > 0x7fffffffLL || g.Mpad > 0x7fffffffLL || g.Npad > 0x7fffffffLL)
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one tensor-core launch");
+    switch (mode) {
+        case tc::kTF32: launch_mode<tc::kTF32>(ga, g, ws, ctas, s); break;
+        case tc::kTF32x3: launch_mode<tc::kTF32x3>(ga, g, ws, ctas, s); break;
+        default: launch_mode<tc::kBF16x3>(ga, g, ws, ctas, s); break;
+    }
+}
 
 // Read and clear the device status word (0 = no kernel gave up a wait).
 int32_t take_device_status() {
