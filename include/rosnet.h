@@ -151,6 +151,36 @@ rosnet_status rosnet_btensor_destroy(rosnet_btensor t);
  */
 rosnet_status rosnet_btensor_upload(rosnet_btensor t, const void *host, void *stream);
 
+/*
+ * Copy `count` complex values, the dense row-major entries [start, start +
+ * count) of the tensor, from a host buffer into the tensor (e.g. to fill a
+ * tensor larger than host memory in pieces).  Same rules as
+ * rosnet_btensor_upload; INVALID_ARG if the range is outside the tensor.
+ */
+rosnet_status rosnet_btensor_upload_range(rosnet_btensor t, const void *host, int64_t start,
+                                          int64_t count, void *stream);
+
+/*
+ * A view of t with its first nfix axes fixed to values[0..nfix): the
+ * projection of those indices onto one basis state each (Sec. II-B, slicing,
+ * which the paper reads as a block division).  Each fixed axis must be a grid
+ * axis (block extent 1), so the view is a contiguous run of t's blocks and
+ * shares t's storage: no copy is made.  The view has rank - nfix axes with
+ * t's remaining extents and block extents; it must be destroyed before t, and
+ * writes through it (upload) change t.  Errors: INVALID_ARG (index out of
+ * range), BLOCK_MISMATCH (a fixed axis with block extent > 1).
+ */
+rosnet_status rosnet_btensor_slice(rosnet_btensor t, int nfix, const int64_t *values,
+                                   rosnet_btensor *view);
+
+/*
+ * A view of one block of t (grid_coords[i] in [0, shape[i] / block_shape[i])):
+ * a tensor whose shape is t's block shape, sharing t's storage (a block is
+ * contiguous in the block-major layout, so this is the unit to move between
+ * device and host).  Destroy it before t.  Errors: INVALID_ARG.
+ */
+rosnet_status rosnet_btensor_block(rosnet_btensor t, const int64_t *grid_coords, rosnet_btensor *view);
+
 /* Copy the tensor into a dense row-major interleaved host array.  Blocks
  * until the data is on the host (synchronises `stream`). */
 rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream);
@@ -213,6 +243,28 @@ rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes,
 rosnet_status rosnet_tensordot_noalloc(rosnet_btensor A, rosnet_btensor B, int naxes,
                                        const int *axes_a, const int *axes_b, rosnet_btensor C,
                                        const rosnet_opts *opts, void *stream);
+
+/*
+ * Out-of-core tensordot (the paper's out-of-core premise, Sec. I and III: data
+ * larger than memory lives on the next storage tier and only task-sized pieces
+ * are resident).  C = tensordot(A, B, axes) is computed in output chunks along
+ * A's first `nsplit` axes, which must be free grid axes (block extent 1):
+ * chunk c fixes them to the row-major digits of c (c in [0, prod of their
+ * extents)), i.e. it is tensordot(slice of A, B), a contiguous run of C's
+ * blocks.  Chunks first_chunk .. first_chunk + nchunks - 1 are computed into
+ * two alternating device buffers and each is copied, on a side stream while
+ * the next one is computed, to host_out: slot (c - first_chunk) % nslots with
+ * nslots = host_bytes / chunk_bytes, chunk_bytes = 2 * chunk entries *
+ * element size, in the raw block-major planar layout (real plane, then
+ * imaginary plane).  host_out should be pinned for the copies to overlap.
+ * Returns when every copy has completed.  Errors as rosnet_tensordot, plus
+ * INVALID_ARG (bad chunk range, host buffer smaller than one chunk) and
+ * BLOCK_MISMATCH (a split axis with block extent > 1).
+ */
+rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B, int naxes,
+                                   const int *axes_a, const int *axes_b, int nsplit,
+                                   int64_t first_chunk, int64_t nchunks, const rosnet_opts *opts,
+                                   void *host_out, size_t host_bytes, void *stream);
 
 /* ----------------------------------------------------------------------- */
 /* networks (Sec. II-A)                                                     */

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
-    "path_greedy_extents", "contract", "tensordot_noalloc",
+    "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc",
     "sync", "kernel_launches", "release_plans", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
     "PREC_TF32X3",
@@ -53,7 +53,8 @@ EXPORTS = [
     "rosnet_btensor_planes", "rosnet_tensordot", "rosnet_path_greedy", "rosnet_contract",
     "rosnet_release_plans", "rosnet_sync", "rosnet_status_string", "rosnet_last_error",
     "rosnet_kernel_launches", "rosnet_path_greedy_extents", "rosnet_timing_drain",
-    "rosnet_tensordot_noalloc",
+    "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range", "rosnet_btensor_slice",
+    "rosnet_btensor_block", "rosnet_tensordot_ooc",
 ]
 
 _lock = threading.Lock()
@@ -107,6 +108,13 @@ def lib():
             L.rosnet_btensor_destroy.argtypes = [vp]
             L.rosnet_btensor_upload.argtypes = [vp, vp, vp]
             L.rosnet_btensor_download.argtypes = [vp, vp, vp]
+            L.rosnet_btensor_upload_range.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
+            L.rosnet_btensor_slice.argtypes = [vp, ctypes.c_int, i64p, ctypes.POINTER(vp)]
+            L.rosnet_btensor_block.argtypes = [vp, i64p, ctypes.POINTER(vp)]
+            L.rosnet_tensordot_ooc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                               ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Opts),
+                                               vp, ctypes.c_size_t, vp]
             L.rosnet_btensor_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i64p, i64p,
                                               ctypes.POINTER(ctypes.c_int)]
             L.rosnet_btensor_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -140,7 +148,8 @@ def lib():
                         "rosnet_btensor_planes", "rosnet_tensordot", "rosnet_path_greedy",
                         "rosnet_contract", "rosnet_release_plans", "rosnet_sync",
                         "rosnet_path_greedy_extents", "rosnet_timing_drain",
-                        "rosnet_tensordot_noalloc"):
+                        "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range",
+                        "rosnet_btensor_slice", "rosnet_btensor_block", "rosnet_tensordot_ooc"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -239,10 +248,11 @@ def _np_dtype(dt):
 class BTensor:
     """Owning handle of a device block tensor."""
 
-    __slots__ = ("_h", "shape", "block_shape", "dtype", "__weakref__")
+    __slots__ = ("_h", "shape", "block_shape", "dtype", "_parent", "__weakref__")
 
     def __init__(self, handle):
         self._h = ctypes.c_void_p(handle)
+        self._parent = None
         L = lib()
         r = ctypes.c_int()
         sh = (ctypes.c_int64 * 64)()
@@ -282,6 +292,31 @@ class BTensor:
             ptr = keep.ctypes.data
         _check(lib().rosnet_btensor_upload(self._h, ctypes.c_void_p(ptr), _stream(stream)), "upload")
         return keep
+
+    def upload_range(self, array, start, stream=None):
+        """Copy host values into the dense row-major entries [start, start + len)."""
+        keep = np.ascontiguousarray(np.asarray(array, dtype=_np_dtype(self.dtype)).reshape(-1))
+        _check(lib().rosnet_btensor_upload_range(self._h, ctypes.c_void_p(keep.ctypes.data), int(start),
+                                                 keep.size, _stream(stream)), "upload_range")
+        return keep
+
+    def slice(self, values):
+        """View with the leading len(values) (grid) axes fixed; shares storage."""
+        h = ctypes.c_void_p()
+        _check(lib().rosnet_btensor_slice(self._h, len(values), _i64arr(values), ctypes.byref(h)),
+               "rosnet_btensor_slice")
+        v = BTensor(h.value)
+        v._parent = self
+        return v
+
+    def block(self, grid_coords):
+        """View of one block (grid coordinates per axis); shares storage."""
+        h = ctypes.c_void_p()
+        _check(lib().rosnet_btensor_block(self._h, _i64arr(grid_coords), ctypes.byref(h)),
+               "rosnet_btensor_block")
+        v = BTensor(h.value)
+        v._parent = self
+        return v
 
     def download(self, out=None, stream=None):
         """Dense row-major host copy (numpy); synchronises the stream."""
@@ -360,6 +395,24 @@ def tensordot_noalloc(A, B, axes_a, axes_b, C, precision=PREC_DEFAULT, stream=No
                                           _i32arr(axes_b), C.handle, ctypes.byref(o),
                                           _stream(stream)), "rosnet_tensordot_noalloc")
     return C
+
+
+def tensordot_ooc(A, B, axes_a, axes_b, nsplit, first_chunk, nchunks, host_out,
+                  precision=PREC_DEFAULT, stream=None):
+    """Out-of-core tensordot: output chunks along A's first nsplit (grid) axes
+    streamed into the pinned host buffer ``host_out`` (a torch CPU tensor or a
+    numpy array; chunk c goes to slot (c - first_chunk) % slots, raw
+    block-major planar).  Returns when the copies are complete."""
+    _init()
+    o = _opts(precision)
+    if hasattr(host_out, "data_ptr"):
+        ptr, nbytes = host_out.data_ptr(), host_out.numel() * host_out.element_size()
+    else:
+        ptr, nbytes = host_out.ctypes.data, host_out.nbytes
+    _check(lib().rosnet_tensordot_ooc(A.handle, B.handle, len(axes_a), _i32arr(axes_a),
+                                      _i32arr(axes_b), int(nsplit), int(first_chunk), int(nchunks),
+                                      ctypes.byref(o), ctypes.c_void_p(ptr), int(nbytes),
+                                      _stream(stream)), "rosnet_tensordot_ooc")
 
 
 class Network:

@@ -36,7 +36,8 @@ int check_precision(const rosnet_opts *opts, int dtype);
 int64_t reduce_ctas(const GettDesc &d);
 bool is_tc_kind(int kind);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
-void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s);
+void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
+                       bool pack_a, bool pack_b);
 
 namespace {
 
@@ -439,9 +440,13 @@ void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream
         const int st = P.desc_step[i];
         const Step &S = P.steps[st];
         GettDesc d = P.slot_desc[i];
-        const Layout &la = S.ia < nt ? net->tensors[S.ia]->lay : P.steps[S.ia - nt].lay;
-        const Layout &lb = S.ib < nt ? net->tensors[S.ib]->lay : P.steps[S.ib - nt].lay;
-        bind_operands(d, ptr_of(S.ia), ptr_of(S.ib), ptr_of(nt + st), la.numel, lb.numel, S.lay.numel);
+        auto pstride_of = [&](int id) -> int64_t {
+            if (id < nt) return net->tensors[id]->pstride;
+            const Step &T = P.steps[id - nt];
+            return T.arena_off == SIZE_MAX ? out->pstride : T.lay.numel;
+        };
+        bind_operands(d, ptr_of(S.ia), ptr_of(S.ib), ptr_of(nt + st), pstride_of(S.ia), pstride_of(S.ib),
+                      pstride_of(nt + st));
         h[i] = d;
         if (!P.mirror_valid || P.mirror[i].a != d.a || P.mirror[i].b != d.b || P.mirror[i].c != d.c) {
             lo = std::min(lo, i);
@@ -481,7 +486,7 @@ void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream
                 ga.descs = dd + L.first;
                 ga.ndesc = 1;
                 launch_tc_problem(L.kind - kKindTcTF32, P.slot_desc[L.first], ga,
-                                  (char *)P.tcws.p + L.tc_ws_off, s);
+                                  (char *)P.tcws.p + L.tc_ws_off, s, true, true);
             } else {
                 launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
             }
@@ -541,7 +546,9 @@ void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream
     if (!P.final_direct) {
         const int last = P.steps.empty() ? 0 : nt + (int)P.steps.size() - 1;
         const Layout &src = P.steps.empty() ? net->tensors[0]->lay : P.steps.back().lay;
-        launch_relayout(src, out->lay, P.final_perm.data(), P.dtype, ptr_of(last), out->data, s);
+        const int64_t sps = P.steps.empty() ? net->tensors[0]->pstride : src.numel;
+        launch_relayout(src, out->lay, P.final_perm.data(), P.dtype, ptr_of(last), sps, out->data,
+                        out->pstride, s);
     }
 }
 

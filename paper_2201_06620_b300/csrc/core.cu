@@ -143,13 +143,15 @@ static void axis_modes(CopyModes &cm, int64_t s, int64_t b1, int64_t g1, int64_t
 }
 
 template <typename T, int MODE>  // MODE 0: interleaved->planar, 1: planar->interleaved, 2: planar->planar
-__global__ void __launch_bounds__(256) copy_modes_kernel(CopyModes cm, int64_t total,
+__global__ void __launch_bounds__(256) copy_modes_kernel(CopyModes cm, int64_t total, int64_t first,
                                                          const T *__restrict__ src, int64_t src_plane,
                                                          T *__restrict__ dst, int64_t dst_plane) {
+    // elements [first, first + total) of the enumeration; the source of MODE 0
+    // holds only that range (it starts at element `first`)
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (; e < total; e += stride) {
-        int64_t r = e, so = 0, dof = 0;
+        int64_t r = e + first, so = 0, dof = 0;
         if (cm.pow2) {
             for (int j = cm.n - 1; j >= 0; --j) {
                 int64_t x = cm.ext[j];
@@ -168,8 +170,8 @@ __global__ void __launch_bounds__(256) copy_modes_kernel(CopyModes cm, int64_t t
         }
         T re, im;
         if (MODE == 0) {
-            re = src[2 * so];
-            im = src[2 * so + 1];
+            re = src[2 * (so - first)];
+            im = src[2 * (so - first) + 1];
         } else {
             re = src[so];
             im = src[so + src_plane];
@@ -192,14 +194,15 @@ static int copy_grid(int64_t total) {
 
 template <int MODE>
 static void launch_copy(const CopyModes &cm, int64_t total, int dtype, const void *src,
-                        int64_t src_plane, void *dst, int64_t dst_plane, cudaStream_t s) {
+                        int64_t src_plane, void *dst, int64_t dst_plane, cudaStream_t s,
+                        int64_t first = 0) {
     if (total == 0) return;
     if (dtype == ROSNET_C64)
         copy_modes_kernel<float, MODE><<<copy_grid(total), 256, 0, s>>>(
-            cm, total, (const float *)src, src_plane, (float *)dst, dst_plane);
+            cm, total, first, (const float *)src, src_plane, (float *)dst, dst_plane);
     else
         copy_modes_kernel<double, MODE><<<copy_grid(total), 256, 0, s>>>(
-            cm, total, (const double *)src, src_plane, (double *)dst, dst_plane);
+            cm, total, first, (const double *)src, src_plane, (double *)dst, dst_plane);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
 }
@@ -223,13 +226,15 @@ static CopyModes dense_block_modes(const Layout &lay) {
     return cm;
 }
 
-void launch_pack(const Layout &lay, int dtype, const void *dense, void *planar, cudaStream_t s) {
-    if (lay.numel == 0) return;
+void launch_pack(const Layout &lay, int dtype, const void *dense, void *planar, int64_t pstride,
+                 int64_t start, int64_t count, cudaStream_t s) {
+    if (lay.numel == 0 || count == 0) return;
     CopyModes cm = dense_block_modes(lay);
-    launch_copy<0>(cm, lay.numel, dtype, dense, 0, planar, lay.numel, s);
+    launch_copy<0>(cm, count, dtype, dense, 0, planar, pstride, s, start);
 }
 
-void launch_unpack(const Layout &lay, int dtype, const void *planar, void *dense, cudaStream_t s) {
+void launch_unpack(const Layout &lay, int dtype, const void *planar, int64_t pstride, void *dense,
+                   cudaStream_t s) {
     if (lay.numel == 0) return;
     CopyModes cm = dense_block_modes(lay);
     // enumerate in dense order: ss = block-major (source), ds = dense (dest)
@@ -238,11 +243,11 @@ void launch_unpack(const Layout &lay, int dtype, const void *planar, void *dense
         cm.ss[j] = cm.ds[j];
         cm.ds[j] = t;
     }
-    launch_copy<1>(cm, lay.numel, dtype, planar, lay.numel, dense, 0, s);
+    launch_copy<1>(cm, lay.numel, dtype, planar, pstride, dense, 0, s);
 }
 
 void launch_relayout(const Layout &src, const Layout &dst, const int *perm, int dtype,
-                     const void *sp, void *dp, cudaStream_t s) {
+                     const void *sp, int64_t spstride, void *dp, int64_t dpstride, cudaStream_t s) {
     if (dst.numel == 0) return;
     // enumerate in destination axis order
     CopyModes cm{};
@@ -253,7 +258,7 @@ void launch_relayout(const Layout &src, const Layout &dst, const int *perm, int 
                    dst.gstride[i], dst.lstride[i]);
     }
     finish_modes(cm);
-    launch_copy<2>(cm, dst.numel, dtype, sp, src.numel, dp, dst.numel, s);
+    launch_copy<2>(cm, dst.numel, dtype, sp, spstride, dp, dpstride, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -269,6 +274,7 @@ rosnet_btensor new_tensor(int rank, const int64_t *shape, const int64_t *block, 
         t->elsize = dtype == ROSNET_C64 ? 4 : 8;
         t->stream = s;
         t->data = dev_alloc(2 * t->lay.numel * t->elsize, s);
+        t->pstride = t->lay.numel;
     } catch (...) {
         delete t;
         throw;
@@ -325,8 +331,86 @@ rosnet_status rosnet_btensor_upload(rosnet_btensor t, const void *host, void *st
     if (bytes == 0) return ROSNET_OK;
     DevBuf stage(bytes, s);
     RN_CHECK_CUDA(cudaMemcpyAsync(stage.p, host, bytes, cudaMemcpyHostToDevice, s));
-    launch_pack(t->lay, t->dtype, stage.p, t->data, s);
-    t->stream = s;
+    launch_pack(t->lay, t->dtype, stage.p, t->data, t->pstride, 0, t->lay.numel, s);
+    if (t->owned) t->stream = s;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_upload_range(rosnet_btensor t, const void *host, int64_t start,
+                                          int64_t count, void *stream) {
+    if (!t || start < 0 || count < 0 || start > t->lay.numel || count > t->lay.numel - start ||
+        (!host && count > 0))
+        return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = 2 * (size_t)count * t->elsize;
+    if (bytes == 0) return ROSNET_OK;
+    DevBuf stage(bytes, s);
+    RN_CHECK_CUDA(cudaMemcpyAsync(stage.p, host, bytes, cudaMemcpyHostToDevice, s));
+    launch_pack(t->lay, t->dtype, stage.p, t->data, t->pstride, start, count, s);
+    if (t->owned) t->stream = s;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_block(rosnet_btensor t, const int64_t *grid_coords, rosnet_btensor *view) {
+    if (!view) return ROSNET_ERR_INVALID_ARG;
+    *view = nullptr;
+    if (!t || (t->lay.rank > 0 && !grid_coords)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    int64_t off = 0;
+    for (int i = 0; i < t->lay.rank; ++i) {
+        const int64_t g = t->lay.shape[i] / t->lay.block[i];
+        if (grid_coords[i] < 0 || grid_coords[i] >= g) RN_FAIL(ROSNET_ERR_INVALID_ARG, "block coordinate out of range");
+        off += grid_coords[i] * t->lay.gstride[i];
+    }
+    rosnet_btensor v = new rosnet_btensor_s();
+    try {
+        v->lay.init(t->lay.rank, t->lay.block, t->lay.block);
+    } catch (...) {
+        delete v;
+        throw;
+    }
+    v->dtype = t->dtype;
+    v->elsize = t->elsize;
+    v->data = (char *)t->data + off * t->elsize;
+    v->pstride = t->pstride;
+    v->stream = t->stream;
+    v->owned = false;
+    *view = v;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_slice(rosnet_btensor t, int nfix, const int64_t *values,
+                                   rosnet_btensor *view) {
+    if (!view) return ROSNET_ERR_INVALID_ARG;
+    *view = nullptr;
+    if (!t || nfix < 0 || nfix > t->lay.rank || (nfix > 0 && !values)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    int64_t off = 0;
+    for (int i = 0; i < nfix; ++i) {
+        if (values[i] < 0 || values[i] >= t->lay.shape[i])
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "slice index out of range");
+        if (t->lay.block[i] != 1)
+            RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "a sliced axis must have block extent 1 (a grid axis)");
+        off += values[i] * t->lay.gstride[i];
+    }
+    rosnet_btensor v = new rosnet_btensor_s();
+    try {
+        v->lay.init(t->lay.rank - nfix, t->lay.shape + nfix, t->lay.block + nfix);
+    } catch (...) {
+        delete v;
+        throw;
+    }
+    v->dtype = t->dtype;
+    v->elsize = t->elsize;
+    v->data = (char *)t->data + off * t->elsize;
+    v->pstride = t->pstride;
+    v->stream = t->stream;
+    v->owned = false;
+    *view = v;
     return ROSNET_OK;
     RN_API_END
 }
@@ -339,7 +423,7 @@ rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream
     if (bytes == 0) return ROSNET_OK;
     {
         DevBuf stage(bytes, s);
-        launch_unpack(t->lay, t->dtype, t->data, stage.p, s);
+        launch_unpack(t->lay, t->dtype, t->data, t->pstride, stage.p, s);
         RN_CHECK_CUDA(cudaMemcpyAsync(host, stage.p, bytes, cudaMemcpyDeviceToHost, s));
     }
     RN_CHECK_CUDA(cudaStreamSynchronize(s));

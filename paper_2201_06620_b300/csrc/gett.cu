@@ -539,7 +539,8 @@ bool tc_mode_of(int precision, int *mode);
 int tc_tile_m();
 int tc_tile_n();
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
-void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s);
+void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
+                       bool pack_a, bool pack_b);
 
 void choose_kernel(GettDesc &d, int dtype, int precision) {
     d.ksplit = 1;
@@ -657,31 +658,57 @@ int64_t reduce_ctas(const GettDesc &d) { return (d.M * d.N + 255) / 256; }
 // ---------------------------------------------------------------------------
 // one pairwise contraction
 // ---------------------------------------------------------------------------
+// A contraction planned once for fixed layouts (offset tables on the device,
+// kernel choice, split-K and tensor-core workspaces) and run for any operand
+// pointers with those layouts.
+struct Prepared {
+    GettDesc d;
+    DevBuf tab, part, tcws;
+    bool empty = false;
+    int dtype = 0;
+    Prepared(const Layout &A, const Layout &B, const Layout &C, int naxes, const int *axa,
+             const int *axb, int dt, int precision, cudaStream_t s) {
+        dtype = dt;
+        memset(&d, 0, sizeof(d));
+        GettView v = make_view(A, B, C, naxes, axa, axb);
+        if (v.Mtot * v.Ntot == 0) {
+            empty = true;
+            return;
+        }
+        tab = DevBuf(table_entries(v) * sizeof(int64_t), s);
+        launch_build_tables(v, (int64_t *)tab.p, s);
+        fill_desc_tables(d, v, (const int64_t *)tab.p);
+        choose_kernel(d, dt, precision);
+        if (is_tc())
+            tcws = DevBuf(tc_workspace_bytes(d, d.kind - kKindTcTF32), s);
+        else
+            part = DevBuf(desc_part_bytes(d, dt), s);
+        d.part = part.p;
+    }
+    bool is_tc() const { return d.kind >= kKindTcTF32 && d.kind <= kKindTcBF16x3; }
+    void run(rosnet_btensor A, rosnet_btensor B, rosnet_btensor C, cudaStream_t s, bool pack_b = true) {
+        if (empty) return;
+        GettDesc x = d;
+        bind_operands(x, A->data, B->data, C->data, A->pstride, B->pstride, C->pstride);
+        if (is_tc()) {
+            GroupArgs ga;
+            memset(&ga, 0, sizeof(ga));
+            ga.ndesc = 1;
+            ga.single = x;
+            // after an operand swap the kernel's first operand is B
+            const bool sw = x.flags & kFlagSwapped;
+            launch_tc_problem(x.kind - kKindTcTF32, x, ga, tcws.p, s, sw ? pack_b : true, sw ? true : pack_b);
+            return;
+        }
+        launch_gett_single(x, x.kind, desc_ctas(x), dtype, s);
+        if (x.part) launch_gett_single(x, kKindReduce, reduce_ctas(x), dtype, s);
+    }
+};
+
 void tensordot_into(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa, const int *axb,
                     rosnet_btensor C, int precision, cudaStream_t s) {
-    GettView v = make_view(A->lay, B->lay, C->lay, naxes, axa, axb);
-    if (v.Mtot * v.Ntot == 0) return;
-    GettDesc d;
-    memset(&d, 0, sizeof(d));
-    DevBuf tab(table_entries(v) * sizeof(int64_t), s);
-    launch_build_tables(v, (int64_t *)tab.p, s);
-    fill_desc_tables(d, v, (const int64_t *)tab.p);
-    choose_kernel(d, A->dtype, precision);
-    bind_operands(d, A->data, B->data, C->data, A->lay.numel, B->lay.numel, C->lay.numel);
-    if (d.kind >= kKindTcTF32 && d.kind <= kKindTcBF16x3) {
-        const int mode = d.kind - kKindTcTF32;
-        DevBuf ws(tc_workspace_bytes(d, mode), s);
-        GroupArgs ga;
-        memset(&ga, 0, sizeof(ga));
-        ga.ndesc = 1;
-        ga.single = d;
-        launch_tc_problem(mode, d, ga, ws.p, s);
-        return;
-    }
-    DevBuf part(desc_part_bytes(d, A->dtype), s);
-    d.part = part.p;
-    launch_gett_single(d, d.kind, desc_ctas(d), A->dtype, s);
-    if (d.part) launch_gett_single(d, kKindReduce, reduce_ctas(d), A->dtype, s);
+    Prepared p(A->lay, B->lay, C->lay, naxes, axa, axb, A->dtype, precision, s);
+    p.run(A, B, C, s);
 }
 
 bool is_tc_kind(int kind) { return kind >= kKindTcTF32 && kind <= kKindTcBF16x3; }
@@ -705,13 +732,13 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
     const size_t need = tab_bytes + extra;
     if (need > ws_bytes) return need;
     launch_build_tables(v, (int64_t *)ws, s);
-    bind_operands(d, A->data, B->data, C->data, A->lay.numel, B->lay.numel, C->lay.numel);
+    bind_operands(d, A->data, B->data, C->data, A->pstride, B->pstride, C->pstride);
     if (tcp) {
         GroupArgs ga;
         memset(&ga, 0, sizeof(ga));
         ga.ndesc = 1;
         ga.single = d;
-        launch_tc_problem(d.kind - kKindTcTF32, d, ga, (char *)ws + tab_bytes, s);
+        launch_tc_problem(d.kind - kKindTcTF32, d, ga, (char *)ws + tab_bytes, s, true, true);
         return need;
     }
     d.part = d.ksplit > 1 ? (char *)ws + tab_bytes : nullptr;
@@ -794,6 +821,99 @@ extern "C" rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, in
         throw;
     }
     *out_C = C;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+// ---------------------------------------------------------------------------
+// out-of-core: output chunks streamed to pinned host memory
+// ---------------------------------------------------------------------------
+extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B, int naxes,
+                                              const int *axes_a, const int *axes_b, int nsplit,
+                                              int64_t first_chunk, int64_t nchunks,
+                                              const rosnet_opts *opts, void *host_out,
+                                              size_t host_bytes, void *stream) {
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!A || !B || nsplit < 0 || nsplit > A->lay.rank || first_chunk < 0 || nchunks < 0)
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad operands or chunk range");
+    int axa[kMaxRank], axb[kMaxRank], rc = 0;
+    int64_t shc[kMaxRank], blc[kMaxRank];
+    check_tensordot(A, B, naxes, axes_a, axes_b, axa, axb, rc, shc, blc);
+    const int prec = check_precision(opts, A->dtype);
+    // the split axes: A's leading axes, free and of block extent 1
+    int64_t total_chunks = 1;
+    for (int i = 0; i < nsplit; ++i) {
+        for (int j = 0; j < naxes; ++j)
+            if (axa[j] == i) RN_FAIL(ROSNET_ERR_INVALID_ARG, "a split axis of A is contracted");
+        if (A->lay.block[i] != 1) RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "a split axis must be a grid axis");
+        total_chunks *= A->lay.shape[i];
+    }
+    if (first_chunk + nchunks > total_chunks) RN_FAIL(ROSNET_ERR_INVALID_ARG, "chunk range beyond the output");
+    // chunk tensors: the slice of A and the matching output piece
+    int axa_s[kMaxRank];
+    for (int j = 0; j < naxes; ++j) axa_s[j] = axa[j] - nsplit;
+    Layout lc;
+    lc.init(rc - nsplit, shc + nsplit, blc + nsplit);
+    const size_t chunk_bytes = 2 * (size_t)lc.numel * A->elsize;
+    const int64_t nslots = chunk_bytes ? (int64_t)(host_bytes / chunk_bytes) : 1;
+    if (nchunks > 0 && (!host_out || nslots < 1))
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "the host buffer cannot hold one output chunk");
+    if (nchunks == 0) return ROSNET_OK;
+    rosnet_btensor_s av;   // slice view of A, re-pointed per chunk
+    av.lay.init(A->lay.rank - nsplit, A->lay.shape + nsplit, A->lay.block + nsplit);
+    av.dtype = A->dtype;
+    av.elsize = A->elsize;
+    av.pstride = A->pstride;
+    av.owned = false;
+    rosnet_btensor_s cv[2];
+    DevBuf cbuf[2];
+    cudaStream_t side = nullptr;
+    cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        if (side) { cudaStreamSynchronize(side); cudaStreamDestroy(side); }
+        for (int i = 0; i < 2; ++i) {
+            if (computed[i]) cudaEventDestroy(computed[i]);
+            if (copied[i]) cudaEventDestroy(copied[i]);
+        }
+    };
+    try {
+        RN_CHECK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            RN_CHECK_CUDA(cudaEventCreateWithFlags(&computed[i], cudaEventDisableTiming));
+            RN_CHECK_CUDA(cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming));
+            cbuf[i] = DevBuf(chunk_bytes, s);
+            cv[i].lay = lc;
+            cv[i].dtype = A->dtype;
+            cv[i].elsize = A->elsize;
+            cv[i].data = cbuf[i].p;
+            cv[i].pstride = lc.numel;
+            cv[i].owned = false;
+        }
+        Prepared prep(av.lay, B->lay, lc, naxes, axa_s, axb, A->dtype, prec, s);
+        for (int64_t c = first_chunk; c < first_chunk + nchunks; ++c) {
+            const int b = (int)((c - first_chunk) & 1);
+            int64_t rem = c, off = 0;
+            for (int i = nsplit - 1; i >= 0; --i) {
+                off += (rem % A->lay.shape[i]) * A->lay.gstride[i];
+                rem /= A->lay.shape[i];
+            }
+            av.data = (char *)A->data + off * A->elsize;
+            if (c - first_chunk >= 2) RN_CHECK_CUDA(cudaStreamWaitEvent(s, copied[b], 0));
+            prep.run(&av, B, &cv[b], s, c == first_chunk);   // B is packed once
+            RN_CHECK_CUDA(cudaEventRecord(computed[b], s));
+            RN_CHECK_CUDA(cudaStreamWaitEvent(side, computed[b], 0));
+            char *dst = (char *)host_out + ((c - first_chunk) % nslots) * chunk_bytes;
+            RN_CHECK_CUDA(cudaMemcpyAsync(dst, cv[b].data, chunk_bytes, cudaMemcpyDeviceToHost, side));
+            RN_CHECK_CUDA(cudaEventRecord(copied[b], side));
+        }
+        // the caller's stream waits for the last copies
+        for (int i = 0; i < 2; ++i) RN_CHECK_CUDA(cudaStreamWaitEvent(s, copied[i], 0));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();   // synchronises the side stream (the copies are complete on return)
     return ROSNET_OK;
     RN_API_END
 }

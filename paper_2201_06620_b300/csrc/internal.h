@@ -105,12 +105,12 @@ struct rosnet_btensor_s {
     rosnet::Layout lay;
     int dtype = 0;           // ROSNET_C64 / ROSNET_C128
     size_t elsize = 0;       // bytes of one real component (4 or 8)
-    void *data = nullptr;    // real plane; imaginary plane at data + numel*elsize
+    void *data = nullptr;    // real plane; imaginary plane at data + pstride*elsize
+    int64_t pstride = 0;     // elements from the real to the imaginary plane
     cudaStream_t stream = nullptr;  // stream of the last write, for ordered free
-    bool owned = true;       // false: a view into a contraction arena
-    void *arena_owner = nullptr;
+    bool owned = true;       // false: a view of another tensor's storage
     void *re() const { return data; }
-    void *im() const { return (char *)data + lay.numel * elsize; }
+    void *im() const { return (char *)data + pstride * elsize; }
 };
 
 namespace rosnet {
@@ -220,16 +220,19 @@ void choose_kernel(GettDesc &d, int dtype, int precision);
 void launch_gett_group(int kind, int dtype, const GettDesc *descs, int ndesc,
                        int64_t total_tiles, cudaStream_t s);
 
-// Pack/unpack between dense row-major interleaved and block-major planar.
+// Pack/unpack between dense row-major interleaved and block-major planar
+// (imaginary plane `pstride` elements after the real one).  Pack covers the
+// dense row-major entries [start, start + count) of the tensor.
 void launch_pack(const Layout &lay, int dtype, const void *dense_interleaved, void *planar,
-                 cudaStream_t s);
-void launch_unpack(const Layout &lay, int dtype, const void *planar, void *dense_interleaved,
-                   cudaStream_t s);
+                 int64_t pstride, int64_t start, int64_t count, cudaStream_t s);
+void launch_unpack(const Layout &lay, int dtype, const void *planar, int64_t pstride,
+                   void *dense_interleaved, cudaStream_t s);
 
 // Copy src (block-major planar) to dst with a different block shape and/or
 // axis permutation: dst axis i = src axis perm[i].
 void launch_relayout(const Layout &src, const Layout &dst, const int *perm, int dtype,
-                     const void *src_planar, void *dst_planar, cudaStream_t s);
+                     const void *src_planar, int64_t src_pstride, void *dst_planar,
+                     int64_t dst_pstride, cudaStream_t s);
 
 // Create / free tensors.
 rosnet_btensor new_tensor(int rank, const int64_t *shape, const int64_t *block, int dtype,

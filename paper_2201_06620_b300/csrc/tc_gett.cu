@@ -505,7 +505,8 @@ void make_map(CUtensorMap *m, void *base, int64_t rows, int64_t Kpad, int esz) {
 }
 
 template <int MODE>
-void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, cudaStream_t s) {
+void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, cudaStream_t s,
+                 bool pack_a, bool pack_b) {
     using C_ = tc::Cfg<MODE>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -517,8 +518,14 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
     unsigned char *pb = pa + g.narr * g.arrA;
     const int64_t ca = (g.Mpad / 32) * (g.Kpad / 32), cb = (g.Npad / 32) * (g.Kpad / 32);
     if (ca > 0x7fffffffLL || cb > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "operand too large to pack");
-    tc::tc_pack_kernel<MODE><<<(unsigned)ca, 256, 0, s>>>(ga, 0, pa, g.Mpad, g.Kpad);
-    tc::tc_pack_kernel<MODE><<<(unsigned)cb, 256, 0, s>>>(ga, 1, pb, g.Npad, g.Kpad);
+    if (pack_a) {
+        tc::tc_pack_kernel<MODE><<<(unsigned)ca, 256, 0, s>>>(ga, 0, pa, g.Mpad, g.Kpad);
+        g_launches++;
+    }
+    if (pack_b) {
+        tc::tc_pack_kernel<MODE><<<(unsigned)cb, 256, 0, s>>>(ga, 1, pb, g.Npad, g.Kpad);
+        g_launches++;
+    }
     tc::TcArgs args;
     memset(&args, 0, sizeof(args));
     for (int a = 0; a < g.narr; ++a) {
@@ -528,7 +535,7 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
     args.g = ga;
     args.nkt = (int)(g.Kpad / g.bk);
     tc::tc_gemm_kernel<MODE><<<(unsigned)ctas, tc::NTHREADS, C_::SMEM, s>>>(args);
-    g_launches += 3;
+    g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -542,17 +549,19 @@ size_t tc_workspace_bytes(const GettDesc &d, int mode) {
 
 // Enqueue pack + GEMM for one tensor-core problem.  `ga` locates the
 // problem's descriptor (by value or in device memory); ws holds
-// tc_workspace_bytes(d, mode) bytes, 256-byte aligned.
-void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s) {
+// tc_workspace_bytes(d, mode) bytes, 256-byte aligned.  pack_a / pack_b = false
+// reuse the packed operand already in ws (same operand as the previous call).
+void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
+                       bool pack_a, bool pack_b) {
     const TcGeom g = tc_geom(d, mode);
     const int64_t ctas = d.tiles_m * d.tiles_n;
     if (ctas <= 0) return;
     if (ctas > 0x7fffffffLL || g.Kpad / g.bk > 0x7fffffffLL || g.Mpad > 0x7fffffffLL || g.Npad > 0x7fffffffLL)
         RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one tensor-core launch");
     switch (mode) {
-        case tc::kTF32: launch_mode<tc::kTF32>(ga, g, ws, ctas, s); break;
-        case tc::kTF32x3: launch_mode<tc::kTF32x3>(ga, g, ws, ctas, s); break;
-        default: launch_mode<tc::kBF16x3>(ga, g, ws, ctas, s); break;
+        case tc::kTF32: launch_mode<tc::kTF32>(ga, g, ws, ctas, s, pack_a, pack_b); break;
+        case tc::kTF32x3: launch_mode<tc::kTF32x3>(ga, g, ws, ctas, s, pack_a, pack_b); break;
+        default: launch_mode<tc::kBF16x3>(ga, g, ws, ctas, s, pack_a, pack_b); break;
     }
 }
 

@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "complex_normal", "SQRT_X", "SQRT_Y", "SQRT_W", "HADAMARD", "CNOT",
+    "complex_normal", "complex_normal_range", "SQRT_X", "SQRT_Y", "SQRT_W", "HADAMARD", "CNOT",
     "fsim", "grid_shape", "grid_sites", "coupler_layer", "PATTERN",
     "Circuit", "random_circuit", "ghz_circuit", "hadamard_circuit",
     "circuit_network", "Network",
@@ -49,6 +49,23 @@ def complex_normal(shape, seed, scale=1.0, dtype=np.complex128):
     re = rng.standard_normal(shape) * s
     im = rng.standard_normal(shape) * s
     return (re + 1j * im).astype(dtype)
+
+
+def complex_normal_range(seed, start, count, scale=1.0, dtype=np.complex64):
+    """Entries [start, start + count) of a counter-addressable stream of i.i.d.
+    complex normals (re, im ~ N(0, 1/2)), so that any piece of a tensor too
+    large for host memory can be generated on its own.
+
+    Entry e uses the 64-bit draws 2e and 2e+1 of numpy's PCG64(seed) as the
+    doubles u1, u2 in [0, 1) (Generator.random) and the Box-Muller map
+    z = sqrt(-ln(1 - u1)) * exp(2 pi i u2), so |z|^2 ~ Exp(1).
+    """
+    bg = np.random.PCG64(seed)
+    bg.advance(2 * int(start))
+    u = np.random.Generator(bg).random(2 * int(count))
+    r = np.sqrt(-np.log1p(-u[0::2])) * scale
+    th = 2.0 * np.pi * u[1::2]
+    return (r * np.cos(th) + 1j * (r * np.sin(th))).astype(dtype)
 
 
 # ---------------------------------------------------------------------------
