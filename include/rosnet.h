@@ -106,6 +106,17 @@ typedef struct {
                                    graph on first use and replay it afterwards      */
 #define ROSNET_OPT_NOGROUP 0x2  /* contract: one launch per step instead of one
                                    grouped launch per dependency wave               */
+/* How the partial products of the B_k matched block pairs of an output tile
+ * are summed (Sec. IV-A).  At most one; none = chosen per problem (split only
+ * when the output tiles cannot fill the GPU, tree-reduced).
+ *   SEQUENTIAL   one CTA loops over every pair of its tile (no split);
+ *   TREE         pairs split over CTAs, partial tiles stored, then summed in
+ *                a fixed order (deterministic);
+ *   COMMUTATIVE  pairs split over CTAs, each adding into C as it finishes
+ *                (order-free, no partial storage, not bitwise reproducible). */
+#define ROSNET_OPT_REDUCE_SEQUENTIAL  0x10
+#define ROSNET_OPT_REDUCE_TREE        0x20
+#define ROSNET_OPT_REDUCE_COMMUTATIVE 0x40
 #define ROSNET_OPT_TIMING 0x4   /* contract: record CUDA events around the plan's
                                    heaviest launch (most 8*M*N*K flops) on the
                                    call's stream; read with rosnet_timing_drain    */

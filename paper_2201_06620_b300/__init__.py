@@ -34,6 +34,7 @@ __all__ = [
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
     "PREC_TF32X3",
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
+    "REDUCE_SEQUENTIAL", "REDUCE_TREE", "REDUCE_COMMUTATIVE",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -42,6 +43,7 @@ LIB_PATH = os.path.join(_HERE, "librosnet.so")
 C64, C128 = 1, 2
 PREC_DEFAULT, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_FP64, PREC_TF32X3 = 0, 1, 2, 3, 4, 5
 OPT_GRAPH, OPT_NOGROUP, OPT_TIMING = 0x1, 0x2, 0x4
+REDUCE_SEQUENTIAL, REDUCE_TREE, REDUCE_COMMUTATIVE = 0x10, 0x20, 0x40
 STATUS = {
     0: "OK", -1: "INVALID_ARG", -2: "SHAPE", -3: "BLOCK_MISMATCH", -4: "DTYPE", -5: "ALLOC",
     -6: "RANK_LIMIT", -7: "CUDA", -8: "TIMEOUT", -9: "UNSUPPORTED",
@@ -375,11 +377,12 @@ def _opts(precision, flags=0, max_block_entries=0):
     return o
 
 
-def tensordot(A, B, axes_a, axes_b, precision=PREC_DEFAULT, stream=None):
-    """C = tensordot(A, B, axes=(axes_a, axes_b)) on the GPU (numpy conventions)."""
+def tensordot(A, B, axes_a, axes_b, precision=PREC_DEFAULT, stream=None, flags=0):
+    """C = tensordot(A, B, axes=(axes_a, axes_b)) on the GPU (numpy conventions).
+    ``flags`` may hold one REDUCE_* mode."""
     _init()
     h = ctypes.c_void_p()
-    o = _opts(precision)
+    o = _opts(precision, flags)
     _check(lib().rosnet_tensordot(A.handle, B.handle, len(axes_a), _i32arr(axes_a), _i32arr(axes_b),
                                   ctypes.byref(o), _stream(stream), ctypes.byref(h)),
            "rosnet_tensordot")

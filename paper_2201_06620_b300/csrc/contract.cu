@@ -334,17 +334,21 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
     // reduction launch right after their wave's launches
     const int64_t *dtab = (const int64_t *)plan->tables.p;
     std::map<std::pair<int, int>, std::vector<int>> groups;
-    std::map<int, std::vector<int>> split_of_wave;
+    std::map<int, std::vector<int>> split_of_wave, atomic_of_wave;
     for (int st = 0; st < path->nsteps; ++st) {
         Step &S = plan->steps[st];
         memset(&S.desc, 0, sizeof(S.desc));
         fill_desc_tables(S.desc, views[st], dtab + S.table_off);
-        choose_kernel(S.desc, plan->dtype, prec);
+        const int red = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
+                        : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
+                        : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
+        choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
         // tensor-core problems carry their own tensor maps: one launch each
         int key_kind = ((flags & ROSNET_OPT_NOGROUP) || is_tc_kind(S.desc.kind)) ? 1000 + st : S.desc.kind;
         groups[{S.wave, key_kind}].push_back(st);
-        if (S.desc.ksplit > 1) split_of_wave[S.wave].push_back(st);
+        if (S.desc.ksplit > 1 && !(S.desc.flags & kFlagAtomic)) split_of_wave[S.wave].push_back(st);
+        if (S.desc.flags & kFlagAtomic) atomic_of_wave[S.wave].push_back(st);
     }
     // split-K partials: one workspace reused by every wave
     size_t part_bytes = 0;
@@ -363,7 +367,7 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
     }
     std::vector<GettDesc> slot_desc;   // per descriptor slot: the static fields
     size_t tc_bytes = 0;
-    auto add_launch = [&](int kind, const std::vector<int> &sts, bool reduce) {
+    auto add_launch = [&](int kind, const std::vector<int> &sts, int role /*0 main 1 reduce 2 zero*/) {
         Plan::Launch L;
         L.kind = kind;
         L.tc_ws_off = 0;
@@ -377,7 +381,7 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
         for (int st : sts) {
             GettDesc d = plan->steps[st].desc;
             d.tile_begin = ctas;
-            ctas += reduce ? reduce_ctas(d) : desc_ctas(d);
+            ctas += role == 1 ? reduce_ctas(d) : role == 2 ? zero_ctas(d) : desc_ctas(d);
             plan->desc_step.push_back(st);
             slot_desc.push_back(d);
         }
@@ -386,10 +390,12 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
     };
     for (auto it = groups.begin(); it != groups.end(); ++it) {
         const int w = it->first.first;
-        add_launch(plan->steps[it->second[0]].desc.kind, it->second, false);
+        if ((it == groups.begin() || std::prev(it)->first.first != w) && atomic_of_wave.count(w))
+            add_launch(kKindZero, atomic_of_wave[w], 2);   // C = 0 before order-free adds
+        add_launch(plan->steps[it->second[0]].desc.kind, it->second, 0);
         auto nx = std::next(it);
         if ((nx == groups.end() || nx->first.first != w) && split_of_wave.count(w))
-            add_launch(kKindReduce, split_of_wave[w], true);
+            add_launch(kKindReduce, split_of_wave[w], 1);
     }
     plan->slot_desc = std::move(slot_desc);
     if (tc_bytes) plan->tcws = DevBuf(tc_bytes, s);
@@ -400,7 +406,7 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
         for (size_t li = 0; li < plan->launches.size(); ++li) {
             const auto &L = plan->launches[li];
             double fl = 0, by = 0;
-            if (L.kind == kKindReduce) continue;
+            if (L.kind == kKindReduce || L.kind == kKindZero) continue;
             for (int q = L.first; q < L.first + L.count; ++q) {
                 const GettDesc &d = plan->slot_desc[q];
                 fl += 8.0 * (double)d.M * (double)d.N * (double)d.K;

@@ -284,6 +284,27 @@ __global__ void __launch_bounds__(256) gett_reduce_kernel(const __grid_constant_
     C[ic + sd.c_plane] = si;
 }
 
+// C = 0 for the problems of a commutative split-K launch (4 entries per thread).
+template <typename T>
+__global__ void __launch_bounds__(256) gett_zero_kernel(const __grid_constant__ GroupArgs g) {
+    __shared__ GettDesc sd;
+    if (threadIdx.x == 0) load_desc(g, sd);
+    __syncthreads();
+    const int64_t MN = sd.M * sd.N;
+    const int64_t o0 = ((int64_t)blockIdx.x - sd.tile_begin) * 1024 + threadIdx.x;
+    T *C = (T *)sd.c;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t o = o0 + i * 256;
+        if (o < MN) {
+            const int64_t m = o / sd.N, n = o % sd.N;
+            const int64_t ic = sd.offCM[m] + sd.offCN[n];
+            C[ic] = 0;
+            C[ic + sd.c_plane] = 0;
+        }
+    }
+}
+
 __device__ __forceinline__ void cp_async_el(void *smem, const void *gsrc, int bytes, bool valid) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     const int n = valid ? bytes : 0;   // 0 source bytes: the shared word is zero-filled
@@ -503,6 +524,7 @@ __global__ void __launch_bounds__(256, 1) gett_tiled_kernel(const __grid_constan
     }
     T *C = (T *)sd.c;
     const int64_t cp = sd.c_plane;
+    const bool atomic = sd.flags & kFlagAtomic;   // commutative split: order-free adds
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
         const int mi = ty * TM + i;
@@ -512,8 +534,13 @@ __global__ void __launch_bounds__(256, 1) gett_tiled_kernel(const __grid_constan
             const int nj = tx * TN + j;
             if (n0 + nj >= N) continue;
             const int64_t o = sCM[mi] + sCN[nj];
-            C[o] = cr[i][j];
-            C[o + cp] = ci[i][j];
+            if (atomic) {
+                atomicAdd(C + o, cr[i][j]);
+                atomicAdd(C + o + cp, ci[i][j]);
+            } else {
+                C[o] = cr[i][j];
+                C[o + cp] = ci[i][j];
+            }
         }
     }
 }
@@ -542,7 +569,7 @@ size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b);
 
-void choose_kernel(GettDesc &d, int dtype, int precision) {
+void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
     d.ksplit = 1;
     d.ktiles_per_split = 0x7fffffff;
     d.part = nullptr;
@@ -565,15 +592,18 @@ void choose_kernel(GettDesc &d, int dtype, int precision) {
         d.tiles_m = (d.M + BM - 1) / BM;
         d.tiles_n = (d.N + BN - 1) / BN;
         // split the contracted range when the tile grid cannot fill the GPU
+        // (or when asked to), unless the sequential reduction is requested
         const int64_t tiles = d.tiles_m * d.tiles_n;
         const int64_t nkt = (d.K + BK - 1) / BK;
-        if (tiles < kSMs && nkt >= 32) {
-            int64_t want = (2 * kSMs + tiles - 1) / tiles;
-            int64_t cap = nkt / 16;            // at least 16 k-tiles per range
+        const bool forced = reduce_mode == kReduceTree || reduce_mode == kReduceCommutative;
+        if (reduce_mode != kReduceSequential && ((tiles < kSMs && nkt >= 32) || (forced && nkt >= 2))) {
+            int64_t want = std::max<int64_t>((2 * kSMs + tiles - 1) / tiles, forced ? 2 : 1);
+            int64_t cap = forced ? nkt : nkt / 16;   // auto: at least 16 k-tiles per range
             int64_t ks = std::max<int64_t>(1, std::min<int64_t>(std::min(want, cap), 64));
             if (ks > 1) {
                 d.ktiles_per_split = (int)((nkt + ks - 1) / ks);
                 d.ksplit = (int)((nkt + d.ktiles_per_split - 1) / d.ktiles_per_split);
+                if (reduce_mode == kReduceCommutative) d.flags |= kFlagAtomic;
             }
         }
         return;
@@ -590,7 +620,7 @@ void choose_kernel(GettDesc &d, int dtype, int precision) {
 }
 
 size_t desc_part_bytes(const GettDesc &d, int dtype) {
-    if (d.ksplit <= 1) return 0;
+    if (d.ksplit <= 1 || (d.flags & kFlagAtomic)) return 0;
     return (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * (dtype == ROSNET_C64 ? 4 : 8);
 }
 
@@ -618,6 +648,7 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindSmall: gett_small_kernel<float><<<grid, 256, 0, s>>>(ga); break;
             case kKindWarpK: gett_warpk_kernel<float><<<grid, 256, 0, s>>>(ga); break;
             case kKindReduce: gett_reduce_kernel<float><<<grid, 256, 0, s>>>(ga); break;
+            case kKindZero: gett_zero_kernel<float><<<grid, 256, 0, s>>>(ga); break;
             case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
             default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
         }
@@ -626,6 +657,7 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindSmall: gett_small_kernel<double><<<grid, 256, 0, s>>>(ga); break;
             case kKindWarpK: gett_warpk_kernel<double><<<grid, 256, 0, s>>>(ga); break;
             case kKindReduce: gett_reduce_kernel<double><<<grid, 256, 0, s>>>(ga); break;
+            case kKindZero: gett_zero_kernel<double><<<grid, 256, 0, s>>>(ga); break;
             default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
         }
     }
@@ -667,7 +699,7 @@ struct Prepared {
     bool empty = false;
     int dtype = 0;
     Prepared(const Layout &A, const Layout &B, const Layout &C, int naxes, const int *axa,
-             const int *axb, int dt, int precision, cudaStream_t s) {
+             const int *axb, int dt, int precision, cudaStream_t s, int reduce_mode = kReduceAuto) {
         dtype = dt;
         memset(&d, 0, sizeof(d));
         GettView v = make_view(A, B, C, naxes, axa, axb);
@@ -678,7 +710,7 @@ struct Prepared {
         tab = DevBuf(table_entries(v) * sizeof(int64_t), s);
         launch_build_tables(v, (int64_t *)tab.p, s);
         fill_desc_tables(d, v, (const int64_t *)tab.p);
-        choose_kernel(d, dt, precision);
+        choose_kernel(d, dt, precision, reduce_mode);
         if (is_tc())
             tcws = DevBuf(tc_workspace_bytes(d, d.kind - kKindTcTF32), s);
         else
@@ -700,15 +732,29 @@ struct Prepared {
             launch_tc_problem(x.kind - kKindTcTF32, x, ga, tcws.p, s, sw ? pack_b : true, sw ? true : pack_b);
             return;
         }
+        if (x.flags & kFlagAtomic) launch_gett_single(x, kKindZero, zero_ctas(x), dtype, s);
         launch_gett_single(x, x.kind, desc_ctas(x), dtype, s);
         if (x.part) launch_gett_single(x, kKindReduce, reduce_ctas(x), dtype, s);
     }
 };
 
 void tensordot_into(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa, const int *axb,
-                    rosnet_btensor C, int precision, cudaStream_t s) {
-    Prepared p(A->lay, B->lay, C->lay, naxes, axa, axb, A->dtype, precision, s);
+                    rosnet_btensor C, int precision, cudaStream_t s, int reduce_mode) {
+    Prepared p(A->lay, B->lay, C->lay, naxes, axa, axb, A->dtype, precision, s, reduce_mode);
     p.run(A, B, C, s);
+}
+
+int check_reduce(const rosnet_opts *opts) {
+    if (!opts) return kReduceAuto;
+    const int f = opts->flags & (ROSNET_OPT_REDUCE_SEQUENTIAL | ROSNET_OPT_REDUCE_TREE |
+                                 ROSNET_OPT_REDUCE_COMMUTATIVE);
+    switch (f) {
+        case 0: return kReduceAuto;
+        case ROSNET_OPT_REDUCE_SEQUENTIAL: return kReduceSequential;
+        case ROSNET_OPT_REDUCE_TREE: return kReduceTree;
+        case ROSNET_OPT_REDUCE_COMMUTATIVE: return kReduceCommutative;
+        default: RN_FAIL(ROSNET_ERR_INVALID_ARG, "at most one reduction flag");
+    }
 }
 
 bool is_tc_kind(int kind) { return kind >= kKindTcTF32 && kind <= kKindTcBF16x3; }
@@ -813,9 +859,10 @@ extern "C" rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, in
     int64_t shc[kMaxRank], blc[kMaxRank];
     check_tensordot(A, B, naxes, axes_a, axes_b, axa, axb, rc, shc, blc);
     int prec = check_precision(opts, A->dtype);
+    const int red = check_reduce(opts);
     rosnet_btensor C = new_tensor(rc, shc, blc, A->dtype, s);
     try {
-        tensordot_into(A, B, naxes, axa, axb, C, prec, s);
+        tensordot_into(A, B, naxes, axa, axb, C, prec, s, red);
     } catch (...) {
         free_tensor(C);
         throw;
@@ -890,7 +937,7 @@ extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B
             cv[i].pstride = lc.numel;
             cv[i].owned = false;
         }
-        Prepared prep(av.lay, B->lay, lc, naxes, axa_s, axb, A->dtype, prec, s);
+        Prepared prep(av.lay, B->lay, lc, naxes, axa_s, axb, A->dtype, prec, s, check_reduce(opts));
         for (int64_t c = first_chunk; c < first_chunk + nchunks; ++c) {
             const int b = (int)((c - first_chunk) & 1);
             int64_t rem = c, off = 0;

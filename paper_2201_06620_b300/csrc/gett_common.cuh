@@ -29,7 +29,7 @@ __device__ __forceinline__ void load_desc(const GroupArgs &g, GettDesc &sd) {
 
 
 // Device status word: kernels set a nonzero code when a bounded wait gives up
-// (see rosnet_sync).  Defined in tc_gett.cu.
+// (see rosnet_sync).
 enum : int32_t { kDevErrNone = 0, kDevErrTimeout = 1 };
 
 }  // namespace rosnet

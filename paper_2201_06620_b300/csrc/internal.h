@@ -178,7 +178,14 @@ enum : int32_t {
     kFlagBNFast = 2,
     kFlagCNFast = 4,
     kFlagSwapped = 8,   // roles of A and B exchanged (the kernel computes C^T = B^T A^T)
+    kFlagAtomic = 16,   // split-K ranges add into C with atomics (C zeroed first)
 };
+
+// How the partial products of the matched block pairs of an output tile are
+// summed (Sec. IV-A): automatic, one CTA over all pairs ("sequential"), split
+// over CTAs with a fixed-order reduction of stored partials ("tree"), or split
+// over CTAs adding into C in whatever order they finish ("commutative").
+enum ReduceMode : int { kReduceAuto = 0, kReduceSequential = 1, kReduceTree = 2, kReduceCommutative = 3 };
 
 enum KernelKind : int32_t {
     kKindSmall = 0,   // one thread per output, full K loop (low arithmetic intensity)
@@ -189,6 +196,7 @@ enum KernelKind : int32_t {
     kKindTcTF32 = 5,     // tcgen05 tensor cores, TF32 products
     kKindTcTF32x3 = 6,   // tcgen05, 3 x TF32 split products
     kKindTcBF16x3 = 7,   // tcgen05, 3 x BF16 split products
+    kKindZero = 8,       // zero C before a commutative (atomic) split-K launch
 };
 
 inline void bind_operands(GettDesc &d, const void *A, const void *B, void *C, int64_t a_numel,
@@ -212,7 +220,9 @@ void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tables);
 
 // Choose the kernel family, tile grid and split-K for a problem (may swap
 // the operand roles; call bind_operands afterwards).
-void choose_kernel(GettDesc &d, int dtype, int precision);
+void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode = kReduceAuto);
+int check_reduce(const rosnet_opts *opts);
+inline int64_t zero_ctas(const GettDesc &d) { return (d.M * d.N + 1023) / 1024; }
 
 // Launch one group of problems of the same kind and dtype.  `descs` is in
 // device memory (ndesc entries, with tile_begin prefix sums); total_tiles is
@@ -243,6 +253,7 @@ void free_tensor(rosnet_btensor t);
 // rosnet_tensordot and the network executor).  workspace for the tables is
 // allocated from the allocator.
 void tensordot_into(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa,
-                    const int *axb, rosnet_btensor C, int precision, cudaStream_t s);
+                    const int *axb, rosnet_btensor C, int precision, cudaStream_t s,
+                    int reduce_mode = kReduceAuto);
 
 }  // namespace rosnet

@@ -203,3 +203,34 @@ def test_fp32_mode_equals_default_c64():
     c0 = R.tensordot(A, B, prob["axes_a"], prob["axes_b"]).download()
     c1 = R.tensordot(A, B, prob["axes_a"], prob["axes_b"], precision=R.PREC_FP32).download()
     assert np.array_equal(c0, c1)
+
+
+@pytest.mark.parametrize("dtype", [R.C64, R.C128])
+@pytest.mark.parametrize("mode", [R.REDUCE_SEQUENTIAL, R.REDUCE_TREE, R.REDUCE_COMMUTATIVE])
+def test_reduction_modes(dtype, mode):
+    """Sec. IV-A's three ways of summing the B_k block-pair partials: one CTA
+    over all pairs, split with a stored-partials tree, split with order-free
+    adds.  All agree with the oracle; sequential and tree are bitwise
+    reproducible."""
+    prob = W._block_tensordot_problem(90, 91, 7, 9, 7, 3, 5, 2, perm_seed=92)   # B_k = 32
+    A = R.btensor(prob["a"].astype(NPT[dtype]), prob["block_a"], dtype)
+    B = R.btensor(prob["b"].astype(NPT[dtype]), prob["block_b"], dtype)
+    ref = ref_of(prob["a"], prob["b"], prob["axes_a"], prob["axes_b"], dtype)
+    c1 = R.tensordot(A, B, prob["axes_a"], prob["axes_b"], flags=mode).download()
+    c2 = R.tensordot(A, B, prob["axes_a"], prob["axes_b"], flags=mode).download()
+    assert oracle.rel_frobenius(c1, ref) <= TOL[dtype]
+    assert oracle.rel_frobenius(c2, ref) <= TOL[dtype]
+    if mode != R.REDUCE_COMMUTATIVE:
+        assert np.array_equal(c1, c2)
+
+
+def test_reduction_modes_matrix_ragged():
+    a = W.complex_normal((70, 3001), 5)
+    b = W.complex_normal((3001, 90), 6)
+    ref = ref_of(a, b, [1], [0], R.C64)
+    A, B = R.btensor(a.astype(np.complex64)), R.btensor(b.astype(np.complex64))
+    for mode in (R.REDUCE_SEQUENTIAL, R.REDUCE_TREE, R.REDUCE_COMMUTATIVE):
+        got = R.tensordot(A, B, [1], [0], flags=mode).download()
+        assert oracle.rel_frobenius(got, ref) <= 1e-5, mode
+    with pytest.raises(R.RosnetError):
+        R.tensordot(A, B, [1], [0], flags=R.REDUCE_TREE | R.REDUCE_COMMUTATIVE)
