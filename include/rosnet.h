@@ -192,6 +192,17 @@ rosnet_status rosnet_btensor_slice(rosnet_btensor t, int nfix, const int64_t *va
  */
 rosnet_status rosnet_btensor_block(rosnet_btensor t, const int64_t *grid_coords, rosnet_btensor *view);
 
+/*
+ * A view of t with axes[j] fixed to values[j] for j < nfix (any axes, any
+ * block extents): the projection of those indices on one basis state each,
+ * i.e. the slicing of those bonds (Sec. II-B).  The view keeps t's strides
+ * for the remaining axes (it need not be contiguous), shares t's storage and
+ * must be destroyed before t.  Errors: INVALID_ARG (repeated or bad axis,
+ * value out of range).
+ */
+rosnet_status rosnet_btensor_fix(rosnet_btensor t, int nfix, const int *axes, const int64_t *values,
+                                 rosnet_btensor *view);
+
 /* Copy the tensor into a dense row-major interleaved host array.  Blocks
  * until the data is on the host (synchronises `stream`). */
 rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream);
@@ -327,6 +338,33 @@ rosnet_status rosnet_path_greedy_extents(int32_t ntensors, const int32_t *ranks,
                                          int32_t *nsteps);
 
 /*
+ * A cheaper path by randomized greedy search (the paper takes its paths from
+ * an external optimiser, Sec. V): trial 0 is rosnet_path_greedy_extents;
+ * every further trial joins, at each step, the connected pair with the
+ * smallest size(result) - size(a) - size(b) perturbed by Gumbel noise of
+ * relative scale `temperature`; the path with the fewest total 8*M*N*K flops
+ * wins (*flops, may be NULL).  Deterministic for a given seed.  Host-only.
+ */
+rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks,
+                                 const int64_t *const *labels, const int64_t *const *extents,
+                                 int32_t nout, const int64_t *out_labels, int32_t ntrials,
+                                 uint64_t seed, double temperature, int32_t *pairs_out,
+                                 int32_t *nsteps, double *flops);
+
+/*
+ * Bonds to slice (Sec. II-B): greedily, nslice times, the bond whose slicing
+ * gives the smallest (largest intermediate, total flops over all slices) for
+ * the given path.  chosen[0..nslice) receives the labels; *max_entries the
+ * largest intermediate of one slice, *flops the total over all slices (either
+ * may be NULL).  Host-only.
+ */
+rosnet_status rosnet_slice_search(int32_t ntensors, const int32_t *ranks,
+                                  const int64_t *const *labels, const int64_t *const *extents,
+                                  int32_t nout, const int64_t *out_labels, int32_t nsteps,
+                                  const int32_t *pairs, int32_t nslice, int64_t *chosen,
+                                  double *max_entries, double *flops);
+
+/*
  * Contract a network along a path; *out is a new tensor whose axes follow
  * out_labels (rank 0 for a closed network such as one amplitude).
  * Intermediates live in one device arena sized from their lifetimes.  With
@@ -353,6 +391,37 @@ rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int3
  * CUDA graph).  Plans are cached by rosnet_contract and kept until this call;
  * the caller must make sure no contraction is still running. */
 rosnet_status rosnet_release_plans(void);
+
+/*
+ * Contract nnet networks (each with its own path, as rosnet_contract) in one
+ * plan: the steps of all networks that sit at the same dependency depth run
+ * in the same grouped launches, and a step whose operands and contraction are
+ * identical to one already planned (same operand tensors -- same storage and
+ * layout -- same contracted axes, same result blocks) is computed once and
+ * shared.  Slices of one network (Sec. II-B) share every step that no sliced
+ * bond reaches, so their common work is done once.  outs[i] receives network
+ * i's result (new tensors owned by the caller).  Networks must share a dtype.
+ * Options and errors as rosnet_contract.
+ */
+rosnet_status rosnet_contract_batch(int32_t nnet, const rosnet_network *nets,
+                                    const rosnet_path *paths, const rosnet_opts *opts,
+                                    void *stream, rosnet_btensor *outs);
+
+/* For a batch already planned (same arguments as rosnet_contract_batch): the
+ * number of path steps requested, of distinct steps planned after merging
+ * identical ones, and of launches per call.  INVALID_ARG if not planned yet. */
+rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                const rosnet_opts *opts, void *stream, int64_t *steps_requested,
+                                int64_t *steps_planned, int64_t *launches);
+
+/*
+ * out = sum of the n tensors ts[0..n) in FP64, in that order (deterministic):
+ * e.g. the sum over slices of a sliced network's results (Sec. II-B).  The
+ * summands must share dtype, shape and block shape and be dense block-major
+ * tensors (results of tensordot/contract are); *out is a new complex128
+ * tensor of that shape.  Errors: INVALID_ARG, DTYPE, SHAPE, UNSUPPORTED.
+ */
+rosnet_status rosnet_sum(int32_t n, const rosnet_btensor *ts, void *stream, rosnet_btensor *out);
 
 /* ----------------------------------------------------------------------- */
 /* misc                                                                     */

@@ -17,6 +17,8 @@ Functions (all complex128):
   pairwise operations between neighbouring tensors).
 * ``greedy_path(network)`` -- the oracle's own contraction order (any order
   gives the same result up to rounding).
+* ``sliced_contract(network, path, cut)`` -- Sec. II-B slicing: the sum over
+  all basis assignments of the cut bonds of the projected networks.
 * ``statevector(circuit)`` / ``amplitude_sv`` -- |psi> = C|0^n> by applying each
   gate to the 2^n state vector (Sec. II-A), an independent check of network
   contraction.
@@ -223,6 +225,30 @@ def greedy_path(network):
         path.append((i, j))
         nxt += 1
     return path
+
+
+def sliced_contract(network, path, cut):
+    """Sec. II-B slicing: the sum, over every basis assignment of the bonds in
+    ``cut``, of the network projected onto that assignment (each tensor that
+    carries a cut bond is indexed at the assigned value and loses that axis),
+    each contracted along the same ``path``; summed in complex128."""
+    import itertools
+    ext = {}
+    for t, l in zip(network.tensors, network.labels):
+        for x, e in zip(l, np.shape(t)):
+            ext[x] = e
+    total = None
+    for vals in itertools.product(*[range(ext[c]) for c in cut]):
+        val = dict(zip(cut, vals))
+        ts, ls = [], []
+        for t, l in zip(network.tensors, network.labels):
+            t = _as_c128(t)
+            idx = tuple(val[x] if x in val else slice(None) for x in l)
+            ts.append(_as_c128(t[idx]) if any(x in val for x in l) else t)
+            ls.append(tuple(x for x in l if x not in val))
+        part = contract(type(network)(tensors=ts, labels=ls, out_labels=list(network.out_labels)), path)
+        total = part if total is None else total + part
+    return total
 
 
 def circuit_order_path(network):

@@ -29,7 +29,8 @@ import numpy as np
 
 __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
-    "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc",
+    "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc", "contract_batch",
+    "plan_stats", "path_search", "slice_search", "sliced_networks", "sum_fp64",
     "sync", "kernel_launches", "release_plans", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
     "PREC_TF32X3",
@@ -56,7 +57,8 @@ EXPORTS = [
     "rosnet_release_plans", "rosnet_sync", "rosnet_status_string", "rosnet_last_error",
     "rosnet_kernel_launches", "rosnet_path_greedy_extents", "rosnet_timing_drain",
     "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range", "rosnet_btensor_slice",
-    "rosnet_btensor_block", "rosnet_tensordot_ooc",
+    "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_contract_batch", "rosnet_plan_stats",
+    "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
 ]
 
 _lock = threading.Lock()
@@ -113,6 +115,22 @@ def lib():
             L.rosnet_btensor_upload_range.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
             L.rosnet_btensor_slice.argtypes = [vp, ctypes.c_int, i64p, ctypes.POINTER(vp)]
             L.rosnet_btensor_block.argtypes = [vp, i64p, ctypes.POINTER(vp)]
+            L.rosnet_btensor_fix.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p,
+                                             ctypes.POINTER(vp)]
+            dpp = ctypes.POINTER(ctypes.c_double)
+            L.rosnet_path_search.argtypes = [ctypes.c_int32, i32p, ctypes.POINTER(i64p),
+                                             ctypes.POINTER(i64p), ctypes.c_int32, i64p, ctypes.c_int32,
+                                             ctypes.c_uint64, ctypes.c_double, i32p, i32p, dpp]
+            L.rosnet_slice_search.argtypes = [ctypes.c_int32, i32p, ctypes.POINTER(i64p),
+                                              ctypes.POINTER(i64p), ctypes.c_int32, i64p, ctypes.c_int32,
+                                              i32p, ctypes.c_int32, i64p, dpp, dpp]
+            L.rosnet_sum.argtypes = [ctypes.c_int32, ctypes.POINTER(vp), vp, ctypes.POINTER(vp)]
+            L.rosnet_contract_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
+                                                ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp,
+                                                ctypes.POINTER(vp)]
+            L.rosnet_plan_stats.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
+                                            ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp, i64p,
+                                            i64p, i64p]
             L.rosnet_tensordot_ooc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Opts),
@@ -151,7 +169,9 @@ def lib():
                         "rosnet_contract", "rosnet_release_plans", "rosnet_sync",
                         "rosnet_path_greedy_extents", "rosnet_timing_drain",
                         "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range",
-                        "rosnet_btensor_slice", "rosnet_btensor_block", "rosnet_tensordot_ooc"):
+                        "rosnet_btensor_slice", "rosnet_btensor_block", "rosnet_tensordot_ooc",
+                        "rosnet_contract_batch", "rosnet_plan_stats", "rosnet_btensor_fix",
+                        "rosnet_path_search", "rosnet_slice_search", "rosnet_sum"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -307,6 +327,15 @@ class BTensor:
         h = ctypes.c_void_p()
         _check(lib().rosnet_btensor_slice(self._h, len(values), _i64arr(values), ctypes.byref(h)),
                "rosnet_btensor_slice")
+        v = BTensor(h.value)
+        v._parent = self
+        return v
+
+    def fix(self, axes, values):
+        """View with axes[j] fixed to values[j] (any axes); shares storage."""
+        h = ctypes.c_void_p()
+        _check(lib().rosnet_btensor_fix(self._h, len(axes), _i32arr(axes), _i64arr(values),
+                                        ctypes.byref(h)), "rosnet_btensor_fix")
         v = BTensor(h.value)
         v._parent = self
         return v
@@ -486,6 +515,78 @@ def path_greedy_extents(labels, extents, out_labels=()):
     return [(pairs[2 * i], pairs[2 * i + 1]) for i in range(ns.value)]
 
 
+def _label_args(labels, extents, out_labels):
+    n = len(labels)
+    P = ctypes.POINTER(ctypes.c_int64)
+    keep = [_i64arr(l) for l in labels] + [_i64arr(e) for e in extents]
+    ranks = (ctypes.c_int32 * max(1, n))(*[len(l) for l in labels])
+    labp = (P * max(1, n))(*[ctypes.cast(a, P) for a in keep[:n]])
+    extp = (P * max(1, n))(*[ctypes.cast(a, P) for a in keep[n:]])
+    out = _i64arr(out_labels)
+    return n, ranks, labp, extp, out, keep
+
+
+def path_search(labels, extents, out_labels=(), ntrials=64, seed=0, temperature=0.3):
+    """Randomised greedy path search (host-only): (path, total flops)."""
+    n, ranks, labp, extp, out, keep = _label_args(labels, extents, out_labels)
+    pairs = (ctypes.c_int32 * max(1, 2 * (n - 1)))()
+    ns = ctypes.c_int32()
+    fl = ctypes.c_double()
+    _check(lib().rosnet_path_search(n, ranks, labp, extp, len(out_labels), out, int(ntrials), int(seed),
+                                    float(temperature), pairs, ctypes.byref(ns), ctypes.byref(fl)),
+           "rosnet_path_search")
+    return [(pairs[2 * i], pairs[2 * i + 1]) for i in range(ns.value)], fl.value
+
+
+def slice_search(labels, extents, out_labels, path, nslice):
+    """Greedy choice of bonds to slice for a path: (labels, max entries, total flops)."""
+    n, ranks, labp, extp, out, keep = _label_args(labels, extents, out_labels)
+    flat = [int(x) for p in path for x in p]
+    parr = (ctypes.c_int32 * max(1, len(flat)))(*flat)
+    chosen = (ctypes.c_int64 * max(1, nslice))()
+    mx, fl = ctypes.c_double(), ctypes.c_double()
+    _check(lib().rosnet_slice_search(n, ranks, labp, extp, len(out_labels), out, len(path), parr,
+                                     int(nslice), chosen, ctypes.byref(mx), ctypes.byref(fl)),
+           "rosnet_slice_search")
+    return [chosen[i] for i in range(nslice)], mx.value, fl.value
+
+
+def sliced_networks(tensors, labels, out_labels, cut):
+    """The projections of a network onto every basis assignment of the bonds in
+    ``cut`` (Sec. II-B): each tensor carrying cut bonds becomes a view with
+    those axes fixed.  Returns [(assignment, Network)] in row-major order of
+    the assignments; views of equal projections share storage."""
+    import itertools
+    ext = {}
+    for t, l in zip(tensors, labels):
+        for x, e in zip(l, t.shape):
+            ext[x] = e
+    cut = list(cut)
+    out = []
+    for vals in itertools.product(*[range(ext[c]) for c in cut]):
+        val = dict(zip(cut, vals))
+        ts, ls = [], []
+        for t, l in zip(tensors, labels):
+            axes = [i for i, x in enumerate(l) if x in val]
+            if axes:
+                ts.append(t.fix(axes, [val[l[i]] for i in axes]))
+                ls.append(tuple(x for x in l if x not in val))
+            else:
+                ts.append(t)
+                ls.append(tuple(l))
+        out.append((vals, Network(ts, ls, out_labels)))
+    return out
+
+
+def sum_fp64(tensors, stream=None):
+    """Elementwise FP64 sum of equal-shape tensors (a complex128 BTensor)."""
+    _init()
+    arr = (ctypes.c_void_p * len(tensors))(*[t.handle.value for t in tensors])
+    h = ctypes.c_void_p()
+    _check(lib().rosnet_sum(len(tensors), arr, _stream(stream), ctypes.byref(h)), "rosnet_sum")
+    return BTensor(h.value)
+
+
 def contract(tensors, labels=None, out_labels=None, path=None, precision=PREC_DEFAULT, flags=0,
              max_block_entries=0, stream=None):
     """Contract a network along an SSA path on the GPU.
@@ -502,6 +603,37 @@ def contract(tensors, labels=None, out_labels=None, path=None, precision=PREC_DE
     _check(lib().rosnet_contract(ctypes.byref(net.net), ctypes.byref(pth), ctypes.byref(o),
                                  _stream(stream), ctypes.byref(h)), "rosnet_contract")
     return BTensor(h.value)
+
+
+def _batch_args(networks, paths):
+    nets = [n if isinstance(n, Network) else Network(*n) for n in networks]
+    arr = (_Network * len(nets))(*[n.net for n in nets])
+    cps = [n._cpath(p) for n, p in zip(nets, paths)]
+    parr = (_Path * len(nets))(*cps)
+    return nets, arr, parr
+
+
+def contract_batch(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_entries=0,
+                   stream=None):
+    """Contract several networks in one plan (common steps computed once);
+    ``networks``: Network objects or (tensors, labels, out_labels) tuples."""
+    _init()
+    nets, arr, parr = _batch_args(networks, paths)
+    o = _opts(precision, flags, max_block_entries)
+    outs = (ctypes.c_void_p * len(nets))()
+    _check(lib().rosnet_contract_batch(len(nets), arr, parr, ctypes.byref(o), _stream(stream), outs),
+           "rosnet_contract_batch")
+    return [BTensor(outs[i]) for i in range(len(nets))]
+
+
+def plan_stats(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_entries=0, stream=None):
+    """(steps requested, distinct steps planned, launches per call) of a planned batch."""
+    nets, arr, parr = _batch_args(networks, paths)
+    o = _opts(precision, flags, max_block_entries)
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().rosnet_plan_stats(len(nets), arr, parr, ctypes.byref(o), _stream(stream),
+                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "rosnet_plan_stats")
+    return a.value, b.value, c.value
 
 
 def sync(stream=None):

@@ -22,6 +22,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <random>
 #include <unordered_map>
 #include <vector>
 
@@ -56,33 +57,46 @@ void host_table(const ModeList &ml, int64_t total, int64_t *o0, int64_t *o1) {
     }
 }
 
+// A global operand id: >= 0 is a step index, < 0 is leaf slot (-1 - id).
 struct Step {
-    int ia, ib;          // operand ids (SSA)
+    int64_t ga, gb;      // operands
     int naxes;
     std::vector<int> axa, axb;
     Layout lay;          // layout of the result
     int wave;
+    int last_use = -1;   // last wave that reads it
     int64_t table_off;   // in int64 entries
-    size_t arena_off;    // for intermediates; SIZE_MAX for the final result
-    GettDesc desc;       // pointers patched per call
+    size_t arena_off;    // SIZE_MAX: written straight into output out_net
+    int out_net = -1;
+    GettDesc desc;
+};
+
+struct Leaf {
+    int net, t;          // first (network, tensor) holding this leaf
+};
+
+struct NetOut {
+    int64_t final_gid;   // step or leaf holding network i's result before its permutation
+    std::vector<int> perm;   // output axis o = result axis perm[o]
+    Layout out_lay;
+    bool direct = false; // the final step writes straight into the output tensor
 };
 
 struct Plan {
-    int ntensors = 0;
+    int nnet = 0;
     int dtype = 0;
     int precision = 0;
     int flags = 0;
     cudaStream_t stream = nullptr;
+    std::vector<Leaf> leaves;
     std::vector<Step> steps;
-    std::vector<int> final_perm;   // output axis i = final tensor axis final_perm[i]
-    bool final_direct = true;      // last step writes straight into the output
-    Layout out_lay;
+    std::vector<NetOut> outs;
     size_t arena_bytes = 0;
     DevBuf arena, tables, descs, partials, tcws;
-    // launch list: (kind, first desc, count, total tiles)
+    // launch list: (kind, first desc, count, total CTAs)
     struct Launch { int kind; int first; int count; int64_t tiles; size_t tc_ws_off; };
     std::vector<Launch> launches;
-    std::vector<int> desc_step;    // desc slot -> step index
+    std::vector<int> desc_step;       // desc slot -> step index
     std::vector<GettDesc> slot_desc;  // desc slot -> static descriptor fields
     // pinned staging ring for descriptor uploads
     static constexpr int kRing = 4;
@@ -101,7 +115,7 @@ struct Plan {
     static constexpr int kTimingRing = 4096;
     std::vector<cudaEvent_t> tev;              // 2 * kTimingRing, created lazily
     int tpos = 0;
-    size_t final_tmp_off = SIZE_MAX;  // arena offset of the last result if a permute follows
+    int64_t steps_requested = 0;               // path steps before common steps were merged
     ~Plan() {
         for (int i = 0; i < kRing; ++i) {
             if (ev[i]) { cudaEventSynchronize(ev[i]); cudaEventDestroy(ev[i]); }
@@ -121,34 +135,76 @@ auto &g_plans = *new std::unordered_map<std::string, std::unique_ptr<Plan>>();
 // (plan, ring slot) of every timed launch not yet drained
 auto &g_timing_log = *new std::vector<std::pair<Plan *, int>>();
 
-struct NetInfo {
-    std::vector<std::vector<int64_t>> labels;
+// Identity of a leaf's contents: storage address, plane stride and layout.
+struct LeafKey {
+    const void *data;
+    int64_t pstride;
+    int rank;
+    bool operator==(const LeafKey &o) const { return data == o.data && pstride == o.pstride && rank == o.rank; }
 };
 
-std::string plan_key(const rosnet_network *net, const rosnet_path *path, int prec, int flags,
-                     int64_t maxblk, cudaStream_t s) {
+// Leaf slots shared by equal tensors (same storage and layout) across the
+// networks of a call; slot[i][t] for tensor t of network i.
+std::vector<std::vector<int>> leaf_slots(int nnet, const rosnet_network *nets, std::vector<Leaf> *leaves) {
+    std::vector<std::vector<int>> slot(nnet);
+    std::vector<rosnet_btensor> rep;
+    std::unordered_map<const void *, std::vector<int>> by_ptr;
+    for (int i = 0; i < nnet; ++i) {
+        slot[i].resize(nets[i].ntensors);
+        for (int t = 0; t < nets[i].ntensors; ++t) {
+            rosnet_btensor x = nets[i].tensors[t];
+            int found = -1;
+            for (int c : by_ptr[x->data]) {
+                rosnet_btensor y = rep[c];
+                bool same = y->pstride == x->pstride && y->dtype == x->dtype && y->lay.rank == x->lay.rank;
+                for (int a = 0; same && a < x->lay.rank; ++a)
+                    same = y->lay.shape[a] == x->lay.shape[a] && y->lay.gstride[a] == x->lay.gstride[a] &&
+                           y->lay.lstride[a] == x->lay.lstride[a] && y->lay.block[a] == x->lay.block[a];
+                if (same) { found = c; break; }
+            }
+            if (found < 0) {
+                found = (int)rep.size();
+                rep.push_back(x);
+                by_ptr[x->data].push_back(found);
+                if (leaves) leaves->push_back({i, t});
+            }
+            slot[i][t] = found;
+        }
+    }
+    return slot;
+}
+
+std::string plan_key(int nnet, const rosnet_network *nets, const rosnet_path *paths,
+                     const std::vector<std::vector<int>> &slot, int prec, int flags, int64_t maxblk,
+                     cudaStream_t s) {
     std::string k;
-    k.reserve(64 + net->ntensors * 48 + path->nsteps * 8);
     auto put = [&k](int64_t v) { k.append((const char *)&v, sizeof(v)); };
-    put(net->ntensors);
+    put(nnet);
     put(prec);
     put(flags);
     put(maxblk);
     put((int64_t)(intptr_t)s);
-    for (int t = 0; t < net->ntensors; ++t) {
-        rosnet_btensor x = net->tensors[t];
-        put(x->dtype);
-        put(x->lay.rank);
-        for (int i = 0; i < x->lay.rank; ++i) {
-            put(x->lay.shape[i]);
-            put(x->lay.block[i]);
-            put(net->labels[t][i]);
+    for (int i = 0; i < nnet; ++i) {
+        const rosnet_network *net = &nets[i];
+        put(net->ntensors);
+        for (int t = 0; t < net->ntensors; ++t) {
+            rosnet_btensor x = net->tensors[t];
+            put(slot[i][t]);
+            put(x->dtype);
+            put(x->lay.rank);
+            for (int a = 0; a < x->lay.rank; ++a) {
+                put(x->lay.shape[a]);
+                put(x->lay.block[a]);
+                put(x->lay.gstride[a]);
+                put(x->lay.lstride[a]);
+                put(net->labels[t][a]);
+            }
         }
+        put(net->nout);
+        for (int o = 0; o < net->nout; ++o) put(net->out_labels[o]);
+        put(paths[i].nsteps);
+        for (int j = 0; j < 2 * paths[i].nsteps; ++j) put(paths[i].pairs[j]);
     }
-    put(net->nout);
-    for (int i = 0; i < net->nout; ++i) put(net->out_labels[i]);
-    put(path->nsteps);
-    for (int i = 0; i < 2 * path->nsteps; ++i) put(path->pairs[i]);
     return k;
 }
 
@@ -187,112 +243,162 @@ void validate_network(const rosnet_network *net) {
     }
 }
 
-std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *path, int prec,
-                                 int flags, int64_t maxblk, cudaStream_t s) {
-    const int nt = net->ntensors;
-    if (!path || path->nsteps != nt - 1 || (path->nsteps > 0 && !path->pairs))
-        RN_FAIL(ROSNET_ERR_INVALID_ARG, "a path must have ntensors - 1 steps");
+std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                 const std::vector<std::vector<int>> &slot, std::vector<Leaf> leaves,
+                                 int prec, int flags, int64_t maxblk, cudaStream_t s) {
     auto plan = std::make_unique<Plan>();
-    plan->ntensors = nt;
-    plan->dtype = net->tensors[0]->dtype;
+    plan->nnet = nnet;
+    plan->dtype = nets[0].tensors[0]->dtype;
     plan->precision = prec;
     plan->flags = flags;
     plan->stream = s;
-    const int total_ids = nt + path->nsteps;
-    std::vector<std::vector<int64_t>> labels(total_ids);
-    std::vector<Layout> lays(total_ids);
-    std::vector<int> wave(total_ids, 0), alive(total_ids, 0), last_use(total_ids, -1);
-    for (int t = 0; t < nt; ++t) {
-        labels[t].assign(net->labels[t], net->labels[t] + net->ranks[t]);
-        lays[t] = net->tensors[t]->lay;
-        alive[t] = 1;
-    }
-    plan->steps.resize(path->nsteps);
-    for (int st = 0; st < path->nsteps; ++st) {
-        int i = path->pairs[2 * st], j = path->pairs[2 * st + 1];
-        if (i < 0 || j < 0 || i >= nt + st || j >= nt + st || i == j || !alive[i] || !alive[j])
-            RN_FAIL(ROSNET_ERR_INVALID_ARG, "path step " + std::to_string(st) + " uses a dead or unknown id");
-        alive[i] = alive[j] = 0;
-        Step &S = plan->steps[st];
-        S.ia = i;
-        S.ib = j;
-        // every label shared by the pair is a bond carried by exactly these two
-        std::vector<int64_t> lc;
-        std::vector<int64_t> shc, blc;
-        const Layout &la = lays[i], &lb = lays[j];
-        std::vector<bool> ca(la.rank, false), cb(lb.rank, false);
-        for (int x = 0; x < la.rank; ++x)
-            for (int y = 0; y < lb.rank; ++y)
-                if (labels[i][x] == labels[j][y]) {
-                    if (la.shape[x] != lb.shape[y])
-                        RN_FAIL(ROSNET_ERR_SHAPE, "a bond has different extents on its two tensors");
-                    S.axa.push_back(x);
-                    S.axb.push_back(y);
-                    ca[x] = cb[y] = true;
-                }
-        S.naxes = (int)S.axa.size();
-        for (int x = 0; x < la.rank; ++x)
-            if (!ca[x]) { lc.push_back(labels[i][x]); shc.push_back(la.shape[x]); blc.push_back(la.block[x]); }
-        for (int y = 0; y < lb.rank; ++y)
-            if (!cb[y]) { lc.push_back(labels[j][y]); shc.push_back(lb.shape[y]); blc.push_back(lb.block[y]); }
-        if ((int)lc.size() > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "intermediate rank > 64");
-        if (maxblk > 0) {
-            int64_t bs = 1;
-            for (int64_t b : blc) bs *= b;
-            for (size_t x = 0; x < blc.size() && bs > maxblk; ++x) {
-                bs /= blc[x];
-                blc[x] = 1;
-            }
+    plan->leaves = std::move(leaves);
+    plan->outs.resize(nnet);
+    const int nleaf = (int)plan->leaves.size();
+    std::vector<int> leaf_last_use(nleaf, -1);
+    std::unordered_map<std::string, int64_t> seen;   // step signature -> step index
+    auto lay_of = [&](int64_t g) -> const Layout & {
+        if (g >= 0) return plan->steps[g].lay;
+        const Leaf &L = plan->leaves[-1 - g];
+        return nets[L.net].tensors[L.t]->lay;
+    };
+    auto wave_of = [&](int64_t g) { return g >= 0 ? plan->steps[g].wave : 0; };
+    for (int i = 0; i < nnet; ++i) {
+        const rosnet_network *net = &nets[i];
+        const rosnet_path *path = &paths[i];
+        if (net->tensors[0]->dtype != plan->dtype) RN_FAIL(ROSNET_ERR_DTYPE, "networks differ in dtype");
+        const int nt = net->ntensors;
+        if (path->nsteps != nt - 1 || (path->nsteps > 0 && !path->pairs))
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "a path must have ntensors - 1 steps");
+        plan->steps_requested += path->nsteps;
+        const int nid = nt + path->nsteps;
+        std::vector<std::vector<int64_t>> labels(nid);
+        std::vector<int64_t> gid(nid);
+        std::vector<int> alive(nid, 0);
+        for (int t = 0; t < nt; ++t) {
+            labels[t].assign(net->labels[t], net->labels[t] + net->ranks[t]);
+            gid[t] = -1 - slot[i][t];
+            alive[t] = 1;
         }
-        const int id = nt + st;
-        labels[id] = lc;
-        lays[id].init((int)lc.size(), shc.data(), blc.data());
-        S.lay = lays[id];
-        wave[id] = std::max(wave[i], wave[j]) + 1;
-        S.wave = wave[id];
-        last_use[i] = last_use[j] = S.wave;
-        alive[id] = 1;
-    }
-    const int final_id = nt + path->nsteps - 1;
-    const int last = path->nsteps > 0 ? final_id : 0;
-    // output permutation
-    const std::vector<int64_t> &fl = labels[last];
-    if ((int)fl.size() != net->nout) RN_FAIL(ROSNET_ERR_INVALID_ARG, "path leaves labels open that are not outputs");
-    plan->final_perm.resize(net->nout);
-    bool ident = true;
-    for (int o = 0; o < net->nout; ++o) {
-        int pos = -1;
-        for (int x = 0; x < (int)fl.size(); ++x)
-            if (fl[x] == net->out_labels[o]) pos = x;
-        if (pos < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "output label not produced by the path");
-        plan->final_perm[o] = pos;
-        if (pos != o) ident = false;
-    }
-    {
+        for (int st = 0; st < path->nsteps; ++st) {
+            const int li = path->pairs[2 * st], lj = path->pairs[2 * st + 1];
+            if (li < 0 || lj < 0 || li >= nt + st || lj >= nt + st || li == lj || !alive[li] || !alive[lj])
+                RN_FAIL(ROSNET_ERR_INVALID_ARG, "path step " + std::to_string(st) + " uses a dead or unknown id");
+            alive[li] = alive[lj] = 0;
+            const int64_t ga = gid[li], gb = gid[lj];
+            const Layout &la = lay_of(ga), &lb = lay_of(gb);
+            std::vector<int> axa, axb;
+            std::vector<int64_t> lc, shc, blc;
+            std::vector<bool> ca(la.rank, false), cb(lb.rank, false);
+            for (int x = 0; x < la.rank; ++x)
+                for (int y = 0; y < lb.rank; ++y)
+                    if (labels[li][x] == labels[lj][y]) {
+                        if (la.shape[x] != lb.shape[y])
+                            RN_FAIL(ROSNET_ERR_SHAPE, "a bond has different extents on its two tensors");
+                        axa.push_back(x);
+                        axb.push_back(y);
+                        ca[x] = cb[y] = true;
+                    }
+            for (int x = 0; x < la.rank; ++x)
+                if (!ca[x]) { lc.push_back(labels[li][x]); shc.push_back(la.shape[x]); blc.push_back(la.block[x]); }
+            for (int y = 0; y < lb.rank; ++y)
+                if (!cb[y]) { lc.push_back(labels[lj][y]); shc.push_back(lb.shape[y]); blc.push_back(lb.block[y]); }
+            if ((int)lc.size() > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "intermediate rank > 64");
+            if (maxblk > 0) {
+                int64_t bs = 1;
+                for (int64_t b : blc) bs *= b;
+                for (size_t x = 0; x < blc.size() && bs > maxblk; ++x) {
+                    bs /= blc[x];
+                    blc[x] = 1;
+                }
+            }
+            // the same operands contracted the same way give the same tensor:
+            // compute it once (slices share every step that no sliced bond reaches)
+            std::string sig;
+            auto put = [&sig](int64_t v) { sig.append((const char *)&v, sizeof(v)); };
+            put(ga);
+            put(gb);
+            put((int64_t)axa.size());
+            for (size_t x = 0; x < axa.size(); ++x) { put(axa[x]); put(axb[x]); }
+            for (size_t x = 0; x < blc.size(); ++x) put(blc[x]);
+            auto it = seen.find(sig);
+            int64_t g;
+            if (it != seen.end()) {
+                g = it->second;
+            } else {
+                Step S;
+                S.ga = ga;
+                S.gb = gb;
+                S.naxes = (int)axa.size();
+                S.axa = axa;
+                S.axb = axb;
+                S.lay.init((int)lc.size(), shc.data(), blc.data());
+                S.wave = std::max(wave_of(ga), wave_of(gb)) + 1;
+                S.arena_off = 0;
+                g = (int64_t)plan->steps.size();
+                plan->steps.push_back(std::move(S));
+                seen.emplace(std::move(sig), g);
+                for (int64_t op : {ga, gb}) {
+                    if (op >= 0) plan->steps[op].last_use = std::max(plan->steps[op].last_use, plan->steps[g].wave);
+                    else leaf_last_use[-1 - op] = std::max(leaf_last_use[-1 - op], plan->steps[g].wave);
+                }
+            }
+            const int id = nt + st;
+            gid[id] = g;
+            labels[id] = lc;
+            alive[id] = 1;
+        }
+        // result of network i and its output permutation
+        const int last = path->nsteps > 0 ? nt + path->nsteps - 1 : 0;
+        const std::vector<int64_t> &fl = labels[last];
+        if ((int)fl.size() != net->nout)
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "path leaves labels open that are not outputs");
+        NetOut &O = plan->outs[i];
+        O.final_gid = gid[last];
+        O.perm.resize(net->nout);
+        bool ident = true;
+        for (int o = 0; o < net->nout; ++o) {
+            int pos = -1;
+            for (int x = 0; x < (int)fl.size(); ++x)
+                if (fl[x] == net->out_labels[o]) pos = x;
+            if (pos < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "output label not produced by the path");
+            O.perm[o] = pos;
+            if (pos != o) ident = false;
+        }
+        const Layout &fin = lay_of(O.final_gid);
         std::vector<int64_t> osh(net->nout), obl(net->nout);
         for (int o = 0; o < net->nout; ++o) {
-            osh[o] = lays[last].shape[plan->final_perm[o]];
-            obl[o] = lays[last].block[plan->final_perm[o]];
+            osh[o] = fin.shape[O.perm[o]];
+            obl[o] = fin.block[O.perm[o]];
         }
-        plan->out_lay.init(net->nout, osh.data(), obl.data());
+        O.out_lay.init(net->nout, osh.data(), obl.data());
+        O.direct = ident && O.final_gid >= 0;
     }
-    plan->final_direct = ident && path->nsteps > 0;
-
-    // arena: intermediates (and the final result if it must be permuted)
+    // a final step writes straight into its output unless another network's
+    // output or a later step also needs it
+    const int end_wave = 1 << 30;
+    for (int i = 0; i < nnet; ++i) {
+        NetOut &O = plan->outs[i];
+        if (O.final_gid < 0) continue;
+        Step &S = plan->steps[O.final_gid];
+        if (O.direct && S.out_net < 0 && S.last_use < 0) {
+            S.out_net = i;
+            S.arena_off = SIZE_MAX;
+        } else {
+            O.direct = false;
+            S.last_use = end_wave;   // copied into the output after the last wave
+        }
+    }
+    // arena: every step not written straight into an output, packed by lifetime
     struct Slot { size_t off, size; int from, to; };
     std::vector<Slot> placed;
     const size_t el2 = 2 * (plan->dtype == ROSNET_C64 ? 4 : 8);
-    for (int st = 0; st < path->nsteps; ++st) {
-        const int id = nt + st;
-        Step &S = plan->steps[st];
-        if (id == final_id && plan->final_direct) {
-            S.arena_off = SIZE_MAX;
-            continue;
-        }
+    for (size_t g = 0; g < plan->steps.size(); ++g) {
+        Step &S = plan->steps[g];
+        if (S.arena_off == SIZE_MAX) continue;
         size_t bytes = ((size_t)S.lay.numel * el2 + 255) & ~(size_t)255;
         if (bytes == 0) bytes = 256;
-        int from = S.wave, to = (id == final_id) ? S.wave + 1 : last_use[id];
-        // first fit among slots whose lifetime overlaps
+        const int from = S.wave, to = S.last_use < 0 ? S.wave : S.last_use;
         std::vector<std::pair<size_t, size_t>> busy;
         for (auto &p : placed)
             if (!(p.to < from || p.from > to)) busy.push_back({p.off, p.off + p.size});
@@ -305,21 +411,20 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
         placed.push_back({off, bytes, from, to});
         S.arena_off = off;
         plan->arena_bytes = std::max(plan->arena_bytes, off + bytes);
-        if (id == final_id) plan->final_tmp_off = off;
     }
-    // tables (host-built, one upload)
-    std::vector<GettView> views(path->nsteps);
+    // offset tables (host-built, one upload)
+    std::vector<GettView> views(plan->steps.size());
     int64_t tab_entries = 0;
-    for (int st = 0; st < path->nsteps; ++st) {
-        Step &S = plan->steps[st];
-        views[st] = make_view(lays[S.ia], lays[S.ib], S.lay, S.naxes, S.axa.data(), S.axb.data());
+    for (size_t g = 0; g < plan->steps.size(); ++g) {
+        Step &S = plan->steps[g];
+        views[g] = make_view(lay_of(S.ga), lay_of(S.gb), S.lay, S.naxes, S.axa.data(), S.axb.data());
         S.table_off = tab_entries;
-        tab_entries += (int64_t)table_entries(views[st]);
+        tab_entries += (int64_t)table_entries(views[g]);
     }
     std::vector<int64_t> htab(std::max<int64_t>(tab_entries, 1));
-    for (int st = 0; st < path->nsteps; ++st) {
-        const GettView &v = views[st];
-        int64_t *t = htab.data() + plan->steps[st].table_off;
+    for (size_t g = 0; g < plan->steps.size(); ++g) {
+        const GettView &v = views[g];
+        int64_t *t = htab.data() + plan->steps[g].table_off;
         host_table(v.M, v.Mtot, t, t + v.Mtot);
         t += 2 * v.Mtot;
         host_table(v.N, v.Ntot, t, t + v.Ntot);
@@ -335,13 +440,14 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
     const int64_t *dtab = (const int64_t *)plan->tables.p;
     std::map<std::pair<int, int>, std::vector<int>> groups;
     std::map<int, std::vector<int>> split_of_wave, atomic_of_wave;
-    for (int st = 0; st < path->nsteps; ++st) {
-        Step &S = plan->steps[st];
+    const int red = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
+                    : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
+                    : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
+    for (size_t g = 0; g < plan->steps.size(); ++g) {
+        Step &S = plan->steps[g];
+        const int st = (int)g;
         memset(&S.desc, 0, sizeof(S.desc));
-        fill_desc_tables(S.desc, views[st], dtab + S.table_off);
-        const int red = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
-                        : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
-                        : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
+        fill_desc_tables(S.desc, views[g], dtab + S.table_off);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
         // tensor-core problems carry their own tensor maps: one launch each
@@ -424,14 +530,22 @@ std::unique_ptr<Plan> build_plan(const rosnet_network *net, const rosnet_path *p
     return plan;
 }
 
-void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream_t s) {
-    const int nt = P.ntensors;
+void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStream_t s) {
     char *arena = (char *)P.arena.p;
-    auto ptr_of = [&](int id) -> void * {
-        if (id < nt) return net->tensors[id]->data;
-        const Step &S = P.steps[id - nt];
-        if (S.arena_off == SIZE_MAX) return out->data;
+    auto leaf_of = [&](int64_t g) -> rosnet_btensor {
+        const Leaf &L = P.leaves[-1 - g];
+        return nets[L.net].tensors[L.t];
+    };
+    auto ptr_of = [&](int64_t g) -> void * {
+        if (g < 0) return leaf_of(g)->data;
+        const Step &S = P.steps[g];
+        if (S.arena_off == SIZE_MAX) return outs[S.out_net]->data;
         return arena + S.arena_off;
+    };
+    auto pstride_of = [&](int64_t g) -> int64_t {
+        if (g < 0) return leaf_of(g)->pstride;
+        const Step &S = P.steps[g];
+        return S.arena_off == SIZE_MAX ? outs[S.out_net]->pstride : S.lay.numel;
     };
     // patch descriptors into the next pinned staging buffer; upload only the
     // range whose operand addresses changed since the last call
@@ -446,13 +560,8 @@ void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream
         const int st = P.desc_step[i];
         const Step &S = P.steps[st];
         GettDesc d = P.slot_desc[i];
-        auto pstride_of = [&](int id) -> int64_t {
-            if (id < nt) return net->tensors[id]->pstride;
-            const Step &T = P.steps[id - nt];
-            return T.arena_off == SIZE_MAX ? out->pstride : T.lay.numel;
-        };
-        bind_operands(d, ptr_of(S.ia), ptr_of(S.ib), ptr_of(nt + st), pstride_of(S.ia), pstride_of(S.ib),
-                      pstride_of(nt + st));
+        bind_operands(d, ptr_of(S.ga), ptr_of(S.gb), ptr_of(st), pstride_of(S.ga), pstride_of(S.gb),
+                      pstride_of(st));
         h[i] = d;
         if (!P.mirror_valid || P.mirror[i].a != d.a || P.mirror[i].b != d.b || P.mirror[i].c != d.c) {
             lo = std::min(lo, i);
@@ -549,12 +658,13 @@ void run_plan(Plan &P, const rosnet_network *net, rosnet_btensor out, cudaStream
         enqueue(false);
     }
     if (timing) g_timing_log.push_back({&P, slot});
-    if (!P.final_direct) {
-        const int last = P.steps.empty() ? 0 : nt + (int)P.steps.size() - 1;
-        const Layout &src = P.steps.empty() ? net->tensors[0]->lay : P.steps.back().lay;
-        const int64_t sps = P.steps.empty() ? net->tensors[0]->pstride : src.numel;
-        launch_relayout(src, out->lay, P.final_perm.data(), P.dtype, ptr_of(last), sps, out->data,
-                        out->pstride, s);
+    // results that are not written in place: permuted, shared, or a lone leaf
+    for (int i = 0; i < P.nnet; ++i) {
+        const NetOut &O = P.outs[i];
+        if (O.direct) continue;
+        const Layout &src = O.final_gid >= 0 ? P.steps[O.final_gid].lay : leaf_of(O.final_gid)->lay;
+        launch_relayout(src, outs[i]->lay, O.perm.data(), P.dtype, ptr_of(O.final_gid),
+                        pstride_of(O.final_gid), outs[i]->data, outs[i]->pstride, s);
     }
 }
 
@@ -566,12 +676,7 @@ using namespace rosnet;
 
 extern "C" {
 
-rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path,
-                              const rosnet_opts *opts, void *stream, rosnet_btensor *out) {
-    if (!out) return ROSNET_ERR_INVALID_ARG;
-    *out = nullptr;
-    RN_API_BEGIN
-    cudaStream_t s = (cudaStream_t)stream;
+static void precheck_network(const rosnet_network *net, const rosnet_path *path) {
     if (!net || net->ntensors < 1 || !net->tensors || !net->ranks || !net->labels)
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed network");
     for (int t = 0; t < net->ntensors; ++t)
@@ -582,30 +687,84 @@ rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed output labels");
     if (!path || path->nsteps < 0 || (path->nsteps > 0 && !path->pairs))
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL path");
-    const int prec = check_precision(opts, net->tensors[0]->dtype);
+}
+
+static void contract_batch(int nnet, const rosnet_network *nets, const rosnet_path *paths,
+                           const rosnet_opts *opts, cudaStream_t s, rosnet_btensor *outs) {
+    if (nnet < 1 || !nets || !paths) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no networks");
+    for (int i = 0; i < nnet; ++i) precheck_network(&nets[i], &paths[i]);
+    const int prec = check_precision(opts, nets[0].tensors[0]->dtype);
     const int flags = opts ? opts->flags : 0;
+    (void)check_reduce(opts);
     const int64_t maxblk = opts ? opts->max_block_entries : 0;
     if (maxblk < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "negative max_block_entries");
-    std::string key = plan_key(net, path, prec, flags, maxblk, s);
+    std::vector<Leaf> leaves;
+    auto slot = leaf_slots(nnet, nets, &leaves);
+    std::string key = plan_key(nnet, nets, paths, slot, prec, flags, maxblk, s);
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
     Plan *P;
     if (it == g_plans.end()) {
-        validate_network(net);  // the key encodes everything validated here
-        auto np = build_plan(net, path, prec, flags, maxblk, s);
+        for (int i = 0; i < nnet; ++i) validate_network(&nets[i]);  // the key encodes all of it
+        auto np = build_plan(nnet, nets, paths, slot, std::move(leaves), prec, flags, maxblk, s);
         P = np.get();
         g_plans.emplace(std::move(key), std::move(np));
     } else {
         P = it->second.get();
+        P->leaves = std::move(leaves);   // same sharing pattern; refresh the representatives
     }
-    rosnet_btensor C = new_tensor(P->out_lay.rank, P->out_lay.shape, P->out_lay.block, P->dtype, s);
+    std::vector<rosnet_btensor> made;
     try {
-        run_plan(*P, net, C, s);
+        for (int i = 0; i < nnet; ++i) {
+            const Layout &L = P->outs[i].out_lay;
+            made.push_back(new_tensor(L.rank, L.shape, L.block, P->dtype, s));
+        }
+        run_plan(*P, nets, made.data(), s);
     } catch (...) {
-        free_tensor(C);
+        for (auto t : made) free_tensor(t);
         throw;
     }
-    *out = C;
+    for (int i = 0; i < nnet; ++i) outs[i] = made[i];
+}
+
+rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path,
+                              const rosnet_opts *opts, void *stream, rosnet_btensor *out) {
+    if (!out) return ROSNET_ERR_INVALID_ARG;
+    *out = nullptr;
+    RN_API_BEGIN
+    contract_batch(1, net, path, opts, (cudaStream_t)stream, out);
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_contract_batch(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                    const rosnet_opts *opts, void *stream, rosnet_btensor *outs) {
+    if (!outs || nnet < 1) return ROSNET_ERR_INVALID_ARG;
+    for (int i = 0; i < nnet; ++i) outs[i] = nullptr;
+    RN_API_BEGIN
+    contract_batch(nnet, nets, paths, opts, (cudaStream_t)stream, outs);
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                const rosnet_opts *opts, void *stream, int64_t *steps_requested,
+                                int64_t *steps_planned, int64_t *launches) {
+    RN_API_BEGIN
+    if (nnet < 1 || !nets || !paths) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no networks");
+    for (int i = 0; i < nnet; ++i) precheck_network(&nets[i], &paths[i]);
+    const int prec = check_precision(opts, nets[0].tensors[0]->dtype);
+    const int flags = opts ? opts->flags : 0;
+    const int64_t maxblk = opts ? opts->max_block_entries : 0;
+    std::vector<Leaf> leaves;
+    auto slot = leaf_slots(nnet, nets, &leaves);
+    std::string key = plan_key(nnet, nets, paths, slot, prec, flags, maxblk, (cudaStream_t)stream);
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it == g_plans.end()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no cached plan for these networks");
+    if (steps_requested) *steps_requested = it->second->steps_requested;
+    if (steps_planned) *steps_planned = (int64_t)it->second->steps.size();
+    if (launches) *launches = (int64_t)it->second->launches.size();
     return ROSNET_OK;
     RN_API_END
 }
@@ -732,6 +891,192 @@ rosnet_status rosnet_path_greedy_extents(int32_t ntensors, const int32_t *ranks,
         ++next;
     }
     *nsteps = nt - 1;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+// ---------------------------------------------------------------------------
+// host-side path and slicing heuristics
+// ---------------------------------------------------------------------------
+namespace {
+
+struct LabelNet {
+    int nt;
+    std::vector<std::vector<int64_t>> lab;
+    std::unordered_map<int64_t, double> ext;
+};
+
+LabelNet label_net(int32_t ntensors, const int32_t *ranks, const int64_t *const *labels,
+                   const int64_t *const *extents) {
+    if (ntensors < 1 || !ranks || !labels || !extents) RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed network");
+    LabelNet n;
+    n.nt = ntensors;
+    n.lab.resize(ntensors);
+    std::unordered_map<int64_t, int> cnt;
+    for (int t = 0; t < ntensors; ++t) {
+        if (ranks[t] < 0 || ranks[t] > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "bad rank");
+        if (ranks[t] > 0 && (!labels[t] || !extents[t])) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL labels");
+        n.lab[t].assign(labels[t], labels[t] + ranks[t]);
+        for (int i = 0; i < ranks[t]; ++i) {
+            auto it = n.ext.find(labels[t][i]);
+            if (it != n.ext.end() && it->second != (double)extents[t][i])
+                RN_FAIL(ROSNET_ERR_SHAPE, "a label has two different extents");
+            n.ext[labels[t][i]] = (double)extents[t][i];
+            if (++cnt[labels[t][i]] > 2) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "a label carried by more than two tensors");
+        }
+    }
+    return n;
+}
+
+// Max intermediate entries and total 8*M*N*K flops of a path, with the
+// labels in `cut` fixed (sliced: extent 1).
+std::pair<double, double> path_cost(const LabelNet &n, const int32_t *pairs, int nsteps,
+                                    const std::vector<int64_t> &cut) {
+    std::unordered_map<int64_t, bool> isc;
+    for (int64_t x : cut) isc[x] = true;
+    auto e = [&](int64_t x) { return isc.count(x) ? 1.0 : n.ext.at(x); };
+    std::vector<std::vector<int64_t>> live(n.nt + nsteps);
+    for (int t = 0; t < n.nt; ++t) live[t] = n.lab[t];
+    double mx = 0, tot = 0;
+    for (int st = 0; st < nsteps; ++st) {
+        const auto &la = live[pairs[2 * st]], &lb = live[pairs[2 * st + 1]];
+        double all = 1, out = 1;
+        std::vector<int64_t> lc;
+        for (int64_t x : la) {
+            all *= e(x);
+            if (std::find(lb.begin(), lb.end(), x) == lb.end()) { lc.push_back(x); out *= e(x); }
+        }
+        for (int64_t x : lb)
+            if (std::find(la.begin(), la.end(), x) == la.end()) { lc.push_back(x); out *= e(x); all *= e(x); }
+        tot += 8.0 * all;
+        mx = std::max(mx, out);
+        live[n.nt + st] = std::move(lc);
+    }
+    return {mx, tot};
+}
+
+}  // namespace
+
+rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks, const int64_t *const *labels,
+                                 const int64_t *const *extents, int32_t nout, const int64_t *out_labels,
+                                 int32_t ntrials, uint64_t seed, double temperature, int32_t *pairs_out,
+                                 int32_t *nsteps, double *flops) {
+    if (!pairs_out || !nsteps || ntrials < 1 || temperature < 0) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    LabelNet n = label_net(ntensors, ranks, labels, extents);
+    const int ns = ntensors - 1;
+    // trial 0: the deterministic greedy min-size path
+    std::vector<int32_t> best(2 * std::max(ns, 0)), cur(2 * std::max(ns, 0));
+    int32_t k = 0;
+    rosnet_status rc = rosnet_path_greedy_extents(ntensors, ranks, labels, extents, nout, out_labels,
+                                                  best.data(), &k);
+    if (rc != ROSNET_OK) return rc;
+    double best_flops = path_cost(n, best.data(), ns, {}).second;
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U(1e-12, 1.0);
+    for (int trial = 1; trial < ntrials; ++trial) {
+        // greedy on cost = size(out) - size(a) - size(b), perturbed by Gumbel
+        // noise of relative scale `temperature`
+        std::vector<std::vector<int64_t>> live(2 * ntensors);
+        std::unordered_map<int64_t, std::vector<int>> holders;
+        std::vector<bool> alive(2 * ntensors, false);
+        for (int t = 0; t < ntensors; ++t) {
+            live[t] = n.lab[t];
+            alive[t] = true;
+            for (int64_t x : n.lab[t]) holders[x].push_back(t);
+        }
+        auto size_of = [&](const std::vector<int64_t> &l) {
+            double v = 1;
+            for (int64_t x : l) v *= n.ext.at(x);
+            return v;
+        };
+        int next = ntensors;
+        for (int st = 0; st < ns; ++st) {
+            double bc = 0;
+            int ba = -1, bb = -1;
+            for (auto &kv : holders) {
+                if (kv.second.size() != 2) continue;
+                const int a = std::min(kv.second[0], kv.second[1]), b = std::max(kv.second[0], kv.second[1]);
+                double out = 1;
+                for (int64_t x : live[a])
+                    if (std::find(live[b].begin(), live[b].end(), x) == live[b].end()) out *= n.ext.at(x);
+                for (int64_t x : live[b])
+                    if (std::find(live[a].begin(), live[a].end(), x) == live[a].end()) out *= n.ext.at(x);
+                double c = out - size_of(live[a]) - size_of(live[b]);
+                c -= temperature * std::log(-std::log(U(rng))) * std::max(1.0, std::fabs(c));
+                if (ba < 0 || c < bc || (c == bc && (a < ba || (a == ba && b < bb)))) { bc = c; ba = a; bb = b; }
+            }
+            if (ba < 0)   // disconnected: the two lowest live ids
+                for (int i = 0; i < next && bb < 0; ++i)
+                    if (alive[i]) { if (ba < 0) ba = i; else bb = i; }
+            std::vector<int64_t> r;
+            for (int64_t x : live[ba])
+                if (std::find(live[bb].begin(), live[bb].end(), x) == live[bb].end()) r.push_back(x);
+            for (int64_t x : live[bb])
+                if (std::find(live[ba].begin(), live[ba].end(), x) == live[ba].end()) r.push_back(x);
+            for (int64_t x : live[ba]) { auto &h = holders[x]; h.erase(std::remove(h.begin(), h.end(), ba), h.end()); }
+            for (int64_t x : live[bb]) { auto &h = holders[x]; h.erase(std::remove(h.begin(), h.end(), bb), h.end()); }
+            alive[ba] = alive[bb] = false;
+            live[next] = r;
+            alive[next] = true;
+            for (int64_t x : r) holders[x].push_back(next);
+            cur[2 * st] = ba;
+            cur[2 * st + 1] = bb;
+            ++next;
+        }
+        const double f = path_cost(n, cur.data(), ns, {}).second;
+        if (f < best_flops) { best_flops = f; best = cur; }
+    }
+    std::copy(best.begin(), best.end(), pairs_out);
+    *nsteps = ns;
+    if (flops) *flops = best_flops;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_slice_search(int32_t ntensors, const int32_t *ranks, const int64_t *const *labels,
+                                  const int64_t *const *extents, int32_t nout, const int64_t *out_labels,
+                                  int32_t nsteps, const int32_t *pairs, int32_t nslice, int64_t *chosen,
+                                  double *max_entries, double *flops) {
+    if (!chosen || nslice < 0 || !pairs || nsteps != ntensors - 1 || (nout > 0 && !out_labels))
+        return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    LabelNet n = label_net(ntensors, ranks, labels, extents);
+    std::unordered_map<int64_t, int> cnt;
+    for (auto &l : n.lab) for (int64_t x : l) cnt[x]++;
+    std::vector<int64_t> bonds;
+    for (auto &kv : cnt) {
+        bool is_out = false;
+        for (int o = 0; o < nout; ++o) is_out |= out_labels[o] == kv.first;
+        if (kv.second == 2 && !is_out) bonds.push_back(kv.first);
+    }
+    std::sort(bonds.begin(), bonds.end());
+    if ((size_t)nslice > bonds.size()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "more slices than bonds");
+    std::vector<int64_t> cut;
+    std::pair<double, double> cost = path_cost(n, pairs, nsteps, cut);
+    for (int r = 0; r < nslice; ++r) {
+        int64_t bl = 0;
+        std::pair<double, double> bc{0, 0};
+        bool have = false;
+        for (int64_t b : bonds) {
+            if (std::find(cut.begin(), cut.end(), b) != cut.end()) continue;
+            cut.push_back(b);
+            auto c = path_cost(n, pairs, nsteps, cut);
+            cut.pop_back();
+            // the slice count multiplies the flops by the sliced extent
+            c.second *= n.ext.at(b);
+            if (!have || c < bc) { bc = c; bl = b; have = true; }
+        }
+        cut.push_back(bl);
+        cost = bc;
+        chosen[r] = bl;
+    }
+    if (max_entries) *max_entries = path_cost(n, pairs, nsteps, cut).first;
+    if (flops) {
+        double mult = 1;
+        for (int64_t x : cut) mult *= n.ext.at(x);
+        *flops = path_cost(n, pairs, nsteps, cut).second * mult;
+    }
     return ROSNET_OK;
     RN_API_END
 }

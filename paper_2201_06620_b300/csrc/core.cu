@@ -8,7 +8,9 @@
 
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -261,6 +263,25 @@ void launch_relayout(const Layout &src, const Layout &dst, const int *perm, int 
     launch_copy<2>(cm, dst.numel, dtype, sp, spstride, dp, dpstride, s);
 }
 
+// out[i] = sum_j in_j[i] in FP64, j in order (deterministic); inputs complex64
+// or complex128 planar with plane strides ps[j], output complex128 planar.
+template <typename T>
+__global__ void __launch_bounds__(256) sum_fp64_kernel(const T *const *__restrict__ in,
+                                                       const int64_t *__restrict__ ps, int n,
+                                                       int64_t numel, double *__restrict__ out,
+                                                       int64_t ops) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < numel;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double sr = 0.0, si = 0.0;
+        for (int j = 0; j < n; ++j) {
+            sr += (double)in[j][i];
+            si += (double)in[j][i + ps[j]];
+        }
+        out[i] = sr;
+        out[i + ops] = si;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // tensors
 // ---------------------------------------------------------------------------
@@ -354,6 +375,102 @@ rosnet_status rosnet_btensor_upload_range(rosnet_btensor t, const void *host, in
     RN_API_END
 }
 
+rosnet_status rosnet_sum(int32_t n, const rosnet_btensor *ts, void *stream, rosnet_btensor *out) {
+    if (!out) return ROSNET_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || !ts) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    const rosnet_btensor t0 = ts[0];
+    if (!t0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL tensor");
+    for (int j = 0; j < n; ++j) {
+        const rosnet_btensor t = ts[j];
+        if (!t) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL tensor");
+        if (t->dtype != t0->dtype) RN_FAIL(ROSNET_ERR_DTYPE, "summands differ in dtype");
+        bool same = t->lay.rank == t0->lay.rank;
+        for (int a = 0; same && a < t->lay.rank; ++a)
+            same = t->lay.shape[a] == t0->lay.shape[a] && t->lay.block[a] == t0->lay.block[a] &&
+                   t->lay.gstride[a] == t0->lay.gstride[a] && t->lay.lstride[a] == t0->lay.lstride[a];
+        if (!same) RN_FAIL(ROSNET_ERR_SHAPE, "summands differ in shape, blocks or strides");
+    }
+    Layout canon;
+    canon.init(t0->lay.rank, t0->lay.shape, t0->lay.block);
+    for (int a = 0; a < canon.rank; ++a)
+        if (canon.gstride[a] != t0->lay.gstride[a] || canon.lstride[a] != t0->lay.lstride[a])
+            RN_FAIL(ROSNET_ERR_UNSUPPORTED, "summands must be dense block-major tensors");
+    rosnet_btensor C = new_tensor(canon.rank, canon.shape, canon.block, ROSNET_C128, s);
+    try {
+        std::vector<const void *> hp(n);
+        std::vector<int64_t> hs(n);
+        for (int j = 0; j < n; ++j) {
+            hp[j] = ts[j]->data;
+            hs[j] = ts[j]->pstride;
+        }
+        DevBuf dp(n * sizeof(void *), s), dps(n * sizeof(int64_t), s);
+        RN_CHECK_CUDA(cudaMemcpyAsync(dp.p, hp.data(), n * sizeof(void *), cudaMemcpyHostToDevice, s));
+        RN_CHECK_CUDA(cudaMemcpyAsync(dps.p, hs.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        const int64_t numel = canon.numel;
+        const int grid = (int)std::min<int64_t>(std::max<int64_t>((numel + 255) / 256, 1), 148 * 8);
+        if (numel > 0) {
+            if (t0->dtype == ROSNET_C64)
+                sum_fp64_kernel<float><<<grid, 256, 0, s>>>((const float *const *)dp.p, (const int64_t *)dps.p,
+                                                            n, numel, (double *)C->data, C->pstride);
+            else
+                sum_fp64_kernel<double><<<grid, 256, 0, s>>>((const double *const *)dp.p,
+                                                             (const int64_t *)dps.p, n, numel,
+                                                             (double *)C->data, C->pstride);
+            g_launches++;
+            RN_CHECK_CUDA(cudaGetLastError());
+        }
+    } catch (...) {
+        free_tensor(C);
+        throw;
+    }
+    *out = C;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_fix(rosnet_btensor t, int nfix, const int *axes, const int64_t *values,
+                                 rosnet_btensor *view) {
+    if (!view) return ROSNET_ERR_INVALID_ARG;
+    *view = nullptr;
+    if (!t || nfix < 0 || nfix > t->lay.rank || (nfix > 0 && (!axes || !values))) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    bool fixed[kMaxRank] = {false};
+    int64_t off = 0;
+    for (int j = 0; j < nfix; ++j) {
+        const int a = axes[j];
+        if (a < 0 || a >= t->lay.rank || fixed[a]) RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad or repeated axis");
+        if (values[j] < 0 || values[j] >= t->lay.shape[a]) RN_FAIL(ROSNET_ERR_INVALID_ARG, "index out of range");
+        fixed[a] = true;
+        const int64_t b = t->lay.block[a];
+        off += (values[j] / b) * t->lay.gstride[a] + (values[j] % b) * t->lay.lstride[a];
+    }
+    rosnet_btensor v = new rosnet_btensor_s();
+    Layout &L = v->lay;
+    L.rank = 0;
+    L.numel = 1;
+    for (int a = 0; a < t->lay.rank; ++a) {
+        if (fixed[a]) continue;
+        L.shape[L.rank] = t->lay.shape[a];
+        L.block[L.rank] = t->lay.block[a];
+        L.gstride[L.rank] = t->lay.gstride[a];
+        L.lstride[L.rank] = t->lay.lstride[a];
+        L.numel *= t->lay.shape[a];
+        L.rank++;
+    }
+    v->dtype = t->dtype;
+    v->elsize = t->elsize;
+    v->data = (char *)t->data + off * t->elsize;
+    v->pstride = t->pstride;
+    v->stream = t->stream;
+    v->owned = false;
+    *view = v;
+    return ROSNET_OK;
+    RN_API_END
+}
+
 rosnet_status rosnet_btensor_block(rosnet_btensor t, const int64_t *grid_coords, rosnet_btensor *view) {
     if (!view) return ROSNET_ERR_INVALID_ARG;
     *view = nullptr;
@@ -398,11 +515,15 @@ rosnet_status rosnet_btensor_slice(rosnet_btensor t, int nfix, const int64_t *va
         off += values[i] * t->lay.gstride[i];
     }
     rosnet_btensor v = new rosnet_btensor_s();
-    try {
-        v->lay.init(t->lay.rank - nfix, t->lay.shape + nfix, t->lay.block + nfix);
-    } catch (...) {
-        delete v;
-        throw;
+    Layout &L = v->lay;
+    L.rank = t->lay.rank - nfix;
+    L.numel = 1;
+    for (int a = 0; a < L.rank; ++a) {
+        L.shape[a] = t->lay.shape[a + nfix];
+        L.block[a] = t->lay.block[a + nfix];
+        L.gstride[a] = t->lay.gstride[a + nfix];
+        L.lstride[a] = t->lay.lstride[a + nfix];
+        L.numel *= L.shape[a];
     }
     v->dtype = t->dtype;
     v->elsize = t->elsize;

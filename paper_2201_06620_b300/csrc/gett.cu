@@ -351,29 +351,23 @@ struct Vec16<double> {
     static constexpr int n = 2;
 };
 
-template <typename T, int BM, int BN, int BK, int STAGES>
-__global__ void __launch_bounds__(256, 1) gett_tiled_kernel(const __grid_constant__ GroupArgs g) {
+// The tile body, specialised on whether A (B) is read along m (n) or along k:
+// with those known at compile time every thread's gather addresses reduce to
+// one base offset per operand plus compile-time strides.
+template <typename T, int BM, int BN, int BK, int STAGES, bool amf, bool bnf>
+__device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int64_t *sCM, int64_t *sCN) {
     using Cfg = TiledCfg<T, BM, BN, BK, STAGES>;
     using V = typename Vec16<T>::type;
     constexpr int NT = Cfg::NT, TM = Cfg::TM, TN = Cfg::TN, LA = Cfg::LA, LB = Cfg::LB;
     constexpr int RA = Cfg::RA, RB = Cfg::RB;
     constexpr int PA = BK * RA, PB = BK * RB;   // one plane of one stage
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *As = reinterpret_cast<T *>(smem_raw);          // [STAGES][2 planes][BK][RA]
-    T *Bs = As + STAGES * 2 * PA;                       // [STAGES][2 planes][BK][RB]
-    __shared__ GettDesc sd;
-    __shared__ int64_t sCM[BM], sCN[BN];
-
     const int tid = threadIdx.x;
-    if (tid == 0) load_desc(g, sd);
-    __syncthreads();
     const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
     const int64_t ntile = sd.tiles_m * sd.tiles_n;
     const int split = (int)(tile / ntile);
     const int64_t t2 = tile - (int64_t)split * ntile;
     const int64_t m0 = (t2 % sd.tiles_m) * BM, n0 = (t2 / sd.tiles_m) * BN;
     const int64_t M = sd.M, N = sd.N, K = sd.K;
-    const bool amf = sd.flags & kFlagAMFast, bnf = sd.flags & kFlagBNFast;
     const T *__restrict__ A = (const T *)sd.a;
     const T *__restrict__ B = (const T *)sd.b;
     const int64_t *__restrict__ offAK = sd.offAK;
@@ -542,6 +536,24 @@ __global__ void __launch_bounds__(256, 1) gett_tiled_kernel(const __grid_constan
                 C[o + cp] = ci[i][j];
             }
         }
+    }
+}
+
+template <typename T, int BM, int BN, int BK, int STAGES>
+__global__ void __launch_bounds__(256, 1) gett_tiled_kernel(const __grid_constant__ GroupArgs g) {
+    using Cfg = TiledCfg<T, BM, BN, BK, STAGES>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);                  // [STAGES][2 planes][BK][RA]
+    T *Bs = As + STAGES * 2 * BK * Cfg::RA;                     // [STAGES][2 planes][BK][RB]
+    __shared__ GettDesc sd;
+    __shared__ int64_t sCM[BM], sCN[BN];
+    if (threadIdx.x == 0) load_desc(g, sd);
+    __syncthreads();
+    switch (((sd.flags & kFlagAMFast) ? 2 : 0) | ((sd.flags & kFlagBNFast) ? 1 : 0)) {
+        case 0: tiled_body<T, BM, BN, BK, STAGES, false, false>(sd, As, Bs, sCM, sCN); break;
+        case 1: tiled_body<T, BM, BN, BK, STAGES, false, true>(sd, As, Bs, sCM, sCN); break;
+        case 2: tiled_body<T, BM, BN, BK, STAGES, true, false>(sd, As, Bs, sCM, sCN); break;
+        default: tiled_body<T, BM, BN, BK, STAGES, true, true>(sd, As, Bs, sCM, sCN); break;
     }
 }
 
@@ -907,8 +919,16 @@ extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B
     if (nchunks > 0 && (!host_out || nslots < 1))
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "the host buffer cannot hold one output chunk");
     if (nchunks == 0) return ROSNET_OK;
-    rosnet_btensor_s av;   // slice view of A, re-pointed per chunk
-    av.lay.init(A->lay.rank - nsplit, A->lay.shape + nsplit, A->lay.block + nsplit);
+    rosnet_btensor_s av;   // slice view of A (A's strides), re-pointed per chunk
+    av.lay.rank = A->lay.rank - nsplit;
+    av.lay.numel = 1;
+    for (int a = 0; a < av.lay.rank; ++a) {
+        av.lay.shape[a] = A->lay.shape[a + nsplit];
+        av.lay.block[a] = A->lay.block[a + nsplit];
+        av.lay.gstride[a] = A->lay.gstride[a + nsplit];
+        av.lay.lstride[a] = A->lay.lstride[a + nsplit];
+        av.lay.numel *= av.lay.shape[a];
+    }
     av.dtype = A->dtype;
     av.elsize = A->elsize;
     av.pstride = A->pstride;
