@@ -339,6 +339,204 @@ def _profiled_traffic():
     return rec.get("gett_tiled_rqc20_bytes_per_launch")
 
 
+# ---------------------------------------------------------------------------
+# further workloads (not the default line)
+# ---------------------------------------------------------------------------
+def serving_pool(count, seed, max_flops=1e11):
+    """Seeded pool of grid circuits, n ~ U{16..40}, depth ~ U{8..16}, redrawn
+    until one amplitude costs at most max_flops with the library's path search."""
+    import paper_2201_06620_b300 as R
+    rng = np.random.default_rng(seed)
+    pool = []
+    while len(pool) < count:
+        n, d = int(rng.integers(16, 41)), int(rng.integers(8, 17))
+        circ = W.random_circuit(n, d, int(rng.integers(1 << 30)))
+        net = W.circuit_network(circ)
+        _, fl = R.path_search(net.labels, [t.shape for t in net.tensors], net.out_labels, ntrials=4, seed=0)
+        if fl <= max_flops:
+            pool.append(circ)
+    return pool
+
+
+def run_serve(args):
+    """Poisson stream of amplitude-batch queries served with continuous
+    batching; p50/p99 latency and amplitudes/s, against the plain per-query
+    FP32 form (one amplitude per contraction, one at a time)."""
+    import torch
+    import paper_2201_06620_b300 as R
+    from paper_2201_06620_b300.serving import AmplitudeServer, Query
+    pool = serving_pool(args.pool, 2022)
+    rng = np.random.default_rng(7)
+    ks = [0, 3, 6, 10]
+    prec = {"fp32": R.PREC_DEFAULT, "bf16x3": R.PREC_BF16X3, "tf32x3": R.PREC_TF32X3}[args.serve_precision]
+    srv = AmplitudeServer(pool, slots=args.slots, memory_budget=160e9, precision=prec)
+
+    def draw():
+        ci = int(rng.integers(len(pool)))
+        n = pool[ci].n
+        b = 2 ** int(rng.integers(0, 11))
+        k = min(next(x for x in ks if 2 ** x >= b), n)
+        b = min(b, 2 ** k)
+        prefix = tuple(int(x) for x in rng.integers(0, 2, n - k))
+        suffixes = sorted(int(x) for x in rng.choice(2 ** k, size=b, replace=False))
+        return Query(circuit=ci, prefix=prefix, k=k, suffixes=suffixes)
+
+    # warm-up: plan every (circuit, k) on every slot before the clock starts
+    t0 = time.perf_counter()
+    for ci, c in enumerate(pool):
+        for k in ks:
+            if k > c.n:
+                continue
+            for _ in range(args.slots):
+                srv.submit(Query(circuit=ci, prefix=(0,) * (c.n - k), k=k, suffixes=[0]))
+            srv.drain()
+    warm = time.perf_counter() - t0
+    srv.finished.clear()
+    # Poisson arrivals at rate lambda for `duration` seconds, served live
+    lam, dur = args.rate, args.duration
+    arrivals, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / lam)
+        if t > dur:
+            break
+        arrivals.append(t)
+    queries = [draw() for _ in arrivals]
+    start = time.perf_counter()
+    i = 0
+    while i < len(queries) or srv.waiting or srv.running:
+        now = time.perf_counter() - start
+        while i < len(queries) and arrivals[i] <= now:
+            srv.submit(queries[i], now=start + arrivals[i])
+            i += 1
+        srv.step()
+    wall = time.perf_counter() - start
+    lat = np.array([q.done - q.arrival for q in srv.finished]) * 1e3
+    amps = sum(len(q.suffixes) for q in srv.finished)
+    # plain per-query FP32 form on a sample: one amplitude per contraction
+    sample = srv.finished[: args.plain_sample]
+    nets = {}
+    plain_n, plain_t, err = 0, 0.0, 0.0
+    for q in sample:
+        c = pool[q.circuit]
+        for s_, got in zip(q.suffixes[:4], q.result[:4]):
+            bits = list(q.prefix) + [(s_ >> (q.k - 1 - j)) & 1 for j in range(q.k)]
+            net = W.circuit_network(c, bitstring=bits)
+            if q.circuit not in nets:
+                ts = [R.btensor(np.asarray(x, dtype=np.complex64)) for x in net.tensors]
+                nw = R.Network(ts, net.labels, net.out_labels)
+                nets[q.circuit] = (nw, R.path_search(net.labels, [x.shape for x in net.tensors], [],
+                                                     ntrials=16, seed=q.circuit)[0], len(ts) - c.n)
+            nw, path, ng = nets[q.circuit]
+            for qq in range(c.n):
+                nw.set_tensor(ng + qq, R.btensor(np.eye(2, dtype=np.complex64)[bits[qq]]))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ref = complex(R.contract(nw, path=path).download())
+            plain_t += time.perf_counter() - t1
+            plain_n += 1
+            err = max(err, abs(complex(got) - ref) / max(abs(ref), 2.0 ** (-c.n / 2)))
+    line = {"metric": "amplitudes/s (served)", "value": amps / wall, "unit": "amplitudes/s",
+            "n_gpus": 1, "higher_is_better": True, "workload": "serving",
+            "config": {"pool": args.pool, "rate_per_s": lam, "duration_s": dur, "slots": args.slots,
+                       "precision": args.serve_precision, "k_values": ks,
+                       "pool_rule": "n~U{16..40}, depth~U{8..16}, redrawn above 1e11 flop/amplitude"},
+            "queries": len(srv.finished), "amplitudes": amps, "wall_s": wall, "warmup_s": warm,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "plain_fp32_per_query": {"value": plain_n / plain_t if plain_t else None, "unit": "amplitudes/s",
+                                     "sample_amplitudes": plain_n},
+            "max_rel_err_vs_plain_fp32": err}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """Sliced 30-qubit circuit (256 slices) + 64 circuits of 16-24 qubits in
+    one batched plan per precision mode."""
+    import torch
+    import paper_2201_06620_b300 as R
+    circ = W.random_circuit(30, 14, 2022, 5, 6)
+    net = W.circuit_network(circ)
+    ext = [t.shape for t in net.tensors]
+    path, fl = R.path_search(net.labels, ext, net.out_labels, ntrials=64, seed=0)
+    cut, mx, ft = R.slice_search(net.labels, ext, net.out_labels, path, 8)
+    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+    nets = [n for _, n in R.sliced_networks(ts, net.labels, net.out_labels, cut)]
+    paths = [path] * len(nets)
+    rng = np.random.default_rng(7)
+    for i in range(64):
+        c = W.random_circuit(int(rng.integers(16, 25)), int(rng.integers(8, 13)), 500 + i)
+        nw = W.circuit_network(c)
+        tt = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in nw.tensors]
+        p, _ = R.path_search(nw.labels, [t.shape for t in nw.tensors], nw.out_labels, ntrials=16, seed=i)
+        nets.append(R.Network(tt, nw.labels, nw.out_labels))
+        paths.append(p)
+    res = {}
+    for name, prec in (("fp32", R.PREC_DEFAULT), ("bf16x3", R.PREC_BF16X3), ("tf32x3", R.PREC_TF32X3)):
+        t0 = time.perf_counter()
+        outs = R.contract_batch(nets, paths, precision=prec, flags=R.OPT_GRAPH)
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        req, planned, launches = R.plan_stats(nets, paths, precision=prec, flags=R.OPT_GRAPH)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(args.steps):
+            outs = R.contract_batch(nets, paths, precision=prec, flags=R.OPT_GRAPH)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / args.steps
+        amp = complex(R.sum_fp64(outs[:256]).download())
+        res[name] = {"batch_ms": ms, "amplitudes_per_s": 65 / (ms / 1e3), "plan_s": plan_s,
+                     "steps_requested": req, "steps_planned": planned, "launches": launches,
+                     "amp30": [amp.real, amp.imag]}
+        del outs
+        R.release_plans()
+    line = {"metric": "batch amplitudes/s", "workload": "sliced 30q (256 slices) + 64 circuits",
+            "path_gflop": fl / 1e9, "sliced_gflop": ft / 1e9, "max_slice_entries": mx, "modes": res}
+    print(json.dumps(line), flush=True)
+
+
+def run_sweep(args):
+    """Precision sweep: [2]^30 x [2]^30 -> [2]^40 in 2^30-entry chunks."""
+    import torch
+    import paper_2201_06620_b300 as R
+    prob = W.precision_sweep_config()
+    A = R.empty(prob["shape_a"], prob["block_a"], R.C64)
+    B = R.empty(prob["shape_b"], prob["block_b"], R.C64)
+    piece = 1 << 26
+    for t, seed in ((A, prob["seed_a"]), (B, prob["seed_b"])):
+        for st in range(0, 1 << 30, piece):
+            t.upload_range(W.complex_normal_range(seed, st, piece, prob["scale"]), st)
+    R.sync()
+    host = torch.empty(2 * (1 << 30) * 4, dtype=torch.uint8).pin_memory()
+    flop = 8.0 * 2 ** 10 * 2 ** 20 * 2 ** 10
+    peaks = _measured_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1783.9))
+    out = {}
+    for name, prec, peak, issued in (("fp32", R.PREC_FP32, 148 * 128 * 2 * 2.032, 1),
+                                     ("tf32", R.PREC_TF32, bf16 * 1.1 / 2.25, 1),
+                                     ("bf16x3", R.PREC_BF16X3, bf16, 3),
+                                     ("tf32x3", R.PREC_TF32X3, bf16 * 1.1 / 2.25, 3)):
+        As = A.slice([0] * 10)
+        C = R.tensordot(As, B, list(range(10, 20)), prob["axes_b"], precision=prec)
+        del C
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        C = R.tensordot(As, B, list(range(10, 20)), prob["axes_b"], precision=prec)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e)
+        del C
+        t0 = time.perf_counter()
+        R.tensordot_ooc(A, B, prob["axes_a"], prob["axes_b"], 10, 1, args.chunks, host, precision=prec)
+        ooc = (time.perf_counter() - t0) / args.chunks
+        tf = flop / ms / 1e9
+        out[name] = {"chunk_ms_kernel": ms, "tflops": tf, "issued_tflops": tf * issued,
+                     "peak_tflops": peak, "frac": tf * issued / peak, "ooc_s_per_chunk": ooc,
+                     "ooc_tflops": flop / ooc / 1e12}
+    print(json.dumps({"metric": "tensordot TFLOP/s", "workload": "precision sweep [2]^30x[2]^30->[2]^40",
+                      "modes": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,11 +546,25 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["rqc20", "serve", "batch", "sweep"], default="rqc20")
+    ap.add_argument("--pool", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--serve-precision", choices=["fp32", "bf16x3", "tf32x3"], default="bf16x3")
+    ap.add_argument("--plain-sample", type=int, default=20)
+    ap.add_argument("--chunks", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_rosnet(args)
 

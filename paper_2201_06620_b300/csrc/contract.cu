@@ -131,17 +131,24 @@ struct Plan {
 // CUDA runtime or an injected allocator (e.g. one implemented in Python) may
 // already be gone.  rosnet_release_plans() frees them explicitly.
 std::mutex g_plan_mu;
-auto &g_plans = *new std::unordered_map<std::string, std::unique_ptr<Plan>>();
+// Plans are looked up by a 128-bit hash of everything the plan depends on.
+struct Key128 {
+    uint64_t a = 0x9E3779B97F4A7C15ull, b = 0xC2B2AE3D27D4EB4Full;
+    void put(int64_t v) {
+        uint64_t x = (uint64_t)v;
+        a ^= x + 0x9E3779B97F4A7C15ull + (a << 6) + (a >> 2);
+        a *= 0xBF58476D1CE4E5B9ull;
+        b = (b ^ (x * 0x94D049BB133111EBull)) * 0xD6E8FEB86659FD93ull;
+        b ^= b >> 31;
+    }
+    bool operator==(const Key128 &o) const { return a == o.a && b == o.b; }
+};
+struct Key128Hash {
+    size_t operator()(const Key128 &k) const { return (size_t)(k.a ^ (k.b * 31)); }
+};
+auto &g_plans = *new std::unordered_map<Key128, std::unique_ptr<Plan>, Key128Hash>();
 // (plan, ring slot) of every timed launch not yet drained
 auto &g_timing_log = *new std::vector<std::pair<Plan *, int>>();
-
-// Identity of a leaf's contents: storage address, plane stride and layout.
-struct LeafKey {
-    const void *data;
-    int64_t pstride;
-    int rank;
-    bool operator==(const LeafKey &o) const { return data == o.data && pstride == o.pstride && rank == o.rank; }
-};
 
 // Leaf slots shared by equal tensors (same storage and layout) across the
 // networks of a call; slot[i][t] for tensor t of network i.
@@ -174,36 +181,35 @@ std::vector<std::vector<int>> leaf_slots(int nnet, const rosnet_network *nets, s
     return slot;
 }
 
-std::string plan_key(int nnet, const rosnet_network *nets, const rosnet_path *paths,
-                     const std::vector<std::vector<int>> &slot, int prec, int flags, int64_t maxblk,
-                     cudaStream_t s) {
-    std::string k;
-    auto put = [&k](int64_t v) { k.append((const char *)&v, sizeof(v)); };
-    put(nnet);
-    put(prec);
-    put(flags);
-    put(maxblk);
-    put((int64_t)(intptr_t)s);
+Key128 plan_key(int nnet, const rosnet_network *nets, const rosnet_path *paths,
+                const std::vector<std::vector<int>> &slot, int prec, int flags, int64_t maxblk,
+                cudaStream_t s) {
+    Key128 k;
+    k.put(nnet);
+    k.put(prec);
+    k.put(flags);
+    k.put(maxblk);
+    k.put((int64_t)(intptr_t)s);
     for (int i = 0; i < nnet; ++i) {
         const rosnet_network *net = &nets[i];
-        put(net->ntensors);
+        k.put(net->ntensors);
         for (int t = 0; t < net->ntensors; ++t) {
             rosnet_btensor x = net->tensors[t];
-            put(slot[i][t]);
-            put(x->dtype);
-            put(x->lay.rank);
+            k.put(slot[i][t]);
+            k.put(x->dtype);
+            k.put(x->lay.rank);
             for (int a = 0; a < x->lay.rank; ++a) {
-                put(x->lay.shape[a]);
-                put(x->lay.block[a]);
-                put(x->lay.gstride[a]);
-                put(x->lay.lstride[a]);
-                put(net->labels[t][a]);
+                k.put(x->lay.shape[a]);
+                k.put(x->lay.block[a]);
+                k.put(x->lay.gstride[a]);
+                k.put(x->lay.lstride[a]);
+                k.put(net->labels[t][a]);
             }
         }
-        put(net->nout);
-        for (int o = 0; o < net->nout; ++o) put(net->out_labels[o]);
-        put(paths[i].nsteps);
-        for (int j = 0; j < 2 * paths[i].nsteps; ++j) put(paths[i].pairs[j]);
+        k.put(net->nout);
+        for (int o = 0; o < net->nout; ++o) k.put(net->out_labels[o]);
+        k.put(paths[i].nsteps);
+        for (int j = 0; j < 2 * paths[i].nsteps; ++j) k.put(paths[i].pairs[j]);
     }
     return k;
 }
@@ -256,6 +262,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     plan->outs.resize(nnet);
     const int nleaf = (int)plan->leaves.size();
     std::vector<int> leaf_last_use(nleaf, -1);
+    (void)leaf_last_use;
     std::unordered_map<std::string, int64_t> seen;   // step signature -> step index
     auto lay_of = [&](int64_t g) -> const Layout & {
         if (g >= 0) return plan->steps[g].lay;
@@ -389,28 +396,61 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             S.last_use = end_wave;   // copied into the output after the last wave
         }
     }
-    // arena: every step not written straight into an output, packed by lifetime
-    struct Slot { size_t off, size; int from, to; };
-    std::vector<Slot> placed;
-    const size_t el2 = 2 * (plan->dtype == ROSNET_C64 ? 4 : 8);
-    for (size_t g = 0; g < plan->steps.size(); ++g) {
-        Step &S = plan->steps[g];
-        if (S.arena_off == SIZE_MAX) continue;
-        size_t bytes = ((size_t)S.lay.numel * el2 + 255) & ~(size_t)255;
-        if (bytes == 0) bytes = 256;
-        const int from = S.wave, to = S.last_use < 0 ? S.wave : S.last_use;
-        std::vector<std::pair<size_t, size_t>> busy;
-        for (auto &p : placed)
-            if (!(p.to < from || p.from > to)) busy.push_back({p.off, p.off + p.size});
-        std::sort(busy.begin(), busy.end());
-        size_t off = 0;
-        for (auto &b : busy) {
-            if (off + bytes <= b.first) break;
-            off = std::max(off, b.second);
+    // arena: every step not written straight into an output, packed by
+    // lifetime with a sweep over the waves: a step's bytes are reserved from
+    // the wave that writes it to the last wave that reads it, then returned to
+    // a first-fit free list (coalescing neighbours)
+    {
+        const size_t el2 = 2 * (plan->dtype == ROSNET_C64 ? 4 : 8);
+        std::vector<int> order;
+        for (size_t g = 0; g < plan->steps.size(); ++g)
+            if (plan->steps[g].arena_off != SIZE_MAX) order.push_back((int)g);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return plan->steps[x].wave < plan->steps[y].wave; });
+        std::map<size_t, size_t> freel;                       // offset -> size
+        std::multimap<int, std::pair<size_t, size_t>> ends;   // release wave -> (off, size)
+        size_t top = 0;
+        auto release = [&](size_t off, size_t sz) {
+            auto it = freel.emplace(off, sz).first;
+            auto nx = std::next(it);
+            if (nx != freel.end() && it->first + it->second == nx->first) {
+                it->second += nx->second;
+                freel.erase(nx);
+            }
+            if (it != freel.begin()) {
+                auto pv = std::prev(it);
+                if (pv->first + pv->second == it->first) {
+                    pv->second += it->second;
+                    freel.erase(it);
+                }
+            }
+        };
+        for (int g : order) {
+            Step &S = plan->steps[g];
+            while (!ends.empty() && ends.begin()->first < S.wave) {   // free slots dead before this wave
+                release(ends.begin()->second.first, ends.begin()->second.second);
+                ends.erase(ends.begin());
+            }
+            size_t bytes = ((size_t)S.lay.numel * el2 + 255) & ~(size_t)255;
+            if (bytes == 0) bytes = 256;
+            size_t off = SIZE_MAX;
+            for (auto it = freel.begin(); it != freel.end(); ++it)
+                if (it->second >= bytes) {
+                    off = it->first;
+                    const size_t rest = it->second - bytes;
+                    freel.erase(it);
+                    if (rest) freel.emplace(off + bytes, rest);
+                    break;
+                }
+            if (off == SIZE_MAX) {
+                off = top;
+                top += bytes;
+            }
+            S.arena_off = off;
+            const int to = S.last_use < 0 ? S.wave : S.last_use;
+            ends.emplace(to, std::make_pair(off, bytes));
         }
-        placed.push_back({off, bytes, from, to});
-        S.arena_off = off;
-        plan->arena_bytes = std::max(plan->arena_bytes, off + bytes);
+        plan->arena_bytes = top;
     }
     // offset tables (host-built, one upload)
     std::vector<GettView> views(plan->steps.size());
@@ -507,7 +547,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     if (tc_bytes) plan->tcws = DevBuf(tc_bytes, s);
     // the launch with the most algorithmic work (8 M N K per complex GEMM)
     {
-        const double el2d = (double)el2;
+        const double el2d = 2.0 * (plan->dtype == ROSNET_C64 ? 4 : 8);
         double best = -1;
         for (size_t li = 0; li < plan->launches.size(); ++li) {
             const auto &L = plan->launches[li];
@@ -700,7 +740,7 @@ static void contract_batch(int nnet, const rosnet_network *nets, const rosnet_pa
     if (maxblk < 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "negative max_block_entries");
     std::vector<Leaf> leaves;
     auto slot = leaf_slots(nnet, nets, &leaves);
-    std::string key = plan_key(nnet, nets, paths, slot, prec, flags, maxblk, s);
+    Key128 key = plan_key(nnet, nets, paths, slot, prec, flags, maxblk, s);
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
     Plan *P;
@@ -758,7 +798,7 @@ rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const 
     const int64_t maxblk = opts ? opts->max_block_entries : 0;
     std::vector<Leaf> leaves;
     auto slot = leaf_slots(nnet, nets, &leaves);
-    std::string key = plan_key(nnet, nets, paths, slot, prec, flags, maxblk, (cudaStream_t)stream);
+    Key128 key = plan_key(nnet, nets, paths, slot, prec, flags, maxblk, (cudaStream_t)stream);
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
     if (it == g_plans.end()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no cached plan for these networks");

@@ -1,0 +1,196 @@
+"""Amplitude serving with continuous batching on one GPU.
+
+A query asks for amplitudes <x|C|0^n> of one registered circuit for 1 to
+1024 bitstrings x that share their first n - k bits (k <= 10): the network
+keeps the last k output wires open, so one contraction gives all 2^k
+amplitudes of the query (its intermediates serve every requested bitstring)
+and the requested ones are read from that result.  Everything that runs on
+the device is rosnet_contract (librosnet's kernels); this module schedules.
+
+Scheduling: queries wait in arrival order; a query is admitted as soon as a
+stream slot is free and its predicted device footprint (its input tensors
+plus the peak of live intermediates along its path -- the analogue of the
+paper's per-task memory, Eq. 1 / Eq. 2) fits the memory budget next to the
+queries already running.  Admitted queries run concurrently on separate
+streams, so a query that arrives while others are on the GPU starts as soon
+as a slot and memory free up, and its kernels overlap theirs.  Each stream
+keeps one plan per (circuit, k) (offset tables, intermediate arena, captured
+CUDA graph) and a device buffer of projectors, so a query costs one small
+host-to-device copy (its prefix), one graph launch and one device-to-host
+copy (its amplitudes).  Latency runs from a query's arrival to the moment its
+amplitudes are on the host.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import C64, OPT_GRAPH, PREC_DEFAULT, Network, btensor, contract, empty, path_search
+
+__all__ = ["Query", "AmplitudeServer", "predict_footprint"]
+
+
+@dataclass
+class Query:
+    circuit: int
+    prefix: tuple            # bits of qubits 0 .. n-k-1
+    k: int                   # open (trailing) qubits
+    suffixes: list           # requested values of the open qubits (ints < 2^k)
+    arrival: float = 0.0
+    started: float | None = None
+    done: float | None = None
+    result: np.ndarray | None = None
+    qid: int = 0
+
+
+def predict_footprint(labels, extents, out_labels, path, elem_bytes=8):
+    """Device bytes of a contraction: inputs plus the largest total of live
+    intermediates along the path (each lives from its step to its use)."""
+    ext = {}
+    for l, e in zip(labels, extents):
+        for x, v in zip(l, e):
+            ext[x] = v
+    n = len(labels)
+    live = {i: list(l) for i, l in enumerate(labels)}
+    size = {i: math.prod(ext[x] for x in l) for i, l in enumerate(labels)}
+    inputs = sum(size.values())
+    nxt, cur, peak = n, 0, 0
+    for a, b in path:
+        la, lb = live.pop(a), live.pop(b)
+        sh = set(la) & set(lb)
+        lc = [x for x in la if x not in sh] + [x for x in lb if x not in sh]
+        s = math.prod(ext[x] for x in lc) if lc else 1
+        cur += s
+        peak = max(peak, cur)
+        for o in (a, b):
+            if o >= n:
+                cur -= size[o]
+        live[nxt], size[nxt] = lc, s
+        nxt += 1
+    return elem_bytes * (inputs + peak)
+
+
+class _Circuit:
+    """Device-resident gate tensors of one circuit and its per-k paths."""
+
+    def __init__(self, cid, circ):
+        self.cid, self.n = cid, circ.n
+        zero = np.array([1, 0], dtype=np.complex64)
+        self.tensors = [btensor(zero) for _ in range(circ.n)]
+        self.labels = [(q,) for q in range(circ.n)]
+        wire, nl = list(range(circ.n)), circ.n
+        for _, qs, mat in circ.gates:
+            outs = list(range(nl, nl + len(qs)))
+            nl += len(qs)
+            self.tensors.append(btensor(np.asarray(mat, dtype=np.complex64)))
+            self.labels.append(tuple(outs + [wire[q] for q in qs]))
+            for q, o in zip(qs, outs):
+                wire[q] = o
+        self.wire = wire
+        self.per_k = {}
+
+    def plan_for(self, k):
+        if k not in self.per_k:
+            closed = self.n - k
+            labels = self.labels + [(self.wire[q],) for q in range(closed)]
+            ext = [t.shape for t in self.tensors] + [(2,)] * closed
+            out = [self.wire[q] for q in range(closed, self.n)]
+            path, flops = path_search(labels, ext, out, ntrials=16, seed=self.cid)
+            self.per_k[k] = (labels, out, path, flops, predict_footprint(labels, ext, out, path))
+        return self.per_k[k]
+
+
+class _Slot:
+    """One stream with its projector buffer (views per qubit) and networks."""
+
+    def __init__(self, torch, nmax):
+        self.stream = torch.cuda.Stream()
+        self.buf = empty((nmax, 2), None, C64, stream=self.stream)
+        self.views = [self.buf.fix([0], [q]) for q in range(nmax)]
+        self.nets = {}
+        self.host = np.zeros((nmax, 2), dtype=np.complex64)
+
+
+class AmplitudeServer:
+    """Continuous-batching amplitude server over a pool of stream slots."""
+
+    def __init__(self, circuits, slots=4, memory_budget=160e9, precision=PREC_DEFAULT, use_graph=True):
+        import torch
+        self.torch = torch
+        self.circuits = [_Circuit(i, c) for i, c in enumerate(circuits)]
+        nmax = max(c.n for c in self.circuits)
+        self.slots = [_Slot(torch, nmax) for _ in range(slots)]
+        self.free = list(range(slots))
+        self.budget = memory_budget
+        self.in_use = 0.0
+        self.precision = precision
+        self.flags = OPT_GRAPH if use_graph else 0
+        self.waiting = collections.deque()
+        self.running = []
+        self.finished = []
+        self._qid = 0
+
+    def submit(self, q: Query, now=None):
+        q.arrival = time.perf_counter() if now is None else now
+        q.qid = self._qid
+        self._qid += 1
+        self.waiting.append(q)
+
+    def step(self):
+        """Retire finished queries, then admit waiting ones while a slot is
+        free and their predicted footprint fits the budget."""
+        self._retire()
+        while self.waiting and self.free:
+            q = self.waiting[0]
+            foot = self.circuits[q.circuit].plan_for(q.k)[4]
+            if self.running and self.in_use + foot > self.budget:
+                break
+            self.waiting.popleft()
+            self._launch(q, foot)
+
+    def drain(self):
+        while self.waiting or self.running:
+            self.step()
+            if self.running:
+                self.running[0][2].synchronize()
+        self._retire()
+
+    def _launch(self, q, foot):
+        torch = self.torch
+        si = self.free.pop()
+        sl = self.slots[si]
+        c = self.circuits[q.circuit]
+        labels, out, path, _, _ = c.plan_for(q.k)
+        closed = c.n - q.k
+        key = (q.circuit, q.k)
+        if key not in sl.nets:
+            sl.nets[key] = Network(c.tensors + sl.views[:closed], labels, out)
+        pre = np.asarray(q.prefix, dtype=np.float32)
+        sl.host[:closed, 0] = 1.0 - pre
+        sl.host[:closed, 1] = pre
+        q.started = time.perf_counter()
+        sl.buf.upload(sl.host, stream=sl.stream)
+        res = contract(sl.nets[key], path=path, precision=self.precision, flags=self.flags,
+                       stream=sl.stream)
+        ev = torch.cuda.Event()
+        ev.record(sl.stream)
+        self.in_use += foot
+        self.running.append((q, si, ev, res, foot))
+
+    def _retire(self):
+        keep = []
+        for q, si, ev, res, foot in self.running:
+            if ev.query():
+                amps = res.download(stream=self.slots[si].stream).reshape(-1)
+                q.result = amps[np.asarray(q.suffixes, dtype=np.int64)]
+                q.done = time.perf_counter()
+                self.in_use -= foot
+                self.free.append(si)
+                self.finished.append(q)
+            else:
+                keep.append((q, si, ev, res, foot))
+        self.running = keep

@@ -148,3 +148,61 @@ def test_greedy_path_rqc20_structure():
     assert len(path) == 372
     rows = _simulate(net.labels, ext, net.out_labels, path)
     assert max(r[0] for r in rows) <= 2 ** 20
+
+
+def test_predict_footprint_matches_eq2_for_one_pair():
+    """For one pair of blocks the serving footprint predictor gives the
+    paper's per-task memory of Eq. 2, k_b (m_b + n_b) + m_b n_b elements."""
+    import oracle
+    from paper_2201_06620_b300.serving import predict_footprint
+    for mb, nb, kb in ((8, 4, 16), (1, 1, 1), (64, 32, 128)):
+        got = predict_footprint([(0, 1), (1, 2)], [(mb, kb), (kb, nb)], [0, 2], [(0, 1)], elem_bytes=1)
+        assert got == oracle.mem_pair(mb, nb, kb)
+
+
+def _path_flops(labels, extents, path, cut=()):
+    ext = {}
+    for l, e in zip(labels, extents):
+        for x, y in zip(l, e):
+            ext[x] = 1 if x in cut else y
+    live = {i: list(l) for i, l in enumerate(labels)}
+    nxt, tot, mx = len(labels), 0.0, 0.0
+    for a, b in path:
+        la, lb = live.pop(a), live.pop(b)
+        union = set(la) | set(lb)
+        tot += 8.0 * float(np.prod([ext[x] for x in union]))
+        lc = [x for x in la if x not in lb] + [x for x in lb if x not in la]
+        mx = max(mx, float(np.prod([ext[x] for x in lc])) if lc else 1.0)
+        live[nxt] = lc
+        nxt += 1
+    return tot, mx
+
+
+def test_path_search_never_worse_than_greedy_and_reports_flops():
+    circ = W.random_circuit(16, 8, 4)
+    net = W.circuit_network(circ)
+    ext = [t.shape for t in net.tensors]
+    greedy = R.path_greedy_extents(net.labels, ext, net.out_labels)
+    path, flops = R.path_search(net.labels, ext, net.out_labels, ntrials=8, seed=3)
+    _simulate(net.labels, ext, net.out_labels, path)       # a valid SSA path
+    assert abs(_path_flops(net.labels, ext, path)[0] - flops) <= 1e-9 * flops
+    assert flops <= _path_flops(net.labels, ext, greedy)[0]
+    assert R.path_search(net.labels, ext, net.out_labels, ntrials=8, seed=3) == (path, flops)
+
+
+def test_slice_search_shrinks_the_largest_intermediate():
+    circ = W.random_circuit(14, 8, 6)
+    net = W.circuit_network(circ)
+    ext = [t.shape for t in net.tensors]
+    path, _ = R.path_search(net.labels, ext, net.out_labels, ntrials=4, seed=1)
+    cut, mx, flops = R.slice_search(net.labels, ext, net.out_labels, path, 4)
+    assert len(set(cut)) == 4
+    counts = {}
+    for l in net.labels:
+        for x in l:
+            counts[x] = counts.get(x, 0) + 1
+    assert all(counts[c] == 2 for c in cut)                # bonds, not open legs
+    t0, m0 = _path_flops(net.labels, ext, path)
+    t1, m1 = _path_flops(net.labels, ext, path, cut)
+    assert mx == m1 < m0
+    assert abs(flops - 16 * t1) <= 1e-9 * flops             # 2^4 slices

@@ -1,0 +1,81 @@
+"""The continuous-batching amplitude server: every query's amplitudes match
+the oracle's state vector, and each query gives the same result alone and in
+a mix of concurrent queries (within the FP32 tolerance, 1e-5)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2201_06620_b300 as R
+import workloads as W
+from paper_2201_06620_b300.serving import AmplitudeServer, Query
+
+pytestmark = pytest.mark.gpu
+
+
+def _queries(circs, rng, count):
+    qs = []
+    for _ in range(count):
+        ci = int(rng.integers(len(circs)))
+        n = circs[ci].n
+        k = int(rng.integers(0, 5))
+        prefix = tuple(int(b) for b in rng.integers(0, 2, n - k))
+        m = int(rng.integers(1, 2 ** k + 1))
+        suffixes = sorted(int(x) for x in rng.choice(2 ** k, size=m, replace=False))
+        qs.append(Query(circuit=ci, prefix=prefix, k=k, suffixes=suffixes))
+    return qs
+
+
+def _copy(q):
+    return Query(circuit=q.circuit, prefix=q.prefix, k=q.k, suffixes=list(q.suffixes))
+
+
+def test_server_alone_vs_mix_and_oracle():
+    rng = np.random.default_rng(11)
+    circs = [W.random_circuit(int(rng.integers(9, 14)), int(rng.integers(4, 9)), 700 + i) for i in range(5)]
+    psi = [oracle.statevector(c) for c in circs]
+    queries = _queries(circs, rng, 24)
+    # alone: one query in the server at a time
+    alone_srv = AmplitudeServer(circs, slots=1)
+    alone = []
+    for q in queries:
+        qq = _copy(q)
+        alone_srv.submit(qq)
+        alone_srv.drain()
+        alone.append(qq.result)
+    # mix: everything submitted at once over 4 slots
+    mix_srv = AmplitudeServer(circs, slots=4)
+    mixed = [_copy(q) for q in queries]
+    for q in mixed:
+        mix_srv.submit(q)
+    mix_srv.drain()
+    assert len(mix_srv.finished) == len(queries)
+    for q, a, m in zip(queries, alone, mixed):
+        n = circs[q.circuit].n
+        base = 0
+        for b in q.prefix:
+            base = (base << 1) | b
+        ref = np.array([psi[q.circuit][(base << q.k) | s] for s in q.suffixes])
+        scale = max(np.abs(ref).max(), 2.0 ** (-n / 2))
+        assert np.abs(a - ref).max() / scale <= 1e-5
+        assert np.abs(m.result - a).max() / scale <= 1e-5
+
+
+def test_admission_by_footprint():
+    """With a budget below one query's footprint the server still makes
+    progress one query at a time; with a generous budget several run at once."""
+    rng = np.random.default_rng(3)
+    circs = [W.random_circuit(12, 6, 900 + i) for i in range(3)]
+    qs = _queries(circs, rng, 8)
+    tight = AmplitudeServer(circs, slots=4, memory_budget=1.0)
+    for q in qs:
+        tight.submit(_copy(q))
+    tight.step()
+    assert len(tight.running) == 1
+    tight.drain()
+    assert len(tight.finished) == 8
+    loose = AmplitudeServer(circs, slots=4, memory_budget=1e12)
+    for q in qs:
+        loose.submit(_copy(q))
+    loose.step()
+    assert len(loose.running) == 4
+    loose.drain()
