@@ -262,6 +262,65 @@ __global__ void __launch_bounds__(256) gett_warpk_kernel(const __grid_constant__
     }
 }
 
+// One CTA per output entry for very long contractions with few outputs
+// (e.g. the final scalar of a network): 256 threads stride over K with four
+// independent loads in flight each, then a fixed-order block reduction.
+template <typename T>
+__global__ void __launch_bounds__(256) gett_dot_kernel(const __grid_constant__ GroupArgs g) {
+    __shared__ GettDesc sd;
+    __shared__ T red[2][8];
+    if (threadIdx.x == 0) load_desc(g, sd);
+    __syncthreads();
+    const int64_t o = (int64_t)blockIdx.x - sd.tile_begin;
+    int64_t m, n;
+    out_coords(sd, o, m, n);
+    const T *__restrict__ A = (const T *)sd.a;
+    const T *__restrict__ B = (const T *)sd.b;
+    const int64_t *__restrict__ offAK = sd.offAK;
+    const int64_t *__restrict__ offBK = sd.offBK;
+    const int64_t am = sd.offAM[m], bn = sd.offBN[n], K = sd.K;
+    const int64_t ap = sd.a_plane, bp = sd.b_plane;
+    T sr = 0, si = 0;
+    int64_t k = threadIdx.x;
+    for (; k + 768 < K; k += 1024) {
+        int64_t ia[4], ib[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ia[u] = am + __ldg(offAK + k + 256 * u);
+            ib[u] = bn + __ldg(offBK + k + 256 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cmac(sr, si, __ldg(A + ia[u]), __ldg(A + ia[u] + ap), __ldg(B + ib[u]),
+                                         __ldg(B + ib[u] + bp));
+    }
+    for (; k < K; k += 256) {
+        const int64_t ia = am + offAK[k], ib = bn + offBK[k];
+        cmac(sr, si, A[ia], A[ia + ap], B[ib], B[ib + bp]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+        si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = sr;
+        red[1][w] = si;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T tr = 0, ti = 0;
+        for (int j = 0; j < 8; ++j) {
+            tr += red[0][j];
+            ti += red[1][j];
+        }
+        T *C = (T *)sd.c;
+        const int64_t ic = sd.offCM[m] + sd.offCN[n];
+        C[ic] = tr;
+        C[ic + sd.c_plane] = ti;
+    }
+}
+
 // Sum of the split-K partials (in split order: deterministic) into C.
 template <typename T>
 __global__ void __launch_bounds__(256) gett_reduce_kernel(const __grid_constant__ GroupArgs g) {
@@ -610,7 +669,7 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
         const bool forced = reduce_mode == kReduceTree || reduce_mode == kReduceCommutative;
         if (reduce_mode != kReduceSequential && ((tiles < kSMs && nkt >= 32) || (forced && nkt >= 2))) {
             int64_t want = std::max<int64_t>((2 * kSMs + tiles - 1) / tiles, forced ? 2 : 1);
-            int64_t cap = forced ? nkt : nkt / 16;   // auto: at least 16 k-tiles per range
+            int64_t cap = forced ? nkt : nkt / 8;    // auto: at least 8 k-tiles per range
             int64_t ks = std::max<int64_t>(1, std::min<int64_t>(std::min(want, cap), 64));
             if (ks > 1) {
                 d.ktiles_per_split = (int)((nkt + ks - 1) / ks);
@@ -620,7 +679,11 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
         }
         return;
     }
-    if (d.K >= 128 && MN <= (int64_t(1) << 16)) {
+    if (d.K >= 1024 && MN <= 256) {
+        d.kind = kKindDot;
+        d.tiles_m = MN;
+        d.tiles_n = 1;
+    } else if (d.K >= 128 && MN <= (int64_t(1) << 16)) {
         d.kind = kKindWarpK;
         d.tiles_m = (MN + 7) / 8;
         d.tiles_n = 1;
@@ -661,6 +724,7 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindWarpK: gett_warpk_kernel<float><<<grid, 256, 0, s>>>(ga); break;
             case kKindReduce: gett_reduce_kernel<float><<<grid, 256, 0, s>>>(ga); break;
             case kKindZero: gett_zero_kernel<float><<<grid, 256, 0, s>>>(ga); break;
+            case kKindDot: gett_dot_kernel<float><<<grid, 256, 0, s>>>(ga); break;
             case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
             default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
         }
@@ -670,6 +734,7 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindWarpK: gett_warpk_kernel<double><<<grid, 256, 0, s>>>(ga); break;
             case kKindReduce: gett_reduce_kernel<double><<<grid, 256, 0, s>>>(ga); break;
             case kKindZero: gett_zero_kernel<double><<<grid, 256, 0, s>>>(ga); break;
+            case kKindDot: gett_dot_kernel<double><<<grid, 256, 0, s>>>(ga); break;
             default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
         }
     }

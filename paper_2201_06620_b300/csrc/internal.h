@@ -197,6 +197,7 @@ enum KernelKind : int32_t {
     kKindTcTF32x3 = 6,   // tcgen05, 3 x TF32 split products
     kKindTcBF16x3 = 7,   // tcgen05, 3 x BF16 split products
     kKindZero = 8,       // zero C before a commutative (atomic) split-K launch
+    kKindDot = 9,        // one CTA per output, long K (e.g. a network's final scalar)
 };
 
 inline void bind_operands(GettDesc &d, const void *A, const void *B, void *C, int64_t a_numel,

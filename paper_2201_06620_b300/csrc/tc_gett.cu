@@ -20,12 +20,12 @@
 //      (cp.async.bulk.tensor, 64-byte swizzle = the MMA's K-major layout);
 //      one thread issues the MMAs; eight warps own the output tile.  The
 //      contracted loop (every matched block pair of the tile, Sec. II-C steps
-//      2-4) is accumulated in chunks of 256 k in two alternating TMEM
-//      accumulators; the eight warps add each finished chunk into FP32
-//      registers while the tensor core fills the other one.  The tensor
-//      core's accumulator adds carry a small one-sided error that grows with
-//      the number of terms; chunking caps it at 256 terms.  The sum over
-//      pairs is order-free (Sec. IV-A); the order here is fixed.
+//      2-4) is accumulated in chunks (256 k for TF32, 64 k for the split
+//      modes) in two alternating TMEM accumulators; the eight warps add each
+//      finished chunk into FP32 registers while the tensor core fills the
+//      other one.  The tensor core's accumulator adds carry a small one-sided
+//      error that grows with the number of terms; chunking caps it.  The sum
+//      over pairs is order-free (Sec. IV-A); the order here is fixed.
 //
 // Every wait is bounded: on timeout the kernel records kDevErrTimeout in a
 // device status word, stops issuing work, waits (bounded) for its own copies
@@ -50,7 +50,10 @@ constexpr int BM = 128, BN = 128;
 constexpr int ROWB = 64;                 // bytes of one K-row of a stage (64B swizzle span)
 constexpr int NTHREADS = 320;            // warp 0 TMA, warp 1 MMA, warps 2-9 accumulators
 constexpr int NACC_WARPS = 8;
-constexpr int CHUNK_K = 256;             // contracted indices per TMEM accumulation chunk
+// contracted indices per TMEM accumulation chunk: 256 for TF32 (its error is
+// set by the operand rounding), 64 for the split modes (their error is set by
+// the accumulator's adds)
+constexpr int chunk_k(int mode) { return mode == 0 ? 256 : 64; }
 constexpr long long kWaitBudget = 4000000000LL;   // cycles (~2 s at 2 GHz)
 
 enum Mode : int { kTF32 = 0, kTF32x3 = 1, kBF16x3 = 2 };
@@ -64,7 +67,7 @@ struct Cfg {
     static constexpr int STAGE = NARR * (ARR_A + ARR_B);
     static constexpr int STAGES = MODE == kTF32 ? 6 : 3;
     static constexpr int KSTEPS = BK / (32 / ESZ);             // MMAs per product per stage
-    static constexpr int CH_STAGES = CHUNK_K / BK;             // stages per chunk
+    static constexpr int CH_STAGES = chunk_k(MODE) / BK;       // stages per chunk
     static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
 };
 
@@ -299,8 +302,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    // raster: the operand with fewer tiles varies fastest, so its tiles stay
+    // resident in L2 while the other operand streams through once
     const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
-    const int64_t m0 = (tile % sd.tiles_m) * BM, n0 = (tile / sd.tiles_m) * BN;
+    const bool n_fast = sd.tiles_n < sd.tiles_m;
+    const int64_t tm = n_fast ? tile / sd.tiles_n : tile % sd.tiles_m;
+    const int64_t tn = n_fast ? tile % sd.tiles_n : tile / sd.tiles_m;
+    const int64_t m0 = tm * BM, n0 = tn * BN;
     const int nkt = p.nkt;
     const int nchunks = (nkt + C_::CH_STAGES - 1) / C_::CH_STAGES;
 

@@ -98,11 +98,12 @@ def test_random_permutations_and_blockings(dtype):
 @pytest.mark.parametrize("dtype", [R.C64, R.C128])
 @pytest.mark.parametrize("mnk", [(130, 70, 37), (64, 64, 16), (65, 33, 17), (200, 3, 300),
                                  (1, 1, 5000), (7, 300, 200), (31, 500, 129), (129, 257, 1),
-                                 (64, 64, 4096), (20, 300, 3001), (300, 20, 2999), (257, 130, 515)])
+                                 (64, 64, 4096), (20, 300, 3001), (300, 20, 2999), (257, 130, 515),
+                                 (7, 30, 3000), (16, 16, 2048)])
 def test_tiles_and_ragged_tails(dtype, mnk):
     """Matrix-shaped problems that span several tiles with ragged edges and
     exercise each kernel family (tiled 128x64 / 64x64, split-K with its
-    reduction, warp-per-output, thread-per-output)."""
+    reduction, CTA-per-output, warp-per-output, thread-per-output)."""
     M, N, K = mnk
     a = W.complex_normal((M, K), 11)
     b = W.complex_normal((K, N), 12)
