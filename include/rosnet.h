@@ -117,6 +117,12 @@ typedef struct {
 #define ROSNET_OPT_REDUCE_SEQUENTIAL  0x10
 #define ROSNET_OPT_REDUCE_TREE        0x20
 #define ROSNET_OPT_REDUCE_COMMUTATIVE 0x40
+#define ROSNET_OPT_AUTOTUNE 0x80 /* contract: when planning, time the candidate
+                                   CUDA-core kernels (tile shape, contracted-range
+                                   split) of every step with >= 1e8 flops on the
+                                   plan's own operands and keep the fastest;
+                                   choices are cached per (dtype, M, N, K, access
+                                   pattern) for the process                       */
 #define ROSNET_OPT_TIMING 0x4   /* contract: record CUDA events around the plan's
                                    heaviest launch (most 8*M*N*K flops) on the
                                    call's stream; read with rosnet_timing_drain    */
@@ -429,6 +435,12 @@ rosnet_status rosnet_sum(int32_t n, const rosnet_btensor *ts, void *stream, rosn
 /* Wait for `stream`; returns CUDA if a kernel failed, TIMEOUT if a bounded
  * device wait of the library gave up. */
 rosnet_status rosnet_sync(void *stream);
+
+/* Launch a kernel that waits on a barrier nothing will complete, giving up
+ * after budget_cycles (<= 4e9) SM cycles: the next rosnet_sync on `stream`
+ * reports ROSNET_ERR_TIMEOUT.  For testing the bounded-wait path of the
+ * library's kernels (no fault, no hang).  The paper has no counterpart. */
+rosnet_status rosnet_selftest_timeout(int64_t budget_cycles, void *stream);
 
 /* Static, human-readable description of a status code. */
 const char *rosnet_status_string(rosnet_status s);

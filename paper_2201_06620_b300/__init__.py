@@ -35,7 +35,7 @@ __all__ = [
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
     "PREC_TF32X3",
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
-    "REDUCE_SEQUENTIAL", "REDUCE_TREE", "REDUCE_COMMUTATIVE",
+    "REDUCE_SEQUENTIAL", "REDUCE_TREE", "REDUCE_COMMUTATIVE", "OPT_AUTOTUNE",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,6 +45,7 @@ C64, C128 = 1, 2
 PREC_DEFAULT, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_FP64, PREC_TF32X3 = 0, 1, 2, 3, 4, 5
 OPT_GRAPH, OPT_NOGROUP, OPT_TIMING = 0x1, 0x2, 0x4
 REDUCE_SEQUENTIAL, REDUCE_TREE, REDUCE_COMMUTATIVE = 0x10, 0x20, 0x40
+OPT_AUTOTUNE = 0x80
 STATUS = {
     0: "OK", -1: "INVALID_ARG", -2: "SHAPE", -3: "BLOCK_MISMATCH", -4: "DTYPE", -5: "ALLOC",
     -6: "RANK_LIMIT", -7: "CUDA", -8: "TIMEOUT", -9: "UNSUPPORTED",
@@ -59,6 +60,7 @@ EXPORTS = [
     "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range", "rosnet_btensor_slice",
     "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_contract_batch", "rosnet_plan_stats",
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
+    "rosnet_selftest_timeout",
 ]
 
 _lock = threading.Lock()
@@ -125,6 +127,7 @@ def lib():
                                               ctypes.POINTER(i64p), ctypes.c_int32, i64p, ctypes.c_int32,
                                               i32p, ctypes.c_int32, i64p, dpp, dpp]
             L.rosnet_sum.argtypes = [ctypes.c_int32, ctypes.POINTER(vp), vp, ctypes.POINTER(vp)]
+            L.rosnet_selftest_timeout.argtypes = [ctypes.c_int64, vp]
             L.rosnet_contract_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
                                                 ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp,
                                                 ctypes.POINTER(vp)]
@@ -171,7 +174,8 @@ def lib():
                         "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range",
                         "rosnet_btensor_slice", "rosnet_btensor_block", "rosnet_tensordot_ooc",
                         "rosnet_contract_batch", "rosnet_plan_stats", "rosnet_btensor_fix",
-                        "rosnet_path_search", "rosnet_slice_search", "rosnet_sum"):
+                        "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
+                        "rosnet_selftest_timeout"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib

@@ -36,6 +36,7 @@ void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *a
 int check_precision(const rosnet_opts *opts, int dtype);
 int64_t reduce_ctas(const GettDesc &d);
 bool is_tc_kind(int kind);
+void autotune_problem(GettDesc &d, int dtype, cudaStream_t s);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b);
@@ -490,6 +491,29 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         fill_desc_tables(S.desc, views[g], dtab + S.table_off);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
+        if ((flags & ROSNET_OPT_AUTOTUNE) && !is_tc_kind(S.desc.kind) &&
+            8.0 * (double)S.desc.M * (double)S.desc.N * (double)S.desc.K >= 1e8) {
+            // time the candidate kernels on the plan's own operands (contents
+            // of intermediates do not matter for timing); C goes to scratch
+            auto bptr = [&](int64_t x) -> std::pair<void *, int64_t> {
+                if (x < 0) {
+                    const Leaf &L = plan->leaves[-1 - x];
+                    rosnet_btensor t = nets[L.net].tensors[L.t];
+                    return {t->data, t->pstride};
+                }
+                return {(char *)plan->arena.p + plan->steps[x].arena_off, plan->steps[x].lay.numel};
+            };
+            DevBuf cs(2 * (size_t)S.lay.numel * (plan->dtype == ROSNET_C64 ? 4 : 8), s);
+            GettDesc x = S.desc;
+            auto pa = bptr(S.ga), pb = bptr(S.gb);
+            bind_operands(x, pa.first, pb.first, cs.p, pa.second, pb.second, S.lay.numel);
+            autotune_problem(x, plan->dtype, s);
+            S.desc.kind = x.kind;
+            S.desc.tiles_m = x.tiles_m;
+            S.desc.tiles_n = x.tiles_n;
+            S.desc.ksplit = x.ksplit;
+            S.desc.ktiles_per_split = x.ktiles_per_split;
+        }
         // tensor-core problems carry their own tensor maps: one launch each
         int key_kind = ((flags & ROSNET_OPT_NOGROUP) || is_tc_kind(S.desc.kind)) ? 1000 + st : S.desc.kind;
         groups[{S.wave, key_kind}].push_back(st);

@@ -17,6 +17,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "internal.h"
 #include "gett_common.cuh"
@@ -759,6 +761,110 @@ static void launch_gett_single(const GettDesc &d, int kind, int64_t ctas, int dt
     ga.single = d;
     ga.single.tile_begin = 0;
     launch_group_args(kind, dtype, ga, ctas, s);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: candidate tile shapes and contracted-range splits, timed
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+    int dtype, flags;
+    int64_t M, N, K;
+    bool operator==(const TuneKey &o) const {
+        return dtype == o.dtype && flags == o.flags && M == o.M && N == o.N && K == o.K;
+    }
+};
+struct TuneKeyHash {
+    size_t operator()(const TuneKey &k) const {
+        return (size_t)(k.M * 1000003 ^ k.N * 10007 ^ k.K * 101 ^ k.flags * 7 ^ k.dtype);
+    }
+};
+struct TuneChoice { int kind; int64_t tiles_m, tiles_n; int32_t ksplit, kps; int32_t flags; };
+std::mutex g_tune_mu;
+auto &g_tune = *new std::unordered_map<TuneKey, TuneChoice, TuneKeyHash>();
+
+void apply_split(GettDesc &d, int BK, int64_t ks) {
+    const int64_t nkt = (d.K + BK - 1) / BK;
+    ks = std::max<int64_t>(1, std::min<int64_t>(ks, std::min<int64_t>(nkt, 64)));
+    d.ktiles_per_split = ks > 1 ? (int)((nkt + ks - 1) / ks) : 0x7fffffff;
+    d.ksplit = ks > 1 ? (int)((nkt + d.ktiles_per_split - 1) / d.ktiles_per_split) : 1;
+}
+}  // namespace
+
+int64_t reduce_ctas(const GettDesc &d);
+
+// Time the candidate kernels of a CUDA-core tiled problem (operands a, b;
+// output written to c_scratch; split partials to a temporary workspace) and
+// keep the fastest in d.  Results are cached by (dtype, M, N, K, flags).
+void autotune_problem(GettDesc &d, int dtype, cudaStream_t s) {
+    if (d.kind != kKindTiled && d.kind != kKindTiledWide) return;
+    if (d.flags & kFlagAtomic) return;
+    const TuneKey key{dtype, d.flags, d.M, d.N, d.K};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            const TuneChoice &c = it->second;
+            d.kind = c.kind;
+            d.tiles_m = c.tiles_m;
+            d.tiles_n = c.tiles_n;
+            d.ksplit = c.ksplit;
+            d.ktiles_per_split = c.kps;
+            return;
+        }
+    }
+    const int BK = dtype == ROSNET_C64 ? 16 : 8;
+    std::vector<GettDesc> cands;
+    const int64_t auto_split = d.ksplit;
+    for (int kind : {(int)kKindTiled, (int)kKindTiledWide}) {
+        if (kind == kKindTiledWide && !(dtype == ROSNET_C64 && d.M >= 128 && d.N >= 48)) continue;
+        const int BM = kind == kKindTiledWide ? 128 : 64;
+        GettDesc x = d;
+        x.kind = kind;
+        x.tiles_m = (d.M + BM - 1) / BM;
+        x.tiles_n = (d.N + 63) / 64;
+        for (int64_t ks : {int64_t(1), auto_split, 2 * auto_split, 4 * auto_split}) {
+            GettDesc y = x;
+            apply_split(y, BK, ks);
+            bool dup = false;
+            for (auto &c : cands)
+                dup |= c.kind == y.kind && c.ksplit == y.ksplit && c.ktiles_per_split == y.ktiles_per_split;
+            if (!dup) cands.push_back(y);
+        }
+    }
+    cudaEvent_t e0, e1;
+    RN_CHECK_CUDA(cudaEventCreate(&e0));
+    RN_CHECK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    GettDesc pick = d;
+    for (GettDesc &c : cands) {
+        DevBuf part(desc_part_bytes(c, dtype), s);
+        c.part = part.p;
+        auto once = [&]() {
+            launch_gett_single(c, c.kind, desc_ctas(c), dtype, s);
+            if (c.part) launch_gett_single(c, kKindReduce, reduce_ctas(c), dtype, s);
+        };
+        once();   // warm-up
+        RN_CHECK_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) once();
+        RN_CHECK_CUDA(cudaEventRecord(e1, s));
+        RN_CHECK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        RN_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    d.kind = pick.kind;
+    d.tiles_m = pick.tiles_m;
+    d.tiles_n = pick.tiles_n;
+    d.ksplit = pick.ksplit;
+    d.ktiles_per_split = pick.ktiles_per_split;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = TuneChoice{d.kind, d.tiles_m, d.tiles_n, d.ksplit, d.ktiles_per_split, d.flags};
 }
 
 // CTAs of the split-K reduction of a problem

@@ -573,6 +573,33 @@ void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *w
     }
 }
 
+// A wait on an mbarrier that nothing completes, bounded by `budget` cycles:
+// exercises the timeout path (status word set, kernel returns) without any
+// fault.  Used by rosnet_selftest_timeout.
+__global__ void selftest_wait_kernel(long long budget, int32_t *result) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = tc::mbar_try(&bar, 0);
+        const long long t0 = clock64();
+        while (!ok) {
+            if (clock64() - t0 > budget) {
+                atomicExch(&g_dev_status, kDevErrTimeout);
+                break;
+            }
+            __nanosleep(64);
+            ok = tc::mbar_try(&bar, 0);
+        }
+        *result = ok ? 1 : 0;
+    }
+}
+
 // Read and clear the device status word (0 = no kernel gave up a wait).
 int32_t take_device_status() {
     int32_t v = 0, z = 0;
@@ -582,3 +609,17 @@ int32_t take_device_status() {
 }
 
 }  // namespace rosnet
+
+extern "C" rosnet_status rosnet_selftest_timeout(int64_t budget_cycles, void *stream) {
+    using namespace rosnet;
+    RN_API_BEGIN
+    if (budget_cycles < 0 || budget_cycles > 4000000000LL)
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "budget must be in [0, 4e9] cycles");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf r(sizeof(int32_t), s);
+    selftest_wait_kernel<<<1, 32, 0, s>>>((long long)budget_cycles, (int32_t *)r.p);
+    g_launches++;
+    RN_CHECK_CUDA(cudaGetLastError());
+    return ROSNET_OK;
+    RN_API_END
+}

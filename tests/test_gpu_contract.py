@@ -131,3 +131,12 @@ def test_contract_errors():
     with pytest.raises(R.RosnetError) as e:
         R.contract([ts[0], tc], [(0,), (0,)], [], [(0, 1)])
     assert e.value.name == "DTYPE"
+
+
+def test_autotuned_plan_matches():
+    """A plan whose CUDA-core steps were autotuned gives the oracle's amplitude."""
+    circ = W.rqc20_config()
+    ref = oracle.amplitude_sv(circ)
+    got, _ = gpu_network(W.circuit_network(circ), R.C64, max_block_entries=256,
+                         flags=R.OPT_GRAPH | R.OPT_AUTOTUNE)
+    assert amp_err(got, ref, 20) <= 1e-5

@@ -235,3 +235,18 @@ def test_reduction_modes_matrix_ragged():
         assert oracle.rel_frobenius(got, ref) <= 1e-5, mode
     with pytest.raises(R.RosnetError):
         R.tensordot(A, B, [1], [0], flags=R.REDUCE_TREE | R.REDUCE_COMMUTATIVE)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A kernel waiting on a barrier that nothing completes gives up after its
+    budget (~1 ms here) and rosnet_sync reports ROSNET_ERR_TIMEOUT; the status
+    is cleared and later work runs normally."""
+    R._init()
+    assert R.lib().rosnet_selftest_timeout(2_000_000, R._default_stream()) == 0
+    with pytest.raises(R.RosnetError) as e:
+        R.sync()
+    assert e.value.name == "TIMEOUT"
+    R.sync()   # cleared
+    a = W.complex_normal((3, 4), 1)
+    _, got = run(a, None, a.T.copy(), None, [1], [0], R.C128)
+    np.testing.assert_allclose(got, a @ a.T, rtol=1e-12, atol=1e-12)
