@@ -13,6 +13,7 @@
 // and the intra-block contraction (step 3), and keeps the partial sums of all
 // pairs in registers (step 4); no transpose pass and no partial block ever
 // reaches memory.  The order of the sum over pairs is free (Sec. IV-A).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +25,8 @@
 #include "gett_common.cuh"
 
 namespace rosnet {
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // planner: the GEMM view
@@ -204,27 +207,34 @@ __device__ __forceinline__ void out_coords(const GettDesc &d, int64_t o, int64_t
 template <typename T>
 __global__ void __launch_bounds__(256) gett_small_kernel(const __grid_constant__ GroupArgs g) {
     __shared__ GettDesc sd;
-    if (threadIdx.x == 0) load_desc(g, sd);
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
     const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
     const int64_t o = tile * 256 + threadIdx.x;
     const int64_t M = sd.M, N = sd.N, K = sd.K;
-    if (o >= M * N) return;
-    int64_t m, n;
-    out_coords(sd, o, m, n);
+    const bool live = o < M * N;
+    int64_t m = 0, n = 0, am = 0, bn = 0, ic = 0;
+    if (live) {
+        out_coords(sd, o, m, n);
+        am = sd.offAM[m];
+        bn = sd.offBN[n];
+        ic = sd.offCM[m] + sd.offCN[n];
+    }
+    grid_dep_wait();
+    if (!live) return;
     const T *__restrict__ A = (const T *)sd.a;
     const T *__restrict__ B = (const T *)sd.b;
     const int64_t *__restrict__ offAK = sd.offAK;
     const int64_t *__restrict__ offBK = sd.offBK;
-    const int64_t am = sd.offAM[m], bn = sd.offBN[n];
     const int64_t ap = sd.a_plane, bp = sd.b_plane;
     T sr = 0, si = 0;
+#pragma unroll 4
     for (int64_t k = 0; k < K; ++k) {
         const int64_t ia = am + offAK[k], ib = bn + offBK[k];
         cmac(sr, si, A[ia], A[ia + ap], B[ib], B[ib + bp]);
     }
     T *C = (T *)sd.c;
-    const int64_t ic = sd.offCM[m] + sd.offCN[n];
     C[ic] = sr;
     C[ic + sd.c_plane] = si;
 }
@@ -233,18 +243,24 @@ __global__ void __launch_bounds__(256) gett_small_kernel(const __grid_constant__
 template <typename T>
 __global__ void __launch_bounds__(256) gett_warpk_kernel(const __grid_constant__ GroupArgs g) {
     __shared__ GettDesc sd;
-    if (threadIdx.x == 0) load_desc(g, sd);
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
     const int64_t o = tile * 8 + (threadIdx.x >> 5);
     const int64_t M = sd.M, N = sd.N, K = sd.K;
-    if (o >= M * N) return;
-    int64_t m, n;
-    out_coords(sd, o, m, n);
+    const bool live = o < M * N;
+    int64_t m = 0, n = 0, am = 0, bn = 0;
+    if (live) {
+        out_coords(sd, o, m, n);
+        am = sd.offAM[m];
+        bn = sd.offBN[n];
+    }
+    grid_dep_wait();
+    if (!live) return;
     const T *__restrict__ A = (const T *)sd.a;
     const T *__restrict__ B = (const T *)sd.b;
-    const int64_t am = sd.offAM[m], bn = sd.offBN[n];
     const int64_t ap = sd.a_plane, bp = sd.b_plane;
     T sr = 0, si = 0;
     for (int64_t k = lane; k < K; k += 32) {
@@ -264,16 +280,26 @@ __global__ void __launch_bounds__(256) gett_warpk_kernel(const __grid_constant__
     }
 }
 
-// One CTA per output entry for very long contractions with few outputs
-// (e.g. the final scalar of a network): 256 threads stride over K with four
-// independent loads in flight each, then a fixed-order block reduction.
+// One cluster of kDotCTAs CTAs per output entry for very long contractions
+// with few outputs (e.g. the final scalar of a network): the cluster's
+// threads stride over K with four independent loads in flight each, every
+// CTA reduces its threads' sums in a fixed order, and CTA 0 of the cluster
+// adds the CTAs' sums in rank order through distributed shared memory.  One
+// launch, no workspace, deterministic.
 template <typename T>
-__global__ void __launch_bounds__(256) gett_dot_kernel(const __grid_constant__ GroupArgs g) {
+__global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
+    gett_dot_kernel(const __grid_constant__ GroupArgs g) {
     __shared__ GettDesc sd;
     __shared__ T red[2][8];
-    if (threadIdx.x == 0) load_desc(g, sd);
+    __shared__ T cta_sum[2];
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
-    const int64_t o = (int64_t)blockIdx.x - sd.tile_begin;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    // tile_begin of every problem is a multiple of kDotCTAs, so one cluster
+    // never spans two problems
+    const int64_t o = ((int64_t)blockIdx.x - sd.tile_begin) / kDotCTAs;
     int64_t m, n;
     out_coords(sd, o, m, n);
     const T *__restrict__ A = (const T *)sd.a;
@@ -282,20 +308,22 @@ __global__ void __launch_bounds__(256) gett_dot_kernel(const __grid_constant__ G
     const int64_t *__restrict__ offBK = sd.offBK;
     const int64_t am = sd.offAM[m], bn = sd.offBN[n], K = sd.K;
     const int64_t ap = sd.a_plane, bp = sd.b_plane;
+    constexpr int64_t stride = 256 * kDotCTAs;
+    grid_dep_wait();
     T sr = 0, si = 0;
-    int64_t k = threadIdx.x;
-    for (; k + 768 < K; k += 1024) {
+    int64_t k = (int64_t)rank * 256 + threadIdx.x;
+    for (; k + 3 * stride < K; k += 4 * stride) {
         int64_t ia[4], ib[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            ia[u] = am + __ldg(offAK + k + 256 * u);
-            ib[u] = bn + __ldg(offBK + k + 256 * u);
+            ia[u] = am + __ldg(offAK + k + stride * u);
+            ib[u] = bn + __ldg(offBK + k + stride * u);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) cmac(sr, si, __ldg(A + ia[u]), __ldg(A + ia[u] + ap), __ldg(B + ib[u]),
                                          __ldg(B + ib[u] + bp));
     }
-    for (; k < K; k += 256) {
+    for (; k < K; k += stride) {
         const int64_t ia = am + offAK[k], ib = bn + offBK[k];
         cmac(sr, si, A[ia], A[ia + ap], B[ib], B[ib + bp]);
     }
@@ -316,27 +344,60 @@ __global__ void __launch_bounds__(256) gett_dot_kernel(const __grid_constant__ G
             tr += red[0][j];
             ti += red[1][j];
         }
+        cta_sum[0] = tr;
+        cta_sum[1] = ti;
+    }
+    cluster.sync();   // every CTA's sum is visible to the cluster
+    if (rank == 0 && threadIdx.x == 0) {
+        T tr = 0, ti = 0;
+        for (int r = 0; r < kDotCTAs; ++r) {
+            const T *p = cluster.map_shared_rank(cta_sum, r);
+            tr += p[0];
+            ti += p[1];
+        }
         T *C = (T *)sd.c;
         const int64_t ic = sd.offCM[m] + sd.offCN[n];
         C[ic] = tr;
         C[ic + sd.c_plane] = ti;
     }
+    cluster.sync();   // no CTA leaves while CTA 0 may still read its sum
 }
 
-// Sum of the split-K partials (in split order: deterministic) into C.
+// Sum of the split-K partials into C, in a fixed order (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(256) gett_reduce_kernel(const __grid_constant__ GroupArgs g) {
+    // 32 outputs per CTA; warp w sums partials w, w + 8, w + 16, ... of its
+    // lane's output (coalesced across lanes, independent loads in flight),
+    // then warp 0 adds the eight sums in warp order: a fixed order, so the
+    // result does not depend on scheduling.
     __shared__ GettDesc sd;
-    if (threadIdx.x == 0) load_desc(g, sd);
+    __shared__ T red[2][8][33];
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
+    grid_dep_wait();
     const int64_t MN = sd.M * sd.N;
-    const int64_t o = ((int64_t)blockIdx.x - sd.tile_begin) * 256 + threadIdx.x;
-    if (o >= MN) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t o = ((int64_t)blockIdx.x - sd.tile_begin) * 32 + lane;
     const T *__restrict__ P = (const T *)sd.part;
     T sr = 0, si = 0;
-    for (int s = 0; s < sd.ksplit; ++s) {
-        sr += P[(2 * (int64_t)s) * MN + o];
-        si += P[(2 * (int64_t)s + 1) * MN + o];
+    if (o < MN) {
+#pragma unroll 4
+        for (int s = w; s < sd.ksplit; s += 8) {
+            sr += __ldg(P + (2 * (int64_t)s) * MN + o);
+            si += __ldg(P + (2 * (int64_t)s + 1) * MN + o);
+        }
+    }
+    red[0][w][lane] = sr;
+    red[1][w][lane] = si;
+    __syncthreads();
+    if (w != 0 || o >= MN) return;
+    sr = red[0][0][lane];
+    si = red[1][0][lane];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) {
+        sr += red[0][j][lane];
+        si += red[1][j][lane];
     }
     const int64_t m = o / sd.N, n = o % sd.N;
     T *C = (T *)sd.c;
@@ -349,8 +410,10 @@ __global__ void __launch_bounds__(256) gett_reduce_kernel(const __grid_constant_
 template <typename T>
 __global__ void __launch_bounds__(256) gett_zero_kernel(const __grid_constant__ GroupArgs g) {
     __shared__ GettDesc sd;
-    if (threadIdx.x == 0) load_desc(g, sd);
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
+    grid_dep_wait();
     const int64_t MN = sd.M * sd.N;
     const int64_t o0 = ((int64_t)blockIdx.x - sd.tile_begin) * 1024 + threadIdx.x;
     T *C = (T *)sd.c;
@@ -387,6 +450,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // intra-block index and keeps all partial sums in registers.  With split-K
 // the CTA covers one contracted range and writes its partial tile to the
 // workspace instead of C (summed by gett_reduce_kernel).
+#ifndef ROSNET_TILED_KU
+#define ROSNET_TILED_KU 2    // unroll of the two-row inner loop
+#endif
+#ifndef ROSNET_TILED_MINB
+#define ROSNET_TILED_MINB 2  // resident CTAs per SM asked of the 64 x 64 FP32 tile
+#endif
+
 template <typename T, int BM, int BN, int BK, int STAGES>
 struct TiledCfg {
     static constexpr int NT = 256;
@@ -509,6 +579,7 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
 #pragma unroll
         for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0;
 
+    grid_dep_wait();   // operands may be the previous kernel's results
     // prologue: tiles 0 .. STAGES-2 in flight, offsets of tile STAGES-1 loaded
 #pragma unroll
     for (int s = 0; s < STAGES - 1; ++s) {
@@ -518,6 +589,38 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
     }
     load_koff(STAGES - 1);
 
+    // one k row of this thread's A and B fragments from shared memory
+    auto frag = [&](const T *a0, const T *b0, int kk, T *xr, T *xi, T *yr, T *yi) {
+#pragma unroll
+        for (int v = 0; v < Cfg::VA; ++v) {
+            V r = *reinterpret_cast<const V *>(a0 + kk * RA + v * Vec16<T>::n);
+            V q = *reinterpret_cast<const V *>(a0 + PA + kk * RA + v * Vec16<T>::n);
+            const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int u = 0; u < Vec16<T>::n; ++u) {
+                xr[v * Vec16<T>::n + u] = rr[u];
+                xi[v * Vec16<T>::n + u] = qq[u];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < Cfg::VB; ++v) {
+            V r = *reinterpret_cast<const V *>(b0 + kk * RB + v * Vec16<T>::n);
+            V q = *reinterpret_cast<const V *>(b0 + PB + kk * RB + v * Vec16<T>::n);
+            const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int u = 0; u < Vec16<T>::n; ++u) {
+                yr[v * Vec16<T>::n + u] = rr[u];
+                yi[v * Vec16<T>::n + u] = qq[u];
+            }
+        }
+    };
+    auto macs = [&](const T *xr, const T *xi, const T *yr, const T *yi) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) cmac(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
+    };
+
     for (int kt = 0; kt < nkt; ++kt) {
         cp_async_wait<STAGES - 2>();
         __syncthreads();   // tile kt visible to all; stage of tile kt-1 free
@@ -525,37 +628,20 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
         cp_async_commit();
         load_koff(kt + STAGES);
         const int st = kt % STAGES;
-        const T *a0 = As + st * 2 * PA + ty * TM, *a1 = a0 + PA;
-        const T *b0 = Bs + st * 2 * PB + tx * TN, *b1 = b0 + PB;
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            T xr[TM], xi[TM], yr[TN], yi[TN];
-#pragma unroll
-            for (int v = 0; v < Cfg::VA; ++v) {
-                V r = *reinterpret_cast<const V *>(a0 + kk * RA + v * Vec16<T>::n);
-                V q = *reinterpret_cast<const V *>(a1 + kk * RA + v * Vec16<T>::n);
-                const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
-#pragma unroll
-                for (int u = 0; u < Vec16<T>::n; ++u) {
-                    xr[v * Vec16<T>::n + u] = rr[u];
-                    xi[v * Vec16<T>::n + u] = qq[u];
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < Cfg::VB; ++v) {
-                V r = *reinterpret_cast<const V *>(b0 + kk * RB + v * Vec16<T>::n);
-                V q = *reinterpret_cast<const V *>(b1 + kk * RB + v * Vec16<T>::n);
-                const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
-#pragma unroll
-                for (int u = 0; u < Vec16<T>::n; ++u) {
-                    yr[v * Vec16<T>::n + u] = rr[u];
-                    yi[v * Vec16<T>::n + u] = qq[u];
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) cmac(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
+        const T *a0 = As + st * 2 * PA + ty * TM;
+        const T *b0 = Bs + st * 2 * PB + tx * TN;
+        // two register fragments: row kk+1 is read from shared memory while
+        // the products of row kk issue; the loop is unrolled only KU times so
+        // that the body stays within the instruction cache
+        constexpr int kKU = ROSNET_TILED_KU;
+        T xr0[TM], xi0[TM], yr0[TN], yi0[TN], xr1[TM], xi1[TM], yr1[TN], yi1[TN];
+        frag(a0, b0, 0, xr0, xi0, yr0, yi0);
+#pragma unroll(kKU)
+        for (int kk = 0; kk < BK; kk += 2) {
+            frag(a0, b0, kk + 1, xr1, xi1, yr1, yi1);
+            macs(xr0, xi0, yr0, yi0);
+            if (kk + 2 < BK) frag(a0, b0, kk + 2, xr0, xi0, yr0, yi0);
+            macs(xr1, xi1, yr1, yi1);
         }
     }
     cp_async_wait<0>();
@@ -601,14 +687,16 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
 }
 
 template <typename T, int BM, int BN, int BK, int STAGES>
-__global__ void __launch_bounds__(256, 1) gett_tiled_kernel(const __grid_constant__ GroupArgs g) {
+__global__ void __launch_bounds__(256, (BM == 64 && sizeof(T) == 4) ? ROSNET_TILED_MINB : 1)
+    gett_tiled_kernel(const __grid_constant__ GroupArgs g) {
     using Cfg = TiledCfg<T, BM, BN, BK, STAGES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);                  // [STAGES][2 planes][BK][RA]
     T *Bs = As + STAGES * 2 * BK * Cfg::RA;                     // [STAGES][2 planes][BK][RB]
     __shared__ GettDesc sd;
     __shared__ int64_t sCM[BM], sCN[BN];
-    if (threadIdx.x == 0) load_desc(g, sd);
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
     switch (((sd.flags & kFlagAMFast) ? 2 : 0) | ((sd.flags & kFlagBNFast) ? 1 : 0)) {
         case 0: tiled_body<T, BM, BN, BK, STAGES, false, false>(sd, As, Bs, sCM, sCN); break;
@@ -684,7 +772,7 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
     if (d.K >= 1024 && MN <= 256) {
         d.kind = kKindDot;
         d.tiles_m = MN;
-        d.tiles_n = 1;
+        d.tiles_n = kDotCTAs;   // one cluster per output
     } else if (d.K >= 128 && MN <= (int64_t(1) << 16)) {
         d.kind = kKindWarpK;
         d.tiles_m = (MN + 7) / 8;
@@ -701,6 +789,26 @@ size_t desc_part_bytes(const GettDesc &d, int dtype) {
     return (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * (dtype == ROSNET_C64 ? 4 : 8);
 }
 
+// Launch a GETT kernel with programmatic stream serialization, so that its
+// prologue (descriptor and offset-table loads) overlaps the end of the
+// previous kernel in the stream; the kernel waits (grid_dep_wait) before it
+// touches operands or results.
+template <typename Kern>
+static void launch_pdl(Kern kern, dim3 grid, size_t smem, cudaStream_t s, const GroupArgs &ga) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    RN_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, ga));
+}
+
 template <typename T, int BM, int BN, int BK>
 static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
     using Cfg = TiledCfg<T, BM, BN, BK, kTiledStages>;
@@ -710,7 +818,7 @@ static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
         attr_set = true;
     }
-    gett_tiled_kernel<T, BM, BN, BK, kTiledStages><<<grid, 256, Cfg::smem, s>>>(ga);
+    launch_pdl(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>, grid, Cfg::smem, s, ga);
 }
 
 static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t total_ctas,
@@ -722,21 +830,21 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "tensor-core problems are launched with their workspace");
     if (dtype == ROSNET_C64) {
         switch (kind) {
-            case kKindSmall: gett_small_kernel<float><<<grid, 256, 0, s>>>(ga); break;
-            case kKindWarpK: gett_warpk_kernel<float><<<grid, 256, 0, s>>>(ga); break;
-            case kKindReduce: gett_reduce_kernel<float><<<grid, 256, 0, s>>>(ga); break;
-            case kKindZero: gett_zero_kernel<float><<<grid, 256, 0, s>>>(ga); break;
-            case kKindDot: gett_dot_kernel<float><<<grid, 256, 0, s>>>(ga); break;
+            case kKindSmall: launch_pdl(gett_small_kernel<float>, grid, 0, s, ga); break;
+            case kKindWarpK: launch_pdl(gett_warpk_kernel<float>, grid, 0, s, ga); break;
+            case kKindReduce: launch_pdl(gett_reduce_kernel<float>, grid, 0, s, ga); break;
+            case kKindZero: launch_pdl(gett_zero_kernel<float>, grid, 0, s, ga); break;
+            case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 0, s, ga); break;
             case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
             default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
         }
     } else {
         switch (kind) {
-            case kKindSmall: gett_small_kernel<double><<<grid, 256, 0, s>>>(ga); break;
-            case kKindWarpK: gett_warpk_kernel<double><<<grid, 256, 0, s>>>(ga); break;
-            case kKindReduce: gett_reduce_kernel<double><<<grid, 256, 0, s>>>(ga); break;
-            case kKindZero: gett_zero_kernel<double><<<grid, 256, 0, s>>>(ga); break;
-            case kKindDot: gett_dot_kernel<double><<<grid, 256, 0, s>>>(ga); break;
+            case kKindSmall: launch_pdl(gett_small_kernel<double>, grid, 0, s, ga); break;
+            case kKindWarpK: launch_pdl(gett_warpk_kernel<double>, grid, 0, s, ga); break;
+            case kKindReduce: launch_pdl(gett_reduce_kernel<double>, grid, 0, s, ga); break;
+            case kKindZero: launch_pdl(gett_zero_kernel<double>, grid, 0, s, ga); break;
+            case kKindDot: launch_pdl(gett_dot_kernel<double>, grid, 0, s, ga); break;
             default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
         }
     }
@@ -868,7 +976,7 @@ void autotune_problem(GettDesc &d, int dtype, cudaStream_t s) {
 }
 
 // CTAs of the split-K reduction of a problem
-int64_t reduce_ctas(const GettDesc &d) { return (d.M * d.N + 255) / 256; }
+int64_t reduce_ctas(const GettDesc &d) { return (d.M * d.N + 31) / 32; }
 
 // ---------------------------------------------------------------------------
 // one pairwise contraction

@@ -197,8 +197,10 @@ enum KernelKind : int32_t {
     kKindTcTF32x3 = 6,   // tcgen05, 3 x TF32 split products
     kKindTcBF16x3 = 7,   // tcgen05, 3 x BF16 split products
     kKindZero = 8,       // zero C before a commutative (atomic) split-K launch
-    kKindDot = 9,        // one CTA per output, long K (e.g. a network's final scalar)
+    kKindDot = 9,        // one CTA cluster per output, long K (e.g. a network's final scalar)
 };
+
+constexpr int kDotCTAs = 8;   // CTAs of the cluster that computes one output of the dot kernel
 
 inline void bind_operands(GettDesc &d, const void *A, const void *B, void *C, int64_t a_numel,
                           int64_t b_numel, int64_t c_numel) {

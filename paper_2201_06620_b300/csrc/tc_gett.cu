@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(const __grid_constant__ Gr
     using C_ = Cfg<MODE>;
     __shared__ GettDesc sd;
     __shared__ float tr[2][32][33];
-    if (threadIdx.x == 0) load_desc(g, sd);
+    if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
     const float *__restrict__ src = (const float *)(which ? sd.b : sd.a);
     const int64_t plane = which ? sd.b_plane : sd.a_plane;
@@ -278,8 +278,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) load_desc(p.g, sd);
     if (tid == 0) {
-        load_desc(p.g, sd);
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
