@@ -35,7 +35,6 @@ void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *a
                      const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc);
 int check_precision(const rosnet_opts *opts, int dtype);
 int64_t reduce_ctas(const GettDesc &d);
-bool is_tc_kind(int kind);
 void autotune_problem(GettDesc &d, int dtype, cudaStream_t s);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
@@ -491,7 +490,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         fill_desc_tables(S.desc, views[g], dtab + S.table_off);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
-        if ((flags & ROSNET_OPT_AUTOTUNE) && !is_tc_kind(S.desc.kind) &&
+        if ((flags & ROSNET_OPT_AUTOTUNE) && !is_packed_kind(S.desc.kind) &&
             8.0 * (double)S.desc.M * (double)S.desc.N * (double)S.desc.K >= 1e8) {
             // time the candidate kernels on the plan's own operands (contents
             // of intermediates do not matter for timing); C goes to scratch
@@ -515,7 +514,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             S.desc.ktiles_per_split = x.ktiles_per_split;
         }
         // tensor-core problems carry their own tensor maps: one launch each
-        int key_kind = ((flags & ROSNET_OPT_NOGROUP) || is_tc_kind(S.desc.kind)) ? 1000 + st : S.desc.kind;
+        int key_kind = ((flags & ROSNET_OPT_NOGROUP) || is_packed_kind(S.desc.kind)) ? 1000 + st : S.desc.kind;
         groups[{S.wave, key_kind}].push_back(st);
         if (S.desc.ksplit > 1 && !(S.desc.flags & kFlagAtomic)) split_of_wave[S.wave].push_back(st);
         if (S.desc.flags & kFlagAtomic) atomic_of_wave[S.wave].push_back(st);
@@ -541,9 +540,9 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         Plan::Launch L;
         L.kind = kind;
         L.tc_ws_off = 0;
-        if (is_tc_kind(kind)) {
+        if (is_packed_kind(kind)) {
             L.tc_ws_off = tc_bytes;
-            tc_bytes += (tc_workspace_bytes(plan->steps[sts[0]].desc, kind - kKindTcTF32) + 255) & ~(size_t)255;
+            tc_bytes += (tc_workspace_bytes(plan->steps[sts[0]].desc, packed_mode(kind)) + 255) & ~(size_t)255;
         }
         L.first = (int)plan->desc_step.size();
         L.count = (int)sts.size();
@@ -659,12 +658,12 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
                 RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal)
                                         : cudaEventRecord(e0, s));
             }
-            if (is_tc_kind(L.kind)) {
+            if (is_packed_kind(L.kind)) {
                 GroupArgs ga;
                 memset(&ga, 0, sizeof(ga));
                 ga.descs = dd + L.first;
                 ga.ndesc = 1;
-                launch_tc_problem(L.kind - kKindTcTF32, P.slot_desc[L.first], ga,
+                launch_tc_problem(packed_mode(L.kind), P.slot_desc[L.first], ga,
                                   (char *)P.tcws.p + L.tc_ws_off, s, true, true);
             } else {
                 launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);

@@ -726,6 +726,8 @@ constexpr int kSMs = 148;
 bool tc_mode_of(int precision, int *mode);
 int tc_tile_m();
 int tc_tile_n();
+int f32p_tile_m();
+int f32p_tile_n();
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b);
@@ -743,6 +745,18 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
         d.tiles_m = (d.M + tc_tile_m() - 1) / tc_tile_m();
         d.tiles_n = (d.N + tc_tile_n() - 1) / tc_tile_n();
         return;
+    }
+    // large FP32 contractions: pack once, then TMA-fed FFMA tiles (no split-K)
+    if (dtype == ROSNET_C64 && reduce_mode != kReduceTree && reduce_mode != kReduceCommutative &&
+        std::min(d.M, d.N) >= 64 && d.K >= 128 && 8.0 * (double)MN * (double)d.K >= 268435456.0) {
+        const int64_t t = ((d.M + f32p_tile_m() - 1) / f32p_tile_m()) * ((d.N + f32p_tile_n() - 1) / f32p_tile_n());
+        if (t >= 120) {
+            if (d.N > d.M) swap_operands(d);
+            d.kind = kKindPackF32;
+            d.tiles_m = (d.M + f32p_tile_m() - 1) / f32p_tile_m();
+            d.tiles_n = (d.N + f32p_tile_n() - 1) / f32p_tile_n();
+            return;
+        }
     }
     const bool tiled_ok = d.K >= 16 && std::min(d.M, d.N) >= 16 && MN >= 2048;
     if (tiled_ok) {
@@ -789,26 +803,6 @@ size_t desc_part_bytes(const GettDesc &d, int dtype) {
     return (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * (dtype == ROSNET_C64 ? 4 : 8);
 }
 
-// Launch a GETT kernel with programmatic stream serialization, so that its
-// prologue (descriptor and offset-table loads) overlaps the end of the
-// previous kernel in the stream; the kernel waits (grid_dep_wait) before it
-// touches operands or results.
-template <typename Kern>
-static void launch_pdl(Kern kern, dim3 grid, size_t smem, cudaStream_t s, const GroupArgs &ga) {
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    RN_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, ga));
-}
-
 template <typename T, int BM, int BN, int BK>
 static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
     using Cfg = TiledCfg<T, BM, BN, BK, kTiledStages>;
@@ -818,7 +812,7 @@ static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
         attr_set = true;
     }
-    launch_pdl(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>, grid, Cfg::smem, s, ga);
+    launch_pdl(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>, grid, 256, Cfg::smem, s, ga);
 }
 
 static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t total_ctas,
@@ -826,25 +820,25 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
     if (total_ctas <= 0) return;
     if (total_ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "too many tiles in one launch");
     dim3 grid((unsigned)total_ctas);
-    if (kind >= kKindTcTF32 && kind <= kKindTcBF16x3)
+    if (is_packed_kind(kind))
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "tensor-core problems are launched with their workspace");
     if (dtype == ROSNET_C64) {
         switch (kind) {
-            case kKindSmall: launch_pdl(gett_small_kernel<float>, grid, 0, s, ga); break;
-            case kKindWarpK: launch_pdl(gett_warpk_kernel<float>, grid, 0, s, ga); break;
-            case kKindReduce: launch_pdl(gett_reduce_kernel<float>, grid, 0, s, ga); break;
-            case kKindZero: launch_pdl(gett_zero_kernel<float>, grid, 0, s, ga); break;
-            case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 0, s, ga); break;
+            case kKindSmall: launch_pdl(gett_small_kernel<float>, grid, 256, 0, s, ga); break;
+            case kKindWarpK: launch_pdl(gett_warpk_kernel<float>, grid, 256, 0, s, ga); break;
+            case kKindReduce: launch_pdl(gett_reduce_kernel<float>, grid, 256, 0, s, ga); break;
+            case kKindZero: launch_pdl(gett_zero_kernel<float>, grid, 256, 0, s, ga); break;
+            case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 256, 0, s, ga); break;
             case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
             default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
         }
     } else {
         switch (kind) {
-            case kKindSmall: launch_pdl(gett_small_kernel<double>, grid, 0, s, ga); break;
-            case kKindWarpK: launch_pdl(gett_warpk_kernel<double>, grid, 0, s, ga); break;
-            case kKindReduce: launch_pdl(gett_reduce_kernel<double>, grid, 0, s, ga); break;
-            case kKindZero: launch_pdl(gett_zero_kernel<double>, grid, 0, s, ga); break;
-            case kKindDot: launch_pdl(gett_dot_kernel<double>, grid, 0, s, ga); break;
+            case kKindSmall: launch_pdl(gett_small_kernel<double>, grid, 256, 0, s, ga); break;
+            case kKindWarpK: launch_pdl(gett_warpk_kernel<double>, grid, 256, 0, s, ga); break;
+            case kKindReduce: launch_pdl(gett_reduce_kernel<double>, grid, 256, 0, s, ga); break;
+            case kKindZero: launch_pdl(gett_zero_kernel<double>, grid, 256, 0, s, ga); break;
+            case kKindDot: launch_pdl(gett_dot_kernel<double>, grid, 256, 0, s, ga); break;
             default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
         }
     }
@@ -1003,12 +997,12 @@ struct Prepared {
         fill_desc_tables(d, v, (const int64_t *)tab.p);
         choose_kernel(d, dt, precision, reduce_mode);
         if (is_tc())
-            tcws = DevBuf(tc_workspace_bytes(d, d.kind - kKindTcTF32), s);
+            tcws = DevBuf(tc_workspace_bytes(d, packed_mode(d.kind)), s);
         else
             part = DevBuf(desc_part_bytes(d, dt), s);
         d.part = part.p;
     }
-    bool is_tc() const { return d.kind >= kKindTcTF32 && d.kind <= kKindTcBF16x3; }
+    bool is_tc() const { return is_packed_kind(d.kind); }
     void run(rosnet_btensor A, rosnet_btensor B, rosnet_btensor C, cudaStream_t s, bool pack_b = true) {
         if (empty) return;
         GettDesc x = d;
@@ -1020,7 +1014,7 @@ struct Prepared {
             ga.single = x;
             // after an operand swap the kernel's first operand is B
             const bool sw = x.flags & kFlagSwapped;
-            launch_tc_problem(x.kind - kKindTcTF32, x, ga, tcws.p, s, sw ? pack_b : true, sw ? true : pack_b);
+            launch_tc_problem(packed_mode(x.kind), x, ga, tcws.p, s, sw ? pack_b : true, sw ? true : pack_b);
             return;
         }
         if (x.flags & kFlagAtomic) launch_gett_single(x, kKindZero, zero_ctas(x), dtype, s);
@@ -1048,7 +1042,6 @@ int check_reduce(const rosnet_opts *opts) {
     }
 }
 
-bool is_tc_kind(int kind) { return kind >= kKindTcTF32 && kind <= kKindTcBF16x3; }
 
 // The same contraction with caller-provided scratch instead of allocations:
 // the offset tables and any split-K partials are placed in `ws` (ws_bytes
@@ -1064,8 +1057,8 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
     const size_t tab_bytes = (table_entries(v) * sizeof(int64_t) + 255) & ~(size_t)255;
     fill_desc_tables(d, v, (const int64_t *)ws);
     choose_kernel(d, A->dtype, precision);
-    const bool tcp = d.kind >= kKindTcTF32 && d.kind <= kKindTcBF16x3;
-    const size_t extra = tcp ? tc_workspace_bytes(d, d.kind - kKindTcTF32) : desc_part_bytes(d, A->dtype);
+    const bool tcp = is_packed_kind(d.kind);
+    const size_t extra = tcp ? tc_workspace_bytes(d, packed_mode(d.kind)) : desc_part_bytes(d, A->dtype);
     const size_t need = tab_bytes + extra;
     if (need > ws_bytes) return need;
     launch_build_tables(v, (int64_t *)ws, s);
@@ -1075,7 +1068,7 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
         memset(&ga, 0, sizeof(ga));
         ga.ndesc = 1;
         ga.single = d;
-        launch_tc_problem(d.kind - kKindTcTF32, d, ga, (char *)ws + tab_bytes, s, true, true);
+        launch_tc_problem(packed_mode(d.kind), d, ga, (char *)ws + tab_bytes, s, true, true);
         return need;
     }
     d.part = d.ksplit > 1 ? (char *)ws + tab_bytes : nullptr;

@@ -1,6 +1,8 @@
 // Device-side pieces shared by the GETT kernel files.
 #pragma once
 
+#include <cstring>
+
 #include "internal.h"
 
 namespace rosnet {
@@ -53,6 +55,25 @@ __device__ __forceinline__ void load_desc(const GroupArgs &g, GettDesc &sd) {
 // Without the attribute both are no-ops.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch a kernel with programmatic stream serialization, so that its
+// prologue overlaps the end of the previous kernel in the stream; the kernel
+// calls grid_dep_wait() before it touches operands, workspaces or results.
+template <typename Kern, typename... Args>
+inline void launch_pdl(Kern kern, dim3 grid, unsigned threads, size_t smem, cudaStream_t s, const Args &...args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    RN_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+}
 
 // Device status word: kernels set a nonzero code when a bounded wait gives up
 // (see rosnet_sync).

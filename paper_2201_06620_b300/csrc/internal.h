@@ -198,7 +198,17 @@ enum KernelKind : int32_t {
     kKindTcBF16x3 = 7,   // tcgen05, 3 x BF16 split products
     kKindZero = 8,       // zero C before a commutative (atomic) split-K launch
     kKindDot = 9,        // one CTA cluster per output, long K (e.g. a network's final scalar)
+    kKindPackF32 = 10,   // plain FP32 on CUDA cores from packed operands (TMA-fed 64x64 tiles)
 };
+
+// Kinds that run as pack kernels + a GEMM on packed operands held in a
+// per-problem workspace (one launch sequence per problem), and their packed
+// mode: 0 TF32, 1 3xTF32, 2 3xBF16 (tcgen05), 3 FP32 (CUDA cores).
+constexpr int kPackedModeF32 = 3;
+inline bool is_packed_kind(int kind) {
+    return (kind >= kKindTcTF32 && kind <= kKindTcBF16x3) || kind == kKindPackF32;
+}
+inline int packed_mode(int kind) { return kind == kKindPackF32 ? kPackedModeF32 : kind - kKindTcTF32; }
 
 constexpr int kDotCTAs = 8;   // CTAs of the cluster that computes one output of the dot kernel
 

@@ -448,6 +448,282 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
+// 3. plain FP32 products on the CUDA cores from packed operands
+// ---------------------------------------------------------------------------
+// The same two-kernel scheme for the FP32 precision: f32_pack_kernel gathers
+// each operand once through its offset tables into [2 planes][Kpad][Rpad]
+// arrays (rows contiguous), and f32_gemm_kernel streams (BM or BN) x BK boxes
+// of them into a ring of shared-memory stages with TMA tensor copies, so the
+// inner loop is FFMAs and shared-memory loads only: no per-element address
+// arithmetic, no offset-table reads.  Each complex product is the four real
+// FP32 products of the definition, accumulated in FP32 registers over every
+// matched block pair of the tile (Sec. II-C steps 2-4) in a fixed order.
+namespace f32p {
+
+#ifndef ROSNET_F32P_BM
+#define ROSNET_F32P_BM 64
+#endif
+#ifndef ROSNET_F32P_BK
+#define ROSNET_F32P_BK 32
+#endif
+#ifndef ROSNET_F32P_STAGES
+#define ROSNET_F32P_STAGES 3
+#endif
+#ifndef ROSNET_F32P_KU
+#define ROSNET_F32P_KU 2
+#endif
+constexpr int NT = 256;   // 16 x 16 threads, TM x TN complex outputs each
+constexpr int BM = ROSNET_F32P_BM, BN = 64, BK = ROSNET_F32P_BK, STAGES = ROSNET_F32P_STAGES;
+constexpr int TM = BM / 16, TN = BN / 16;
+constexpr int KU = ROSNET_F32P_KU;                         // unroll of the two-row inner loop
+constexpr int PA = BK * BM, PB = BK * BN;                  // floats of one plane of one stage
+constexpr uint32_t STAGE_BYTES = 2u * (PA + PB) * 4u;
+constexpr int KQ = 32;                                     // k tile of the pack kernel
+static_assert(KQ % BK == 0 && TM % 4 == 0 && TN % 4 == 0, "tile shape");
+// the finished C tile is staged through the (then idle) stage ring as two
+// planes of [BN][BM + 1] (or [BM][BN + 1]) floats
+constexpr size_t EPI_BYTES = 2 * (size_t)(BM + 1) * (BN + 1) * 4;
+constexpr size_t RING_BYTES = (size_t)STAGES * STAGE_BYTES;
+constexpr size_t SMEM = (RING_BYTES > EPI_BYTES ? RING_BYTES : EPI_BYTES) + 128;
+
+struct Args {
+    CUtensorMap mapA, mapB;   // packed operands as 2-D {Rpad, 2 * Kpad} FP32 arrays
+    GroupArgs g;              // the problem (C pointer, C offset tables, M, N, K, tiles)
+    int32_t nkt;              // k-stages (Kpad / BK)
+    int32_t kpad;             // rows of one plane
+};
+
+// out[p][k][r] = operand(r, k) plane p (0 outside R x K), for A (the first
+// na CTAs) and then B.  32 x 32 (row, k) tiles transposed through shared
+// memory so that the gather (along the operand's unit-stride digit) and the
+// store (along rows) both coalesce.
+__global__ void __launch_bounds__(256) f32_pack_kernel(const __grid_constant__ GroupArgs g, float *__restrict__ outA,
+                                                       float *__restrict__ outB, int64_t Mpad, int64_t Npad,
+                                                       int64_t Kpad, int64_t na, int skip_a) {
+    __shared__ GettDesc sd;
+    __shared__ float tr[2][32][33];
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
+    __syncthreads();
+    const int which = (skip_a || (int64_t)blockIdx.x >= na) ? 1 : 0;
+    const int64_t bid = (int64_t)blockIdx.x - (which && !skip_a ? na : 0);
+    const float *__restrict__ src = (const float *)(which ? sd.b : sd.a);
+    float *__restrict__ out = which ? outB : outA;
+    const int64_t Rpad = which ? Npad : Mpad;
+    const int64_t plane = which ? sd.b_plane : sd.a_plane;
+    const int64_t *__restrict__ offR = which ? sd.offBN : sd.offAM;
+    const int64_t *__restrict__ offK = which ? sd.offBK : sd.offAK;
+    const int64_t R = which ? sd.N : sd.M, K = sd.K;
+    const bool row_fast = which ? (sd.flags & kFlagBNFast) : (sd.flags & kFlagAMFast);
+    const int64_t rtiles = Rpad / 32;
+    const int64_t r0 = (bid % rtiles) * 32, k0 = (bid / rtiles) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    int64_t o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {   // offsets first (static tables), operands after the wait
+        const int a = tx, b = ty + 8 * j;
+        const int64_t r = r0 + (row_fast ? a : b), k = k0 + (row_fast ? b : a);
+        o[j] = (r < R && k < K) ? offR[r] + offK[k] : -1;
+    }
+    grid_dep_wait();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int a = tx, b = ty + 8 * j;
+        const int rr = row_fast ? a : b, kk = row_fast ? b : a;
+        tr[0][kk][rr] = o[j] >= 0 ? src[o[j]] : 0.f;
+        tr[1][kk][rr] = o[j] >= 0 ? src[o[j] + plane] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int kk = ty + 8 * j, rr = tx;
+        const size_t e = (size_t)(k0 + kk) * Rpad + (r0 + rr);
+        out[e] = tr[0][kk][rr];
+        out[(size_t)Kpad * Rpad + e] = tr[1][kk][rr];
+    }
+}
+
+__device__ __forceinline__ void cmac4(float &cr, float &ci, float ar, float ai, float br, float bi) {
+    cr = fmaf(ar, br, cr);
+    cr = fmaf(-ai, bi, cr);
+    ci = fmaf(ar, bi, ci);
+    ci = fmaf(ai, br, ci);
+}
+
+__global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __grid_constant__ Args p) {
+    extern __shared__ unsigned char dsm_raw[];
+    float *stg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~(uintptr_t)127);
+    __shared__ GettDesc sd;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    grid_dep_launch();
+    if (warp == 0) load_desc(p.g, sd);
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full_bar[s], 1);
+            tc::mbar_init(&empty_bar[s], NT / 32);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // raster: the operand with fewer tiles varies fastest (its tiles stay in L2)
+    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
+    const bool n_fast = sd.tiles_n < sd.tiles_m;
+    const int64_t tm = n_fast ? tile / sd.tiles_n : tile % sd.tiles_m;
+    const int64_t tn = n_fast ? tile % sd.tiles_n : tile / sd.tiles_m;
+    const int m0 = (int)(tm * BM), n0 = (int)(tn * BN);
+    const int nkt = p.nkt;
+    grid_dep_wait();   // the packed operands are the previous kernel's output
+
+    auto issue = [&](int kt) {   // one thread: tile kt into its stage
+        const int s = kt % STAGES;
+        tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+        const uint32_t sa = tc::su32(stg + (size_t)s * 2 * (PA + PB));
+        const uint32_t sb = sa + 2u * PA * 4u;
+        tc::tma_load_2d(sa, &p.mapA, m0, kt * BK, &full_bar[s]);
+        tc::tma_load_2d(sa + PA * 4u, &p.mapA, m0, p.kpad + kt * BK, &full_bar[s]);
+        tc::tma_load_2d(sb, &p.mapB, n0, kt * BK, &full_bar[s]);
+        tc::tma_load_2d(sb + PB * 4u, &p.mapB, n0, p.kpad + kt * BK, &full_bar[s]);
+    };
+    int issued = 0;
+    if (tid == 0)
+        for (; issued < min(STAGES, nkt); ++issued) issue(issued);
+
+    const int ty = tid >> 4, tx = tid & 15;
+    float cr[TM][TN], ci[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0.f;
+
+    auto frag = [&](const float *a0, const float *b0, int kk, float *xr, float *xi, float *yr, float *yi) {
+#pragma unroll
+        for (int v = 0; v < TM / 4; ++v) {
+            const float4 r = *reinterpret_cast<const float4 *>(a0 + kk * BM + 4 * v);
+            const float4 q = *reinterpret_cast<const float4 *>(a0 + PA + kk * BM + 4 * v);
+            xr[4 * v] = r.x; xr[4 * v + 1] = r.y; xr[4 * v + 2] = r.z; xr[4 * v + 3] = r.w;
+            xi[4 * v] = q.x; xi[4 * v + 1] = q.y; xi[4 * v + 2] = q.z; xi[4 * v + 3] = q.w;
+        }
+#pragma unroll
+        for (int v = 0; v < TN / 4; ++v) {
+            const float4 r = *reinterpret_cast<const float4 *>(b0 + kk * BN + 4 * v);
+            const float4 q = *reinterpret_cast<const float4 *>(b0 + PB + kk * BN + 4 * v);
+            yr[4 * v] = r.x; yr[4 * v + 1] = r.y; yr[4 * v + 2] = r.z; yr[4 * v + 3] = r.w;
+            yi[4 * v] = q.x; yi[4 * v + 1] = q.y; yi[4 * v + 2] = q.z; yi[4 * v + 3] = q.w;
+        }
+    };
+    auto macs = [&](const float *xr, const float *xi, const float *yr, const float *yi) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) cmac4(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
+    };
+
+    int done0 = 0;   // tiles whose full barrier thread 0 has passed
+    for (int kt = 0; kt < nkt; ++kt) {
+        const int s = kt % STAGES;
+        // every lane observes the phase itself; the warp leaves together
+        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&full_bar[s], (kt / STAGES) & 1, &abort_flag));
+        if (!ok) break;
+        if (tid == 0) done0 = kt + 1;
+        const float *a0 = stg + (size_t)s * 2 * (PA + PB) + ty * TM;
+        const float *b0 = stg + (size_t)s * 2 * (PA + PB) + 2 * PA + tx * TN;
+        float xr0[TM], xi0[TM], yr0[TN], yi0[TN], xr1[TM], xi1[TM], yr1[TN], yi1[TN];
+        frag(a0, b0, 0, xr0, xi0, yr0, yi0);
+#pragma unroll(KU)
+        for (int kk = 0; kk < BK; kk += 2) {
+            frag(a0, b0, kk + 1, xr1, xi1, yr1, yi1);
+            macs(xr0, xi0, yr0, yi0);
+            if (kk + 2 < BK) frag(a0, b0, kk + 2, xr0, xi0, yr0, yi0);
+            macs(xr1, xi1, yr1, yi1);
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty_bar[s]);
+        // warp 0 refills the stage consumed one iteration ago (all warps have
+        // normally released it by now), keeping STAGES - 1 tiles ahead; the
+        // whole warp takes the branch so that no lane computes alone
+        if (warp == 0 && kt >= 1 && kt - 1 + STAGES < nkt) {
+            bool ok2 = true;
+            if (lane == 0) {
+                const int t = kt - 1;
+                ok2 = tc::mbar_wait(&empty_bar[t % STAGES], (t / STAGES) & 1, &abort_flag);
+                if (ok2) {
+                    issue(t + STAGES);
+                    issued = t + STAGES + 1;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0)) break;
+        }
+    }
+    if (tid == 0)   // no copy may still be landing in shared memory when the CTA exits
+        for (int t = done0; t < issued; ++t)
+            tc::mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1, &abort_flag, false);
+    __syncthreads();
+    if (abort_flag) return;
+
+    // epilogue: stage the tile in shared memory, then write C with the lanes
+    // of a warp running along C's unit-stride dimension (m unless kFlagCNFast)
+    float *C = (float *)sd.c;
+    const int64_t cp = sd.c_plane;
+    const bool m_fast = !(sd.flags & kFlagCNFast);
+    float *cs = stg;
+    const int ld = m_fast ? BM + 1 : BN + 1;             // row length of the staged tile
+    const int plane = (m_fast ? BN : BM) * ld;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int ml = ty * TM + i, nl = tx * TN + j;
+            const int e = m_fast ? nl * ld + ml : ml * ld + nl;
+            cs[e] = cr[i][j];
+            cs[plane + e] = ci[i][j];
+        }
+    __syncthreads();
+    const int64_t M = sd.M, N = sd.N;
+    if (m_fast) {
+        int64_t cm[BM / 32];
+#pragma unroll
+        for (int u = 0; u < BM / 32; ++u) {
+            const int64_t m = m0 + lane + 32 * u;
+            cm[u] = m < M ? __ldg(sd.offCM + m) : -1;
+        }
+        for (int nl = warp; nl < BN; nl += NT / 32) {
+            const int64_t n = n0 + nl;
+            if (n >= N) break;
+            const int64_t cn = __ldg(sd.offCN + n);
+#pragma unroll
+            for (int u = 0; u < BM / 32; ++u)
+                if (cm[u] >= 0) {
+                    C[cm[u] + cn] = cs[nl * ld + lane + 32 * u];
+                    C[cm[u] + cn + cp] = cs[plane + nl * ld + lane + 32 * u];
+                }
+        }
+    } else {
+        int64_t cn[BN / 32];
+#pragma unroll
+        for (int u = 0; u < BN / 32; ++u) {
+            const int64_t n = n0 + lane + 32 * u;
+            cn[u] = n < N ? __ldg(sd.offCN + n) : -1;
+        }
+        for (int ml = warp; ml < BM; ml += NT / 32) {
+            const int64_t m = m0 + ml;
+            if (m >= M) break;
+            const int64_t cm = __ldg(sd.offCM + m);
+#pragma unroll
+            for (int u = 0; u < BN / 32; ++u)
+                if (cn[u] >= 0) {
+                    C[cm + cn[u]] = cs[ml * ld + lane + 32 * u];
+                    C[cm + cn[u] + cp] = cs[plane + ml * ld + lane + 32 * u];
+                }
+        }
+    }
+}
+
+}  // namespace f32p
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 bool tc_mode_of(int precision, int *mode) {
@@ -547,10 +823,76 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
     RN_CHECK_CUDA(cudaGetLastError());
 }
 
+struct F32Geom {
+    int64_t Mpad, Npad, Kpad;
+};
+
+F32Geom f32_geom(const GettDesc &d) {
+    F32Geom g;
+    g.Mpad = (d.M + f32p::BM - 1) / f32p::BM * f32p::BM;
+    g.Npad = (d.N + f32p::BN - 1) / f32p::BN * f32p::BN;
+    g.Kpad = (d.K + f32p::KQ - 1) / f32p::KQ * f32p::KQ;   // KQ is a multiple of BK
+    return g;
+}
+
+// 2-D map over one packed [2 planes][Kpad][rows] FP32 operand: {rows, 2 Kpad},
+// boxes of `box_rows` rows x BK k (no swizzle: the GEMM reads rows as float4).
+void make_map_f32(CUtensorMap *m, void *base, int64_t rows, int64_t Kpad, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)(2 * Kpad)};
+    cuuint64_t strides[1] = {(cuuint64_t)(rows * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)f32p::BK};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) RN_FAIL(ROSNET_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
+void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, cudaStream_t s, bool pack_a,
+                bool pack_b) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)f32p::SMEM));
+        attr_set = true;
+    }
+    const F32Geom g = f32_geom(d);
+    float *pa = (float *)ws;
+    float *pb = pa + 2 * g.Mpad * g.Kpad;
+    const int64_t ca = (g.Mpad / 32) * (g.Kpad / 32), cb = (g.Npad / 32) * (g.Kpad / 32);
+    if (ca > 0x7fffffffLL || cb > 0x7fffffffLL || 2 * g.Kpad > 0x7fffffffLL || g.Mpad > 0x7fffffffLL ||
+        g.Npad > 0x7fffffffLL)
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "operand too large to pack");
+    if (pack_a || pack_b) {
+        const int64_t n = (pack_a ? ca : 0) + (pack_b ? cb : 0);
+        if (n > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "operands too large to pack");
+        launch_pdl(f32p::f32_pack_kernel, dim3((unsigned)n), 256, 0, s, ga, pa, pb, g.Mpad, g.Npad, g.Kpad,
+                   pack_a ? ca : (int64_t)0, pack_a ? 0 : 1);
+        g_launches++;
+    }
+    f32p::Args args;
+    memset(&args, 0, sizeof(args));
+    make_map_f32(&args.mapA, pa, g.Mpad, g.Kpad, f32p::BM);
+    make_map_f32(&args.mapB, pb, g.Npad, g.Kpad, f32p::BN);
+    args.g = ga;
+    args.nkt = (int)(g.Kpad / f32p::BK);
+    args.kpad = (int)g.Kpad;
+    launch_pdl(f32p::f32_gemm_kernel, dim3((unsigned)ctas), f32p::NT, f32p::SMEM, s, args);
+    g_launches++;
+    RN_CHECK_CUDA(cudaGetLastError());
+}
+
 }  // namespace
 
-// Workspace bytes of the packed operands of a tensor-core problem.
+int f32p_tile_m() { return f32p::BM; }
+int f32p_tile_n() { return f32p::BN; }
+
+// Workspace bytes of the packed operands of a packed-kind problem.
 size_t tc_workspace_bytes(const GettDesc &d, int mode) {
+    if (mode == kPackedModeF32) {
+        const F32Geom g = f32_geom(d);
+        return (size_t)2 * (g.Mpad + g.Npad) * g.Kpad * 4;
+    }
     TcGeom g = tc_geom(d, mode);
     return g.narr * (g.arrA + g.arrB);
 }
@@ -561,9 +903,14 @@ size_t tc_workspace_bytes(const GettDesc &d, int mode) {
 // reuse the packed operand already in ws (same operand as the previous call).
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b) {
-    const TcGeom g = tc_geom(d, mode);
     const int64_t ctas = d.tiles_m * d.tiles_n;
     if (ctas <= 0) return;
+    if (ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one launch");
+    if (mode == kPackedModeF32) {
+        launch_f32(ga, d, ws, ctas, s, pack_a, pack_b);
+        return;
+    }
+    const TcGeom g = tc_geom(d, mode);
     if (ctas > 0x7fffffffLL || g.Kpad / g.bk > 0x7fffffffLL || g.Mpad > 0x7fffffffLL || g.Npad > 0x7fffffffLL)
         RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one tensor-core launch");
     switch (mode) {
