@@ -38,6 +38,13 @@ import workloads as W  # noqa: E402
 N_QUBITS = 20
 MAX_BLOCK = 256           # 2^8-entry blocks on every intermediate of rank > 8
 WORKLOAD = "rqc20_4x5_d12_amplitude"
+# kernel family of the heaviest launch (rosnet_timing_drain kinds)
+KERNEL_NAMES = {
+    2: "gett_tiled_kernel 64x64 (offset-table gathers, FFMA)",
+    3: "gett_tiled_kernel 128x64 (offset-table gathers, FFMA)",
+    10: "f32_gemm_kernel (packed FP32 operands, TMA-fed FFMA 64x64x32; packs excluded)",
+    5: "tc_gemm_kernel TF32 (tcgen05)", 6: "tc_gemm_kernel 3xTF32 (tcgen05)", 7: "tc_gemm_kernel 3xBF16 (tcgen05)",
+}
 METRIC = "amplitudes/s"
 
 
@@ -152,6 +159,9 @@ def run_rosnet(args):
     # |0> and |1> for every output qubit, resident; a step binds its bitstring's
     proj = [[R.btensor(np.eye(2, dtype=np.complex64)[b]) for b in (0, 1)] for _ in range(N_QUBITS)]
     flags = R.OPT_GRAPH | R.OPT_TIMING | (0 if args.no_autotune else R.OPT_AUTOTUNE)
+    if args.tune_file and os.path.exists(args.tune_file):
+        with open(args.tune_file) as f:
+            R.tune_import(f.read())          # kernel choices of an earlier run
 
     def bind(i):
         for q in range(N_QUBITS):
@@ -166,6 +176,9 @@ def run_rosnet(args):
         outs.append(R.contract(net, path=path, flags=flags, max_block_entries=MAX_BLOCK))
     torch.cuda.synchronize()
     R.timing_drain()
+    if args.tune_file:
+        with open(args.tune_file, "w") as f:
+            f.write(R.tune_export())
     launches0 = R.kernel_launches()
     clocks = ClockSampler(local)
     clocks.start()
@@ -204,12 +217,13 @@ def run_rosnet(args):
     hms = [h[0] for h in heavy]
     hflops = heavy[0][1] if heavy else 0.0
     hbytes = heavy[0][2] if heavy else 0.0
+    hkind = heavy[0][3] if heavy else -1
     h_avg = statistics.mean(hms) if hms else float("nan")
     achieved = hflops / (h_avg * 1e-3) / 1e12 if hms else None
     traffic = _profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
-                "kernel": "gett_tiled (heaviest grouped launch)", "launch_ms": h_avg,
+                "kernel": KERNEL_NAMES.get(hkind, f"kind {hkind}"), "launch_ms": h_avg,
                 "flops_per_launch": hflops, "bytes_per_launch": hbytes,
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)"}
 
@@ -255,7 +269,7 @@ def run_e2e(args, R, torch, circ, net, path, ngates, stream):
     for q in range(N_QUBITS):
         net.set_tensor(ngates + q, rows[q])
     out_host = torch.empty((), dtype=torch.complex64).pin_memory()
-    flags = R.OPT_GRAPH
+    flags = R.OPT_GRAPH | (0 if args.no_autotune else R.OPT_AUTOTUNE)   # the timed run's kernel choices
     h2d = N_QUBITS * 2 * 8
     t0 = None
     for i in range(steps):
@@ -555,6 +569,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-file", default=None,
+                    help="load autotuner decisions from this file if it exists; save them after planning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", choices=["rqc20", "serve", "batch", "sweep"], default="rqc20")
     ap.add_argument("--pool", type=int, default=64)

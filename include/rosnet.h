@@ -385,13 +385,36 @@ rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path
 /*
  * Elapsed device time of the heaviest launch of every rosnet_contract call
  * made with ROSNET_OPT_TIMING since the last drain (oldest first, at most the
- * newest 4096).  Waits for those events.  ms[i] receives the milliseconds,
- * flops[i] / bytes[i] (either may be NULL) the launch's algorithmic work:
- * sum of 8*M*N*K and of (|A| + |B| + |C|) * element size over its problems.
- * *n receives the number of entries written (<= max_entries).
+ * newest 4096).  Waits for those events.  The heaviest launch is the one with
+ * the most algorithmic work; for a packed-operand launch (tensor-core or
+ * packed FP32) the time covers its GEMM kernel, after the operand packs.
+ * ms[i] receives the milliseconds; flops[i] / bytes[i] / kinds[i] (any may
+ * be NULL) the launch's algorithmic work -- sum of 8*M*N*K and of
+ * (|A| + |B| + |C|) * element size over its problems -- and its kernel family
+ * (2 = 64x64 tiles, 3 = 128x64 tiles, 5-7 = tcgen05 TF32 / 3xTF32 / 3xBF16,
+ * 10 = packed FP32; others are the small-problem kernels).  *n receives the
+ * number of entries written (<= max_entries).
  */
-rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t max_entries,
-                                  int32_t *n);
+rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t *kinds,
+                                  int32_t max_entries, int32_t *n);
+
+/*
+ * Autotuner decisions (ROSNET_OPT_AUTOTUNE) as text, so that a later process
+ * can plan with the same kernels without timing them again.  One line per
+ * tuned problem shape, seven integers separated by spaces:
+ *     dtype key_flags M N K kind ksplit
+ * (kind: 2 = 64x64 tiles, 3 = 128x64 tiles, 10 = packed FP32; ksplit = number
+ * of contracted-index ranges, 1 = none).
+ * rosnet_tune_export writes the text, NUL-terminated, into buf when cap is
+ * large enough; *len always receives the bytes needed (terminator included).
+ * rosnet_tune_import merges the lines of a NUL-terminated text into the
+ * table (later entries replace earlier ones of the same shape).  Every entry
+ * is checked against its shape first; INVALID_ARG (and nothing merged) for a
+ * malformed line, an unknown kind or dtype, or a split a problem of that
+ * shape cannot have.  Neither call touches the device.
+ */
+rosnet_status rosnet_tune_export(char *buf, size_t cap, size_t *len);
+rosnet_status rosnet_tune_import(const char *text);
 
 /* Free every cached contraction plan (arena, offset tables, descriptors,
  * CUDA graph).  Plans are cached by rosnet_contract and kept until this call;

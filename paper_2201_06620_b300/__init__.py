@@ -60,7 +60,7 @@ EXPORTS = [
     "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range", "rosnet_btensor_slice",
     "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_contract_batch", "rosnet_plan_stats",
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
-    "rosnet_selftest_timeout",
+    "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
 ]
 
 _lock = threading.Lock()
@@ -155,7 +155,7 @@ def lib():
                                           ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
             L.rosnet_release_plans.argtypes = []
             dp = ctypes.POINTER(ctypes.c_double)
-            L.rosnet_timing_drain.argtypes = [dp, dp, dp, ctypes.c_int32, i32p]
+            L.rosnet_timing_drain.argtypes = [dp, dp, dp, i32p, ctypes.c_int32, i32p]
             L.rosnet_sync.argtypes = [vp]
             L.rosnet_status_string.argtypes = [ctypes.c_int]
             L.rosnet_status_string.restype = ctypes.c_char_p
@@ -163,6 +163,8 @@ def lib():
             L.rosnet_last_error.restype = ctypes.c_char_p
             L.rosnet_kernel_launches.argtypes = []
             L.rosnet_kernel_launches.restype = ctypes.c_int64
+            L.rosnet_tune_export.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+            L.rosnet_tune_import.argtypes = [ctypes.c_char_p]
             for name in EXPORTS:
                 f = getattr(L, name)
                 if f.restype is ctypes.c_int or name in (
@@ -175,7 +177,7 @@ def lib():
                         "rosnet_btensor_slice", "rosnet_btensor_block", "rosnet_tensordot_ooc",
                         "rosnet_contract_batch", "rosnet_plan_stats", "rosnet_btensor_fix",
                         "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
-                        "rosnet_selftest_timeout"):
+                        "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -649,14 +651,31 @@ def kernel_launches():
 
 
 def timing_drain(max_entries=4096):
-    """[(ms, flops, bytes)] of the heaviest launch of each timed contract call."""
+    """[(ms, flops, bytes, kind)] of the heaviest launch of each timed contract
+    call (for packed-operand launches: the GEMM kernel alone)."""
     ms = (ctypes.c_double * max_entries)()
     fl = (ctypes.c_double * max_entries)()
     by = (ctypes.c_double * max_entries)()
+    kd = (ctypes.c_int32 * max_entries)()
     n = ctypes.c_int32()
-    _check(lib().rosnet_timing_drain(ms, fl, by, max_entries, ctypes.byref(n)), "rosnet_timing_drain")
-    return [(ms[i], fl[i], by[i]) for i in range(n.value)]
+    _check(lib().rosnet_timing_drain(ms, fl, by, kd, max_entries, ctypes.byref(n)), "rosnet_timing_drain")
+    return [(ms[i], fl[i], by[i], kd[i]) for i in range(n.value)]
 
 
 def release_plans():
     _check(lib().rosnet_release_plans(), "rosnet_release_plans")
+
+
+def tune_export():
+    """The autotuner's decisions as text (one line per tuned problem shape)."""
+    L = lib()
+    n = ctypes.c_size_t()
+    _check(L.rosnet_tune_export(None, 0, ctypes.byref(n)), "rosnet_tune_export")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(L.rosnet_tune_export(buf, n.value, ctypes.byref(n)), "rosnet_tune_export")
+    return buf.value.decode()
+
+
+def tune_import(text):
+    """Merge decisions written by tune_export (checked against their shapes)."""
+    _check(lib().rosnet_tune_import(text.encode()), "rosnet_tune_import")

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -35,10 +36,10 @@ void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *a
                      const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc);
 int check_precision(const rosnet_opts *opts, int dtype);
 int64_t reduce_ctas(const GettDesc &d);
-void autotune_problem(GettDesc &d, int dtype, cudaStream_t s);
+void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
-                       bool pack_a, bool pack_b);
+                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {});
 
 namespace {
 
@@ -112,6 +113,7 @@ struct Plan {
     // timing of the heaviest launch (ROSNET_OPT_TIMING)
     int heavy = -1;
     double heavy_flops = 0, heavy_bytes = 0;
+    int heavy_kind = -1;
     static constexpr int kTimingRing = 4096;
     std::vector<cudaEvent_t> tev;              // 2 * kTimingRing, created lazily
     int tpos = 0;
@@ -490,8 +492,10 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         fill_desc_tables(S.desc, views[g], dtab + S.table_off);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
-        if ((flags & ROSNET_OPT_AUTOTUNE) && !is_packed_kind(S.desc.kind) &&
-            8.0 * (double)S.desc.M * (double)S.desc.N * (double)S.desc.K >= 1e8) {
+        const bool cuda_core_gemm = S.desc.kind == kKindTiled || S.desc.kind == kKindTiledWide ||
+                                    S.desc.kind == kKindPackF32;
+        if ((flags & ROSNET_OPT_AUTOTUNE) && cuda_core_gemm &&
+            8.0 * (double)S.desc.M * (double)S.desc.N * (double)S.desc.K >= 1e6) {
             // time the candidate kernels on the plan's own operands (contents
             // of intermediates do not matter for timing); C goes to scratch
             auto bptr = [&](int64_t x) -> std::pair<void *, int64_t> {
@@ -506,7 +510,9 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             GettDesc x = S.desc;
             auto pa = bptr(S.ga), pb = bptr(S.gb);
             bind_operands(x, pa.first, pb.first, cs.p, pa.second, pb.second, S.lay.numel);
-            autotune_problem(x, plan->dtype, s);
+            const bool fp32_class = prec != ROSNET_PREC_TF32 && prec != ROSNET_PREC_TF32X3 &&
+                                    prec != ROSNET_PREC_BF16X3;
+            autotune_problem(x, plan->dtype, fp32_class && (red == kReduceAuto || red == kReduceSequential), s);
             S.desc.kind = x.kind;
             S.desc.tiles_m = x.tiles_m;
             S.desc.tiles_n = x.tiles_n;
@@ -581,7 +587,13 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
                 fl += 8.0 * (double)d.M * (double)d.N * (double)d.K;
                 by += el2d * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
             }
-            if (fl > best) { best = fl; plan->heavy = (int)li; plan->heavy_flops = fl; plan->heavy_bytes = by; }
+            if (fl > best) {
+                best = fl;
+                plan->heavy = (int)li;
+                plan->heavy_flops = fl;
+                plan->heavy_bytes = by;
+                plan->heavy_kind = L.kind;
+            }
         }
     }
     const size_t nd = std::max<size_t>(plan->desc_step.size(), 1);
@@ -653,18 +665,23 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
         for (size_t li = 0; li < P.launches.size(); ++li) {
             const auto &L = P.launches[li];
             const bool th = timing && (int)li == P.heavy;
-            if (th) {
+            // the timed region is the GEMM kernel itself (after the packs of a
+            // packed-operand launch)
+            auto start = [&]() {
                 cudaEvent_t e0 = P.tev[2 * slot];
                 RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal)
                                         : cudaEventRecord(e0, s));
-            }
+            };
+            if (th && !is_packed_kind(L.kind)) start();
             if (is_packed_kind(L.kind)) {
                 GroupArgs ga;
                 memset(&ga, 0, sizeof(ga));
                 ga.descs = dd + L.first;
                 ga.ndesc = 1;
+                std::function<void()> hook;
+                if (th) hook = start;
                 launch_tc_problem(packed_mode(L.kind), P.slot_desc[L.first], ga,
-                                  (char *)P.tcws.p + L.tc_ws_off, s, true, true);
+                                  (char *)P.tcws.p + L.tc_ws_off, s, true, true, hook);
             } else {
                 launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
             }
@@ -832,8 +849,8 @@ rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const 
     RN_API_END
 }
 
-rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t max_entries,
-                                  int32_t *n) {
+rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t *kinds,
+                                  int32_t max_entries, int32_t *n) {
     if (!n || max_entries < 0 || (max_entries > 0 && !ms)) return ROSNET_ERR_INVALID_ARG;
     RN_API_BEGIN
     std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -850,6 +867,7 @@ rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int3
         ms[k] = t;
         if (flops) flops[k] = P->heavy_flops;
         if (bytes) bytes[k] = P->heavy_bytes;
+        if (kinds) kinds[k] = P->heavy_kind;
         ++k;
     }
     g_timing_log.clear();

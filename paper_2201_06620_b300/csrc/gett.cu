@@ -17,8 +17,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cstring>
 #include <mutex>
+#include <sstream>
+#include <string>
 #include <unordered_map>
 
 #include "internal.h"
@@ -467,6 +470,8 @@ struct TiledCfg {
     static constexpr int VA = TM * (int)sizeof(T) / 16;    // 16-byte vectors per row fragment
     static constexpr int VB = TN * (int)sizeof(T) / 16;
     static constexpr size_t smem = sizeof(T) * (size_t)STAGES * 2 * BK * (RA + RB);
+    // one plane of the output tile is staged in the ring after the K loop
+    static_assert((size_t)(BM + 1) * (BN + 1) * sizeof(T) <= smem, "epilogue staging exceeds the ring");
 };
 
 template <typename T>
@@ -645,44 +650,58 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
         }
     }
     cp_async_wait<0>();
+    __syncthreads();   // every warp is done with the ring: it holds the output tile now
 
-    if (sd.part != nullptr) {   // split-K: partial tile to the workspace
-        const int64_t MN = M * N;
-        T *P = (T *)sd.part + (2 * (int64_t)split) * MN;
+    // Epilogue: one plane at a time, the tile goes through shared memory and
+    // out with the lanes of a warp along the destination's unit-stride
+    // dimension (n for the split-K partials [m][n], else C's own), so stores
+    // coalesce whatever the output layout.
+    const bool part = sd.part != nullptr;
+    const bool m_fast = !part && !(sd.flags & kFlagCNFast);
+    const bool atomic = sd.flags & kFlagAtomic;   // commutative split: order-free adds
+    const int64_t MN = M * N;
+    T *__restrict__ dst = part ? (T *)sd.part + (2 * (int64_t)split) * MN : (T *)sd.c;
+    const int64_t dplane = part ? MN : sd.c_plane;
+    T *cs = As;
+    const int ld = m_fast ? BM + 1 : BN + 1;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll 1
+    for (int pl = 0; pl < 2; ++pl) {
 #pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            const int64_t m = m0 + ty * TM + i;
-            if (m >= M) continue;
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
             for (int j = 0; j < TN; ++j) {
-                const int64_t n = n0 + tx * TN + j;
-                if (n >= N) continue;
-                P[m * N + n] = cr[i][j];
-                P[MN + m * N + n] = ci[i][j];
+                const int ml = ty * TM + i, nl = tx * TN + j;
+                cs[m_fast ? nl * ld + ml : ml * ld + nl] = pl ? ci[i][j] : cr[i][j];
+            }
+        __syncthreads();
+        T *__restrict__ out = dst + pl * dplane;
+        if (m_fast) {
+            for (int nl = warp; nl < BN; nl += NT / 32) {
+                if (n0 + nl >= N) break;
+                const int64_t cn = sCN[nl];
+                for (int ml = lane; ml < BM; ml += 32) {
+                    if (m0 + ml >= M) break;
+                    const int64_t o = sCM[ml] + cn;
+                    if (atomic) atomicAdd(out + o, cs[nl * ld + ml]);
+                    else out[o] = cs[nl * ld + ml];
+                }
+            }
+        } else {
+            for (int ml = warp; ml < BM; ml += NT / 32) {
+                const int64_t m = m0 + ml;
+                if (m >= M) break;
+                const int64_t base = part ? m * N : sCM[ml];
+                for (int nl = lane; nl < BN; nl += 32) {
+                    const int64_t n = n0 + nl;
+                    if (n >= N) break;
+                    const int64_t o = base + (part ? n : sCN[nl]);
+                    if (atomic) atomicAdd(out + o, cs[ml * ld + nl]);
+                    else out[o] = cs[ml * ld + nl];
+                }
             }
         }
-        return;
-    }
-    T *C = (T *)sd.c;
-    const int64_t cp = sd.c_plane;
-    const bool atomic = sd.flags & kFlagAtomic;   // commutative split: order-free adds
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        const int mi = ty * TM + i;
-        if (m0 + mi >= M) continue;
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int nj = tx * TN + j;
-            if (n0 + nj >= N) continue;
-            const int64_t o = sCM[mi] + sCN[nj];
-            if (atomic) {
-                atomicAdd(C + o, cr[i][j]);
-                atomicAdd(C + o + cp, ci[i][j]);
-            } else {
-                C[o] = cr[i][j];
-                C[o + cp] = ci[i][j];
-            }
-        }
+        __syncthreads();   // the next plane reuses the staging area
     }
 }
 
@@ -730,7 +749,7 @@ int f32p_tile_m();
 int f32p_tile_n();
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
-                       bool pack_a, bool pack_b);
+                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {});
 
 void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
     d.ksplit = 1;
@@ -895,13 +914,17 @@ void apply_split(GettDesc &d, int BK, int64_t ks) {
 
 int64_t reduce_ctas(const GettDesc &d);
 
-// Time the candidate kernels of a CUDA-core tiled problem (operands a, b;
-// output written to c_scratch; split partials to a temporary workspace) and
-// keep the fastest in d.  Results are cached by (dtype, M, N, K, flags).
-void autotune_problem(GettDesc &d, int dtype, cudaStream_t s) {
-    if (d.kind != kKindTiled && d.kind != kKindTiledWide) return;
+// Time the candidate kernels of a CUDA-core problem (operands a, b; output
+// written to c_scratch; split partials and packed operands to temporary
+// workspaces) and keep the fastest in d: 64x64 and 128x64 register tiles,
+// each with several contracted-range splits, and -- for plain FP32 when no
+// reduction mode is forced -- the packed path.  Results are cached by
+// (dtype, M, N, K, layout flags).
+void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
+    if (d.kind != kKindTiled && d.kind != kKindTiledWide && d.kind != kKindPackF32) return;
     if (d.flags & kFlagAtomic) return;
-    const TuneKey key{dtype, d.flags, d.M, d.N, d.K};
+    packed_ok = packed_ok && dtype == ROSNET_C64;
+    const TuneKey key{dtype, d.flags | (packed_ok ? 1 << 30 : 0), d.M, d.N, d.K};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -917,7 +940,12 @@ void autotune_problem(GettDesc &d, int dtype, cudaStream_t s) {
     }
     const int BK = dtype == ROSNET_C64 ? 16 : 8;
     std::vector<GettDesc> cands;
-    const int64_t auto_split = d.ksplit;
+    // the split the heuristic would pick for a 64x64 tiling
+    int64_t auto_split = d.kind == kKindPackF32 ? 1 : d.ksplit;
+    if (d.kind == kKindPackF32) {
+        const int64_t tiles = ((d.M + 63) / 64) * ((d.N + 63) / 64), nkt = (d.K + BK - 1) / BK;
+        if (tiles < kSMs && nkt >= 32) auto_split = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, nkt / 8);
+    }
     for (int kind : {(int)kKindTiled, (int)kKindTiledWide}) {
         if (kind == kKindTiledWide && !(dtype == ROSNET_C64 && d.M >= 128 && d.N >= 48)) continue;
         const int BM = kind == kKindTiledWide ? 128 : 64;
@@ -934,15 +962,34 @@ void autotune_problem(GettDesc &d, int dtype, cudaStream_t s) {
             if (!dup) cands.push_back(y);
         }
     }
+    if (packed_ok) {
+        GettDesc y = d;
+        y.kind = kKindPackF32;
+        y.tiles_m = (d.M + f32p_tile_m() - 1) / f32p_tile_m();
+        y.tiles_n = (d.N + f32p_tile_n() - 1) / f32p_tile_n();
+        apply_split(y, BK, 1);
+        cands.push_back(y);
+    }
     cudaEvent_t e0, e1;
     RN_CHECK_CUDA(cudaEventCreate(&e0));
     RN_CHECK_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     GettDesc pick = d;
     for (GettDesc &c : cands) {
-        DevBuf part(desc_part_bytes(c, dtype), s);
+        const bool packed = c.kind == kKindPackF32;
+        DevBuf part(packed ? 0 : desc_part_bytes(c, dtype), s);
+        DevBuf ws(packed ? tc_workspace_bytes(c, kPackedModeF32) : 0, s);
         c.part = part.p;
+        GroupArgs ga;
+        memset(&ga, 0, sizeof(ga));
+        ga.ndesc = 1;
+        ga.single = c;
+        ga.single.tile_begin = 0;
         auto once = [&]() {
+            if (packed) {
+                launch_tc_problem(kPackedModeF32, c, ga, ws.p, s, true, true);
+                return;
+            }
             launch_gett_single(c, c.kind, desc_ctas(c), dtype, s);
             if (c.part) launch_gett_single(c, kKindReduce, reduce_ctas(c), dtype, s);
         };
@@ -958,8 +1005,8 @@ void autotune_problem(GettDesc &d, int dtype, cudaStream_t s) {
             pick = c;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEvent_t ev[2] = {e0, e1};
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
     d.kind = pick.kind;
     d.tiles_m = pick.tiles_m;
     d.tiles_n = pick.tiles_n;
@@ -967,6 +1014,34 @@ void autotune_problem(GettDesc &d, int dtype, cudaStream_t s) {
     d.ktiles_per_split = pick.ktiles_per_split;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = TuneChoice{d.kind, d.tiles_m, d.tiles_n, d.ksplit, d.ktiles_per_split, d.flags};
+}
+
+// Geometry of a tuned choice for a problem of shape (M, N, K): tile grid
+// and contracted-range split, as autotune_problem would have set them.
+// False if the choice is not one the autotuner can make for that shape.
+static bool tune_geometry(int dtype, int kind, int64_t M, int64_t N, int64_t K, int64_t ksplit,
+                          TuneChoice *out) {
+    if (M < 1 || N < 1 || K < 1 || ksplit < 1 || ksplit > 64) return false;
+    const int BK = dtype == ROSNET_C64 ? 16 : 8;
+    GettDesc y;
+    memset(&y, 0, sizeof(y));
+    y.M = M;
+    y.N = N;
+    y.K = K;
+    if (kind == kKindTiled || (kind == kKindTiledWide && dtype == ROSNET_C64 && M >= 128 && N >= 48)) {
+        const int BM = kind == kKindTiledWide ? 128 : 64;
+        y.tiles_m = (M + BM - 1) / BM;
+        y.tiles_n = (N + 63) / 64;
+    } else if (kind == kKindPackF32 && dtype == ROSNET_C64 && ksplit == 1) {
+        y.tiles_m = (M + f32p_tile_m() - 1) / f32p_tile_m();
+        y.tiles_n = (N + f32p_tile_n() - 1) / f32p_tile_n();
+    } else {
+        return false;
+    }
+    apply_split(y, BK, ksplit);
+    if (y.ksplit != ksplit) return false;   // not a split this shape can have
+    *out = TuneChoice{kind, y.tiles_m, y.tiles_n, y.ksplit, y.ktiles_per_split, 0};
+    return true;
 }
 
 // CTAs of the split-K reduction of a problem
@@ -1253,6 +1328,57 @@ extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B
         throw;
     }
     cleanup();   // synchronises the side stream (the copies are complete on return)
+    return ROSNET_OK;
+    RN_API_END
+}
+
+extern "C" rosnet_status rosnet_tune_export(char *buf, size_t cap, size_t *len) {
+    using namespace rosnet;
+    if (!len) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    std::string t;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto &e : g_tune) {
+            const TuneKey &k = e.first;
+            const TuneChoice &c = e.second;
+            t += std::to_string(k.dtype) + " " + std::to_string(k.flags) + " " + std::to_string(k.M) + " " +
+                 std::to_string(k.N) + " " + std::to_string(k.K) + " " + std::to_string(c.kind) + " " +
+                 std::to_string(c.ksplit) + "\n";
+        }
+    }
+    *len = t.size() + 1;
+    if (buf && cap >= t.size() + 1) memcpy(buf, t.c_str(), t.size() + 1);
+    return ROSNET_OK;
+    RN_API_END
+}
+
+extern "C" rosnet_status rosnet_tune_import(const char *text) {
+    using namespace rosnet;
+    if (!text) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    std::vector<std::pair<TuneKey, TuneChoice>> add;
+    std::istringstream in(text);
+    std::string line;
+    while (std::getline(in, line)) {
+        if (line.find_first_not_of(" \t\r") == std::string::npos) continue;
+        std::istringstream ls(line);
+        long long v[7];
+        for (int i = 0; i < 7; ++i)
+            if (!(ls >> v[i])) RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed tuning line: " + line);
+        std::string rest;
+        if (ls >> rest) RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed tuning line: " + line);
+        if (v[0] != ROSNET_C64 && v[0] != ROSNET_C128) RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad dtype: " + line);
+        if (v[1] < 0 || v[1] > 0x7fffffffLL)
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad tuning line: " + line);
+        TuneChoice c;
+        if (!tune_geometry((int)v[0], (int)v[5], v[2], v[3], v[4], v[6], &c))
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "choice impossible for this shape: " + line);
+        c.flags = (int32_t)(v[1] & 0x3fffffff);
+        add.push_back({TuneKey{(int)v[0], (int)v[1], v[2], v[3], v[4]}, c});
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &e : add) g_tune[e.first] = e.second;
     return ROSNET_OK;
     RN_API_END
 }

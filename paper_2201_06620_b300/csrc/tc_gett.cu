@@ -36,6 +36,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <mutex>
 
 #include "gett_common.cuh"
@@ -494,14 +495,16 @@ struct Args {
 };
 
 // out[p][k][r] = operand(r, k) plane p (0 outside R x K), for A (the first
-// na CTAs) and then B.  32 x 32 (row, k) tiles transposed through shared
-// memory so that the gather (along the operand's unit-stride digit) and the
-// store (along rows) both coalesce.
+// na CTAs) and then B.  Each CTA packs 32 rows x PKT k, transposed through
+// shared memory so that the gather (along the operand's unit-stride digit)
+// and the store (along rows) both coalesce; every thread has 16 independent
+// loads in flight.
+constexpr int PKT = 128;
 __global__ void __launch_bounds__(256) f32_pack_kernel(const __grid_constant__ GroupArgs g, float *__restrict__ outA,
                                                        float *__restrict__ outB, int64_t Mpad, int64_t Npad,
                                                        int64_t Kpad, int64_t na, int skip_a) {
     __shared__ GettDesc sd;
-    __shared__ float tr[2][32][33];
+    __shared__ float tr[2][PKT][33];
     grid_dep_launch();
     if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
@@ -516,27 +519,37 @@ __global__ void __launch_bounds__(256) f32_pack_kernel(const __grid_constant__ G
     const int64_t R = which ? sd.N : sd.M, K = sd.K;
     const bool row_fast = which ? (sd.flags & kFlagBNFast) : (sd.flags & kFlagAMFast);
     const int64_t rtiles = Rpad / 32;
-    const int64_t r0 = (bid % rtiles) * 32, k0 = (bid / rtiles) * 32;
+    const int64_t r0 = (bid % rtiles) * 32, k0 = (bid / rtiles) * PKT;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    int64_t o[4];
+    constexpr int NE = 32 * PKT / 256;                        // elements per thread
+    int64_t o[NE];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {   // offsets first (static tables), operands after the wait
-        const int a = tx, b = ty + 8 * j;
-        const int64_t r = r0 + (row_fast ? a : b), k = k0 + (row_fast ? b : a);
+    for (int j = 0; j < NE; ++j) {   // offsets first (static tables), operands after the wait
+        // lanes along rows (row-fast operand) or along k (k-fast operand)
+        const int rr = row_fast ? tx : ty + 8 * (j & 3);
+        const int kk = row_fast ? ty + 8 * j : tx + 32 * (j >> 2);
+        const int64_t r = r0 + rr, k = k0 + kk;
         o[j] = (r < R && k < K) ? offR[r] + offK[k] : -1;
     }
     grid_dep_wait();
+    float xr[NE], xi[NE];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int a = tx, b = ty + 8 * j;
-        const int rr = row_fast ? a : b, kk = row_fast ? b : a;
-        tr[0][kk][rr] = o[j] >= 0 ? src[o[j]] : 0.f;
-        tr[1][kk][rr] = o[j] >= 0 ? src[o[j] + plane] : 0.f;
+    for (int j = 0; j < NE; ++j) {
+        xr[j] = o[j] >= 0 ? src[o[j]] : 0.f;
+        xi[j] = o[j] >= 0 ? src[o[j] + plane] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+        const int rr = row_fast ? tx : ty + 8 * (j & 3);
+        const int kk = row_fast ? ty + 8 * j : tx + 32 * (j >> 2);
+        tr[0][kk][rr] = xr[j];
+        tr[1][kk][rr] = xi[j];
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NE; ++j) {
         const int kk = ty + 8 * j, rr = tx;
+        if (k0 + kk >= Kpad) break;
         const size_t e = (size_t)(k0 + kk) * Rpad + (r0 + rr);
         out[e] = tr[0][kk][rr];
         out[(size_t)Kpad * Rpad + e] = tr[1][kk][rr];
@@ -614,11 +627,32 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
             yi[4 * v] = q.x; yi[4 * v + 1] = q.y; yi[4 * v + 2] = q.z; yi[4 * v + 3] = q.w;
         }
     };
+#ifndef ROSNET_F32P_ORDER
+#define ROSNET_F32P_ORDER 0
+#endif
     auto macs = [&](const float *xr, const float *xi, const float *yr, const float *yi) {
+        if (ROSNET_F32P_ORDER == 0) {
 #pragma unroll
-        for (int i = 0; i < TM; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < TN; ++j) cmac4(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
+                for (int j = 0; j < TN; ++j) cmac4(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
+        } else {
+            // two outer products: Re(x) (x) (Re y, Im y), then Im(x) (x) (-Im y, Re y)
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    cr[i][j] = fmaf(xr[i], yr[j], cr[i][j]);
+                    ci[i][j] = fmaf(xr[i], yi[j], ci[i][j]);
+                }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    cr[i][j] = fmaf(-xi[i], yi[j], cr[i][j]);
+                    ci[i][j] = fmaf(xi[i], yr[j], ci[i][j]);
+                }
+        }
     };
 
     int done0 = 0;   // tiles whose full barrier thread 0 has passed
@@ -790,7 +824,7 @@ void make_map(CUtensorMap *m, void *base, int64_t rows, int64_t Kpad, int esz) {
 
 template <int MODE>
 void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, cudaStream_t s,
-                 bool pack_a, bool pack_b) {
+                 bool pack_a, bool pack_b, const std::function<void()> &before_gemm) {
     using C_ = tc::Cfg<MODE>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -818,6 +852,7 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
     }
     args.g = ga;
     args.nkt = (int)(g.Kpad / g.bk);
+    if (before_gemm) before_gemm();
     tc::tc_gemm_kernel<MODE><<<(unsigned)ctas, tc::NTHREADS, C_::SMEM, s>>>(args);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
@@ -849,7 +884,7 @@ void make_map_f32(CUtensorMap *m, void *base, int64_t rows, int64_t Kpad, int bo
 }
 
 void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, cudaStream_t s, bool pack_a,
-                bool pack_b) {
+                bool pack_b, const std::function<void()> &before_gemm) {
     static bool attr_set = false;
     if (!attr_set) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -859,7 +894,8 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     const F32Geom g = f32_geom(d);
     float *pa = (float *)ws;
     float *pb = pa + 2 * g.Mpad * g.Kpad;
-    const int64_t ca = (g.Mpad / 32) * (g.Kpad / 32), cb = (g.Npad / 32) * (g.Kpad / 32);
+    const int64_t kt = (g.Kpad + f32p::PKT - 1) / f32p::PKT;
+    const int64_t ca = (g.Mpad / 32) * kt, cb = (g.Npad / 32) * kt;
     if (ca > 0x7fffffffLL || cb > 0x7fffffffLL || 2 * g.Kpad > 0x7fffffffLL || g.Mpad > 0x7fffffffLL ||
         g.Npad > 0x7fffffffLL)
         RN_FAIL(ROSNET_ERR_UNSUPPORTED, "operand too large to pack");
@@ -877,6 +913,7 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     args.g = ga;
     args.nkt = (int)(g.Kpad / f32p::BK);
     args.kpad = (int)g.Kpad;
+    if (before_gemm) before_gemm();
     launch_pdl(f32p::f32_gemm_kernel, dim3((unsigned)ctas), f32p::NT, f32p::SMEM, s, args);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
@@ -901,22 +938,24 @@ size_t tc_workspace_bytes(const GettDesc &d, int mode) {
 // problem's descriptor (by value or in device memory); ws holds
 // tc_workspace_bytes(d, mode) bytes, 256-byte aligned.  pack_a / pack_b = false
 // reuse the packed operand already in ws (same operand as the previous call).
+// before_gemm, when set, is called after the pack launches and before the
+// GEMM launch (e.g. to record a timing event around the GEMM alone).
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
-                       bool pack_a, bool pack_b) {
+                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm) {
     const int64_t ctas = d.tiles_m * d.tiles_n;
     if (ctas <= 0) return;
     if (ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one launch");
     if (mode == kPackedModeF32) {
-        launch_f32(ga, d, ws, ctas, s, pack_a, pack_b);
+        launch_f32(ga, d, ws, ctas, s, pack_a, pack_b, before_gemm);
         return;
     }
     const TcGeom g = tc_geom(d, mode);
     if (ctas > 0x7fffffffLL || g.Kpad / g.bk > 0x7fffffffLL || g.Mpad > 0x7fffffffLL || g.Npad > 0x7fffffffLL)
         RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one tensor-core launch");
     switch (mode) {
-        case tc::kTF32: launch_mode<tc::kTF32>(ga, g, ws, ctas, s, pack_a, pack_b); break;
-        case tc::kTF32x3: launch_mode<tc::kTF32x3>(ga, g, ws, ctas, s, pack_a, pack_b); break;
-        default: launch_mode<tc::kBF16x3>(ga, g, ws, ctas, s, pack_a, pack_b); break;
+        case tc::kTF32: launch_mode<tc::kTF32>(ga, g, ws, ctas, s, pack_a, pack_b, before_gemm); break;
+        case tc::kTF32x3: launch_mode<tc::kTF32x3>(ga, g, ws, ctas, s, pack_a, pack_b, before_gemm); break;
+        default: launch_mode<tc::kBF16x3>(ga, g, ws, ctas, s, pack_a, pack_b, before_gemm); break;
     }
 }
 

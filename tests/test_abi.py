@@ -206,3 +206,28 @@ def test_slice_search_shrinks_the_largest_intermediate():
     t1, m1 = _path_flops(net.labels, ext, path, cut)
     assert mx == m1 < m0
     assert abs(flops - 16 * t1) <= 1e-9 * flops             # 2^4 slices
+
+
+def test_tune_table_roundtrip_and_validation():
+    """Autotuner decisions move between processes as text; every imported
+    entry is checked against its shape (no device needed)."""
+    good = "1 9 4096 256 256 10 1\n1 11 2048 512 32 3 1\n2 0 300 200 5000 2 16\n"
+    R.tune_import(good)
+    lines = set(R.tune_export().splitlines())
+    assert set(good.splitlines()) <= lines
+    R.tune_import("1 9 4096 256 256 2 4\n")          # replaces the first entry
+    assert "1 9 4096 256 256 2 4" in R.tune_export().splitlines()
+    bad = ["1 9 4096 256 256 10 2",      # packed kind cannot split
+           "1 9 100 40 256 3 1",         # 128x64 tiles need M >= 128, N >= 48
+           "2 0 64 64 64 10 1",          # packed FP32 is complex64 only
+           "1 0 64 64 64 2 5",           # 4 k-tiles cannot make 5 ranges
+           "1 0 64 64 64 7 1",           # not a CUDA-core GEMM kind
+           "3 0 64 64 64 2 1",           # unknown dtype
+           "1 0 64 64",                  # short line
+           "1 0 64 64 64 2 1 9"]         # extra field
+    before = R.tune_export()
+    for b in bad:
+        with pytest.raises(R.RosnetError) as e:
+            R.tune_import("1 0 128 128 128 2 1\n" + b + "\n")
+        assert e.value.name == "INVALID_ARG", b
+    assert R.tune_export() == before      # nothing merged from a rejected text

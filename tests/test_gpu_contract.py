@@ -140,3 +140,21 @@ def test_autotuned_plan_matches():
     got, _ = gpu_network(W.circuit_network(circ), R.C64, max_block_entries=256,
                          flags=R.OPT_GRAPH | R.OPT_AUTOTUNE)
     assert amp_err(got, ref, 20) <= 1e-5
+
+
+def test_timing_records_heaviest_launch_under_graph():
+    """ROSNET_OPT_TIMING under a captured graph: one entry per call with the
+    heaviest launch's work and kernel family; the amplitude is unchanged."""
+    circ = W.rqc20_config()
+    ref = oracle.amplitude_sv(circ)
+    R.timing_drain()
+    for _ in range(3):
+        got, _ = gpu_network(W.circuit_network(circ), R.C64, max_block_entries=256,
+                             flags=R.OPT_GRAPH | R.OPT_TIMING)
+        assert amp_err(got, ref, 20) <= 1e-5
+    recs = R.timing_drain()
+    assert len(recs) == 3
+    for ms, fl, by, kind in recs:
+        assert ms > 0 and fl in (8.0 * 4096 * 256 * 256, 16.0 * 4096 * 256 * 256) and by > 0
+        assert kind in (2, 3, 10)
+    assert R.timing_drain() == []
