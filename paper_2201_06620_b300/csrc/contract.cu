@@ -492,8 +492,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         fill_desc_tables(S.desc, views[g], dtab + S.table_off);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
-        const bool cuda_core_gemm = S.desc.kind == kKindTiled || S.desc.kind == kKindTiledWide ||
-                                    S.desc.kind == kKindPackF32;
+        const bool cuda_core_gemm = is_tiled_kind(S.desc.kind) || S.desc.kind == kKindPackF32;
         if ((flags & ROSNET_OPT_AUTOTUNE) && cuda_core_gemm &&
             8.0 * (double)S.desc.M * (double)S.desc.N * (double)S.desc.K >= 1e6) {
             // time the candidate kernels on the plan's own operands (contents

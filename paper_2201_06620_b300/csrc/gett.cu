@@ -463,7 +463,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <typename T, int BM, int BN, int BK, int STAGES>
 struct TiledCfg {
     static constexpr int NT = 256;
-    static constexpr int TM = BM / 16, TN = BN / 16;
+    // threads: TXN along n (4 complex columns each), NT / TXN along m
+    static constexpr int TN = 4, TXN = BN / TN, TY = NT / TXN, TM = BM / TY;
+    static_assert(TXN * TY == NT && TM * TY == BM && TM % 4 == 0, "tile shape");
     static constexpr int LA = BM * BK / NT, LB = BN * BK / NT;
     static constexpr int PAD = 16 / sizeof(T);
     static constexpr int RA = BM + PAD, RB = BN + PAD;    // shared row lengths
@@ -577,7 +579,7 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
         }
     };
 
-    const int ty = tid >> 4, tx = tid & 15;
+    const int ty = tid / Cfg::TXN, tx = tid % Cfg::TXN;
     T cr[TM][TN], ci[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -706,7 +708,7 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
 }
 
 template <typename T, int BM, int BN, int BK, int STAGES>
-__global__ void __launch_bounds__(256, (BM == 64 && sizeof(T) == 4) ? ROSNET_TILED_MINB : 1)
+__global__ void __launch_bounds__(256, (TiledCfg<T, BM, BN, BK, STAGES>::TM == 4 && TiledCfg<T, BM, BN, BK, STAGES>::LA <= 4 && sizeof(T) == 4) ? ROSNET_TILED_MINB : 1)
     gett_tiled_kernel(const __grid_constant__ GroupArgs g) {
     using Cfg = TiledCfg<T, BM, BN, BK, STAGES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -780,9 +782,15 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
     const bool tiled_ok = d.K >= 16 && std::min(d.M, d.N) >= 16 && MN >= 2048;
     if (tiled_ok) {
         if (d.N > d.M) swap_operands(d);   // the BM side takes the larger extent
-        const bool wide = dtype == ROSNET_C64 && d.M >= 128 && d.N >= 48;
-        const int BM = wide ? 128 : 64, BN = 64, BK = dtype == ROSNET_C64 ? 16 : 8;
-        d.kind = wide ? kKindTiledWide : kKindTiled;
+        // few columns: narrow tiles; else 128x64 when both sides are large
+        int kind = kKindTiled;
+        if (d.N <= 16 && d.M >= 256 && tiled_kind_ok(kKindTiled256x16, dtype, d.M, d.N)) kind = kKindTiled256x16;
+        else if (d.N <= 32 && d.M >= 128 && tiled_kind_ok(kKindTiled128x32, dtype, d.M, d.N)) kind = kKindTiled128x32;
+        else if (tiled_kind_ok(kKindTiledWide, dtype, d.M, d.N)) kind = kKindTiledWide;
+        int BM, BN;
+        tiled_tile(kind, &BM, &BN);
+        const int BK = dtype == ROSNET_C64 ? 16 : 8;
+        d.kind = kind;
         d.tiles_m = (d.M + BM - 1) / BM;
         d.tiles_n = (d.N + BN - 1) / BN;
         // split the contracted range when the tile grid cannot fill the GPU
@@ -849,6 +857,8 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindZero: launch_pdl(gett_zero_kernel<float>, grid, 256, 0, s, ga); break;
             case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 256, 0, s, ga); break;
             case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
+            case kKindTiled256x16: launch_tiled<float, 256, 16, 16>(grid, ga, s); break;
+            case kKindTiled128x32: launch_tiled<float, 128, 32, 16>(grid, ga, s); break;
             default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
         }
     } else {
@@ -921,7 +931,7 @@ int64_t reduce_ctas(const GettDesc &d);
 // reduction mode is forced -- the packed path.  Results are cached by
 // (dtype, M, N, K, layout flags).
 void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
-    if (d.kind != kKindTiled && d.kind != kKindTiledWide && d.kind != kKindPackF32) return;
+    if (!is_tiled_kind(d.kind) && d.kind != kKindPackF32) return;
     if (d.flags & kFlagAtomic) return;
     packed_ok = packed_ok && dtype == ROSNET_C64;
     const TuneKey key{dtype, d.flags | (packed_ok ? 1 << 30 : 0), d.M, d.N, d.K};
@@ -946,13 +956,14 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
         const int64_t tiles = ((d.M + 63) / 64) * ((d.N + 63) / 64), nkt = (d.K + BK - 1) / BK;
         if (tiles < kSMs && nkt >= 32) auto_split = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, nkt / 8);
     }
-    for (int kind : {(int)kKindTiled, (int)kKindTiledWide}) {
-        if (kind == kKindTiledWide && !(dtype == ROSNET_C64 && d.M >= 128 && d.N >= 48)) continue;
-        const int BM = kind == kKindTiledWide ? 128 : 64;
+    for (int kind : {(int)kKindTiled, (int)kKindTiledWide, (int)kKindTiled256x16, (int)kKindTiled128x32}) {
+        if (!tiled_kind_ok(kind, dtype, d.M, d.N)) continue;
+        int BM, BN;
+        tiled_tile(kind, &BM, &BN);
         GettDesc x = d;
         x.kind = kind;
         x.tiles_m = (d.M + BM - 1) / BM;
-        x.tiles_n = (d.N + 63) / 64;
+        x.tiles_n = (d.N + BN - 1) / BN;
         for (int64_t ks : {int64_t(1), auto_split, 2 * auto_split, 4 * auto_split}) {
             GettDesc y = x;
             apply_split(y, BK, ks);
@@ -1028,10 +1039,11 @@ static bool tune_geometry(int dtype, int kind, int64_t M, int64_t N, int64_t K, 
     y.M = M;
     y.N = N;
     y.K = K;
-    if (kind == kKindTiled || (kind == kKindTiledWide && dtype == ROSNET_C64 && M >= 128 && N >= 48)) {
-        const int BM = kind == kKindTiledWide ? 128 : 64;
+    if (is_tiled_kind(kind) && tiled_kind_ok(kind, dtype, M, N)) {
+        int BM, BN;
+        tiled_tile(kind, &BM, &BN);
         y.tiles_m = (M + BM - 1) / BM;
-        y.tiles_n = (N + 63) / 64;
+        y.tiles_n = (N + BN - 1) / BN;
     } else if (kind == kKindPackF32 && dtype == ROSNET_C64 && ksplit == 1) {
         y.tiles_m = (M + f32p_tile_m() - 1) / f32p_tile_m();
         y.tiles_n = (N + f32p_tile_n() - 1) / f32p_tile_n();

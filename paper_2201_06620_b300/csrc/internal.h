@@ -199,7 +199,31 @@ enum KernelKind : int32_t {
     kKindZero = 8,       // zero C before a commutative (atomic) split-K launch
     kKindDot = 9,        // one CTA cluster per output, long K (e.g. a network's final scalar)
     kKindPackF32 = 10,   // plain FP32 on CUDA cores from packed operands (TMA-fed 64x64 tiles)
+    kKindTiled256x16 = 11,  // 256x16 tiles (complex64 only): problems with few columns
+    kKindTiled128x32 = 12,  // 128x32 tiles (complex64 only)
 };
+
+// Register-tiled CUDA-core kinds (gett_tiled_kernel), their CTA tile, and
+// whether one applies to a problem of dtype and (M, N).
+inline bool is_tiled_kind(int kind) {
+    return kind == kKindTiled || kind == kKindTiledWide || kind == kKindTiled256x16 || kind == kKindTiled128x32;
+}
+inline void tiled_tile(int kind, int *bm, int *bn) {
+    switch (kind) {
+        case kKindTiledWide: *bm = 128; *bn = 64; break;
+        case kKindTiled256x16: *bm = 256; *bn = 16; break;
+        case kKindTiled128x32: *bm = 128; *bn = 32; break;
+        default: *bm = 64; *bn = 64; break;
+    }
+}
+inline bool tiled_kind_ok(int kind, int dtype, int64_t M, int64_t N) {
+    if (kind == kKindTiled) return true;
+    if (dtype != ROSNET_C64) return false;
+    if (kind == kKindTiledWide) return M >= 128 && N >= 48;
+    if (kind == kKindTiled256x16) return M >= 128;
+    if (kind == kKindTiled128x32) return M >= 64;
+    return false;
+}
 
 // Kinds that run as pack kernels + a GEMM on packed operands held in a
 // per-problem workspace (one launch sequence per problem), and their packed

@@ -123,6 +123,13 @@ __device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile in
     return true;
 }
 
+// The same wait with the uncontended case inline (one try_wait, no call):
+// for hot loops that usually find the phase already complete.
+__device__ __forceinline__ bool mbar_wait_fast(uint64_t *b, uint32_t parity, volatile int *abort) {
+    if (mbar_try(b, parity)) return true;
+    return mbar_wait(b, parity, abort);
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -659,7 +666,7 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
     for (int kt = 0; kt < nkt; ++kt) {
         const int s = kt % STAGES;
         // every lane observes the phase itself; the warp leaves together
-        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&full_bar[s], (kt / STAGES) & 1, &abort_flag));
+        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_fast(&full_bar[s], (kt / STAGES) & 1, &abort_flag));
         if (!ok) break;
         if (tid == 0) done0 = kt + 1;
         const float *a0 = stg + (size_t)s * 2 * (PA + PB) + ty * TM;
@@ -667,12 +674,15 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
         float xr0[TM], xi0[TM], yr0[TN], yi0[TN], xr1[TM], xi1[TM], yr1[TN], yi1[TN];
         frag(a0, b0, 0, xr0, xi0, yr0, yi0);
 #pragma unroll(KU)
-        for (int kk = 0; kk < BK; kk += 2) {
+        for (int kk = 0; kk < BK - 2; kk += 2) {
             frag(a0, b0, kk + 1, xr1, xi1, yr1, yi1);
             macs(xr0, xi0, yr0, yi0);
-            if (kk + 2 < BK) frag(a0, b0, kk + 2, xr0, xi0, yr0, yi0);
+            frag(a0, b0, kk + 2, xr0, xi0, yr0, yi0);
             macs(xr1, xi1, yr1, yi1);
         }
+        frag(a0, b0, BK - 1, xr1, xi1, yr1, yi1);   // last two rows: no prefetch
+        macs(xr0, xi0, yr0, yi0);
+        macs(xr1, xi1, yr1, yi1);
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&empty_bar[s]);
         // warp 0 refills the stage consumed one iteration ago (all warps have
@@ -682,7 +692,7 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
             bool ok2 = true;
             if (lane == 0) {
                 const int t = kt - 1;
-                ok2 = tc::mbar_wait(&empty_bar[t % STAGES], (t / STAGES) & 1, &abort_flag);
+                ok2 = tc::mbar_wait_fast(&empty_bar[t % STAGES], (t / STAGES) & 1, &abort_flag);
                 if (ok2) {
                     issue(t + STAGES);
                     issued = t + STAGES + 1;

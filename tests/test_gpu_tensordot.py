@@ -112,6 +112,21 @@ def test_tiles_and_ragged_tails(dtype, mnk):
     assert oracle.rel_frobenius(got, ref) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("mnk", [(300, 13, 200), (513, 16, 4000), (16, 700, 333), (200, 30, 300),
+                                 (130, 29, 2000), (1000, 17, 64)])
+def test_narrow_tiles(mnk):
+    """Few-column problems take the 256x16 / 128x32 tiles (with and without a
+    contracted-range split); ragged in every dimension."""
+    M, N, K = mnk
+    a = W.complex_normal((M, K), 13)
+    b = W.complex_normal((K, N), 14)
+    A, B = R.btensor(a.astype(np.complex64)), R.btensor(b.astype(np.complex64))
+    ref = ref_of(a, b, [1], [0], R.C64)
+    for flags in (0, R.REDUCE_TREE, R.REDUCE_COMMUTATIVE):
+        got = R.tensordot(A, B, [1], [0], flags=flags).download()
+        assert oracle.rel_frobenius(got, ref) <= 1e-5, flags
+
+
 @pytest.mark.parametrize("dtype", [R.C64, R.C128])
 def test_qubit_tensors_permuted_blocked(dtype):
     """[2]^r tensors with seeded axis permutations and mixed grid/intra axes."""
