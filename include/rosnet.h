@@ -135,11 +135,18 @@ typedef struct {
  * memory usable in stream order on `stream` (or NULL on failure); free(ptr,
  * stream, ctx) releases it in stream order.  Passing alloc = free = NULL
  * restores the built-in allocator (cudaMallocAsync / cudaFreeAsync on the
- * device's default memory pool).  Not thread-safe with concurrent calls.
+ * device's default memory pool, which then keeps freed memory for reuse).
+ * A block is always freed by the allocator that made it, so switching to a
+ * different allocator while library blocks are outstanding (tensors, cached
+ * plans) returns INVALID_ARG.  Not thread-safe with concurrent calls.
  */
 rosnet_status rosnet_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
                                    void (*free)(void *ptr, void *stream, void *ctx),
                                    void *ctx);
+
+/* Device blocks the library has requested from its allocator since load
+ * (*requests) and those not yet freed (*live); either pointer may be NULL. */
+rosnet_status rosnet_alloc_stats(int64_t *requests, int64_t *live);
 
 /* ----------------------------------------------------------------------- */
 /* block tensors (Sec. II-C)                                                */
@@ -212,6 +219,11 @@ rosnet_status rosnet_btensor_fix(rosnet_btensor t, int nfix, const int *axes, co
 /* Copy the tensor into a dense row-major interleaved host array.  Blocks
  * until the data is on the host (synchronises `stream`). */
 rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream);
+
+/* As rosnet_btensor_download, but only enqueued on `stream` (no wait): the
+ * host buffer must stay valid, and is complete once the stream reaches this
+ * point; with page-locked host memory the copy overlaps other work. */
+rosnet_status rosnet_btensor_download_async(rosnet_btensor t, void *host, void *stream);
 
 /* Shape, block shape (arrays of at least `rank` entries; either may be NULL)
  * and dtype (may be NULL) of a tensor.  *rank is always written. */

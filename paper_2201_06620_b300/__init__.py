@@ -61,6 +61,7 @@ EXPORTS = [
     "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_contract_batch", "rosnet_plan_stats",
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
+    "rosnet_btensor_download_async", "rosnet_alloc_stats",
 ]
 
 _lock = threading.Lock()
@@ -165,6 +166,8 @@ def lib():
             L.rosnet_kernel_launches.restype = ctypes.c_int64
             L.rosnet_tune_export.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
             L.rosnet_tune_import.argtypes = [ctypes.c_char_p]
+            L.rosnet_btensor_download_async.argtypes = [vp, vp, vp]
+            L.rosnet_alloc_stats.argtypes = [i64p, i64p]
             for name in EXPORTS:
                 f = getattr(L, name)
                 if f.restype is ctypes.c_int or name in (
@@ -177,7 +180,8 @@ def lib():
                         "rosnet_btensor_slice", "rosnet_btensor_block", "rosnet_tensordot_ooc",
                         "rosnet_contract_batch", "rosnet_plan_stats", "rosnet_btensor_fix",
                         "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
-                        "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import"):
+                        "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
+                        "rosnet_btensor_download_async", "rosnet_alloc_stats"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -210,7 +214,9 @@ def _stream(stream):
 
 def use_torch_allocator(enable=True):
     """Route the library's device allocations through torch's caching allocator
-    (enable=False restores the built-in cudaMallocAsync pool)."""
+    (enable=False restores the built-in cudaMallocAsync pool, the default).
+    Only possible while the library holds no device memory (no tensors or
+    cached plans alive)."""
     global _alloc_cbs
     L = lib()
     if not enable:
@@ -254,7 +260,6 @@ def _init():
         torch = _torch()
         if torch.cuda.is_available():
             torch.cuda.init()
-            use_torch_allocator(True)
             atexit.register(_at_exit)
         _init_done = True
 
@@ -367,6 +372,15 @@ class BTensor:
                "download")
         return out
 
+    def download_async(self, out, stream=None):
+        """Enqueue a dense row-major copy into ``out`` (a page-locked torch
+        tensor or numpy array of the right size) on the stream, without
+        waiting: ``out`` is complete once the stream reaches this point."""
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        _check(lib().rosnet_btensor_download_async(self._h, ctypes.c_void_p(ptr), _stream(stream)),
+               "download_async")
+        return out
+
     def destroy(self):
         if _shutting_down:   # the allocator behind the handle may be gone
             self._h = None
@@ -476,6 +490,7 @@ class Network:
                             len(out_labels), ctypes.cast(self._out, ctypes.POINTER(ctypes.c_int64)))
         self._path = None
         self._path_key = None
+        self._path_src = None
 
     def set_tensor(self, i, t):
         self.tensors[i] = t
@@ -490,6 +505,9 @@ class Network:
         return [(pairs[2 * i], pairs[2 * i + 1]) for i in range(ns.value)]
 
     def _cpath(self, path):
+        if path is self._path_src:        # the same list object as last time
+            return self._path
+        self._path_src = path
         key = tuple(tuple(p) for p in path)
         if key != self._path_key:
             flat = [int(x) for p in key for x in p]
@@ -664,6 +682,13 @@ def timing_drain(max_entries=4096):
 
 def release_plans():
     _check(lib().rosnet_release_plans(), "rosnet_release_plans")
+
+
+def alloc_stats():
+    """(device blocks requested since load, blocks still live)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().rosnet_alloc_stats(ctypes.byref(a), ctypes.byref(b)), "rosnet_alloc_stats")
+    return a.value, b.value
 
 
 def tune_export():

@@ -6,6 +6,8 @@
 // and all imaginary parts after them (planar complex).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -28,6 +30,28 @@ const char *last_error_cstr() { return t_last_error.c_str(); }
 static void *(*g_alloc)(size_t, void *, void *) = nullptr;
 static void (*g_free)(void *, void *, void *) = nullptr;
 static void *g_alloc_ctx = nullptr;
+static std::atomic<int64_t> g_live_allocs{0};   // blocks handed out and not yet freed
+static std::atomic<int64_t> g_alloc_requests{0};   // blocks handed out in total
+
+// The built-in allocator draws on the device's default stream-ordered pool;
+// freed blocks stay in the pool across synchronisations (release threshold
+// raised once per device, for this process) so that steady-state calls do
+// not map and unmap memory.
+static void keep_pool_memory() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
 
 void *dev_alloc(size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
@@ -36,19 +60,25 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
         p = g_alloc(bytes, (void *)s, g_alloc_ctx);
         if (!p) RN_FAIL(ROSNET_ERR_ALLOC, "injected allocator returned NULL for " +
                                               std::to_string(bytes) + " bytes");
+        ++g_live_allocs;
+        ++g_alloc_requests;
         return p;
     }
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess || !p) {
         cudaGetLastError();
         RN_FAIL(ROSNET_ERR_ALLOC, "cudaMallocAsync(" + std::to_string(bytes) +
                                       "): " + cudaGetErrorString(e));
     }
+    ++g_live_allocs;
+    ++g_alloc_requests;
     return p;
 }
 
 void dev_free(void *p, cudaStream_t s) {
     if (!p) return;
+    --g_live_allocs;
     if (g_free) {
         g_free(p, (void *)s, g_alloc_ctx);
         return;
@@ -318,9 +348,18 @@ using namespace rosnet;
 // ---------------------------------------------------------------------------
 extern "C" {
 
+rosnet_status rosnet_alloc_stats(int64_t *requests, int64_t *live) {
+    if (requests) *requests = g_alloc_requests.load();
+    if (live) *live = g_live_allocs.load();
+    return ROSNET_OK;
+}
+
 rosnet_status rosnet_set_allocator(void *(*alloc)(size_t, void *, void *),
                                    void (*freef)(void *, void *, void *), void *ctx) {
     if ((alloc == nullptr) != (freef == nullptr)) return ROSNET_ERR_INVALID_ARG;
+    // a block must be freed by the allocator that made it
+    if (g_live_allocs.load() != 0 && (alloc != g_alloc || freef != g_free || ctx != g_alloc_ctx))
+        return ROSNET_ERR_INVALID_ARG;
     g_alloc = alloc;
     g_free = freef;
     g_alloc_ctx = ctx;
@@ -536,18 +575,28 @@ rosnet_status rosnet_btensor_slice(rosnet_btensor t, int nfix, const int64_t *va
     RN_API_END
 }
 
+static void download_enqueue(rosnet_btensor t, void *host, cudaStream_t s) {
+    size_t bytes = 2 * t->lay.numel * t->elsize;
+    if (bytes == 0) return;
+    DevBuf stage(bytes, s);   // freed stream-ordered, after the copy
+    launch_unpack(t->lay, t->dtype, t->data, t->pstride, stage.p, s);
+    RN_CHECK_CUDA(cudaMemcpyAsync(host, stage.p, bytes, cudaMemcpyDeviceToHost, s));
+}
+
 rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream) {
     if (!t || (!host && t->lay.numel > 0)) return ROSNET_ERR_INVALID_ARG;
     RN_API_BEGIN
     cudaStream_t s = (cudaStream_t)stream;
-    size_t bytes = 2 * t->lay.numel * t->elsize;
-    if (bytes == 0) return ROSNET_OK;
-    {
-        DevBuf stage(bytes, s);
-        launch_unpack(t->lay, t->dtype, t->data, t->pstride, stage.p, s);
-        RN_CHECK_CUDA(cudaMemcpyAsync(host, stage.p, bytes, cudaMemcpyDeviceToHost, s));
-    }
+    download_enqueue(t, host, s);
     RN_CHECK_CUDA(cudaStreamSynchronize(s));
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_download_async(rosnet_btensor t, void *host, void *stream) {
+    if (!t || (!host && t->lay.numel > 0)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    download_enqueue(t, host, (cudaStream_t)stream);
     return ROSNET_OK;
     RN_API_END
 }

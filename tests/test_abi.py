@@ -234,3 +234,15 @@ def test_tune_table_roundtrip_and_validation():
             R.tune_import("1 0 128 128 128 2 1\n" + b + "\n")
         assert e.value.name == "INVALID_ARG", b
     assert R.tune_export() == before      # nothing merged from a rejected text
+
+
+def test_allocator_switch_needs_no_live_blocks_and_stats():
+    """A block is freed by the allocator that made it: with no library memory
+    alive the allocator can be swapped back and forth (no device needed)."""
+    req, live = R.alloc_stats()
+    assert req >= 0 and live >= 0
+    if live == 0:
+        alloc = R._ALLOC_T(lambda n, s, c: None)
+        free = R._FREE_T(lambda p, s, c: None)
+        assert R.lib().rosnet_set_allocator(alloc, free, None) == 0
+        assert R.lib().rosnet_set_allocator(R._ALLOC_T(), R._FREE_T(), None) == 0
