@@ -106,6 +106,11 @@ struct Plan {
     int ring = 0;
     cudaGraphExec_t graph = nullptr;
     cudaGraph_t graph_src = nullptr;           // kept for event-node updates
+    // graphs cannot be captured on the legacy default stream: a plan called
+    // there replays its graph on a stream of its own, ordered after and
+    // before the caller's work by two events
+    cudaStream_t side = nullptr;
+    cudaEvent_t join[2] = {nullptr, nullptr};
     cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
     int graph_nodes = 0;
     std::vector<GettDesc> mirror;              // descriptor contents last enqueued
@@ -125,6 +130,8 @@ struct Plan {
         }
         if (graph) cudaGraphExecDestroy(graph);
         if (graph_src) cudaGraphDestroy(graph_src);
+        if (side) { cudaStreamSynchronize(side); cudaStreamDestroy(side); }
+        for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : tev) if (e) cudaEventDestroy(e);
     }
 };
@@ -153,28 +160,50 @@ auto &g_plans = *new std::unordered_map<Key128, std::unique_ptr<Plan>, Key128Has
 auto &g_timing_log = *new std::vector<std::pair<Plan *, int>>();
 
 // Leaf slots shared by equal tensors (same storage and layout) across the
-// networks of a call; slot[i][t] for tensor t of network i.
+// networks of a call; slot[i][t] for tensor t of network i.  Tensors are
+// grouped by storage pointer in an open-addressing table (reused between
+// calls, no allocation in steady state); within a group the layouts decide.
+static bool same_tensor_view(rosnet_btensor x, rosnet_btensor y) {
+    if (y->pstride != x->pstride || y->dtype != x->dtype || y->lay.rank != x->lay.rank) return false;
+    for (int a = 0; a < x->lay.rank; ++a)
+        if (y->lay.shape[a] != x->lay.shape[a] || y->lay.gstride[a] != x->lay.gstride[a] ||
+            y->lay.lstride[a] != x->lay.lstride[a] || y->lay.block[a] != x->lay.block[a])
+            return false;
+    return true;
+}
+
 std::vector<std::vector<int>> leaf_slots(int nnet, const rosnet_network *nets, std::vector<Leaf> *leaves) {
+    struct Ent { const void *p; int rep; int next; };   // next: same storage, other layout
+    thread_local std::vector<int> head;
+    thread_local std::vector<Ent> ents;
+    thread_local std::vector<rosnet_btensor> rep;
+    size_t total = 0;
+    for (int i = 0; i < nnet; ++i) total += (size_t)std::max(nets[i].ntensors, 0);
+    size_t cap = 16;
+    while (cap < 2 * total) cap <<= 1;
+    head.assign(cap, -1);
+    ents.clear();
+    rep.clear();
     std::vector<std::vector<int>> slot(nnet);
-    std::vector<rosnet_btensor> rep;
-    std::unordered_map<const void *, std::vector<int>> by_ptr;
     for (int i = 0; i < nnet; ++i) {
         slot[i].resize(nets[i].ntensors);
         for (int t = 0; t < nets[i].ntensors; ++t) {
             rosnet_btensor x = nets[i].tensors[t];
-            int found = -1;
-            for (int c : by_ptr[x->data]) {
-                rosnet_btensor y = rep[c];
-                bool same = y->pstride == x->pstride && y->dtype == x->dtype && y->lay.rank == x->lay.rank;
-                for (int a = 0; same && a < x->lay.rank; ++a)
-                    same = y->lay.shape[a] == x->lay.shape[a] && y->lay.gstride[a] == x->lay.gstride[a] &&
-                           y->lay.lstride[a] == x->lay.lstride[a] && y->lay.block[a] == x->lay.block[a];
-                if (same) { found = c; break; }
+            uint64_t hv = (uint64_t)(uintptr_t)x->data * 0x9E3779B97F4A7C15ull;
+            size_t h = (size_t)(hv >> 32) & (cap - 1);
+            while (head[h] >= 0 && ents[head[h]].p != x->data) h = (h + 1) & (cap - 1);
+            int found = -1, last = -1;
+            for (int e = head[h]; e >= 0; e = ents[e].next) {
+                if (same_tensor_view(x, rep[ents[e].rep])) { found = ents[e].rep; break; }
+                last = e;
             }
             if (found < 0) {
                 found = (int)rep.size();
                 rep.push_back(x);
-                by_ptr[x->data].push_back(found);
+                ents.push_back({x->data, found, -1});
+                const int e = (int)ents.size() - 1;
+                if (last >= 0) ents[last].next = e;
+                else head[h] = e;
                 if (leaves) leaves->push_back({i, t});
             }
             slot[i][t] = found;
@@ -492,7 +521,8 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         fill_desc_tables(S.desc, views[g], dtab + S.table_off);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
-        const bool cuda_core_gemm = is_tiled_kind(S.desc.kind) || S.desc.kind == kKindPackF32;
+        const bool cuda_core_gemm =
+            is_tiled_kind(S.desc.kind) || S.desc.kind == kKindPackF32 || S.desc.kind == kKindDirect;
         if ((flags & ROSNET_OPT_AUTOTUNE) && cuda_core_gemm &&
             8.0 * (double)S.desc.M * (double)S.desc.N * (double)S.desc.K >= 1e6) {
             // time the candidate kernels on the plan's own operands (contents
@@ -621,8 +651,22 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
         const Step &S = P.steps[g];
         return S.arena_off == SIZE_MAX ? outs[S.out_net]->pstride : S.lay.numel;
     };
-    // patch descriptors into the next pinned staging buffer; upload only the
-    // range whose operand addresses changed since the last call
+    // the stream the plan's work goes on: the caller's, or for a graph
+    // requested on the legacy default stream (where graphs cannot be
+    // captured) the plan's own stream, ordered after the caller's work
+    const bool want_graph = (P.flags & ROSNET_OPT_GRAPH) && !P.launches.empty();
+    const cudaStream_t caller = s;
+    if (want_graph && s == nullptr) {
+        if (!P.side) {
+            RN_CHECK_CUDA(cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking));
+            for (auto &e : P.join) RN_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        RN_CHECK_CUDA(cudaEventRecord(P.join[0], caller));
+        RN_CHECK_CUDA(cudaStreamWaitEvent(P.side, P.join[0], 0));
+        s = P.side;
+    }
+    // patch descriptors; stage and upload only the range whose operands
+    // changed since the last call
     const int r = P.ring;
     P.ring = (P.ring + 1) % Plan::kRing;
     RN_CHECK_CUDA(cudaEventSynchronize(P.ev[r]));
@@ -636,17 +680,20 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
         GettDesc d = P.slot_desc[i];
         bind_operands(d, ptr_of(S.ga), ptr_of(S.gb), ptr_of(st), pstride_of(S.ga), pstride_of(S.gb),
                       pstride_of(st));
-        h[i] = d;
-        if (!P.mirror_valid || P.mirror[i].a != d.a || P.mirror[i].b != d.b || P.mirror[i].c != d.c) {
+        const GettDesc &m = P.mirror[i];
+        if (!P.mirror_valid || m.a != d.a || m.b != d.b || m.c != d.c || m.a_plane != d.a_plane ||
+            m.b_plane != d.b_plane || m.c_plane != d.c_plane) {
             lo = std::min(lo, i);
             hi = i + 1;
             P.mirror[i] = d;
         }
     }
     P.mirror_valid = true;
-    if (lo < hi)
+    if (lo < hi) {
+        std::copy(P.mirror.begin() + lo, P.mirror.begin() + hi, h + lo);
         RN_CHECK_CUDA(cudaMemcpyAsync((GettDesc *)P.descs.p + lo, h + lo, (hi - lo) * sizeof(GettDesc),
                                       cudaMemcpyHostToDevice, s));
+    }
     RN_CHECK_CUDA(cudaEventRecord(P.ev[r], s));
 
     const bool timing = (P.flags & ROSNET_OPT_TIMING) && P.heavy >= 0;
@@ -691,7 +738,7 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
             }
         }
     };
-    const bool use_graph = (P.flags & ROSNET_OPT_GRAPH) && s != nullptr && !P.launches.empty();
+    const bool use_graph = want_graph && s != nullptr;
     if (use_graph) {
         if (!P.graph) {
             cudaGraph_t gr = nullptr;
@@ -744,6 +791,10 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
         const Layout &src = O.final_gid >= 0 ? P.steps[O.final_gid].lay : leaf_of(O.final_gid)->lay;
         launch_relayout(src, outs[i]->lay, O.perm.data(), P.dtype, ptr_of(O.final_gid),
                         pstride_of(O.final_gid), outs[i]->data, outs[i]->pstride, s);
+    }
+    if (s != caller) {   // the caller's later work sees the results
+        RN_CHECK_CUDA(cudaEventRecord(P.join[1], s));
+        RN_CHECK_CUDA(cudaStreamWaitEvent(caller, P.join[1], 0));
     }
 }
 

@@ -489,6 +489,82 @@ struct Vec16<double> {
     static constexpr int n = 2;
 };
 
+// Epilogue of a register-tiled output tile (TM x TN complex values per thread
+// at rows ty*TM.., columns tx*TN..): one plane at a time the tile goes through
+// shared memory (cs: at least (BM + 1) * (BN + 1) elements, free for reuse)
+// and out with the lanes of a warp along the destination's unit-stride
+// dimension (n for split-K partials [m][n], else C's own), so stores coalesce
+// whatever the output layout.  sCM / sCN: C offsets of the tile's rows and
+// columns (unused for partials).  All 256 threads call it.
+template <typename T, int BM, int BN, int TM, int TN>
+__device__ __forceinline__ void store_tile(const GettDesc &sd, const T (&cr)[TM][TN], const T (&ci)[TM][TN], T *cs,
+                                           const int64_t *sCM, const int64_t *sCN, int64_t m0, int64_t n0,
+                                           int split, int ty, int tx) {
+    constexpr int NT = 256;
+    const int64_t M = sd.M, N = sd.N;
+    const bool part = sd.part != nullptr;
+    const bool m_fast = !part && !(sd.flags & kFlagCNFast);
+    const bool atomic = sd.flags & kFlagAtomic;   // commutative split: order-free adds
+    const int64_t MN = M * N;
+    T *__restrict__ dst = part ? (T *)sd.part + (2 * (int64_t)split) * MN : (T *)sd.c;
+    const int64_t dplane = part ? MN : sd.c_plane;
+    const int ld = m_fast ? BM + 1 : BN + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll 1
+    for (int pl = 0; pl < 2; ++pl) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int ml = ty * TM + i, nl = tx * TN + j;
+                cs[m_fast ? nl * ld + ml : ml * ld + nl] = pl ? ci[i][j] : cr[i][j];
+            }
+        __syncthreads();
+        T *__restrict__ out = dst + pl * dplane;
+        if (m_fast) {   // lanes along m: this lane's rows' offsets once
+            constexpr int UM = (BM + 31) / 32;
+            int64_t cm[UM];
+#pragma unroll
+            for (int u = 0; u < UM; ++u) {
+                const int ml = lane + 32 * u;
+                cm[u] = (ml < BM && m0 + ml < M) ? sCM[ml] : -1;
+            }
+            for (int nl = warp; nl < BN; nl += NT / 32) {
+                if (n0 + nl >= N) break;
+                const int64_t cn = sCN[nl];
+                const T *row = cs + nl * ld + lane;
+#pragma unroll
+                for (int u = 0; u < UM; ++u)
+                    if (cm[u] >= 0) {
+                        if (atomic) atomicAdd(out + cm[u] + cn, row[32 * u]);
+                        else out[cm[u] + cn] = row[32 * u];
+                    }
+            }
+        } else {        // lanes along n: this lane's columns' offsets once
+            constexpr int UN = (BN + 31) / 32;
+            int64_t cn[UN];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int nl = lane + 32 * u;
+                cn[u] = (nl < BN && n0 + nl < N) ? (part ? n0 + nl : sCN[nl]) : -1;
+            }
+            for (int ml = warp; ml < BM; ml += NT / 32) {
+                const int64_t m = m0 + ml;
+                if (m >= M) break;
+                const int64_t base = part ? m * N : sCM[ml];
+                const T *row = cs + ml * ld + lane;
+#pragma unroll
+                for (int u = 0; u < UN; ++u)
+                    if (cn[u] >= 0) {
+                        if (atomic) atomicAdd(out + base + cn[u], row[32 * u]);
+                        else out[base + cn[u]] = row[32 * u];
+                    }
+            }
+        }
+        __syncthreads();   // the next plane reuses the staging area
+    }
+}
+
 // The tile body, specialised on whether A (B) is read along m (n) or along k:
 // with those known at compile time every thread's gather addresses reduce to
 // one base offset per operand plus compile-time strides.
@@ -654,56 +730,140 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
     cp_async_wait<0>();
     __syncthreads();   // every warp is done with the ring: it holds the output tile now
 
-    // Epilogue: one plane at a time, the tile goes through shared memory and
-    // out with the lanes of a warp along the destination's unit-stride
-    // dimension (n for the split-K partials [m][n], else C's own), so stores
-    // coalesce whatever the output layout.
-    const bool part = sd.part != nullptr;
-    const bool m_fast = !part && !(sd.flags & kFlagCNFast);
-    const bool atomic = sd.flags & kFlagAtomic;   // commutative split: order-free adds
-    const int64_t MN = M * N;
-    T *__restrict__ dst = part ? (T *)sd.part + (2 * (int64_t)split) * MN : (T *)sd.c;
-    const int64_t dplane = part ? MN : sd.c_plane;
-    T *cs = As;
-    const int ld = m_fast ? BM + 1 : BN + 1;
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll 1
-    for (int pl = 0; pl < 2; ++pl) {
+    store_tile<T, BM, BN, TM, TN>(sd, cr, ci, As, sCM, sCN, m0, n0, split, ty, tx);
+}
+
+// Short contractions (K <= kDirectK): each CTA gathers its whole A (64 x K)
+// and B (K x 64) tiles into shared memory in one pass -- every thread's loads
+// issued before any is used, coalesced along each operand's unit-stride digit,
+// offsets read from shared copies of the offset tables -- then runs the K loop
+// from shared memory.  No staging ring, no split, small code: for steps whose
+// K is too short to fill a pipeline.
+template <typename T>
+struct DirectCfg {
+    static constexpr int BM = 64, BN = 64, KM = kDirectK, TM = 4, TN = 4;
+    static constexpr int PAD = 16 / (int)sizeof(T);
+    static constexpr int RA = BM + PAD, RB = BN + PAD;
+    static constexpr int NE = BM * KM / 256;   // elements of one operand per thread
+    static constexpr size_t smem = sizeof(T) * 2 * (size_t)KM * (RA + RB);
+    static_assert((size_t)(BM + 1) * (BN + 1) * sizeof(T) <= smem, "epilogue staging exceeds the tiles");
+};
+
+template <typename T, bool amf, bool bnf>
+__device__ __forceinline__ void direct_body(const GettDesc &sd, T *As, T *Bs, int64_t *sAM, int64_t *sBN,
+                                            int64_t *sAK, int64_t *sBK, int64_t *sCM, int64_t *sCN) {
+    using Cfg = DirectCfg<T>;
+    using V = typename Vec16<T>::type;
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, KM = Cfg::KM, TM = Cfg::TM, TN = Cfg::TN;
+    constexpr int RA = Cfg::RA, RB = Cfg::RB, NE = Cfg::NE;
+    const int tid = threadIdx.x;
+    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
+    const int64_t m0 = (tile % sd.tiles_m) * BM, n0 = (tile / sd.tiles_m) * BN;
+    const int64_t M = sd.M, N = sd.N;
+    const int K = (int)sd.K;
+    // offsets of this tile's rows / columns / contracted indices (static tables)
+    for (int i = tid; i < 2 * (BM + KM); i += 256) {
+        if (i < BM) {
+            sAM[i] = m0 + i < M ? sd.offAM[m0 + i] : -1;
+            sCM[i] = m0 + i < M ? sd.offCM[m0 + i] : 0;
+        } else if (i < BM + BN) {
+            const int j = i - BM;
+            sBN[j] = n0 + j < N ? sd.offBN[n0 + j] : -1;
+            sCN[j] = n0 + j < N ? sd.offCN[n0 + j] : 0;
+        } else if (i < BM + BN + KM) {
+            const int k = i - BM - BN;
+            sAK[k] = k < K ? sd.offAK[k] : 0;
+        } else {
+            const int k = i - BM - BN - KM;
+            sBK[k] = k < K ? sd.offBK[k] : 0;
+        }
+    }
+    __syncthreads();
+    grid_dep_wait();   // operands may be the previous kernel's results
+    const T *__restrict__ A = (const T *)sd.a;
+    const T *__restrict__ B = (const T *)sd.b;
+    const int64_t ap = sd.a_plane, bp = sd.b_plane;
+    T ar[NE], ai[NE], br[NE], bi[NE];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {   // all loads first
+        const int e = tid + 256 * j;
+        const int am = amf ? e % BM : e / KM, ak = amf ? e / BM : e % KM;
+        const int bn = bnf ? e % BN : e / KM, bk = bnf ? e / BN : e % KM;
+        const int64_t oa = (ak < K && sAM[am] >= 0) ? sAM[am] + sAK[ak] : -1;
+        const int64_t ob = (bk < K && sBN[bn] >= 0) ? sBN[bn] + sBK[bk] : -1;
+        ar[j] = oa >= 0 ? A[oa] : T(0);
+        ai[j] = oa >= 0 ? A[oa + ap] : T(0);
+        br[j] = ob >= 0 ? B[ob] : T(0);
+        bi[j] = ob >= 0 ? B[ob + bp] : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+        const int e = tid + 256 * j;
+        const int am = amf ? e % BM : e / KM, ak = amf ? e / BM : e % KM;
+        const int bn = bnf ? e % BN : e / KM, bk = bnf ? e / BN : e % KM;
+        As[ak * RA + am] = ar[j];
+        As[KM * RA + ak * RA + am] = ai[j];
+        Bs[bk * RB + bn] = br[j];
+        Bs[KM * RB + bk * RB + bn] = bi[j];
+    }
+    __syncthreads();
+    const int ty = tid >> 4, tx = tid & 15;
+    T cr[TM][TN], ci[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0;
+    const T *a0 = As + ty * TM, *b0 = Bs + tx * TN;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        T xr[TM], xi[TM], yr[TN], yi[TN];
+#pragma unroll
+        for (int v = 0; v < TM * (int)sizeof(T) / 16; ++v) {
+            const V r = *reinterpret_cast<const V *>(a0 + k * RA + v * Vec16<T>::n);
+            const V q = *reinterpret_cast<const V *>(a0 + KM * RA + k * RA + v * Vec16<T>::n);
+            const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int u = 0; u < Vec16<T>::n; ++u) {
+                xr[v * Vec16<T>::n + u] = rr[u];
+                xi[v * Vec16<T>::n + u] = qq[u];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < TN * (int)sizeof(T) / 16; ++v) {
+            const V r = *reinterpret_cast<const V *>(b0 + k * RB + v * Vec16<T>::n);
+            const V q = *reinterpret_cast<const V *>(b0 + KM * RB + k * RB + v * Vec16<T>::n);
+            const T *rr = reinterpret_cast<const T *>(&r), *qq = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int u = 0; u < Vec16<T>::n; ++u) {
+                yr[v * Vec16<T>::n + u] = rr[u];
+                yi[v * Vec16<T>::n + u] = qq[u];
+            }
+        }
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                const int ml = ty * TM + i, nl = tx * TN + j;
-                cs[m_fast ? nl * ld + ml : ml * ld + nl] = pl ? ci[i][j] : cr[i][j];
-            }
-        __syncthreads();
-        T *__restrict__ out = dst + pl * dplane;
-        if (m_fast) {
-            for (int nl = warp; nl < BN; nl += NT / 32) {
-                if (n0 + nl >= N) break;
-                const int64_t cn = sCN[nl];
-                for (int ml = lane; ml < BM; ml += 32) {
-                    if (m0 + ml >= M) break;
-                    const int64_t o = sCM[ml] + cn;
-                    if (atomic) atomicAdd(out + o, cs[nl * ld + ml]);
-                    else out[o] = cs[nl * ld + ml];
-                }
-            }
-        } else {
-            for (int ml = warp; ml < BM; ml += NT / 32) {
-                const int64_t m = m0 + ml;
-                if (m >= M) break;
-                const int64_t base = part ? m * N : sCM[ml];
-                for (int nl = lane; nl < BN; nl += 32) {
-                    const int64_t n = n0 + nl;
-                    if (n >= N) break;
-                    const int64_t o = base + (part ? n : sCN[nl]);
-                    if (atomic) atomicAdd(out + o, cs[ml * ld + nl]);
-                    else out[o] = cs[ml * ld + nl];
-                }
-            }
-        }
-        __syncthreads();   // the next plane reuses the staging area
+            for (int j = 0; j < TN; ++j) cmac(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
+    }
+    __syncthreads();   // the operand tiles become the output staging area
+    store_tile<T, BM, BN, TM, TN>(sd, cr, ci, As, sCM, sCN, m0, n0, 0, ty, tx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gett_direct_kernel(const __grid_constant__ GroupArgs g) {
+    using Cfg = DirectCfg<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);          // [2 planes][KM][RA]
+    T *Bs = As + 2 * Cfg::KM * Cfg::RA;                // [2 planes][KM][RB]
+    __shared__ GettDesc sd;
+    __shared__ int64_t sAM[Cfg::BM], sBN[Cfg::BN], sAK[Cfg::KM], sBK[Cfg::KM], sCM[Cfg::BM], sCN[Cfg::BN];
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
+    __syncthreads();
+    switch (((sd.flags & kFlagAMFast) ? 2 : 0) | ((sd.flags & kFlagBNFast) ? 1 : 0)) {
+        case 0: direct_body<T, false, false>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
+        case 1: direct_body<T, false, true>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
+        case 2: direct_body<T, true, false>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
+        default: direct_body<T, true, true>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
     }
 }
 
@@ -779,6 +939,14 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
             return;
         }
     }
+    // short contractions: whole tiles in one pass
+    if (d.K >= 8 && d.K <= kDirectK && std::min(d.M, d.N) >= 16 && MN >= 4096) {
+        if (d.N > d.M) swap_operands(d);
+        d.kind = kKindDirect;
+        d.tiles_m = (d.M + 63) / 64;
+        d.tiles_n = (d.N + 63) / 64;
+        return;
+    }
     const bool tiled_ok = d.K >= 16 && std::min(d.M, d.N) >= 16 && MN >= 2048;
     if (tiled_ok) {
         if (d.N > d.M) swap_operands(d);   // the BM side takes the larger extent
@@ -830,6 +998,17 @@ size_t desc_part_bytes(const GettDesc &d, int dtype) {
     return (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * (dtype == ROSNET_C64 ? 4 : 8);
 }
 
+template <typename T>
+static void launch_direct(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
+    static bool attr_set = false;   // once per process (one device)
+    if (!attr_set) {
+        RN_CHECK_CUDA(cudaFuncSetAttribute(gett_direct_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)DirectCfg<T>::smem));
+        attr_set = true;
+    }
+    launch_pdl(gett_direct_kernel<T>, grid, 256, DirectCfg<T>::smem, s, ga);
+}
+
 template <typename T, int BM, int BN, int BK>
 static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
     using Cfg = TiledCfg<T, BM, BN, BK, kTiledStages>;
@@ -858,6 +1037,7 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 256, 0, s, ga); break;
             case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
             case kKindTiled256x16: launch_tiled<float, 256, 16, 16>(grid, ga, s); break;
+            case kKindDirect: launch_direct<float>(grid, ga, s); break;
             case kKindTiled128x32: launch_tiled<float, 128, 32, 16>(grid, ga, s); break;
             default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
         }
@@ -868,6 +1048,7 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindReduce: launch_pdl(gett_reduce_kernel<double>, grid, 256, 0, s, ga); break;
             case kKindZero: launch_pdl(gett_zero_kernel<double>, grid, 256, 0, s, ga); break;
             case kKindDot: launch_pdl(gett_dot_kernel<double>, grid, 256, 0, s, ga); break;
+            case kKindDirect: launch_direct<double>(grid, ga, s); break;
             default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
         }
     }
@@ -931,7 +1112,7 @@ int64_t reduce_ctas(const GettDesc &d);
 // reduction mode is forced -- the packed path.  Results are cached by
 // (dtype, M, N, K, layout flags).
 void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
-    if (!is_tiled_kind(d.kind) && d.kind != kKindPackF32) return;
+    if (!is_tiled_kind(d.kind) && d.kind != kKindPackF32 && d.kind != kKindDirect) return;
     if (d.flags & kFlagAtomic) return;
     packed_ok = packed_ok && dtype == ROSNET_C64;
     const TuneKey key{dtype, d.flags | (packed_ok ? 1 << 30 : 0), d.M, d.N, d.K};
@@ -951,8 +1132,8 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
     const int BK = dtype == ROSNET_C64 ? 16 : 8;
     std::vector<GettDesc> cands;
     // the split the heuristic would pick for a 64x64 tiling
-    int64_t auto_split = d.kind == kKindPackF32 ? 1 : d.ksplit;
-    if (d.kind == kKindPackF32) {
+    int64_t auto_split = (d.kind == kKindPackF32 || d.kind == kKindDirect) ? 1 : d.ksplit;
+    if (d.kind == kKindPackF32 || d.kind == kKindDirect) {
         const int64_t tiles = ((d.M + 63) / 64) * ((d.N + 63) / 64), nkt = (d.K + BK - 1) / BK;
         if (tiles < kSMs && nkt >= 32) auto_split = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, nkt / 8);
     }
@@ -972,6 +1153,14 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
                 dup |= c.kind == y.kind && c.ksplit == y.ksplit && c.ktiles_per_split == y.ktiles_per_split;
             if (!dup) cands.push_back(y);
         }
+    }
+    if (d.K <= kDirectK) {
+        GettDesc y = d;
+        y.kind = kKindDirect;
+        y.tiles_m = (d.M + 63) / 64;
+        y.tiles_n = (d.N + 63) / 64;
+        apply_split(y, BK, 1);
+        cands.push_back(y);
     }
     if (packed_ok) {
         GettDesc y = d;
@@ -1044,6 +1233,9 @@ static bool tune_geometry(int dtype, int kind, int64_t M, int64_t N, int64_t K, 
         tiled_tile(kind, &BM, &BN);
         y.tiles_m = (M + BM - 1) / BM;
         y.tiles_n = (N + BN - 1) / BN;
+    } else if (kind == kKindDirect && K <= kDirectK && ksplit == 1) {
+        y.tiles_m = (M + 63) / 64;
+        y.tiles_n = (N + 63) / 64;
     } else if (kind == kKindPackF32 && dtype == ROSNET_C64 && ksplit == 1) {
         y.tiles_m = (M + f32p_tile_m() - 1) / f32p_tile_m();
         y.tiles_n = (N + f32p_tile_n() - 1) / f32p_tile_n();

@@ -201,7 +201,10 @@ enum KernelKind : int32_t {
     kKindPackF32 = 10,   // plain FP32 on CUDA cores from packed operands (TMA-fed 64x64 tiles)
     kKindTiled256x16 = 11,  // 256x16 tiles (complex64 only): problems with few columns
     kKindTiled128x32 = 12,  // 128x32 tiles (complex64 only)
+    kKindDirect = 13,       // 64x64 tiles, whole K (<= kDirectK) gathered in one pass
 };
+
+constexpr int kDirectK = 32;   // longest contraction of the direct kernel
 
 // Register-tiled CUDA-core kinds (gett_tiled_kernel), their CTA tile, and
 // whether one applies to a problem of dtype and (M, N).

@@ -112,6 +112,17 @@ def test_tiles_and_ragged_tails(dtype, mnk):
     assert oracle.rel_frobenius(got, ref) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", [R.C64, R.C128])
+@pytest.mark.parametrize("mnk", [(2048, 512, 32), (1000, 70, 8), (130, 200, 17), (64, 64, 31), (3000, 20, 9)])
+def test_short_contractions_direct(dtype, mnk):
+    """K of 8..32: whole tiles gathered in one pass (direct kernel), ragged."""
+    M, N, K = mnk
+    a = W.complex_normal((M, K), 15)
+    b = W.complex_normal((K, N), 16)
+    _, got = run(a, None, b, None, [1], [0], dtype)
+    assert oracle.rel_frobenius(got, ref_of(a, b, [1], [0], dtype)) <= TOL[dtype]
+
+
 @pytest.mark.parametrize("mnk", [(300, 13, 200), (513, 16, 4000), (16, 700, 333), (200, 30, 300),
                                  (130, 29, 2000), (1000, 17, 64)])
 def test_narrow_tiles(mnk):
