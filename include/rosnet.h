@@ -403,8 +403,8 @@ rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path
  * ms[i] receives the milliseconds; flops[i] / bytes[i] / kinds[i] (any may
  * be NULL) the launch's algorithmic work -- sum of 8*M*N*K and of
  * (|A| + |B| + |C|) * element size over its problems -- and its kernel family
- * (2 = 64x64 tiles, 3 = 128x64, 11 = 256x16, 12 = 128x32, 13 = direct
- * short-K tiles, 5-7 = tcgen05 TF32 / 3xTF32 / 3xBF16, 10 = packed FP32;
+ * (2 = 64x64 tiles, 3 = 128x64, 11 = 256x16, 12 = 128x32, 13 / 14 = direct
+ * short-range tiles, 5-7 = tcgen05 TF32 / 3xTF32 / 3xBF16, 10 = packed FP32;
  * others are the small-problem kernels).  *n receives the
  * number of entries written (<= max_entries).
  */
@@ -416,8 +416,9 @@ rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int3
  * can plan with the same kernels without timing them again.  One line per
  * tuned problem shape, seven integers separated by spaces:
  *     dtype key_flags M N K kind ksplit
- * (kind: 2 = 64x64 tiles, 3 = 128x64, 11 = 256x16, 12 = 128x32, 13 = direct
- * 64x64 for K <= 32, 10 = packed FP32; ksplit = number of contracted-index
+ * (kind: 2 = 64x64 tiles, 3 = 128x64, 11 = 256x16, 12 = 128x32, 13 / 14 =
+ * direct 64x64 / 256x16 (one 32-long contracted range per CTA, so ksplit =
+ * ceil(K / 32)), 10 = packed FP32; ksplit = number of contracted-index
  * ranges, 1 = none).
  * rosnet_tune_export writes the text, NUL-terminated, into buf when cap is
  * large enough; *len always receives the bytes needed (terminator included).

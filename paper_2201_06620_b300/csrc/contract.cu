@@ -522,7 +522,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
         const bool cuda_core_gemm =
-            is_tiled_kind(S.desc.kind) || S.desc.kind == kKindPackF32 || S.desc.kind == kKindDirect;
+            is_tiled_kind(S.desc.kind) || S.desc.kind == kKindPackF32 || is_direct_kind(S.desc.kind);
         if ((flags & ROSNET_OPT_AUTOTUNE) && cuda_core_gemm &&
             8.0 * (double)S.desc.M * (double)S.desc.N * (double)S.desc.K >= 1e6) {
             // time the candidate kernels on the plan's own operands (contents

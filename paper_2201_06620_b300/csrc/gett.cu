@@ -733,36 +733,44 @@ __device__ __forceinline__ void tiled_body(const GettDesc &sd, T *As, T *Bs, int
     store_tile<T, BM, BN, TM, TN>(sd, cr, ci, As, sCM, sCN, m0, n0, split, ty, tx);
 }
 
-// Short contractions (K <= kDirectK): each CTA gathers its whole A (64 x K)
-// and B (K x 64) tiles into shared memory in one pass -- every thread's loads
-// issued before any is used, coalesced along each operand's unit-stride digit,
-// offsets read from shared copies of the offset tables -- then runs the K loop
-// from shared memory.  No staging ring, no split, small code: for steps whose
-// K is too short to fill a pipeline.
-template <typename T>
+// Short contraction ranges: each CTA gathers its whole A (BM x Kc) and B
+// (Kc x BN) tiles into shared memory in one pass -- every thread's loads
+// issued before any is used, coalesced along each operand's unit-stride
+// digit, offsets read from shared copies of the offset tables -- then runs
+// the Kc loop from shared memory.  Kc <= kDirectK: the whole K, or with a
+// split one kDirectK-long slice of it per CTA (partials summed by
+// gett_reduce_kernel).  No staging ring, small code: for contractions whose
+// per-CTA range is too short to fill a pipeline.
+template <typename T, int BM_, int BN_>
 struct DirectCfg {
-    static constexpr int BM = 64, BN = 64, KM = kDirectK, TM = 4, TN = 4;
+    static constexpr int BM = BM_, BN = BN_, KM = kDirectK;
+    static constexpr int TN = 4, TXN = BN / TN, TY = 256 / TXN, TM = BM / TY;   // 4 columns per thread
     static constexpr int PAD = 16 / (int)sizeof(T);
     static constexpr int RA = BM + PAD, RB = BN + PAD;
-    static constexpr int NE = BM * KM / 256;   // elements of one operand per thread
+    static constexpr int NEA = BM * KM / 256, NEB = BN * KM / 256;   // elements per thread
     static constexpr size_t smem = sizeof(T) * 2 * (size_t)KM * (RA + RB);
+    static_assert(TXN * TY == 256 && TM * TY == BM && TM % 4 == 0 && NEB >= 1, "tile shape");
     static_assert((size_t)(BM + 1) * (BN + 1) * sizeof(T) <= smem, "epilogue staging exceeds the tiles");
 };
 
-template <typename T, bool amf, bool bnf>
+template <typename T, int BM, int BN, bool amf, bool bnf>
 __device__ __forceinline__ void direct_body(const GettDesc &sd, T *As, T *Bs, int64_t *sAM, int64_t *sBN,
                                             int64_t *sAK, int64_t *sBK, int64_t *sCM, int64_t *sCN) {
-    using Cfg = DirectCfg<T>;
+    using Cfg = DirectCfg<T, BM, BN>;
     using V = typename Vec16<T>::type;
-    constexpr int BM = Cfg::BM, BN = Cfg::BN, KM = Cfg::KM, TM = Cfg::TM, TN = Cfg::TN;
-    constexpr int RA = Cfg::RA, RB = Cfg::RB, NE = Cfg::NE;
+    constexpr int KM = Cfg::KM, TM = Cfg::TM, TN = Cfg::TN, TXN = Cfg::TXN;
+    constexpr int RA = Cfg::RA, RB = Cfg::RB, NEA = Cfg::NEA, NEB = Cfg::NEB;
     const int tid = threadIdx.x;
-    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
-    const int64_t m0 = (tile % sd.tiles_m) * BM, n0 = (tile / sd.tiles_m) * BN;
+    const int64_t t = (int64_t)blockIdx.x - sd.tile_begin;
+    const int64_t ntile = sd.tiles_m * sd.tiles_n;
+    const int split = (int)(t / ntile);
+    const int64_t t2 = t - (int64_t)split * ntile;
+    const int64_t m0 = (t2 % sd.tiles_m) * BM, n0 = (t2 / sd.tiles_m) * BN;
     const int64_t M = sd.M, N = sd.N;
-    const int K = (int)sd.K;
+    const int64_t k0 = (int64_t)split * KM;
+    const int K = (int)min((int64_t)KM, sd.K - k0);   // this CTA's contracted range
     // offsets of this tile's rows / columns / contracted indices (static tables)
-    for (int i = tid; i < 2 * (BM + KM); i += 256) {
+    for (int i = tid; i < BM + BN + 2 * KM; i += 256) {
         if (i < BM) {
             sAM[i] = m0 + i < M ? sd.offAM[m0 + i] : -1;
             sCM[i] = m0 + i < M ? sd.offCM[m0 + i] : 0;
@@ -772,10 +780,10 @@ __device__ __forceinline__ void direct_body(const GettDesc &sd, T *As, T *Bs, in
             sCN[j] = n0 + j < N ? sd.offCN[n0 + j] : 0;
         } else if (i < BM + BN + KM) {
             const int k = i - BM - BN;
-            sAK[k] = k < K ? sd.offAK[k] : 0;
+            sAK[k] = k < K ? sd.offAK[k0 + k] : 0;
         } else {
             const int k = i - BM - BN - KM;
-            sBK[k] = k < K ? sd.offBK[k] : 0;
+            sBK[k] = k < K ? sd.offBK[k0 + k] : 0;
         }
     }
     __syncthreads();
@@ -783,31 +791,47 @@ __device__ __forceinline__ void direct_body(const GettDesc &sd, T *As, T *Bs, in
     const T *__restrict__ A = (const T *)sd.a;
     const T *__restrict__ B = (const T *)sd.b;
     const int64_t ap = sd.a_plane, bp = sd.b_plane;
-    T ar[NE], ai[NE], br[NE], bi[NE];
+    // loads in flight together, at most GA elements of A (and all of B, in the
+    // first batch) per thread at a time
+    constexpr int GA = NEA < 16 ? NEA : 16;
+#pragma unroll 1
+    for (int j0 = 0; j0 < NEA; j0 += GA) {
+        T ar[GA], ai[GA], br[NEB], bi[NEB];
 #pragma unroll
-    for (int j = 0; j < NE; ++j) {   // all loads first
-        const int e = tid + 256 * j;
-        const int am = amf ? e % BM : e / KM, ak = amf ? e / BM : e % KM;
-        const int bn = bnf ? e % BN : e / KM, bk = bnf ? e / BN : e % KM;
-        const int64_t oa = (ak < K && sAM[am] >= 0) ? sAM[am] + sAK[ak] : -1;
-        const int64_t ob = (bk < K && sBN[bn] >= 0) ? sBN[bn] + sBK[bk] : -1;
-        ar[j] = oa >= 0 ? A[oa] : T(0);
-        ai[j] = oa >= 0 ? A[oa + ap] : T(0);
-        br[j] = ob >= 0 ? B[ob] : T(0);
-        bi[j] = ob >= 0 ? B[ob + bp] : T(0);
-    }
+        for (int j = 0; j < GA; ++j) {
+            const int e = tid + 256 * (j0 + j);
+            const int am = amf ? e % BM : e / KM, ak = amf ? e / BM : e % KM;
+            const int64_t oa = (ak < K && sAM[am] >= 0) ? sAM[am] + sAK[ak] : -1;
+            ar[j] = oa >= 0 ? A[oa] : T(0);
+            ai[j] = oa >= 0 ? A[oa + ap] : T(0);
+        }
+        if (j0 == 0) {
 #pragma unroll
-    for (int j = 0; j < NE; ++j) {
-        const int e = tid + 256 * j;
-        const int am = amf ? e % BM : e / KM, ak = amf ? e / BM : e % KM;
-        const int bn = bnf ? e % BN : e / KM, bk = bnf ? e / BN : e % KM;
-        As[ak * RA + am] = ar[j];
-        As[KM * RA + ak * RA + am] = ai[j];
-        Bs[bk * RB + bn] = br[j];
-        Bs[KM * RB + bk * RB + bn] = bi[j];
+            for (int j = 0; j < NEB; ++j) {
+                const int e = tid + 256 * j;
+                const int bn = bnf ? e % BN : e / KM, bk = bnf ? e / BN : e % KM;
+                const int64_t ob = (bk < K && sBN[bn] >= 0) ? sBN[bn] + sBK[bk] : -1;
+                br[j] = ob >= 0 ? B[ob] : T(0);
+                bi[j] = ob >= 0 ? B[ob + bp] : T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < NEB; ++j) {
+                const int e = tid + 256 * j;
+                const int bn = bnf ? e % BN : e / KM, bk = bnf ? e / BN : e % KM;
+                Bs[bk * RB + bn] = br[j];
+                Bs[KM * RB + bk * RB + bn] = bi[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < GA; ++j) {
+            const int e = tid + 256 * (j0 + j);
+            const int am = amf ? e % BM : e / KM, ak = amf ? e / BM : e % KM;
+            As[ak * RA + am] = ar[j];
+            As[KM * RA + ak * RA + am] = ai[j];
+        }
     }
     __syncthreads();
-    const int ty = tid >> 4, tx = tid & 15;
+    const int ty = tid / TXN, tx = tid % TXN;
     T cr[TM][TN], ci[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -845,25 +869,25 @@ __device__ __forceinline__ void direct_body(const GettDesc &sd, T *As, T *Bs, in
             for (int j = 0; j < TN; ++j) cmac(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
     }
     __syncthreads();   // the operand tiles become the output staging area
-    store_tile<T, BM, BN, TM, TN>(sd, cr, ci, As, sCM, sCN, m0, n0, 0, ty, tx);
+    store_tile<T, BM, BN, TM, TN>(sd, cr, ci, As, sCM, sCN, m0, n0, split, ty, tx);
 }
 
-template <typename T>
+template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(256) gett_direct_kernel(const __grid_constant__ GroupArgs g) {
-    using Cfg = DirectCfg<T>;
+    using Cfg = DirectCfg<T, BM, BN>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);          // [2 planes][KM][RA]
     T *Bs = As + 2 * Cfg::KM * Cfg::RA;                // [2 planes][KM][RB]
     __shared__ GettDesc sd;
-    __shared__ int64_t sAM[Cfg::BM], sBN[Cfg::BN], sAK[Cfg::KM], sBK[Cfg::KM], sCM[Cfg::BM], sCN[Cfg::BN];
+    __shared__ int64_t sAM[BM], sBN[BN], sAK[Cfg::KM], sBK[Cfg::KM], sCM[BM], sCN[BN];
     grid_dep_launch();
     if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
     switch (((sd.flags & kFlagAMFast) ? 2 : 0) | ((sd.flags & kFlagBNFast) ? 1 : 0)) {
-        case 0: direct_body<T, false, false>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
-        case 1: direct_body<T, false, true>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
-        case 2: direct_body<T, true, false>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
-        default: direct_body<T, true, true>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
+        case 0: direct_body<T, BM, BN, false, false>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
+        case 1: direct_body<T, BM, BN, false, true>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
+        case 2: direct_body<T, BM, BN, true, false>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
+        default: direct_body<T, BM, BN, true, true>(sd, As, Bs, sAM, sBN, sAK, sBK, sCM, sCN); break;
     }
 }
 
@@ -998,15 +1022,16 @@ size_t desc_part_bytes(const GettDesc &d, int dtype) {
     return (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * (dtype == ROSNET_C64 ? 4 : 8);
 }
 
-template <typename T>
+template <typename T, int BM, int BN>
 static void launch_direct(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
+    using Cfg = DirectCfg<T, BM, BN>;
     static bool attr_set = false;   // once per process (one device)
     if (!attr_set) {
-        RN_CHECK_CUDA(cudaFuncSetAttribute(gett_direct_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)DirectCfg<T>::smem));
+        RN_CHECK_CUDA(cudaFuncSetAttribute(gett_direct_kernel<T, BM, BN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
         attr_set = true;
     }
-    launch_pdl(gett_direct_kernel<T>, grid, 256, DirectCfg<T>::smem, s, ga);
+    launch_pdl(gett_direct_kernel<T, BM, BN>, grid, 256, Cfg::smem, s, ga);
 }
 
 template <typename T, int BM, int BN, int BK>
@@ -1037,7 +1062,8 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 256, 0, s, ga); break;
             case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
             case kKindTiled256x16: launch_tiled<float, 256, 16, 16>(grid, ga, s); break;
-            case kKindDirect: launch_direct<float>(grid, ga, s); break;
+            case kKindDirect: launch_direct<float, 64, 64>(grid, ga, s); break;
+            case kKindDirect256x16: launch_direct<float, 256, 16>(grid, ga, s); break;
             case kKindTiled128x32: launch_tiled<float, 128, 32, 16>(grid, ga, s); break;
             default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
         }
@@ -1048,7 +1074,7 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             case kKindReduce: launch_pdl(gett_reduce_kernel<double>, grid, 256, 0, s, ga); break;
             case kKindZero: launch_pdl(gett_zero_kernel<double>, grid, 256, 0, s, ga); break;
             case kKindDot: launch_pdl(gett_dot_kernel<double>, grid, 256, 0, s, ga); break;
-            case kKindDirect: launch_direct<double>(grid, ga, s); break;
+            case kKindDirect: launch_direct<double, 64, 64>(grid, ga, s); break;
             default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
         }
     }
@@ -1101,6 +1127,15 @@ void apply_split(GettDesc &d, int BK, int64_t ks) {
     d.ktiles_per_split = ks > 1 ? (int)((nkt + ks - 1) / ks) : 0x7fffffff;
     d.ksplit = ks > 1 ? (int)((nkt + d.ktiles_per_split - 1) / d.ktiles_per_split) : 1;
 }
+// Direct kinds split K into kDirectK-long slices, one per CTA (ktiles_per_split
+// counts slices); false when the partial sums would exceed 2^24 entries.
+bool direct_split(GettDesc &d) {
+    const int64_t ks = (d.K + kDirectK - 1) / kDirectK;
+    if (ks > 1 && (double)ks * (double)d.M * (double)d.N > (double)(1 << 24)) return false;
+    d.ksplit = (int)std::max<int64_t>(ks, 1);
+    d.ktiles_per_split = ks > 1 ? 1 : 0x7fffffff;
+    return true;
+}
 }  // namespace
 
 int64_t reduce_ctas(const GettDesc &d);
@@ -1112,7 +1147,7 @@ int64_t reduce_ctas(const GettDesc &d);
 // reduction mode is forced -- the packed path.  Results are cached by
 // (dtype, M, N, K, layout flags).
 void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
-    if (!is_tiled_kind(d.kind) && d.kind != kKindPackF32 && d.kind != kKindDirect) return;
+    if (!is_tiled_kind(d.kind) && d.kind != kKindPackF32 && !is_direct_kind(d.kind)) return;
     if (d.flags & kFlagAtomic) return;
     packed_ok = packed_ok && dtype == ROSNET_C64;
     const TuneKey key{dtype, d.flags | (packed_ok ? 1 << 30 : 0), d.M, d.N, d.K};
@@ -1132,8 +1167,8 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
     const int BK = dtype == ROSNET_C64 ? 16 : 8;
     std::vector<GettDesc> cands;
     // the split the heuristic would pick for a 64x64 tiling
-    int64_t auto_split = (d.kind == kKindPackF32 || d.kind == kKindDirect) ? 1 : d.ksplit;
-    if (d.kind == kKindPackF32 || d.kind == kKindDirect) {
+    int64_t auto_split = (d.kind == kKindPackF32 || is_direct_kind(d.kind)) ? 1 : d.ksplit;
+    if (d.kind == kKindPackF32 || is_direct_kind(d.kind)) {
         const int64_t tiles = ((d.M + 63) / 64) * ((d.N + 63) / 64), nkt = (d.K + BK - 1) / BK;
         if (tiles < kSMs && nkt >= 32) auto_split = std::min<int64_t>((2 * kSMs + tiles - 1) / tiles, nkt / 8);
     }
@@ -1154,13 +1189,15 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
             if (!dup) cands.push_back(y);
         }
     }
-    if (d.K <= kDirectK) {
+    for (int kind : {(int)kKindDirect, (int)kKindDirect256x16}) {
+        if (!direct_kind_ok(kind, dtype, d.M, d.N)) continue;
         GettDesc y = d;
-        y.kind = kKindDirect;
-        y.tiles_m = (d.M + 63) / 64;
-        y.tiles_n = (d.N + 63) / 64;
-        apply_split(y, BK, 1);
-        cands.push_back(y);
+        int bm, bn;
+        direct_tile(kind, &bm, &bn);
+        y.kind = kind;
+        y.tiles_m = (d.M + bm - 1) / bm;
+        y.tiles_n = (d.N + bn - 1) / bn;
+        if (direct_split(y)) cands.push_back(y);
     }
     if (packed_ok) {
         GettDesc y = d;
@@ -1221,7 +1258,7 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
 // False if the choice is not one the autotuner can make for that shape.
 static bool tune_geometry(int dtype, int kind, int64_t M, int64_t N, int64_t K, int64_t ksplit,
                           TuneChoice *out) {
-    if (M < 1 || N < 1 || K < 1 || ksplit < 1 || ksplit > 64) return false;
+    if (M < 1 || N < 1 || K < 1 || ksplit < 1 || ksplit > (1 << 20)) return false;
     const int BK = dtype == ROSNET_C64 ? 16 : 8;
     GettDesc y;
     memset(&y, 0, sizeof(y));
@@ -1233,9 +1270,14 @@ static bool tune_geometry(int dtype, int kind, int64_t M, int64_t N, int64_t K, 
         tiled_tile(kind, &BM, &BN);
         y.tiles_m = (M + BM - 1) / BM;
         y.tiles_n = (N + BN - 1) / BN;
-    } else if (kind == kKindDirect && K <= kDirectK && ksplit == 1) {
-        y.tiles_m = (M + 63) / 64;
-        y.tiles_n = (N + 63) / 64;
+    } else if (is_direct_kind(kind) && direct_kind_ok(kind, dtype, M, N)) {
+        int bm, bn;
+        direct_tile(kind, &bm, &bn);
+        y.tiles_m = (M + bm - 1) / bm;
+        y.tiles_n = (N + bn - 1) / bn;
+        if (!direct_split(y) || y.ksplit != ksplit) return false;
+        *out = TuneChoice{kind, y.tiles_m, y.tiles_n, y.ksplit, y.ktiles_per_split, 0};
+        return true;
     } else if (kind == kKindPackF32 && dtype == ROSNET_C64 && ksplit == 1) {
         y.tiles_m = (M + f32p_tile_m() - 1) / f32p_tile_m();
         y.tiles_n = (N + f32p_tile_n() - 1) / f32p_tile_n();

@@ -201,10 +201,22 @@ enum KernelKind : int32_t {
     kKindPackF32 = 10,   // plain FP32 on CUDA cores from packed operands (TMA-fed 64x64 tiles)
     kKindTiled256x16 = 11,  // 256x16 tiles (complex64 only): problems with few columns
     kKindTiled128x32 = 12,  // 128x32 tiles (complex64 only)
-    kKindDirect = 13,       // 64x64 tiles, whole K (<= kDirectK) gathered in one pass
+    kKindDirect = 13,       // 64x64 tiles, each CTA's K range (<= kDirectK) gathered in one pass
+    kKindDirect256x16 = 14, // 256x16 tiles of the same kernel (complex64 only)
 };
 
-constexpr int kDirectK = 32;   // longest contraction of the direct kernel
+constexpr int kDirectK = 32;   // longest contraction range of one direct-kernel CTA
+
+inline bool is_direct_kind(int kind) { return kind == kKindDirect || kind == kKindDirect256x16; }
+// CTA tile of a direct kind, and whether it applies to a problem
+inline void direct_tile(int kind, int *bm, int *bn) {
+    if (kind == kKindDirect256x16) { *bm = 256; *bn = 16; }
+    else { *bm = 64; *bn = 64; }
+}
+inline bool direct_kind_ok(int kind, int dtype, int64_t M, int64_t N) {
+    if (kind == kKindDirect) return true;
+    return kind == kKindDirect256x16 && dtype == ROSNET_C64 && M >= 128;
+}
 
 // Register-tiled CUDA-core kinds (gett_tiled_kernel), their CTA tile, and
 // whether one applies to a problem of dtype and (M, N).

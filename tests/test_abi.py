@@ -212,7 +212,8 @@ def test_tune_table_roundtrip_and_validation():
     """Autotuner decisions move between processes as text; every imported
     entry is checked against its shape (no device needed)."""
     good = ("1 9 4096 256 256 10 1\n1 11 2048 512 32 3 1\n2 0 300 200 5000 2 16\n"
-            "1 1 300 13 4000 11 8\n1 1 200 30 300 12 1\n1 3 2048 512 32 13 1\n2 3 300 40 20 13 1\n")
+            "1 1 300 13 4000 11 8\n1 1 200 30 300 12 1\n1 3 2048 512 32 13 1\n2 3 300 40 20 13 1\n"
+            "1 9 256 16 4096 14 128\n1 9 300 200 100 13 4\n")
     R.tune_import(good)
     lines = set(R.tune_export().splitlines())
     assert set(good.splitlines()) <= lines
@@ -228,8 +229,10 @@ def test_tune_table_roundtrip_and_validation():
            "1 0 64 64 64 2 1 9",         # extra field
            "2 0 300 13 200 11 1",        # 256x16 tiles are complex64 only
            "1 0 100 13 200 11 1",        # 256x16 tiles need M >= 128
-           "1 0 300 300 33 13 1",        # direct tiles hold K <= 32
-           "1 0 300 300 32 13 2"]        # and never split
+           "1 0 300 300 33 13 1",        # direct tiles hold 32 contracted indices per CTA
+           "1 0 300 300 32 13 2",        # so K = 32 is one range
+           "1 0 300 13 4096 14 64",      # and K = 4096 is 128, not 64
+           "2 0 300 13 4096 14 128"]     # 256x16 direct tiles are complex64 only
     before = R.tune_export()
     for b in bad:
         with pytest.raises(R.RosnetError) as e:

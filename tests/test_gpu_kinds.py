@@ -1,0 +1,72 @@
+"""Every CUDA-core GEMM family on the same problems, forced through the
+autotuner's table (rosnet_tune_import), against the complex128 oracle.
+
+For each problem the contraction is planned once with ROSNET_OPT_AUTOTUNE to
+learn its table key (dtype, layout flags, M, N, K); the entry is then
+replaced by a chosen kernel family and split, the plan cache is dropped, and
+the contraction is planned and run again.  The timing record of the heaviest
+launch confirms which family ran.  Bar: relative Frobenius error <= 1e-5
+(complex64) / 1e-12 (complex128).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2201_06620_b300 as R
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NPT = {R.C64: np.complex64, R.C128: np.complex128}
+TOL = {R.C64: 1e-5, R.C128: 1e-12}
+
+# kernel family -> splits to try
+FAMILIES = {2: [1, 4], 3: [1], 11: [1, 8], 12: [1], 13: [None], 14: [None], 10: [1]}
+
+
+def _run(A, B, flags):
+    return R.contract([A, B], [(0, 1), (1, 2)], [0, 2], [(0, 1)], flags=flags)
+
+
+def _key(M, N, K):
+    for line in R.tune_export().splitlines():
+        f = line.split()
+        if (int(f[2]), int(f[3]), int(f[4])) in ((M, N, K), (N, M, K)):
+            return f
+    return None
+
+
+@pytest.mark.parametrize("dtype", [R.C64, R.C128])
+@pytest.mark.parametrize("mnk", [(300, 16, 4000), (1000, 700, 200), (130, 200, 17), (520, 96, 100)])
+def test_every_family_matches_oracle(dtype, mnk):
+    M, N, K = mnk
+    a = W.complex_normal((M, K), 71).astype(NPT[dtype])
+    b = W.complex_normal((K, N), 72).astype(NPT[dtype])
+    A, B = R.btensor(a, None, dtype), R.btensor(b, None, dtype)
+    ref = oracle.tensordot(a, b, [1], [0])
+    R.release_plans()
+    _run(A, B, R.OPT_AUTOTUNE).download()
+    key = _key(M, N, K)
+    assert key is not None, "the autotuner recorded no entry for this problem"
+    tried = 0
+    for kind, splits in FAMILIES.items():
+        for ks in splits:
+            if ks is None:   # direct kinds: one 32-long contracted range per CTA
+                ks = max(1, -(-K // 32))
+            line = " ".join(key[:5] + [str(kind), str(ks)])
+            try:
+                R.tune_import(line + "\n")
+            except R.RosnetError as e:   # not a choice this shape (or dtype) can have
+                assert e.name == "INVALID_ARG"
+                continue
+            R.release_plans()
+            R.timing_drain()
+            got = _run(A, B, R.OPT_AUTOTUNE | R.OPT_TIMING).download()
+            recs = R.timing_drain()
+            assert recs and recs[-1][3] == kind, (kind, ks, recs[-1:])
+            err = oracle.rel_frobenius(got, ref)
+            assert err <= TOL[dtype], (kind, ks, err)
+            tried += 1
+    assert tried >= (2 if dtype == R.C128 else 5)
+    R.tune_import(" ".join(key) + "\n")   # the autotuner's own choice back for later tests
+    R.release_plans()
