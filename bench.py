@@ -53,6 +53,20 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def _whole_job(local_ms, steps, world, device=None):
+    """Replicas: every rank timed `steps` amplitudes of its own bitstrings in
+    local_ms; the job's time is the slowest rank's, its throughput all ranks'
+    amplitudes over that time.  Returns (max_ms, amplitudes/s)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms / 1e3)
+
+
 def _bitstrings(seed, count):
     rng = np.random.default_rng(seed)
     return [rng.integers(0, 2, N_QUBITS) for _ in range(count)]
@@ -203,12 +217,7 @@ def run_rosnet(args):
     step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.warmup, steps)]
     heavy = R.timing_drain()
     amps = [complex(o.download()) for o in outs[args.warmup:]]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms, value = _whole_job(sum(step_ms), args.steps, world, dev)
 
     # roofline of the heaviest launch (FP32 FFMA, plain ALU bound)
     peaks = _measured_peaks()
