@@ -124,6 +124,14 @@ struct Plan {
     int tpos = 0;
     int64_t steps_requested = 0;               // path steps before common steps were merged
     ~Plan() {
+        // device buffers go first, while every stream they were allocated or
+        // last used on still exists (the side stream is destroyed below)
+        if (side) cudaStreamSynchronize(side);
+        arena.reset();
+        tables.reset();
+        descs.reset();
+        partials.reset();
+        tcws.reset();
         for (int i = 0; i < kRing; ++i) {
             if (ev[i]) { cudaEventSynchronize(ev[i]); cudaEventDestroy(ev[i]); }
             if (pinned[i]) cudaFreeHost(pinned[i]);

@@ -28,10 +28,10 @@ def _run(A, B, flags):
     return R.contract([A, B], [(0, 1), (1, 2)], [0, 2], [(0, 1)], flags=flags)
 
 
-def _key(M, N, K):
+def _key(dtype, M, N, K):
     for line in R.tune_export().splitlines():
         f = line.split()
-        if (int(f[2]), int(f[3]), int(f[4])) in ((M, N, K), (N, M, K)):
+        if int(f[0]) == dtype and (int(f[2]), int(f[3]), int(f[4])) in ((M, N, K), (N, M, K)):
             return f
     return None
 
@@ -46,7 +46,7 @@ def test_every_family_matches_oracle(dtype, mnk):
     ref = oracle.tensordot(a, b, [1], [0])
     R.release_plans()
     _run(A, B, R.OPT_AUTOTUNE).download()
-    key = _key(M, N, K)
+    key = _key(dtype, M, N, K)
     assert key is not None, "the autotuner recorded no entry for this problem"
     tried = 0
     for kind, splits in FAMILIES.items():
