@@ -225,6 +225,19 @@ rosnet_status rosnet_btensor_download(rosnet_btensor t, void *host, void *stream
  * point; with page-locked host memory the copy overlaps other work. */
 rosnet_status rosnet_btensor_download_async(rosnet_btensor t, void *host, void *stream);
 
+/*
+ * Copy the raw storage of a tensor that owns it -- 2 * numel elements of its
+ * dtype's real type: the real plane, then the imaginary plane, each in the
+ * tensor's block-major element order (plain row-major for a one-block
+ * tensor) -- from / to host memory, enqueued on `stream` without waiting, one
+ * copy and no kernel.  The host buffer must stay valid until the stream
+ * reaches this point; page-locked memory lets the copy overlap other work.
+ * INVALID_ARG for NULL arguments, UNSUPPORTED for views (slice / fix /
+ * block), whose storage belongs to another tensor.
+ */
+rosnet_status rosnet_btensor_upload_raw(rosnet_btensor t, const void *host, void *stream);
+rosnet_status rosnet_btensor_download_raw(rosnet_btensor t, void *host, void *stream);
+
 /* Shape, block shape (arrays of at least `rank` entries; either may be NULL)
  * and dtype (may be NULL) of a tensor.  *rank is always written. */
 rosnet_status rosnet_btensor_info(rosnet_btensor t, int *rank, int64_t *shape,

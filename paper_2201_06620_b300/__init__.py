@@ -61,7 +61,8 @@ EXPORTS = [
     "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_contract_batch", "rosnet_plan_stats",
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
-    "rosnet_btensor_download_async", "rosnet_alloc_stats",
+    "rosnet_btensor_download_async", "rosnet_alloc_stats", "rosnet_btensor_upload_raw",
+    "rosnet_btensor_download_raw",
 ]
 
 _lock = threading.Lock()
@@ -168,6 +169,8 @@ def lib():
             L.rosnet_tune_import.argtypes = [ctypes.c_char_p]
             L.rosnet_btensor_download_async.argtypes = [vp, vp, vp]
             L.rosnet_alloc_stats.argtypes = [i64p, i64p]
+            L.rosnet_btensor_upload_raw.argtypes = [vp, vp, vp]
+            L.rosnet_btensor_download_raw.argtypes = [vp, vp, vp]
             for name in EXPORTS:
                 f = getattr(L, name)
                 if f.restype is ctypes.c_int or name in (
@@ -181,7 +184,8 @@ def lib():
                         "rosnet_contract_batch", "rosnet_plan_stats", "rosnet_btensor_fix",
                         "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
                         "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
-                        "rosnet_btensor_download_async", "rosnet_alloc_stats"):
+                        "rosnet_btensor_download_async", "rosnet_alloc_stats",
+                        "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -380,6 +384,27 @@ class BTensor:
         _check(lib().rosnet_btensor_download_async(self._h, ctypes.c_void_p(ptr), _stream(stream)),
                "download_async")
         return out
+
+    def _raw_ptr(self, buf):
+        nbytes = buf.numel() * buf.element_size() if hasattr(buf, "data_ptr") else buf.nbytes
+        if nbytes != 2 * self.numel * (4 if self.dtype == C64 else 8):
+            raise ValueError("raw buffer must hold 2 * numel real values (real plane, imaginary plane)")
+        return buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+
+    def upload_raw(self, buf, stream=None):
+        """Copy the real plane then the imaginary plane (block-major order) from
+        ``buf`` (page-locked torch tensor or numpy array of 2 * numel reals)
+        into the tensor's storage: one enqueued copy, no kernel."""
+        _check(lib().rosnet_btensor_upload_raw(self._h, ctypes.c_void_p(self._raw_ptr(buf)), _stream(stream)),
+               "upload_raw")
+        return buf
+
+    def download_raw(self, buf, stream=None):
+        """Enqueue a copy of the tensor's storage (real plane, imaginary plane)
+        into ``buf`` without waiting."""
+        _check(lib().rosnet_btensor_download_raw(self._h, ctypes.c_void_p(self._raw_ptr(buf)), _stream(stream)),
+               "download_raw")
+        return buf
 
     def destroy(self):
         if _shutting_down:   # the allocator behind the handle may be gone

@@ -601,6 +601,33 @@ rosnet_status rosnet_btensor_download_async(rosnet_btensor t, void *host, void *
     RN_API_END
 }
 
+static void check_raw(rosnet_btensor t) {
+    if (!t->owned || t->pstride != t->lay.numel)
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "raw copies need a tensor that owns its storage (not a view)");
+}
+
+rosnet_status rosnet_btensor_upload_raw(rosnet_btensor t, const void *host, void *stream) {
+    if (!t || (!host && t->lay.numel > 0)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    check_raw(t);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = 2 * (size_t)t->lay.numel * t->elsize;
+    if (bytes) RN_CHECK_CUDA(cudaMemcpyAsync(t->data, host, bytes, cudaMemcpyHostToDevice, s));
+    t->stream = s;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_btensor_download_raw(rosnet_btensor t, void *host, void *stream) {
+    if (!t || (!host && t->lay.numel > 0)) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    check_raw(t);
+    const size_t bytes = 2 * (size_t)t->lay.numel * t->elsize;
+    if (bytes) RN_CHECK_CUDA(cudaMemcpyAsync(host, t->data, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    return ROSNET_OK;
+    RN_API_END
+}
+
 rosnet_status rosnet_btensor_info(rosnet_btensor t, int *rank, int64_t *shape, int64_t *block_shape,
                                   rosnet_dtype *dtype) {
     if (!t || !rank) return ROSNET_ERR_INVALID_ARG;

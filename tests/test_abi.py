@@ -69,6 +69,8 @@ def test_null_arguments_rejected():
     assert L.rosnet_tensordot(None, None, 0, None, None, None, None, ctypes.byref(out)) == -1
     assert out.value is None
     assert L.rosnet_btensor_destroy(None) == 0
+    assert L.rosnet_btensor_upload_raw(None, None, None) == -1
+    assert L.rosnet_btensor_download_raw(None, None, None) == -1
     assert L.rosnet_contract(None, None, None, None, ctypes.byref(out)) == -1
     rk = ctypes.c_int()
     assert L.rosnet_btensor_info(None, ctypes.byref(rk), None, None, None) == -1

@@ -202,6 +202,37 @@ def test_upload_download_roundtrip_blocked():
             assert np.array_equal(t.download(), x)
 
 
+def test_raw_storage_copies():
+    """upload_raw / download_raw move the planar storage (real plane, then
+    imaginary plane, block-major order) with one copy; they agree with the
+    regular (interleaved, any layout) copies and refuse views."""
+    import torch
+    for dtype in (R.C64, R.C128):
+        real = np.float32 if dtype == R.C64 else np.float64
+        x = W.complex_normal((6, 4), 81).astype(NPT[dtype])
+        t = R.btensor(x, None, dtype)                   # one block: row-major storage
+        raw = np.zeros(2 * x.size, dtype=real)
+        t.download_raw(raw)
+        R.sync()
+        assert np.array_equal(raw[:x.size], x.real.ravel()) and np.array_equal(raw[x.size:], x.imag.ravel())
+        y = W.complex_normal((6, 4), 82).astype(NPT[dtype])
+        host = torch.from_numpy(np.concatenate([y.real.ravel(), y.imag.ravel()]).astype(real)).pin_memory()
+        t.upload_raw(host)
+        assert np.array_equal(t.download(), y)
+        # the result of a tensordot, read raw, equals its regular download
+        c = R.tensordot(t, R.btensor(x.T.copy(), None, dtype), [1], [0])
+        out = np.zeros(2 * c.numel, dtype=real)
+        c.download_raw(out)
+        R.sync()
+        ref = c.download()
+        assert np.array_equal(out[:c.numel] + 1j * out[c.numel:].astype(np.complex128), ref.ravel())
+        with pytest.raises(R.RosnetError) as e:
+            t.fix([0], [1]).download_raw(np.zeros(8, dtype=real))
+        assert e.value.name == "UNSUPPORTED"
+        with pytest.raises(ValueError):
+            t.upload_raw(np.zeros(3, dtype=real))
+
+
 def test_error_codes():
     a = R.btensor(W.complex_normal((4, 4), 1), (2, 2), R.C128)
     b = R.btensor(W.complex_normal((4, 4), 2), (4, 2), R.C128)
