@@ -444,8 +444,8 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// BM x BN output tile per CTA, 256 threads (16 x 16) each owning TM x TN
-// complex outputs.  A and B tiles of BK contracted indices are gathered
+// BM x BN output tile per CTA, 256 threads (BM / TM rows x BN / 4 columns of
+// threads) each owning TM x 4 complex outputs.  A and B tiles of BK contracted indices are gathered
 // element by element through the offset tables (consecutive threads take
 // consecutive values of A's / B's unit-stride digit, so the gathers
 // coalesce) with cp.async into a STAGES-deep shared-memory ring of planar

@@ -634,32 +634,11 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
             yi[4 * v] = q.x; yi[4 * v + 1] = q.y; yi[4 * v + 2] = q.z; yi[4 * v + 3] = q.w;
         }
     };
-#ifndef ROSNET_F32P_ORDER
-#define ROSNET_F32P_ORDER 0
-#endif
     auto macs = [&](const float *xr, const float *xi, const float *yr, const float *yi) {
-        if (ROSNET_F32P_ORDER == 0) {
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) cmac4(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
-        } else {
-            // two outer products: Re(x) (x) (Re y, Im y), then Im(x) (x) (-Im y, Re y)
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    cr[i][j] = fmaf(xr[i], yr[j], cr[i][j]);
-                    ci[i][j] = fmaf(xr[i], yi[j], ci[i][j]);
-                }
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    cr[i][j] = fmaf(-xi[i], yi[j], cr[i][j]);
-                    ci[i][j] = fmaf(xi[i], yr[j], ci[i][j]);
-                }
-        }
+            for (int j = 0; j < TN; ++j) cmac4(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
     };
 
     int done0 = 0;   // tiles whose full barrier thread 0 has passed
