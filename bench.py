@@ -550,6 +550,53 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reduction(args):
+    """The paper's reduction comparison (Sec. IV-A, its node experiment: an
+    8 x 6 grid of output blocks, B_k contracted block pairs per output block),
+    scaled to blocks of m_b = n_b = 2^10, k_b = 2^9 so that a sweep of
+    B_k = 2..32 takes seconds.  Per B_k and reduction mode: device time of the
+    whole contraction (split reductions included), algorithmic TFLOP/s and the
+    kernel family that ran (the sequential mode may take the packed path,
+    which never splits; tree and commutative split K across CTAs)."""
+    import torch
+    import paper_2201_06620_b300 as R
+    m_b, n_b, k_b, gm, gn = 1 << 10, 1 << 10, 1 << 9, 8, 6
+    piece = 1 << 24
+    modes = (("auto", 0), ("sequential", R.REDUCE_SEQUENTIAL), ("tree", R.REDUCE_TREE),
+             ("commutative", R.REDUCE_COMMUTATIVE))
+    rows = []
+    for bk in (2, 4, 8, 16, 32):
+        M, N, K = gm * m_b, gn * n_b, bk * k_b
+        A = R.empty((M, K), (m_b, k_b), R.C64)
+        B = R.empty((K, N), (k_b, n_b), R.C64)
+        for t, seed in ((A, 11), (B, 12)):
+            for st in range(0, t.numel, piece):
+                t.upload_range(W.complex_normal_range(seed, st, min(piece, t.numel - st), 1.0), st)
+        R.sync()
+        for name, flag in modes:
+            fl = R.OPT_GRAPH | R.OPT_TIMING | flag
+            run = lambda: R.contract([A, B], [(0, 1), (1, 2)], [0, 2], [(0, 1)], flags=fl)
+            run()
+            torch.cuda.synchronize()
+            R.timing_drain()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                C = run()
+                del C
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            kinds = {k for *_, k in R.timing_drain()}
+            rows.append({"B_k": bk, "mode": name, "ms": ms, "tflops": 8.0 * M * N * K / (ms * 1e-3) / 1e12,
+                         "kernel": "/".join(KERNEL_NAMES.get(k, f"kind {k}").split(" (")[0] for k in sorted(kinds))})
+            R.release_plans()
+        del A, B
+    print(json.dumps({"metric": "tensordot TFLOP/s by reduction mode", "unit": "TFLOP/s",
+                      "workload": "8 x 6 grid of 2^10 x 2^10 output blocks, k_b = 2^9, B_k = 2..32, complex64",
+                      "rows": rows}), flush=True)
+
+
 def run_sweep(args):
     """Precision sweep: [2]^30 x [2]^30 -> [2]^40 in 2^30-entry chunks."""
     import torch
@@ -606,7 +653,7 @@ def main():
     ap.add_argument("--tune-file", default=None,
                     help="load autotuner decisions from this file if it exists; save them after planning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["rqc20", "serve", "batch", "sweep"], default="rqc20")
+    ap.add_argument("--workload", choices=["rqc20", "serve", "batch", "sweep", "reduction"], default="rqc20")
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=20.0)
@@ -627,6 +674,8 @@ def main():
         run_batch(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "reduction":
+        run_reduction(args)
     else:
         run_rosnet(args)
 
