@@ -236,6 +236,9 @@ def run_rosnet(args):
                 "flops_per_launch": hflops, "bytes_per_launch": hbytes,
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)"}
 
+    others = None
+    if not args.no_precision_modes:
+        others = run_precision_modes(args, R, torch, net, path, bind, amps, flush, stream, flags)
     e2e = run_e2e(args, R, torch, circ, net, path, ngates, stream) if not args.no_e2e else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -259,10 +262,46 @@ def run_rosnet(args):
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "other_precisions": others,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_precision_modes(args, R, torch, net, path, bind, amps_fp32, flush, stream, flags):
+    """The same amplitudes with the tensor-core precision modes (complex
+    products as 3xTF32 / 3xBF16 split products or plain TF32 on tcgen05, FP32
+    accumulation), timed like the main loop (L2 flushed before each step) on
+    up to 400 of its bitstrings, each with its largest amplitude error against
+    the plain FP32 result, |a - a_fp32| / max(|a_fp32|, 2^-10).  Not the
+    headline: the workload specifies plain FP32."""
+    out = {}
+    n = min(args.steps, 400)
+    fl = flags & ~R.OPT_TIMING
+    for name, prec in (("tf32x3", R.PREC_TF32X3), ("bf16x3", R.PREC_BF16X3), ("tf32", R.PREC_TF32)):
+        try:
+            for i in range(3):
+                bind(i)
+                R.contract(net, path=path, precision=prec, flags=fl, max_block_entries=MAX_BLOCK)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+            res = []
+            for i in range(n):
+                flush.fill_(i & 0xff)
+                bind(args.warmup + i)
+                ev[i][0].record(stream)
+                res.append(R.contract(net, path=path, precision=prec, flags=fl, max_block_entries=MAX_BLOCK))
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev)
+            err = max(abs(complex(r.download()) - a) / max(abs(a), 2.0 ** -10)
+                      for r, a in zip(res, amps_fp32[:n]))
+            out[name] = {"value": n / (ms / 1e3), "unit": "amplitudes/s", "steps": n,
+                         "max_rel_err_vs_fp32": err, "within_1e-5": bool(err <= 1e-5)}
+        except Exception as e:   # a mode that fails is reported, not fatal to the line
+            out[name] = {"error": str(e)[:200]}
+    return out
 
 
 def run_e2e(args, R, torch, circ, net, path, ngates, stream):
@@ -650,6 +689,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-precision-modes", action="store_true",
+                    help="skip timing the tensor-core precision modes on the default workload")
     ap.add_argument("--tune-file", default=None,
                     help="load autotuner decisions from this file if it exists; save them after planning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
