@@ -158,7 +158,7 @@ rosnet_status rosnet_alloc_stats(int64_t *requests, int64_t *live);
  * axis i is shape[i] / block_shape[i].  Device memory (numel * element size)
  * comes from the allocator in stream order on `stream`.
  * Errors: INVALID_ARG (out == NULL, shape == NULL with rank > 0, extent < 0),
- * RANK_LIMIT, BLOCK_MISMATCH, DTYPE, ALLOC.
+ * SHAPE (more than 2^58 elements), RANK_LIMIT, BLOCK_MISMATCH, DTYPE, ALLOC.
  */
 rosnet_status rosnet_btensor_create(int rank, const int64_t *shape, const int64_t *block_shape,
                                     rosnet_dtype dtype, void *stream, rosnet_btensor *out);

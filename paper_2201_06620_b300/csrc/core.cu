@@ -106,8 +106,8 @@ void Layout::init(int r, const int64_t *sh, const int64_t *bl) {
                                                    std::to_string(i));
         shape[i] = sh[i];
         block[i] = b;
-        if (sh[i] > 0 && numel > (int64_t(1) << 62) / sh[i])
-            RN_FAIL(ROSNET_ERR_SHAPE, "tensor too large");
+        if (sh[i] > 0 && numel > kMaxNumel / sh[i])
+            RN_FAIL(ROSNET_ERR_SHAPE, "tensor too large (more than 2^58 elements)");
         numel *= sh[i];
     }
     int64_t bs = 1;

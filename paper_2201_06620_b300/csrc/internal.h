@@ -85,6 +85,9 @@ struct DevBuf {
 // block tensors
 // ---------------------------------------------------------------------------
 constexpr int kMaxRank = ROSNET_MAX_RANK;
+// Largest element count of a tensor: its two planes of 8-byte values,
+// 2^62 bytes, and every byte offset into them stay within int64_t.
+constexpr int64_t kMaxNumel = int64_t(1) << 58;
 
 struct Layout {
     int rank = 0;

@@ -59,6 +59,14 @@ def test_create_validates_before_allocating():
     assert _create(1, [4], [0])[0] == -3                     # block extent < 1
     assert _create(1, [-1], [1])[0] == -1                    # negative extent
     assert _create(1, [4], [4], dtype=7)[0] == -4            # unknown dtype
+    # 2^60 complex128 entries would need 2^65 bytes: refused before any
+    # allocation (the byte count must not wrap around)
+    assert _create(2, [1 << 30, 1 << 30], [1, 1 << 30], dtype=R.C128)[0] == -2   # SHAPE
+    assert _create(3, [1 << 20, 1 << 20, 1 << 19], None)[0] == -2
+    rc, h = _create(2, [0, 1 << 62], None)                  # empty: nothing to size
+    assert rc != -2
+    if rc == 0:
+        L.rosnet_btensor_destroy(h)
     sh = (ctypes.c_int64 * 1)(4)
     assert L.rosnet_btensor_create(1, sh, None, 1, None, None) == -1  # NULL out
 
