@@ -387,7 +387,9 @@ rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks,
  * gives the smallest (largest intermediate, total flops over all slices) for
  * the given path.  chosen[0..nslice) receives the labels; *max_entries the
  * largest intermediate of one slice, *flops the total over all slices (either
- * may be NULL).  Host-only.
+ * may be NULL).  Host-only.  INVALID_ARG if the path is not a valid SSA path
+ * of ntensors - 1 steps (an id out of range, reused, or paired with itself)
+ * or nslice exceeds the number of bonds.
  */
 rosnet_status rosnet_slice_search(int32_t ntensors, const int32_t *ranks,
                                   const int64_t *const *labels, const int64_t *const *extents,

@@ -791,7 +791,13 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
     } else {
         enqueue(false);
     }
-    if (timing) g_timing_log.push_back({&P, slot});
+    if (timing) {
+        g_timing_log.push_back({&P, slot});
+        // a drain reports only the newest kTimingRing entries: keep the log
+        // bounded for callers that time without draining
+        if (g_timing_log.size() > 2 * (size_t)Plan::kTimingRing)
+            g_timing_log.erase(g_timing_log.begin(), g_timing_log.end() - Plan::kTimingRing);
+    }
     // results that are not written in place: permuted, shared, or a lone leaf
     for (int i = 0; i < P.nnet; ++i) {
         const NetOut &O = P.outs[i];
@@ -1067,6 +1073,19 @@ LabelNet label_net(int32_t ntensors, const int32_t *ranks, const int64_t *const 
     return n;
 }
 
+// A path in SSA form (step t joins two live ids and creates id nt + t): every
+// id in range, the two ids of a step distinct, and each id used once.
+void check_ssa_path(int nt, const int32_t *pairs, int nsteps) {
+    if (nsteps != nt - 1 || (nsteps > 0 && !pairs)) RN_FAIL(ROSNET_ERR_INVALID_ARG, "a path must have ntensors - 1 steps");
+    std::vector<char> used(nt + nsteps, 0);
+    for (int st = 0; st < nsteps; ++st) {
+        const int32_t a = pairs[2 * st], b = pairs[2 * st + 1];
+        if (a < 0 || b < 0 || a >= nt + st || b >= nt + st || a == b || used[a] || used[b])
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "path step " + std::to_string(st) + " uses a dead or unknown id");
+        used[a] = used[b] = 1;
+    }
+}
+
 // Max intermediate entries and total 8*M*N*K flops of a path, with the
 // labels in `cut` fixed (sliced: extent 1).
 std::pair<double, double> path_cost(const LabelNet &n, const int32_t *pairs, int nsteps,
@@ -1181,6 +1200,7 @@ rosnet_status rosnet_slice_search(int32_t ntensors, const int32_t *ranks, const 
         return ROSNET_ERR_INVALID_ARG;
     RN_API_BEGIN
     LabelNet n = label_net(ntensors, ranks, labels, extents);
+    check_ssa_path(ntensors, pairs, nsteps);
     std::unordered_map<int64_t, int> cnt;
     for (auto &l : n.lab) for (int64_t x : l) cnt[x]++;
     std::vector<int64_t> bonds;

@@ -218,6 +218,26 @@ def test_slice_search_shrinks_the_largest_intermediate():
     assert abs(flops - 16 * t1) <= 1e-9 * flops             # 2^4 slices
 
 
+
+def test_slice_search_rejects_malformed_paths():
+    circ = W.random_circuit(6, 4, 2)
+    net = W.circuit_network(circ)
+    ext = [t.shape for t in net.tensors]
+    path = R.path_greedy_extents(net.labels, ext, net.out_labels)
+    nt = len(net.labels)
+    R.slice_search(net.labels, ext, net.out_labels, path, 1)          # the valid path is accepted
+    bad = [
+        path[:-1],                                                      # a step short
+        [(0, nt + 5)] + path[1:],                                       # an id not yet created
+        [(0, 0)] + path[1:],                                            # an id paired with itself
+        [path[0], (path[0][0], path[1][1])] + path[2:],                 # an id used twice
+        [(-1, path[0][1])] + path[1:],                                  # negative id
+    ]
+    for p in bad:
+        with pytest.raises(R.RosnetError) as e:
+            R.slice_search(net.labels, ext, net.out_labels, p, 1)
+        assert e.value.name == "INVALID_ARG", p
+
 def test_tune_table_roundtrip_and_validation():
     """Autotuner decisions move between processes as text; every imported
     entry is checked against its shape (no device needed)."""
