@@ -452,6 +452,19 @@ rosnet_status rosnet_tune_import(const char *text);
 rosnet_status rosnet_release_plans(void);
 
 /*
+ * Keep at most max_plans cached contraction plans (0: no limit, the
+ * default; a negative value leaves the limit as it is, to query).  When a new
+ * plan would exceed the limit, the least recently used plans are freed
+ * first; lowering the limit frees the excess at once.  Work that a freed plan
+ * already enqueued completes normally (its device buffers are released in
+ * stream order, a graph still running is freed when it completes); its
+ * undrained timing records are dropped.  A later call with a freed plan's
+ * structure plans it again.  *cached (may be NULL) receives the number of
+ * cached plans after the call.  Host-side; never fails on valid input.
+ */
+rosnet_status rosnet_plan_cache_limit(int32_t max_plans, int32_t *cached);
+
+/*
  * Contract nnet networks (each with its own path, as rosnet_contract) in one
  * plan: the steps of all networks that sit at the same dependency depth run
  * in the same grouped launches, and a step whose operands and contraction are

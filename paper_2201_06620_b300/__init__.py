@@ -31,7 +31,7 @@ __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
     "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc", "contract_batch",
     "plan_stats", "path_search", "slice_search", "sliced_networks", "sum_fp64",
-    "sync", "kernel_launches", "release_plans", "lib", "use_torch_allocator",
+    "sync", "kernel_launches", "release_plans", "plan_cache_limit", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
     "PREC_TF32X3",
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
@@ -62,7 +62,7 @@ EXPORTS = [
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
     "rosnet_btensor_download_async", "rosnet_alloc_stats", "rosnet_btensor_upload_raw",
-    "rosnet_btensor_download_raw",
+    "rosnet_btensor_download_raw", "rosnet_plan_cache_limit",
 ]
 
 _lock = threading.Lock()
@@ -171,6 +171,7 @@ def lib():
             L.rosnet_alloc_stats.argtypes = [i64p, i64p]
             L.rosnet_btensor_upload_raw.argtypes = [vp, vp, vp]
             L.rosnet_btensor_download_raw.argtypes = [vp, vp, vp]
+            L.rosnet_plan_cache_limit.argtypes = [ctypes.c_int32, i32p]
             for name in EXPORTS:
                 f = getattr(L, name)
                 if f.restype is ctypes.c_int or name in (
@@ -185,7 +186,8 @@ def lib():
                         "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
                         "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
                         "rosnet_btensor_download_async", "rosnet_alloc_stats",
-                        "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw"):
+                        "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw",
+                        "rosnet_plan_cache_limit"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -707,6 +709,15 @@ def timing_drain(max_entries=4096):
 
 def release_plans():
     _check(lib().rosnet_release_plans(), "rosnet_release_plans")
+
+
+def plan_cache_limit(max_plans=-1):
+    """Set the most contraction plans kept cached (0: no limit; least recently
+    used freed first); a negative value only queries.  Returns the number of
+    plans cached after the call."""
+    n = ctypes.c_int32()
+    _check(lib().rosnet_plan_cache_limit(int(max_plans), ctypes.byref(n)), "rosnet_plan_cache_limit")
+    return n.value
 
 
 def alloc_stats():

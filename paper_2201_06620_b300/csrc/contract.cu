@@ -123,6 +123,7 @@ struct Plan {
     std::vector<cudaEvent_t> tev;              // 2 * kTimingRing, created lazily
     int tpos = 0;
     int64_t steps_requested = 0;               // path steps before common steps were merged
+    uint64_t last_used = 0;                    // cache clock of the latest call
     ~Plan() {
         // device buffers go first, while every stream they were allocated or
         // last used on still exists (the side stream is destroyed below)
@@ -166,6 +167,25 @@ struct Key128Hash {
 auto &g_plans = *new std::unordered_map<Key128, std::unique_ptr<Plan>, Key128Hash>();
 // (plan, ring slot) of every timed launch not yet drained
 auto &g_timing_log = *new std::vector<std::pair<Plan *, int>>();
+// at most this many cached plans (0: no limit); the least recently used go first
+int32_t g_plan_limit = 0;
+uint64_t g_plan_clock = 0;
+
+// Free least recently used plans until at most n remain (g_plan_mu held).
+// Work a freed plan already enqueued completes normally: its buffers are
+// released in stream order and a graph still running is freed on completion.
+void evict_plans_to(size_t n) {
+    while (g_plans.size() > n) {
+        auto victim = g_plans.begin();
+        for (auto it = g_plans.begin(); it != g_plans.end(); ++it)
+            if (it->second->last_used < victim->second->last_used) victim = it;
+        Plan *vp = victim->second.get();
+        g_timing_log.erase(std::remove_if(g_timing_log.begin(), g_timing_log.end(),
+                                          [vp](const std::pair<Plan *, int> &e) { return e.first == vp; }),
+                           g_timing_log.end());
+        g_plans.erase(victim);
+    }
+}
 
 // Leaf slots shared by equal tensors (same storage and layout) across the
 // networks of a call; slot[i][t] for tensor t of network i.  Tensors are
@@ -851,12 +871,14 @@ static void contract_batch(int nnet, const rosnet_network *nets, const rosnet_pa
     if (it == g_plans.end()) {
         for (int i = 0; i < nnet; ++i) validate_network(&nets[i]);  // the key encodes all of it
         auto np = build_plan(nnet, nets, paths, slot, std::move(leaves), prec, flags, maxblk, s);
+        if (g_plan_limit > 0) evict_plans_to((size_t)g_plan_limit - 1);
         P = np.get();
         g_plans.emplace(std::move(key), std::move(np));
     } else {
         P = it->second.get();
         P->leaves = std::move(leaves);   // same sharing pattern; refresh the representatives
     }
+    P->last_used = ++g_plan_clock;
     std::vector<rosnet_btensor> made;
     try {
         for (int i = 0; i < nnet; ++i) {
@@ -936,6 +958,18 @@ rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int3
     }
     g_timing_log.clear();
     *n = k;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_plan_cache_limit(int32_t max_plans, int32_t *cached) {
+    RN_API_BEGIN
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (max_plans >= 0) {
+        g_plan_limit = max_plans;
+        if (max_plans > 0) evict_plans_to((size_t)max_plans);
+    }
+    if (cached) *cached = (int32_t)g_plans.size();
     return ROSNET_OK;
     RN_API_END
 }

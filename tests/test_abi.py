@@ -281,3 +281,12 @@ def test_allocator_switch_needs_no_live_blocks_and_stats():
         free = R._FREE_T(lambda p, s, c: None)
         assert R.lib().rosnet_set_allocator(alloc, free, None) == 0
         assert R.lib().rosnet_set_allocator(R._ALLOC_T(), R._FREE_T(), None) == 0
+
+
+def test_plan_cache_limit_is_host_side():
+    """Setting and querying the plan-cache bound needs no device (nothing is
+    cached in a process without contractions)."""
+    assert R.plan_cache_limit() == 0
+    assert R.plan_cache_limit(3) == 0
+    assert R.plan_cache_limit(-1) == 0
+    assert R.plan_cache_limit(0) == 0

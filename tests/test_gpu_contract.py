@@ -158,3 +158,46 @@ def test_timing_records_heaviest_launch_under_graph():
         assert ms > 0 and fl in (8.0 * 4096 * 256 * 256, 16.0 * 4096 * 256 * 256) and by > 0
         assert kind in (2, 3, 10)
     assert R.timing_drain() == []
+
+
+def test_plan_cache_limit_evicts_least_recently_used():
+    """With a bound of two plans, a third structure frees the least recently
+    used plan; a freed structure is planned again and gives the same result."""
+    circs = [W.random_circuit(n, 6, 40 + n) for n in (6, 7, 8)]
+    nets = [W.circuit_network(c) for c in circs]
+    refs = [oracle.amplitude_sv(c) for c in circs]
+    R.release_plans()
+    try:
+        assert R.plan_cache_limit(2) == 0
+        runs = []
+        for net in nets:
+            ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+            gn = R.Network(ts, net.labels, net.out_labels)
+            runs.append((gn, gn.greedy_path()))
+
+        def run(i):
+            gn, path = runs[i]
+            return complex(R.contract(gn, path=path, flags=R.OPT_GRAPH).download())
+
+        def cached(i):
+            gn, path = runs[i]
+            try:
+                R.plan_stats([gn], [path], flags=R.OPT_GRAPH)
+                return True
+            except R.RosnetError as e:
+                assert e.name == "INVALID_ARG"
+                return False
+
+        first = [run(i) for i in range(3)]            # plans 0, 1, 2: plan 0 freed
+        assert R.plan_cache_limit() == 2
+        assert [cached(i) for i in range(3)] == [False, True, True]
+        assert run(1) == first[1]                      # 1 is now the most recent
+        assert run(0) == first[0]                      # planned again; frees 2
+        assert [cached(i) for i in range(3)] == [True, True, False]
+        for i in range(3):
+            assert amp_err(first[i], refs[i], 6 + i) <= 1e-5
+        assert R.plan_cache_limit(1) == 1              # lowering frees at once
+        assert [cached(i) for i in range(3)] == [True, False, False]
+    finally:
+        R.plan_cache_limit(0)
+        R.release_plans()
