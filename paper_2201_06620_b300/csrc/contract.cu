@@ -319,9 +319,6 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     plan->stream = s;
     plan->leaves = std::move(leaves);
     plan->outs.resize(nnet);
-    const int nleaf = (int)plan->leaves.size();
-    std::vector<int> leaf_last_use(nleaf, -1);
-    (void)leaf_last_use;
     std::unordered_map<std::string, int64_t> seen;   // step signature -> step index
     auto lay_of = [&](int64_t g) -> const Layout & {
         if (g >= 0) return plan->steps[g].lay;
@@ -404,10 +401,8 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
                 g = (int64_t)plan->steps.size();
                 plan->steps.push_back(std::move(S));
                 seen.emplace(std::move(sig), g);
-                for (int64_t op : {ga, gb}) {
+                for (int64_t op : {ga, gb})   // leaves live for the whole call
                     if (op >= 0) plan->steps[op].last_use = std::max(plan->steps[op].last_use, plan->steps[g].wave);
-                    else leaf_last_use[-1 - op] = std::max(leaf_last_use[-1 - op], plan->steps[g].wave);
-                }
             }
             const int id = nt + st;
             gid[id] = g;
