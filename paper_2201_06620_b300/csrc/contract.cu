@@ -66,7 +66,7 @@ struct Step {
     Layout lay;          // layout of the result
     int wave;
     int last_use = -1;   // last wave that reads it
-    int64_t table_off;   // in int64 entries
+    int64_t table_off[3];   // M, N and K offset tables, in int64 entries
     size_t arena_off;    // SIZE_MAX: written straight into output out_net
     int out_net = -1;
     GettDesc desc;
@@ -506,24 +506,39 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         }
         plan->arena_bytes = top;
     }
-    // offset tables (host-built, one upload)
+    // offset tables (host-built, one upload).  A table depends only on the
+    // digits of its index class (extents and strides in both tensors), so
+    // classes with equal digits -- the same step in every slice of a network,
+    // repeated gate contractions -- share one copy.
+    static_assert(sizeof(Mode) == 3 * sizeof(int64_t), "a digit list is compared as bytes");
     std::vector<GettView> views(plan->steps.size());
+    std::unordered_map<std::string, int64_t> table_at;   // digits -> first entry
+    std::vector<std::pair<size_t, int>> owners;          // (step, class) that fills each table
     int64_t tab_entries = 0;
+    auto class_of = [&](const GettView &v, int c) -> std::pair<const ModeList *, int64_t> {
+        return c == 0 ? std::make_pair(&v.M, v.Mtot) : c == 1 ? std::make_pair(&v.N, v.Ntot)
+                                                               : std::make_pair(&v.K, v.Ktot);
+    };
     for (size_t g = 0; g < plan->steps.size(); ++g) {
         Step &S = plan->steps[g];
         views[g] = make_view(lay_of(S.ga), lay_of(S.gb), S.lay, S.naxes, S.axa.data(), S.axb.data());
-        S.table_off = tab_entries;
-        tab_entries += (int64_t)table_entries(views[g]);
+        for (int c = 0; c < 3; ++c) {
+            const auto mt = class_of(views[g], c);
+            std::string key((const char *)&mt.second, sizeof(int64_t));
+            key.append((const char *)mt.first->m, (size_t)mt.first->n * sizeof(Mode));
+            auto ins = table_at.emplace(std::move(key), tab_entries);
+            if (ins.second) {
+                owners.push_back({g, c});
+                tab_entries += 2 * mt.second;
+            }
+            S.table_off[c] = ins.first->second;
+        }
     }
     std::vector<int64_t> htab(std::max<int64_t>(tab_entries, 1));
-    for (size_t g = 0; g < plan->steps.size(); ++g) {
-        const GettView &v = views[g];
-        int64_t *t = htab.data() + plan->steps[g].table_off;
-        host_table(v.M, v.Mtot, t, t + v.Mtot);
-        t += 2 * v.Mtot;
-        host_table(v.N, v.Ntot, t, t + v.Ntot);
-        t += 2 * v.Ntot;
-        host_table(v.K, v.Ktot, t, t + v.Ktot);
+    for (const auto &o : owners) {
+        const auto mt = class_of(views[o.first], o.second);
+        int64_t *t = htab.data() + plan->steps[o.first].table_off[o.second];
+        host_table(*mt.first, mt.second, t, t + mt.second);
     }
     plan->tables = DevBuf(htab.size() * sizeof(int64_t), s);
     plan->arena = DevBuf(std::max<size_t>(plan->arena_bytes, 256), s);
@@ -541,7 +556,8 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         Step &S = plan->steps[g];
         const int st = (int)g;
         memset(&S.desc, 0, sizeof(S.desc));
-        fill_desc_tables(S.desc, views[g], dtab + S.table_off);
+        fill_desc_tables(S.desc, views[g], dtab + S.table_off[0], dtab + S.table_off[1],
+                         dtab + S.table_off[2]);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
         const bool cuda_core_gemm =

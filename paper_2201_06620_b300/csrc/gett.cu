@@ -168,14 +168,17 @@ void launch_build_tables(const GettView &v, int64_t *t, cudaStream_t s) {
 }
 
 void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *t) {
-    d.offAM = t;
-    d.offCM = t + v.Mtot;
-    t += 2 * v.Mtot;
-    d.offBN = t;
-    d.offCN = t + v.Ntot;
-    t += 2 * v.Ntot;
-    d.offAK = t;
-    d.offBK = t + v.Ktot;
+    fill_desc_tables(d, v, t, t + 2 * v.Mtot, t + 2 * v.Mtot + 2 * v.Ntot);
+}
+
+void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tm, const int64_t *tn,
+                      const int64_t *tk) {
+    d.offAM = tm;
+    d.offCM = tm + v.Mtot;
+    d.offBN = tn;
+    d.offCN = tn + v.Ntot;
+    d.offAK = tk;
+    d.offBK = tk + v.Ktot;
     d.M = v.Mtot;
     d.N = v.Ntot;
     d.K = v.Ktot;

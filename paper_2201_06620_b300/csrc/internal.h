@@ -272,6 +272,10 @@ size_t desc_part_bytes(const GettDesc &d, int dtype);
 size_t table_entries(const GettView &v);
 void launch_build_tables(const GettView &v, int64_t *tables, cudaStream_t s);
 void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tables);
+// The same with the M, N and K tables ([offsets in the first tensor | in the
+// second] of each class) at separate addresses.
+void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tm, const int64_t *tn,
+                      const int64_t *tk);
 
 // Choose the kernel family, tile grid and split-K for a problem (may swap
 // the operand roles; call bind_operands afterwards).
