@@ -1090,10 +1090,18 @@ rosnet_status rosnet_path_greedy_extents(int32_t ntensors, const int32_t *ranks,
 // ---------------------------------------------------------------------------
 namespace {
 
+// A network's labels renumbered 0..L-1 (in order of first appearance) with
+// their extents.  Membership of a label in a tensor is tested with a stamp
+// array instead of a scan; every product below is still taken over the same
+// labels in the same order, so costs are the same doubles as a plain scan
+// would give.
 struct LabelNet {
     int nt;
-    std::vector<std::vector<int64_t>> lab;
-    std::unordered_map<int64_t, double> ext;
+    std::vector<std::vector<int64_t>> lab;   // original labels per tensor
+    std::vector<std::vector<int>> id;        // the same as dense ids
+    std::vector<int64_t> label;              // dense id -> label
+    std::vector<double> ext;                 // dense id -> extent
+    std::unordered_map<int64_t, int> dense;  // label -> dense id
 };
 
 LabelNet label_net(int32_t ntensors, const int32_t *ranks, const int64_t *const *labels,
@@ -1102,20 +1110,61 @@ LabelNet label_net(int32_t ntensors, const int32_t *ranks, const int64_t *const 
     LabelNet n;
     n.nt = ntensors;
     n.lab.resize(ntensors);
-    std::unordered_map<int64_t, int> cnt;
+    n.id.resize(ntensors);
+    std::vector<int> cnt;
     for (int t = 0; t < ntensors; ++t) {
         if (ranks[t] < 0 || ranks[t] > kMaxRank) RN_FAIL(ROSNET_ERR_RANK_LIMIT, "bad rank");
         if (ranks[t] > 0 && (!labels[t] || !extents[t])) RN_FAIL(ROSNET_ERR_INVALID_ARG, "NULL labels");
         n.lab[t].assign(labels[t], labels[t] + ranks[t]);
         for (int i = 0; i < ranks[t]; ++i) {
-            auto it = n.ext.find(labels[t][i]);
-            if (it != n.ext.end() && it->second != (double)extents[t][i])
-                RN_FAIL(ROSNET_ERR_SHAPE, "a label has two different extents");
-            n.ext[labels[t][i]] = (double)extents[t][i];
-            if (++cnt[labels[t][i]] > 2) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "a label carried by more than two tensors");
+            auto ins = n.dense.emplace(labels[t][i], (int)n.label.size());
+            if (ins.second) {
+                n.label.push_back(labels[t][i]);
+                n.ext.push_back((double)extents[t][i]);
+                cnt.push_back(0);
+            }
+            const int x = ins.first->second;
+            if (n.ext[x] != (double)extents[t][i]) RN_FAIL(ROSNET_ERR_SHAPE, "a label has two different extents");
+            if (++cnt[x] > 2) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "a label carried by more than two tensors");
+            n.id[t].push_back(x);
         }
     }
     return n;
+}
+
+// Stamps for membership tests: mark(l) tags the labels of l, and has(x) is
+// true for those labels until the next mark().
+struct Marks {
+    std::vector<uint32_t> m;
+    uint32_t tok = 0;
+    explicit Marks(size_t n) : m(n, 0) {}
+    void mark(const std::vector<int> &l) {
+        if (++tok == 0) {   // wrapped: clear the stamps once
+            std::fill(m.begin(), m.end(), 0);
+            tok = 1;
+        }
+        for (int x : l) m[x] = tok;
+    }
+    bool has(int x) const { return m[x] == tok; }
+};
+
+// Entries of a tensor: the product of its extents in label order.
+double entries(const LabelNet &n, const std::vector<int> &l) {
+    double v = 1;
+    for (int x : l) v *= n.ext[x];
+    return v;
+}
+
+// Labels of the result of joining a and b: a's labels not in b, then b's
+// not in a.
+void joined(const std::vector<int> &a, const std::vector<int> &b, Marks &mk, std::vector<int> &r) {
+    r.clear();
+    mk.mark(b);
+    for (int x : a)
+        if (!mk.has(x)) r.push_back(x);
+    mk.mark(a);
+    for (int x : b)
+        if (!mk.has(x)) r.push_back(x);
 }
 
 // A path in SSA form (step t joins two live ids and creates id nt + t): every
@@ -1132,30 +1181,45 @@ void check_ssa_path(int nt, const int32_t *pairs, int nsteps) {
 }
 
 // Max intermediate entries and total 8*M*N*K flops of a path, with the
-// labels in `cut` fixed (sliced: extent 1).
+// labels flagged in `cut` (by dense id) fixed (sliced: extent 1).  `live`
+// is scratch reused between calls.
 std::pair<double, double> path_cost(const LabelNet &n, const int32_t *pairs, int nsteps,
-                                    const std::vector<int64_t> &cut) {
-    std::unordered_map<int64_t, bool> isc;
-    for (int64_t x : cut) isc[x] = true;
-    auto e = [&](int64_t x) { return isc.count(x) ? 1.0 : n.ext.at(x); };
-    std::vector<std::vector<int64_t>> live(n.nt + nsteps);
-    for (int t = 0; t < n.nt; ++t) live[t] = n.lab[t];
+                                    const std::vector<char> &cut, Marks &mk,
+                                    std::vector<std::vector<int>> &live) {
+    auto e = [&](int x) { return cut.empty() || !cut[x] ? n.ext[x] : 1.0; };
+    if (live.size() < (size_t)(n.nt + nsteps)) live.resize(n.nt + nsteps);
+    for (int t = 0; t < n.nt; ++t) live[t] = n.id[t];
     double mx = 0, tot = 0;
     for (int st = 0; st < nsteps; ++st) {
         const auto &la = live[pairs[2 * st]], &lb = live[pairs[2 * st + 1]];
+        auto &lc = live[n.nt + st];
+        lc.clear();
         double all = 1, out = 1;
-        std::vector<int64_t> lc;
-        for (int64_t x : la) {
+        mk.mark(lb);
+        for (int x : la) {
             all *= e(x);
-            if (std::find(lb.begin(), lb.end(), x) == lb.end()) { lc.push_back(x); out *= e(x); }
+            if (!mk.has(x)) { lc.push_back(x); out *= e(x); }
         }
-        for (int64_t x : lb)
-            if (std::find(la.begin(), la.end(), x) == la.end()) { lc.push_back(x); out *= e(x); all *= e(x); }
+        mk.mark(la);
+        for (int x : lb)
+            if (!mk.has(x)) { lc.push_back(x); out *= e(x); all *= e(x); }
         tot += 8.0 * all;
         mx = std::max(mx, out);
-        live[n.nt + st] = std::move(lc);
     }
     return {mx, tot};
+}
+
+// The bonds of a network in the order in which a label -> holders hash map,
+// filled tensor by tensor and label by label, visits its keys (dense ids).
+// Trials of the randomised search visit candidates in this order.
+std::vector<int> visit_order(const LabelNet &n) {
+    std::unordered_map<int64_t, std::vector<int>> holders;
+    for (int t = 0; t < n.nt; ++t)
+        for (int64_t x : n.lab[t]) holders[x].push_back(t);
+    std::vector<int> order;
+    order.reserve(holders.size());
+    for (const auto &kv : holders) order.push_back(n.dense.at(kv.first));
+    return order;
 }
 
 }  // namespace
@@ -1167,6 +1231,7 @@ rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks, const i
     if (!pairs_out || !nsteps || ntrials < 1 || temperature < 0) return ROSNET_ERR_INVALID_ARG;
     RN_API_BEGIN
     LabelNet n = label_net(ntensors, ranks, labels, extents);
+    Marks mk(n.ext.size());
     const int ns = ntensors - 1;
     // trial 0: the deterministic greedy min-size path
     std::vector<int32_t> best(2 * std::max(ns, 0)), cur(2 * std::max(ns, 0));
@@ -1174,60 +1239,77 @@ rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks, const i
     rosnet_status rc = rosnet_path_greedy_extents(ntensors, ranks, labels, extents, nout, out_labels,
                                                   best.data(), &k);
     if (rc != ROSNET_OK) return rc;
-    double best_flops = path_cost(n, best.data(), ns, {}).second;
+    std::vector<std::vector<int>> scratch0;
+    double best_flops = path_cost(n, best.data(), ns, {}, mk, scratch0).second;
     std::mt19937_64 rng(seed);
     std::uniform_real_distribution<double> U(1e-12, 1.0);
+    std::vector<int> r;
+    std::vector<std::vector<int>> scratch;
+    const std::vector<int> order = visit_order(n);
+    // holders of each label (at most two live tensors carry it), in the order
+    // they took it up
+    struct Hold {
+        int t[2];
+        int k;
+        void drop(int v) {   // remove every occurrence of v, keeping the rest in order
+            int w = 0;
+            for (int i = 0; i < k; ++i)
+                if (t[i] != v) t[w++] = t[i];
+            k = w;
+        }
+        void add(int v) {
+            if (k >= 2) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "a label carried by more than two tensors");
+            t[k++] = v;
+        }
+    };
     for (int trial = 1; trial < ntrials; ++trial) {
         // greedy on cost = size(out) - size(a) - size(b), perturbed by Gumbel
-        // noise of relative scale `temperature`
-        std::vector<std::vector<int64_t>> live(2 * ntensors);
-        std::unordered_map<int64_t, std::vector<int>> holders;
+        // noise of relative scale `temperature`, candidates in visit order
+        std::vector<std::vector<int>> live(2 * ntensors);
+        std::vector<double> size(2 * ntensors, 1.0);
+        std::vector<Hold> hold(n.ext.size(), Hold{{-1, -1}, 0});
         std::vector<bool> alive(2 * ntensors, false);
         for (int t = 0; t < ntensors; ++t) {
-            live[t] = n.lab[t];
+            live[t] = n.id[t];
+            size[t] = entries(n, live[t]);
             alive[t] = true;
-            for (int64_t x : n.lab[t]) holders[x].push_back(t);
+            for (int x : live[t]) hold[x].add(t);
         }
-        auto size_of = [&](const std::vector<int64_t> &l) {
-            double v = 1;
-            for (int64_t x : l) v *= n.ext.at(x);
-            return v;
-        };
         int next = ntensors;
         for (int st = 0; st < ns; ++st) {
             double bc = 0;
             int ba = -1, bb = -1;
-            for (auto &kv : holders) {
-                if (kv.second.size() != 2) continue;
-                const int a = std::min(kv.second[0], kv.second[1]), b = std::max(kv.second[0], kv.second[1]);
+            for (int lx : order) {
+                const Hold &h = hold[lx];
+                if (h.k != 2) continue;
+                const int a = std::min(h.t[0], h.t[1]), b = std::max(h.t[0], h.t[1]);
                 double out = 1;
-                for (int64_t x : live[a])
-                    if (std::find(live[b].begin(), live[b].end(), x) == live[b].end()) out *= n.ext.at(x);
-                for (int64_t x : live[b])
-                    if (std::find(live[a].begin(), live[a].end(), x) == live[a].end()) out *= n.ext.at(x);
-                double c = out - size_of(live[a]) - size_of(live[b]);
+                mk.mark(live[b]);
+                for (int x : live[a])
+                    if (!mk.has(x)) out *= n.ext[x];
+                mk.mark(live[a]);
+                for (int x : live[b])
+                    if (!mk.has(x)) out *= n.ext[x];
+                double c = out - size[a] - size[b];
                 c -= temperature * std::log(-std::log(U(rng))) * std::max(1.0, std::fabs(c));
                 if (ba < 0 || c < bc || (c == bc && (a < ba || (a == ba && b < bb)))) { bc = c; ba = a; bb = b; }
             }
             if (ba < 0)   // disconnected: the two lowest live ids
                 for (int i = 0; i < next && bb < 0; ++i)
                     if (alive[i]) { if (ba < 0) ba = i; else bb = i; }
-            std::vector<int64_t> r;
-            for (int64_t x : live[ba])
-                if (std::find(live[bb].begin(), live[bb].end(), x) == live[bb].end()) r.push_back(x);
-            for (int64_t x : live[bb])
-                if (std::find(live[ba].begin(), live[ba].end(), x) == live[ba].end()) r.push_back(x);
-            for (int64_t x : live[ba]) { auto &h = holders[x]; h.erase(std::remove(h.begin(), h.end(), ba), h.end()); }
-            for (int64_t x : live[bb]) { auto &h = holders[x]; h.erase(std::remove(h.begin(), h.end(), bb), h.end()); }
+            joined(live[ba], live[bb], mk, r);
+            for (int x : live[ba]) hold[x].drop(ba);
+            for (int x : live[bb]) hold[x].drop(bb);
             alive[ba] = alive[bb] = false;
             live[next] = r;
+            size[next] = entries(n, r);
             alive[next] = true;
-            for (int64_t x : r) holders[x].push_back(next);
+            for (int x : r) hold[x].add(next);
             cur[2 * st] = ba;
             cur[2 * st + 1] = bb;
             ++next;
         }
-        const double f = path_cost(n, cur.data(), ns, {}).second;
+        const double f = path_cost(n, cur.data(), ns, {}, mk, scratch).second;
         if (f < best_flops) { best_flops = f; best = cur; }
     }
     std::copy(best.begin(), best.end(), pairs_out);
@@ -1246,6 +1328,8 @@ rosnet_status rosnet_slice_search(int32_t ntensors, const int32_t *ranks, const 
     RN_API_BEGIN
     LabelNet n = label_net(ntensors, ranks, labels, extents);
     check_ssa_path(ntensors, pairs, nsteps);
+    Marks mk(n.ext.size());
+    std::vector<std::vector<int>> scratch;
     std::unordered_map<int64_t, int> cnt;
     for (auto &l : n.lab) for (int64_t x : l) cnt[x]++;
     std::vector<int64_t> bonds;
@@ -1256,30 +1340,33 @@ rosnet_status rosnet_slice_search(int32_t ntensors, const int32_t *ranks, const 
     }
     std::sort(bonds.begin(), bonds.end());
     if ((size_t)nslice > bonds.size()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "more slices than bonds");
-    std::vector<int64_t> cut;
-    std::pair<double, double> cost = path_cost(n, pairs, nsteps, cut);
+    std::vector<char> cut(n.ext.size(), 0);   // by dense id
+    std::vector<int64_t> order;               // the chosen labels, in order
+    std::pair<double, double> cost = path_cost(n, pairs, nsteps, cut, mk, scratch);
     for (int r = 0; r < nslice; ++r) {
         int64_t bl = 0;
         std::pair<double, double> bc{0, 0};
         bool have = false;
         for (int64_t b : bonds) {
-            if (std::find(cut.begin(), cut.end(), b) != cut.end()) continue;
-            cut.push_back(b);
-            auto c = path_cost(n, pairs, nsteps, cut);
-            cut.pop_back();
+            const int x = n.dense.at(b);
+            if (cut[x]) continue;
+            cut[x] = 1;
+            auto c = path_cost(n, pairs, nsteps, cut, mk, scratch);
+            cut[x] = 0;
             // the slice count multiplies the flops by the sliced extent
-            c.second *= n.ext.at(b);
+            c.second *= n.ext[x];
             if (!have || c < bc) { bc = c; bl = b; have = true; }
         }
-        cut.push_back(bl);
+        cut[n.dense.at(bl)] = 1;
+        order.push_back(bl);
         cost = bc;
         chosen[r] = bl;
     }
-    if (max_entries) *max_entries = path_cost(n, pairs, nsteps, cut).first;
+    if (max_entries) *max_entries = path_cost(n, pairs, nsteps, cut, mk, scratch).first;
     if (flops) {
         double mult = 1;
-        for (int64_t x : cut) mult *= n.ext.at(x);
-        *flops = path_cost(n, pairs, nsteps, cut).second * mult;
+        for (int64_t x : order) mult *= n.ext[n.dense.at(x)];
+        *flops = path_cost(n, pairs, nsteps, cut, mk, scratch).second * mult;
     }
     return ROSNET_OK;
     RN_API_END
