@@ -1268,6 +1268,10 @@ rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks, const i
         std::vector<std::vector<int>> live(2 * ntensors);
         std::vector<double> size(2 * ntensors, 1.0);
         std::vector<Hold> hold(n.ext.size(), Hold{{-1, -1}, 0});
+        // size(out) - size(a) - size(b) of each bond's pair, kept until one
+        // of the pair is joined (it depends on the two tensors alone)
+        std::vector<double> base(n.ext.size(), 0.0);
+        std::vector<char> fresh(n.ext.size(), 0);
         std::vector<bool> alive(2 * ntensors, false);
         for (int t = 0; t < ntensors; ++t) {
             live[t] = n.id[t];
@@ -1283,14 +1287,18 @@ rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks, const i
                 const Hold &h = hold[lx];
                 if (h.k != 2) continue;
                 const int a = std::min(h.t[0], h.t[1]), b = std::max(h.t[0], h.t[1]);
-                double out = 1;
-                mk.mark(live[b]);
-                for (int x : live[a])
-                    if (!mk.has(x)) out *= n.ext[x];
-                mk.mark(live[a]);
-                for (int x : live[b])
-                    if (!mk.has(x)) out *= n.ext[x];
-                double c = out - size[a] - size[b];
+                if (!fresh[lx]) {
+                    double out = 1;
+                    mk.mark(live[b]);
+                    for (int x : live[a])
+                        if (!mk.has(x)) out *= n.ext[x];
+                    mk.mark(live[a]);
+                    for (int x : live[b])
+                        if (!mk.has(x)) out *= n.ext[x];
+                    base[lx] = out - size[a] - size[b];
+                    fresh[lx] = 1;
+                }
+                double c = base[lx];
                 c -= temperature * std::log(-std::log(U(rng))) * std::max(1.0, std::fabs(c));
                 if (ba < 0 || c < bc || (c == bc && (a < ba || (a == ba && b < bb)))) { bc = c; ba = a; bb = b; }
             }
@@ -1304,7 +1312,10 @@ rosnet_status rosnet_path_search(int32_t ntensors, const int32_t *ranks, const i
             live[next] = r;
             size[next] = entries(n, r);
             alive[next] = true;
-            for (int x : r) hold[x].add(next);
+            for (int x : r) {
+                hold[x].add(next);
+                fresh[x] = 0;   // its pair now includes the new tensor
+            }
             cur[2 * st] = ba;
             cur[2 * st + 1] = bb;
             ++next;
