@@ -275,6 +275,21 @@ def _i64arr(seq):
     return (ctypes.c_int64 * max(1, len(seq)))(*seq)
 
 
+def _rows_i64(rows):
+    """Rows of integers for the C ABI's ``const int64_t *const *`` arguments:
+    one flat int64 array holding every row, and an array of pointers to the
+    rows' starts.  Returns (flat, pointers); keep both alive while the C side
+    may read them."""
+    rows = [[int(x) for x in r] for r in rows]
+    flat = (ctypes.c_int64 * max(1, sum(len(r) for r in rows)))(*[x for r in rows for x in r])
+    base, offs, o = ctypes.addressof(flat), [], 0
+    for r in rows:
+        offs.append(base + 8 * o if r else base)
+        o += len(r)
+    ptrs = (ctypes.c_void_p * max(1, len(rows)))(*offs)
+    return flat, ctypes.cast(ptrs, ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)))
+
+
 def _i32arr(seq):
     seq = [int(x) for x in seq]
     return (ctypes.c_int * max(1, len(seq)))(*seq)
@@ -507,13 +522,10 @@ class Network:
         self.out_labels = [int(x) for x in out_labels]
         self.handles = (ctypes.c_void_p * max(1, n))(*[t.handle.value for t in tensors])
         self.ranks = (ctypes.c_int32 * max(1, n))(*[len(l) for l in labels])
-        self._lab = [_i64arr(l) for l in labels]
-        self._labp = (ctypes.POINTER(ctypes.c_int64) * max(1, n))(
-            *[ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)) for a in self._lab])
+        self._lab, self._labp = _rows_i64(self.labels)
         self._out = _i64arr(out_labels)
         self.net = _Network(n, ctypes.cast(self.handles, ctypes.POINTER(ctypes.c_void_p)),
-                            ctypes.cast(self.ranks, ctypes.POINTER(ctypes.c_int32)),
-                            ctypes.cast(self._labp, ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))),
+                            ctypes.cast(self.ranks, ctypes.POINTER(ctypes.c_int32)), self._labp,
                             len(out_labels), ctypes.cast(self._out, ctypes.POINTER(ctypes.c_int64)))
         self._path = None
         self._path_key = None
@@ -551,14 +563,7 @@ def path_greedy(tensors, labels, out_labels=()):
 
 def path_greedy_extents(labels, extents, out_labels=()):
     """Greedy path from labels and extents alone (host-only, no GPU needed)."""
-    n = len(labels)
-    ranks = (ctypes.c_int32 * max(1, n))(*[len(l) for l in labels])
-    lab = [_i64arr(l) for l in labels]
-    ext = [_i64arr(e) for e in extents]
-    P = ctypes.POINTER(ctypes.c_int64)
-    labp = (P * max(1, n))(*[ctypes.cast(a, P) for a in lab])
-    extp = (P * max(1, n))(*[ctypes.cast(a, P) for a in ext])
-    out = _i64arr(out_labels)
+    n, ranks, labp, extp, out, keep = _label_args(labels, extents, out_labels)
     pairs = (ctypes.c_int32 * max(1, 2 * (n - 1)))()
     ns = ctypes.c_int32()
     _check(lib().rosnet_path_greedy_extents(n, ranks, labp, extp, len(out_labels), out, pairs,
@@ -568,13 +573,11 @@ def path_greedy_extents(labels, extents, out_labels=()):
 
 def _label_args(labels, extents, out_labels):
     n = len(labels)
-    P = ctypes.POINTER(ctypes.c_int64)
-    keep = [_i64arr(l) for l in labels] + [_i64arr(e) for e in extents]
     ranks = (ctypes.c_int32 * max(1, n))(*[len(l) for l in labels])
-    labp = (P * max(1, n))(*[ctypes.cast(a, P) for a in keep[:n]])
-    extp = (P * max(1, n))(*[ctypes.cast(a, P) for a in keep[n:]])
+    lab, labp = _rows_i64(labels)
+    ext, extp = _rows_i64(extents)
     out = _i64arr(out_labels)
-    return n, ranks, labp, extp, out, keep
+    return n, ranks, labp, extp, out, (lab, ext)
 
 
 def path_search(labels, extents, out_labels=(), ntrials=64, seed=0, temperature=0.3):

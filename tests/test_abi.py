@@ -290,3 +290,26 @@ def test_plan_cache_limit_is_host_side():
     assert R.plan_cache_limit(3) == 0
     assert R.plan_cache_limit(-1) == 0
     assert R.plan_cache_limit(0) == 0
+
+
+def test_network_labels_reach_the_c_side_unchanged():
+    """The binding packs all label rows into one flat array with row pointers;
+    every label, rank and output label reads back through the structure the C
+    side receives (empty rows and 64-bit labels included)."""
+    rng = np.random.default_rng(5)
+
+    class Handle:   # Network only records a tensor's handle
+        handle = ctypes.c_void_p(0)
+
+    for _ in range(50):
+        n = int(rng.integers(1, 30))
+        labels = [tuple(int(x) for x in rng.integers(-10**12, 10**12, int(rng.integers(0, 7))))
+                  for _ in range(n)]
+        out = [int(x) for x in rng.integers(0, 100, int(rng.integers(0, 5)))]
+        net = R.Network([Handle() for _ in range(n)], labels, out)
+        assert net.net.ntensors == n and net.net.nout == len(out)
+        for t, l in enumerate(labels):
+            assert net.net.ranks[t] == len(l)
+            assert [net.net.labels[t][i] for i in range(len(l))] == list(l)
+        assert [net.net.out_labels[i] for i in range(len(out))] == out
+
