@@ -222,29 +222,59 @@ def run_rosnet(args):
     # roofline of the heaviest launch (FP32 FFMA, plain ALU bound)
     peaks = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA
     hms = [h[0] for h in heavy]
     hflops = heavy[0][1] if heavy else 0.0
     hbytes = heavy[0][2] if heavy else 0.0
     hkind = heavy[0][3] if heavy else -1
     h_avg = statistics.mean(hms) if hms else float("nan")
+    h_whole = statistics.mean([h[4] for h in heavy]) if heavy else float("nan")
     achieved = hflops / (h_avg * 1e-3) / 1e12 if hms else None
+    achieved_whole = hflops / (h_whole * 1e-3) / 1e12 if hms else None
     traffic = _profiled_traffic(hkind)
+    probed = probe_peaks(R, torch, dev) if not args.no_probes else None
+    ffma = probed["fp32_ffma_tflops"] if probed else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
                 "kernel": KERNEL_NAMES.get(hkind, f"kind {hkind}"), "launch_ms": h_avg,
                 "flops_per_launch": hflops, "bytes_per_launch": hbytes,
-                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)"}
+                "peak_source": f"{sms} SMs (queried) x 128 FP32 lanes x 2 flop x sm_max_mhz "
+                               "(MEASURED_PEAKS.json)",
+                "launch_ms_with_packs": h_whole, "achieved_with_packs": achieved_whole,
+                "frac_with_packs": (achieved_whole / fp32_peak) if achieved_whole else None,
+                "peak_probed_ffma": ffma,
+                "frac_of_probed_ffma": (achieved / ffma) if (achieved and ffma) else None}
 
     others = None
     if not args.no_precision_modes:
         others = run_precision_modes(args, R, torch, net, path, bind, amps, flush, stream, flags)
     e2e = run_e2e(args, R, torch, circ, net, path, ngates, stream) if not args.no_e2e else None
-    cpu = None
+    extras = None if args.no_extras else run_extras(R, torch, dev, probed)
+    cpu, ref_amps = None, []
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(circ, bits[args.warmup:], args.cpu_seconds)
-    # check: oracle-independent sanity (amplitudes are finite and not all equal)
+        cpu, ref_amps = cpu_baseline(circ, bits[args.warmup:], args.cpu_seconds)
     assert all(np.isfinite(a.real) and np.isfinite(a.imag) for a in amps)
+    # parity of the timed amplitudes against the oracle's, on the bitstrings
+    # the CPU baseline contracted: |a - a_ref| / max(|a_ref|, 2^-n/2)
+    parity = None
+    if ref_amps:
+        floor = 2.0 ** (-N_QUBITS / 2)
+        err = max(abs(a - r) / max(abs(r), floor) for a, r in zip(amps, ref_amps))
+        parity = {"max_rel_err_vs_oracle": err, "amplitudes_checked": len(ref_amps), "bar": 1e-5,
+                  "ok": bool(err <= 1e-5)}
+        if others:
+            for o in others.values():
+                got = o.pop("_amps", None)
+                if got:
+                    m = min(len(got), len(ref_amps))
+                    e = max(abs(a - r) / max(abs(r), floor) for a, r in zip(got[:m], ref_amps[:m]))
+                    o["max_rel_err_vs_oracle"] = e
+                    o["oracle_checked"] = m
+                    o["within_1e-5_vs_oracle"] = bool(e <= 1e-5)
+    if others:
+        for o in others.values():
+            o.pop("_amps", None)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
@@ -262,11 +292,143 @@ def run_rosnet(args):
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "parity": parity,
+            "peaks_probed": probed,
             "other_precisions": others,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
+        if parity is not None and not parity["ok"]:
+            sys.exit(f"amplitudes differ from the oracle by {parity['max_rel_err_vs_oracle']:.3g} > 1e-5")
     if world > 1:
         dist.destroy_process_group()
+
+
+def probe_peaks(R, torch, dev):
+    """Peak rates measured on this GPU: the library's FP32 FFMA, FP64 DFMA and
+    tcgen05 TF32 / BF16 MMA probes (each launched once to warm up, once timed),
+    and page-locked host <-> device copy bandwidth (three 1 GiB copies each
+    way after a warm-up copy, CUDA events)."""
+    out = {}
+    for key, kind in (("fp32_ffma_tflops", R.PROBE_FFMA), ("fp64_dfma_tflops", R.PROBE_DFMA),
+                      ("tf32_tcgen05_tflops", R.PROBE_TF32), ("bf16_tcgen05_tflops", R.PROBE_BF16)):
+        try:
+            out[key] = R.probe_peak(kind)[0]
+        except Exception as e:   # reported, not fatal to the line
+            out[key] = None
+            out[key + "_error"] = str(e)[:160]
+    n = 1 << 30
+    h = torch.empty(n, dtype=torch.uint8).pin_memory()
+    d = torch.empty(n, dtype=torch.uint8, device=dev)
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 3 * n / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del h, d
+    return out
+
+
+def _net_labels(rank_a, rank_b, axes_a, axes_b):
+    """Labels of a two-tensor network equal to tensordot(A, B, (axes_a, axes_b))."""
+    la = list(range(rank_a))
+    lb = [1000 + j for j in range(rank_b)]
+    for x, y in zip(axes_a, axes_b):
+        lb[y] = la[x]
+    out = [la[i] for i in range(rank_a) if i not in axes_a] + [lb[j] for j in range(rank_b) if j not in axes_b]
+    return [la, lb], out
+
+
+def _timed_contract(R, torch, ts, labels, out, precision, reps):
+    """Plan (graph, timing) once, then `reps` replays: (ms per call from
+    events around the calls, [(gemm ms, flops, bytes, kind, whole ms)])."""
+    fl = R.OPT_GRAPH | R.OPT_TIMING
+    for _ in range(2):
+        C = R.contract(ts, labels, out, [(0, 1)], precision=precision, flags=fl)
+        del C
+    torch.cuda.synchronize()
+    R.timing_drain()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        C = R.contract(ts, labels, out, [(0, 1)], precision=precision, flags=fl)
+        del C
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, R.timing_drain()
+
+
+def run_extras(R, torch, dev, probed):
+    """Measurements beside the headline, each against the probed peak of its
+    arithmetic: (1) the single blocked FP64 tensordot ([2]^14 x [2]^14 in
+    2^10-entry blocks, 6 contracted axes, complex128); (2) the precision
+    sweep's chunk contraction ([2]^20 x [2]^30 -> [2]^30: M = 2^10, N = 2^20,
+    K = 2^10, complex64, 2^12-entry blocks, entries ~ 2^-15 complex normal from
+    a seeded device generator) in every precision mode, GEMM kernel alone and
+    with its operand packs."""
+    probed = probed or {}
+    out = {}
+    try:
+        prob = W.tensordot_single_config()
+        A = R.btensor(prob["a"], prob["block_a"], R.C128)
+        B = R.btensor(prob["b"], prob["block_b"], R.C128)
+        labels, ol = _net_labels(14, 14, prob["axes_a"], prob["axes_b"])
+        ms, recs = _timed_contract(R, torch, [A, B], labels, ol, R.PREC_DEFAULT, 20)
+        flop = 8.0 * 2 ** 8 * 2 ** 8 * 2 ** 6
+        gemm = statistics.mean(r[0] for r in recs)
+        peak = probed.get("fp64_dfma_tflops")
+        out["fp64_blocked_tensordot"] = {
+            "shape": "[2]^14 x [2]^14 -> [2]^16, blocks 2^10, B_k = 4, complex128", "flop": flop,
+            "call_ms": ms, "gemm_kernel_ms": gemm, "tflops": flop / (ms * 1e-3) / 1e12,
+            "gemm_tflops": flop / (gemm * 1e-3) / 1e12, "peak_probed_dfma": peak,
+            "frac_of_probed_dfma": (flop / (ms * 1e-3) / 1e12 / peak) if peak else None,
+            "what": "call_ms: events around rosnet_contract of the cached two-tensor plan (graph replay: "
+                    "GEMM, split-K sum, descriptor patch); gemm_kernel_ms: the GEMM launch alone"}
+        del A, B
+        R.release_plans()
+    except Exception as e:
+        out["fp64_blocked_tensordot"] = {"error": str(e)[:200]}
+    try:
+        prob = W.precision_sweep_config()
+        As = R.empty((2,) * 20, prob["block_a"][10:], R.C64)
+        B = R.empty(prob["shape_b"], prob["block_b"], R.C64)
+        g = torch.Generator(device=dev)
+        for t, seed in ((As, prob["seed_a"]), (B, prob["seed_b"])):
+            g.manual_seed(seed)
+            raw = torch.randn(2 * t.numel, device=dev, generator=g) * (prob["scale"] * 0.5 ** 0.5)
+            t.upload_raw(raw)
+            torch.cuda.synchronize()
+            del raw
+        labels, ol = _net_labels(20, 30, list(range(10, 20)), prob["axes_b"])
+        flop = 8.0 * 2 ** 10 * 2 ** 20 * 2 ** 10
+        rows = {}
+        for name, prec, issued, pk in (("fp32", R.PREC_FP32, 1, "fp32_ffma_tflops"),
+                                       ("tf32", R.PREC_TF32, 1, "tf32_tcgen05_tflops"),
+                                       ("tf32x3", R.PREC_TF32X3, 3, "tf32_tcgen05_tflops"),
+                                       ("bf16x3", R.PREC_BF16X3, 3, "bf16_tcgen05_tflops")):
+            ms, recs = _timed_contract(R, torch, [As, B], labels, ol, prec, 3)
+            gemm = statistics.mean(r[0] for r in recs)
+            whole = statistics.mean(r[4] for r in recs)
+            tf, tfw = flop / (gemm * 1e-3) / 1e12, flop / (whole * 1e-3) / 1e12
+            peak = probed.get(pk)
+            rows[name] = {"gemm_kernel_ms": gemm, "with_packs_ms": whole, "call_ms": ms,
+                          "tflops": tf, "tflops_with_packs": tfw, "issued_tflops": tf * issued,
+                          "peak_probed": peak, "peak_kind": pk,
+                          "frac_issued_of_probed": (tf * issued / peak) if peak else None,
+                          "frac_issued_with_packs": (tfw * issued / peak) if peak else None,
+                          "kernel_kind": recs[0][3] if recs else None}
+            R.release_plans()
+        out["sweep_chunk"] = {"shape": "M = 2^10, N = 2^20, K = 2^10 complex64 (2^12-entry blocks, B_k = 16)",
+                              "flop": flop, "modes": rows}
+        del As, B
+    except Exception as e:
+        out["sweep_chunk"] = {"error": str(e)[:200]}
+    return out
 
 
 def run_precision_modes(args, R, torch, net, path, bind, amps_fp32, flush, stream, flags):
@@ -274,8 +436,9 @@ def run_precision_modes(args, R, torch, net, path, bind, amps_fp32, flush, strea
     products as 3xTF32 / 3xBF16 split products or plain TF32 on tcgen05, FP32
     accumulation), timed like the main loop (L2 flushed before each step) on
     up to 400 of its bitstrings, each with its largest amplitude error against
-    the plain FP32 result, |a - a_fp32| / max(|a_fp32|, 2^-10).  Not the
-    headline: the workload specifies plain FP32."""
+    the plain FP32 result, |a - a_fp32| / max(|a_fp32|, 2^-10), and (filled in
+    after the CPU baseline) against the oracle on the bitstrings it
+    contracted.  Not the headline: the workload specifies plain FP32."""
     out = {}
     n = min(args.steps, 400)
     fl = flags & ~R.OPT_TIMING
@@ -295,10 +458,10 @@ def run_precision_modes(args, R, torch, net, path, bind, amps_fp32, flush, strea
                 ev[i][1].record(stream)
             torch.cuda.synchronize()
             ms = sum(a.elapsed_time(b) for a, b in ev)
-            err = max(abs(complex(r.download()) - a) / max(abs(a), 2.0 ** -10)
-                      for r, a in zip(res, amps_fp32[:n]))
+            got = [complex(r.download()) for r in res]
+            err = max(abs(g - a) / max(abs(a), 2.0 ** -10) for g, a in zip(got, amps_fp32[:n]))
             out[name] = {"value": n / (ms / 1e3), "unit": "amplitudes/s", "steps": n,
-                         "max_rel_err_vs_fp32": err, "within_1e-5": bool(err <= 1e-5)}
+                         "max_rel_err_vs_fp32": err, "_amps": got}
         except Exception as e:   # a mode that fails is reported, not fatal to the line
             out[name] = {"error": str(e)[:200]}
     return out
@@ -365,18 +528,20 @@ def run_e2e(args, R, torch, circ, net, path, ngates, stream):
 # CPU baseline / reference arm: the oracle as it stands
 # ---------------------------------------------------------------------------
 def cpu_baseline(circ, bits, seconds):
+    """The oracle timed on the first bitstrings of the timed loop; returns the
+    baseline record and the oracle's amplitudes (for the parity check)."""
     import oracle
     net = W.circuit_network(circ, bitstring=bits[0])
     path = oracle.greedy_path(net)
-    n = 0
+    n, ref = 0, []
     t0 = time.perf_counter()
     while n < len(bits) and (n == 0 or time.perf_counter() - t0 < seconds):
-        oracle.contract(W.circuit_network(circ, bitstring=bits[n]), path)
+        ref.append(complex(np.asarray(oracle.contract(W.circuit_network(circ, bitstring=bits[n]), path))))
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "amplitudes/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} amplitudes of the same circuit (oracle complex128 loop contraction, "
-                      f"oracle greedy path), {dt:.1f} s"}
+    return ({"value": n / dt, "unit": "amplitudes/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"{n} amplitudes of the same circuit (oracle complex128 loop contraction, "
+                       f"oracle greedy path), {dt:.1f} s"}, ref)
 
 
 def run_reference(args):
@@ -626,7 +791,7 @@ def run_reduction(args):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / 3
-            kinds = {k for *_, k in R.timing_drain()}
+            kinds = {r[3] for r in R.timing_drain()}
             rows.append({"B_k": bk, "mode": name, "ms": ms, "tflops": 8.0 * M * N * K / (ms * 1e-3) / 1e12,
                          "kernel": "/".join(KERNEL_NAMES.get(k, f"kind {k}").split(" (")[0] for k in sorted(kinds))})
             R.release_plans()
@@ -653,7 +818,8 @@ def run_sweep(args):
     peaks = _measured_peaks()
     bf16 = float(peaks.get("bf16_tflops", 1783.9))
     out = {}
-    fp32 = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6   # TFLOP/s, FFMA
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32 = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6   # TFLOP/s, FFMA
     for name, prec, peak, issued in (("fp32", R.PREC_FP32, fp32, 1),
                                      ("tf32", R.PREC_TF32, bf16 * 1.1 / 2.25, 1),
                                      ("bf16x3", R.PREC_BF16X3, bf16, 3),
@@ -694,6 +860,9 @@ def main():
     ap.add_argument("--tune-file", default=None,
                     help="load autotuner decisions from this file if it exists; save them after planning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-probes", action="store_true", help="skip the peak-rate probes")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra measurements (FP64 blocked tensordot, large tensor-core contractions)")
     ap.add_argument("--workload", choices=["rqc20", "serve", "batch", "sweep", "reduction"], default="rqc20")
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0)

@@ -229,8 +229,9 @@ rosnet_status rosnet_btensor_download_async(rosnet_btensor t, void *host, void *
  * Copy the raw storage of a tensor that owns it -- 2 * numel elements of its
  * dtype's real type: the real plane, then the imaginary plane, each in the
  * tensor's block-major element order (plain row-major for a one-block
- * tensor) -- from / to host memory, enqueued on `stream` without waiting, one
- * copy and no kernel.  The host buffer must stay valid until the stream
+ * tensor) -- from / to host memory (or device memory of the same GPU: the
+ * copy direction follows the pointer), enqueued on `stream` without waiting,
+ * one copy and no kernel.  The buffer must stay valid until the stream
  * reaches this point; page-locked memory lets the copy overlap other work.
  * INVALID_ARG for NULL arguments, UNSUPPORTED for views (slice / fix /
  * block), whose storage belongs to another tensor.
@@ -276,21 +277,29 @@ rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes,
  *
  * The caller passes the operands and an already created output tensor C whose
  * shape, block shape and dtype are those rosnet_tensordot would give the
- * result (else SHAPE / BLOCK_MISMATCH / DTYPE); C must not alias A or B.  The
- * call allocates nothing: the offset tables and split-K partial sums the
- * kernels need are placed in one fixed device array of
+ * result (else SHAPE / BLOCK_MISMATCH / DTYPE).  C's storage must not overlap
+ * A's or B's: the byte range from a tensor's data pointer to the end of its
+ * imaginary plane is compared, so a view of an operand's storage is refused
+ * like the operand itself (INVALID_ARG).  The call allocates nothing: the
+ * offset tables, split-K partial sums and packed operands of the tensor-core
+ * and packed-FP32 kernels are placed in one fixed device array of
  * ROSNET_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
  * loads the library keeps until the process exits.  A problem needing more
  * scratch is rejected with ROSNET_ERR_UNSUPPORTED before anything is launched
- * (rosnet_last_error() gives the bytes needed).
+ * (rosnet_last_error() gives the bytes needed).  opts as rosnet_tensordot:
+ * the precision and the reduction flags are honoured; ROSNET_OPT_AUTOTUNE is
+ * refused (UNSUPPORTED), because timing candidate kernels needs buffers of
+ * their own.
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the previous call's
- * contents; every byte a call reads from it is written earlier by the same
- * call, so nothing needs clearing, but calls that overlap on the GPU (on
- * different streams, or from different threads) race on it: serialise them.
- * Errors as rosnet_tensordot.
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset() on a device the entry point must not be used on it again.
+ * All calls share the array and it keeps the previous call's contents; every
+ * byte a call reads from it is written earlier by the same call, so nothing
+ * needs clearing, but calls that overlap on the GPU (on different streams, or
+ * from different threads) race on it: serialise them.  Errors as
+ * rosnet_tensordot.
  */
 #define ROSNET_NOALLOC_SCRATCH_BYTES (4u << 20)
 rosnet_status rosnet_tensordot_noalloc(rosnet_btensor A, rosnet_btensor B, int naxes,
@@ -413,18 +422,20 @@ rosnet_status rosnet_contract(const rosnet_network *net, const rosnet_path *path
  * Elapsed device time of the heaviest launch of every rosnet_contract call
  * made with ROSNET_OPT_TIMING since the last drain (oldest first, at most the
  * newest 4096).  Waits for those events.  The heaviest launch is the one with
- * the most algorithmic work; for a packed-operand launch (tensor-core or
- * packed FP32) the time covers its GEMM kernel, after the operand packs.
- * ms[i] receives the milliseconds; flops[i] / bytes[i] / kinds[i] (any may
- * be NULL) the launch's algorithmic work -- sum of 8*M*N*K and of
+ * the most algorithmic work.  ms[i] receives the milliseconds of its GEMM
+ * kernel (for a packed-operand launch -- tensor-core or packed FP32 -- after
+ * the operand packs) and ms_whole[i] those of the whole launch, operand packs
+ * included (the same for launches without packs); ms_whole, flops, bytes and
+ * kinds may be NULL.  flops[i] / bytes[i] / kinds[i] receive the launch's
+ * algorithmic work -- sum of 8*M*N*K and of
  * (|A| + |B| + |C|) * element size over its problems -- and its kernel family
  * (2 = 64x64 tiles, 3 = 128x64, 11 = 256x16, 12 = 128x32, 13 / 14 = direct
  * short-range tiles, 5-7 = tcgen05 TF32 / 3xTF32 / 3xBF16, 10 = packed FP32;
  * others are the small-problem kernels).  *n receives the
  * number of entries written (<= max_entries).
  */
-rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t *kinds,
-                                  int32_t max_entries, int32_t *n);
+rosnet_status rosnet_timing_drain(double *ms, double *ms_whole, double *flops, double *bytes,
+                                  int32_t *kinds, int32_t max_entries, int32_t *n);
 
 /*
  * Autotuner decisions (ROSNET_OPT_AUTOTUNE) as text, so that a later process
@@ -507,6 +518,25 @@ rosnet_status rosnet_sync(void *stream);
  * reports ROSNET_ERR_TIMEOUT.  For testing the bounded-wait path of the
  * library's kernels (no fault, no hang).  The paper has no counterpart. */
 rosnet_status rosnet_selftest_timeout(int64_t budget_cycles, void *stream);
+
+/* Measure a peak arithmetic rate of the current GPU with a microkernel, so
+ * that the contraction kernels' roofline fractions can be stated against
+ * measured rates (the paper has no counterpart; its block products ran on
+ * CPU cores, Sec. V):
+ *   ROSNET_PROBE_FFMA  FP32 fused multiply-adds on the CUDA cores
+ *   ROSNET_PROBE_DFMA  FP64 fused multiply-adds on the CUDA cores
+ *   ROSNET_PROBE_TF32  tcgen05.mma kind::tf32 (128 x 256 x 8), TMEM accumulators
+ *   ROSNET_PROBE_BF16  tcgen05.mma kind::f16, bf16 operands (128 x 256 x 16)
+ * The probe is launched once to warm up and once timed with CUDA events on
+ * `stream`; *flops receives the floating-point operations of the timed launch
+ * (2 per multiply-add) and *ms its device time.  Synchronous.  INVALID_ARG
+ * for an unknown kind or NULL outputs; TIMEOUT if the MMA probe's bounded
+ * wait gave up. */
+#define ROSNET_PROBE_FFMA 0
+#define ROSNET_PROBE_DFMA 1
+#define ROSNET_PROBE_TF32 2
+#define ROSNET_PROBE_BF16 3
+rosnet_status rosnet_probe_peak(int32_t kind, void *stream, double *flops, double *ms);
 
 /* Static, human-readable description of a status code. */
 const char *rosnet_status_string(rosnet_status s);

@@ -36,6 +36,7 @@ __all__ = [
     "PREC_TF32X3",
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
     "REDUCE_SEQUENTIAL", "REDUCE_TREE", "REDUCE_COMMUTATIVE", "OPT_AUTOTUNE",
+    "probe_peak", "PROBE_FFMA", "PROBE_DFMA", "PROBE_TF32", "PROBE_BF16",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -62,7 +63,7 @@ EXPORTS = [
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
     "rosnet_btensor_download_async", "rosnet_alloc_stats", "rosnet_btensor_upload_raw",
-    "rosnet_btensor_download_raw", "rosnet_plan_cache_limit",
+    "rosnet_btensor_download_raw", "rosnet_plan_cache_limit", "rosnet_probe_peak",
 ]
 
 _lock = threading.Lock()
@@ -130,6 +131,8 @@ def lib():
                                               i32p, ctypes.c_int32, i64p, dpp, dpp]
             L.rosnet_sum.argtypes = [ctypes.c_int32, ctypes.POINTER(vp), vp, ctypes.POINTER(vp)]
             L.rosnet_selftest_timeout.argtypes = [ctypes.c_int64, vp]
+            L.rosnet_probe_peak.argtypes = [ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]
             L.rosnet_contract_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
                                                 ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp,
                                                 ctypes.POINTER(vp)]
@@ -157,7 +160,7 @@ def lib():
                                           ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
             L.rosnet_release_plans.argtypes = []
             dp = ctypes.POINTER(ctypes.c_double)
-            L.rosnet_timing_drain.argtypes = [dp, dp, dp, i32p, ctypes.c_int32, i32p]
+            L.rosnet_timing_drain.argtypes = [dp, dp, dp, dp, i32p, ctypes.c_int32, i32p]
             L.rosnet_sync.argtypes = [vp]
             L.rosnet_status_string.argtypes = [ctypes.c_int]
             L.rosnet_status_string.restype = ctypes.c_char_p
@@ -187,7 +190,7 @@ def lib():
                         "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
                         "rosnet_btensor_download_async", "rosnet_alloc_stats",
                         "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw",
-                        "rosnet_plan_cache_limit"):
+                        "rosnet_plan_cache_limit", "rosnet_probe_peak"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -410,8 +413,9 @@ class BTensor:
 
     def upload_raw(self, buf, stream=None):
         """Copy the real plane then the imaginary plane (block-major order) from
-        ``buf`` (page-locked torch tensor or numpy array of 2 * numel reals)
-        into the tensor's storage: one enqueued copy, no kernel."""
+        ``buf`` (a page-locked or CUDA torch tensor, or a numpy array, of
+        2 * numel reals) into the tensor's storage: one enqueued copy, no
+        kernel."""
         _check(lib().rosnet_btensor_upload_raw(self._h, ctypes.c_void_p(self._raw_ptr(buf)), _stream(stream)),
                "upload_raw")
         return buf
@@ -480,11 +484,12 @@ def tensordot(A, B, axes_a, axes_b, precision=PREC_DEFAULT, stream=None, flags=0
     return BTensor(h.value)
 
 
-def tensordot_noalloc(A, B, axes_a, axes_b, C, precision=PREC_DEFAULT, stream=None):
+def tensordot_noalloc(A, B, axes_a, axes_b, C, precision=PREC_DEFAULT, stream=None, flags=0):
     """tensordot into an existing tensor C without any device allocation (the
-    library's fixed scratch array holds the kernels' workspace)."""
+    library's fixed scratch array holds the kernels' workspace).  ``flags``
+    may hold one REDUCE_* mode."""
     _init()
-    o = _opts(precision)
+    o = _opts(precision, flags)
     _check(lib().rosnet_tensordot_noalloc(A.handle, B.handle, len(axes_a), _i32arr(axes_a),
                                           _i32arr(axes_b), C.handle, ctypes.byref(o),
                                           _stream(stream)), "rosnet_tensordot_noalloc")
@@ -698,16 +703,30 @@ def kernel_launches():
     return int(lib().rosnet_kernel_launches())
 
 
+PROBE_FFMA, PROBE_DFMA, PROBE_TF32, PROBE_BF16 = 0, 1, 2, 3
+
+
+def probe_peak(kind, stream=None):
+    """Measured peak of one kind of arithmetic (PROBE_*): (TFLOP/s, flops, ms)."""
+    _init()
+    fl, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().rosnet_probe_peak(int(kind), _stream(stream), ctypes.byref(fl), ctypes.byref(ms)),
+           "rosnet_probe_peak")
+    return fl.value / (ms.value * 1e-3) / 1e12, fl.value, ms.value
+
+
 def timing_drain(max_entries=4096):
-    """[(ms, flops, bytes, kind)] of the heaviest launch of each timed contract
-    call (for packed-operand launches: the GEMM kernel alone)."""
+    """[(ms, flops, bytes, kind, ms_whole)] of the heaviest launch of each
+    timed contract call: ms covers its GEMM kernel (for packed-operand
+    launches after the operand packs), ms_whole the whole launch."""
     ms = (ctypes.c_double * max_entries)()
+    mw = (ctypes.c_double * max_entries)()
     fl = (ctypes.c_double * max_entries)()
     by = (ctypes.c_double * max_entries)()
     kd = (ctypes.c_int32 * max_entries)()
     n = ctypes.c_int32()
-    _check(lib().rosnet_timing_drain(ms, fl, by, kd, max_entries, ctypes.byref(n)), "rosnet_timing_drain")
-    return [(ms[i], fl[i], by[i], kd[i]) for i in range(n.value)]
+    _check(lib().rosnet_timing_drain(ms, mw, fl, by, kd, max_entries, ctypes.byref(n)), "rosnet_timing_drain")
+    return [(ms[i], fl[i], by[i], kd[i], mw[i]) for i in range(n.value)]
 
 
 def release_plans():

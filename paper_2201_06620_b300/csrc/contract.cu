@@ -39,7 +39,8 @@ int64_t reduce_ctas(const GettDesc &d);
 void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
-                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {});
+                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {},
+                       bool pdl = true);
 
 namespace {
 
@@ -111,7 +112,7 @@ struct Plan {
     // before the caller's work by two events
     cudaStream_t side = nullptr;
     cudaEvent_t join[2] = {nullptr, nullptr};
-    cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+    cudaGraphNode_t ev_node[3] = {nullptr, nullptr, nullptr};
     int graph_nodes = 0;
     std::vector<GettDesc> mirror;              // descriptor contents last enqueued
     bool mirror_valid = false;
@@ -120,7 +121,9 @@ struct Plan {
     double heavy_flops = 0, heavy_bytes = 0;
     int heavy_kind = -1;
     static constexpr int kTimingRing = 4096;
-    std::vector<cudaEvent_t> tev;              // 2 * kTimingRing, created lazily
+    // 3 * kTimingRing, created lazily: per slot the heaviest launch's start
+    // (before its operand packs), its GEMM kernel's start, and its end
+    std::vector<cudaEvent_t> tev;
     int tpos = 0;
     int64_t steps_requested = 0;               // path steps before common steps were merged
     uint64_t last_used = 0;                    // cache clock of the latest call
@@ -739,7 +742,7 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
     int slot = -1;
     if (timing) {
         if (P.tev.empty()) {
-            P.tev.resize(2 * Plan::kTimingRing, nullptr);
+            P.tev.resize(3 * Plan::kTimingRing, nullptr);
             for (auto &e : P.tev) RN_CHECK_CUDA(cudaEventCreate(&e));
         }
         slot = P.tpos;
@@ -750,31 +753,27 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
         for (size_t li = 0; li < P.launches.size(); ++li) {
             const auto &L = P.launches[li];
             const bool th = timing && (int)li == P.heavy;
-            // the timed region is the GEMM kernel itself (after the packs of a
-            // packed-operand launch)
-            auto start = [&]() {
-                cudaEvent_t e0 = P.tev[2 * slot];
-                RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal)
-                                        : cudaEventRecord(e0, s));
+            // timed: the whole launch (operand packs included) and, for a
+            // packed-operand launch, its GEMM kernel alone
+            auto rec = [&](int which) {
+                cudaEvent_t e = P.tev[3 * slot + which];
+                RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                        : cudaEventRecord(e, s));
             };
-            if (th && !is_packed_kind(L.kind)) start();
+            if (th) rec(0);
             if (is_packed_kind(L.kind)) {
                 GroupArgs ga;
                 memset(&ga, 0, sizeof(ga));
                 ga.descs = dd + L.first;
                 ga.ndesc = 1;
                 std::function<void()> hook;
-                if (th) hook = start;
+                if (th) hook = [&]() { rec(1); };
                 launch_tc_problem(packed_mode(L.kind), P.slot_desc[L.first], ga,
                                   (char *)P.tcws.p + L.tc_ws_off, s, true, true, hook);
             } else {
                 launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
             }
-            if (th) {
-                cudaEvent_t e1 = P.tev[2 * slot + 1];
-                RN_CHECK_CUDA(capturing ? cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal)
-                                        : cudaEventRecord(e1, s));
-            }
+            if (th) rec(2);
         }
     };
     const bool use_graph = want_graph && s != nullptr;
@@ -793,29 +792,28 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
             P.graph_nodes = (int)(g_launches.load() - before);
             g_launches -= P.graph_nodes;  // counted at replay
             RN_CHECK_CUDA(cudaStreamEndCapture(s, &gr));
-            if (timing) {  // find the two event-record nodes
+            if (timing) {  // find the event-record nodes (two, or three for a packed launch)
                 size_t nn = 0;
                 RN_CHECK_CUDA(cudaGraphGetNodes(gr, nullptr, &nn));
                 std::vector<cudaGraphNode_t> nodes(nn);
                 RN_CHECK_CUDA(cudaGraphGetNodes(gr, nodes.data(), &nn));
-                int k = 0;
                 for (auto nd_ : nodes) {
                     cudaGraphNodeType ty;
                     RN_CHECK_CUDA(cudaGraphNodeGetType(nd_, &ty));
-                    if (ty == cudaGraphNodeTypeEventRecord && k < 2) {
-                        cudaEvent_t e;
-                        RN_CHECK_CUDA(cudaGraphEventRecordNodeGetEvent(nd_, &e));
-                        P.ev_node[e == P.tev[2 * slot] ? 0 : 1] = nd_;
-                        ++k;
-                    }
+                    if (ty != cudaGraphNodeTypeEventRecord) continue;
+                    cudaEvent_t e;
+                    RN_CHECK_CUDA(cudaGraphEventRecordNodeGetEvent(nd_, &e));
+                    for (int w = 0; w < 3; ++w)
+                        if (e == P.tev[3 * slot + w]) P.ev_node[w] = nd_;
                 }
             }
             cudaError_t e = cudaGraphInstantiate(&P.graph, gr, 0);
             P.graph_src = gr;
             RN_CHECK_CUDA(e);
-        } else if (timing && P.ev_node[0] && P.ev_node[1]) {
-            RN_CHECK_CUDA(cudaGraphExecEventRecordNodeSetEvent(P.graph, P.ev_node[0], P.tev[2 * slot]));
-            RN_CHECK_CUDA(cudaGraphExecEventRecordNodeSetEvent(P.graph, P.ev_node[1], P.tev[2 * slot + 1]));
+        } else if (timing) {
+            for (int w = 0; w < 3; ++w)
+                if (P.ev_node[w])
+                    RN_CHECK_CUDA(cudaGraphExecEventRecordNodeSetEvent(P.graph, P.ev_node[w], P.tev[3 * slot + w]));
         }
         RN_CHECK_CUDA(cudaGraphLaunch(P.graph, s));
         g_launches += P.graph_nodes;
@@ -946,8 +944,8 @@ rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const 
     RN_API_END
 }
 
-rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int32_t *kinds,
-                                  int32_t max_entries, int32_t *n) {
+rosnet_status rosnet_timing_drain(double *ms, double *ms_whole, double *flops, double *bytes,
+                                  int32_t *kinds, int32_t max_entries, int32_t *n) {
     if (!n || max_entries < 0 || (max_entries > 0 && !ms)) return ROSNET_ERR_INVALID_ARG;
     RN_API_BEGIN
     std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -958,10 +956,13 @@ rosnet_status rosnet_timing_drain(double *ms, double *flops, double *bytes, int3
     for (size_t i = start; i < g_timing_log.size() && k < max_entries; ++i) {
         Plan *P = g_timing_log[i].first;
         int slot = g_timing_log[i].second;
-        RN_CHECK_CUDA(cudaEventSynchronize(P->tev[2 * slot + 1]));
-        float t = 0;
-        RN_CHECK_CUDA(cudaEventElapsedTime(&t, P->tev[2 * slot], P->tev[2 * slot + 1]));
+        RN_CHECK_CUDA(cudaEventSynchronize(P->tev[3 * slot + 2]));
+        const bool packed = is_packed_kind(P->heavy_kind);
+        float t = 0, tw = 0;
+        RN_CHECK_CUDA(cudaEventElapsedTime(&t, P->tev[3 * slot + (packed ? 1 : 0)], P->tev[3 * slot + 2]));
+        RN_CHECK_CUDA(cudaEventElapsedTime(&tw, P->tev[3 * slot], P->tev[3 * slot + 2]));
         ms[k] = t;
+        if (ms_whole) ms_whole[k] = tw;
         if (flops) flops[k] = P->heavy_flops;
         if (bytes) bytes[k] = P->heavy_bytes;
         if (kinds) kinds[k] = P->heavy_kind;

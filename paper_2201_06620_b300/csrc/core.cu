@@ -20,6 +20,21 @@ namespace rosnet {
 
 std::atomic<int64_t> g_launches{0};
 
+int num_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];   // 0 = not yet queried
+    int dev = 0;
+    RN_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "device index out of range");
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        RN_CHECK_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        if (n <= 0) RN_FAIL(ROSNET_ERR_CUDA, "device reports no multiprocessors");
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 static thread_local std::string t_last_error;
 void set_last_error(const std::string &s) { t_last_error = s; }
 const char *last_error_cstr() { return t_last_error.c_str(); }
@@ -220,7 +235,7 @@ __global__ void __launch_bounds__(256) copy_modes_kernel(CopyModes cm, int64_t t
 
 static int copy_grid(int64_t total) {
     int64_t b = (total + 255) / 256;
-    int64_t cap = 148 * 16;
+    int64_t cap = (int64_t)num_sms() * 16;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
@@ -449,7 +464,8 @@ rosnet_status rosnet_sum(int32_t n, const rosnet_btensor *ts, void *stream, rosn
         RN_CHECK_CUDA(cudaMemcpyAsync(dp.p, hp.data(), n * sizeof(void *), cudaMemcpyHostToDevice, s));
         RN_CHECK_CUDA(cudaMemcpyAsync(dps.p, hs.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         const int64_t numel = canon.numel;
-        const int grid = (int)std::min<int64_t>(std::max<int64_t>((numel + 255) / 256, 1), 148 * 8);
+        const int grid = (int)std::min<int64_t>(std::max<int64_t>((numel + 255) / 256, 1),
+                                                        (int64_t)num_sms() * 8);
         if (numel > 0) {
             if (t0->dtype == ROSNET_C64)
                 sum_fp64_kernel<float><<<grid, 256, 0, s>>>((const float *const *)dp.p, (const int64_t *)dps.p,
@@ -612,7 +628,7 @@ rosnet_status rosnet_btensor_upload_raw(rosnet_btensor t, const void *host, void
     check_raw(t);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = 2 * (size_t)t->lay.numel * t->elsize;
-    if (bytes) RN_CHECK_CUDA(cudaMemcpyAsync(t->data, host, bytes, cudaMemcpyHostToDevice, s));
+    if (bytes) RN_CHECK_CUDA(cudaMemcpyAsync(t->data, host, bytes, cudaMemcpyDefault, s));
     t->stream = s;
     return ROSNET_OK;
     RN_API_END
@@ -623,7 +639,7 @@ rosnet_status rosnet_btensor_download_raw(rosnet_btensor t, void *host, void *st
     RN_API_BEGIN
     check_raw(t);
     const size_t bytes = 2 * (size_t)t->lay.numel * t->elsize;
-    if (bytes) RN_CHECK_CUDA(cudaMemcpyAsync(host, t->data, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    if (bytes) RN_CHECK_CUDA(cudaMemcpyAsync(host, t->data, bytes, cudaMemcpyDefault, (cudaStream_t)stream));
     return ROSNET_OK;
     RN_API_END
 }

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) build_table_kernel(ModeList ml, int64_t t
 static void launch_table(const ModeList &ml, int64_t total, int64_t *o0, int64_t *o1,
                          cudaStream_t s) {
     if (total <= 0) return;
-    int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 8);
+    int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 8);
     build_table_kernel<<<(int)blocks, 256, 0, s>>>(ml, total, o0, o1);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
@@ -929,7 +929,6 @@ static void swap_operands(GettDesc &d) {
 }
 
 constexpr int kTiledStages = 3;
-constexpr int kSMs = 148;
 
 bool tc_mode_of(int precision, int *mode);
 int tc_tile_m();
@@ -938,9 +937,11 @@ int f32p_tile_m();
 int f32p_tile_n();
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
-                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {});
+                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {},
+                       bool pdl = true);
 
 void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
+    const int64_t kSMs = num_sms();
     d.ksplit = 1;
     d.ktiles_per_split = 0x7fffffff;
     d.part = nullptr;
@@ -993,9 +994,16 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
         const int64_t tiles = d.tiles_m * d.tiles_n;
         const int64_t nkt = (d.K + BK - 1) / BK;
         const bool forced = reduce_mode == kReduceTree || reduce_mode == kReduceCommutative;
-        if (reduce_mode != kReduceSequential && ((tiles < kSMs && nkt >= 32) || (forced && nkt >= 2))) {
+        // FP64 runs at a small fraction of the FP32 rate on this GPU (a few
+        // DFMA per clock per SM), so even one k-tile of a 64 x 64 tile keeps a
+        // CTA busy far longer than its prologue: complex128 problems split
+        // down to single k-tiles to occupy every SM
+        const bool fp64 = dtype == ROSNET_C128;
+        if (reduce_mode != kReduceSequential &&
+            ((tiles < kSMs && (nkt >= 32 || (fp64 && nkt >= 2))) || (forced && nkt >= 2))) {
             int64_t want = std::max<int64_t>((2 * kSMs + tiles - 1) / tiles, forced ? 2 : 1);
-            int64_t cap = forced ? nkt : nkt / 8;    // auto: at least 8 k-tiles per range
+            // auto: at least 8 k-tiles per range (complex64), 1 (complex128)
+            int64_t cap = (forced || fp64) ? nkt : nkt / 8;
             int64_t ks = std::max<int64_t>(1, std::min<int64_t>(std::min(want, cap), 64));
             if (ks > 1) {
                 d.ktiles_per_split = (int)((nkt + ks - 1) / ks);
@@ -1026,7 +1034,7 @@ size_t desc_part_bytes(const GettDesc &d, int dtype) {
 }
 
 template <typename T, int BM, int BN>
-static void launch_direct(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
+static void launch_direct(dim3 grid, const GroupArgs &ga, cudaStream_t s, bool pdl) {
     using Cfg = DirectCfg<T, BM, BN>;
     static bool attr_set = false;   // once per process (one device)
     if (!attr_set) {
@@ -1034,11 +1042,11 @@ static void launch_direct(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
         attr_set = true;
     }
-    launch_pdl(gett_direct_kernel<T, BM, BN>, grid, 256, Cfg::smem, s, ga);
+    launch_pdl(gett_direct_kernel<T, BM, BN>, grid, 256, Cfg::smem, s, pdl, ga);
 }
 
 template <typename T, int BM, int BN, int BK>
-static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
+static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s, bool pdl) {
     using Cfg = TiledCfg<T, BM, BN, BK, kTiledStages>;
     static bool attr_set = false;   // once per process (one device)
     if (!attr_set) {
@@ -1046,11 +1054,11 @@ static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s) {
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
         attr_set = true;
     }
-    launch_pdl(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>, grid, 256, Cfg::smem, s, ga);
+    launch_pdl(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>, grid, 256, Cfg::smem, s, pdl, ga);
 }
 
 static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t total_ctas,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool pdl = true) {
     if (total_ctas <= 0) return;
     if (total_ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "too many tiles in one launch");
     dim3 grid((unsigned)total_ctas);
@@ -1058,27 +1066,27 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "tensor-core problems are launched with their workspace");
     if (dtype == ROSNET_C64) {
         switch (kind) {
-            case kKindSmall: launch_pdl(gett_small_kernel<float>, grid, 256, 0, s, ga); break;
-            case kKindWarpK: launch_pdl(gett_warpk_kernel<float>, grid, 256, 0, s, ga); break;
-            case kKindReduce: launch_pdl(gett_reduce_kernel<float>, grid, 256, 0, s, ga); break;
-            case kKindZero: launch_pdl(gett_zero_kernel<float>, grid, 256, 0, s, ga); break;
-            case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 256, 0, s, ga); break;
-            case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s); break;
-            case kKindTiled256x16: launch_tiled<float, 256, 16, 16>(grid, ga, s); break;
-            case kKindDirect: launch_direct<float, 64, 64>(grid, ga, s); break;
-            case kKindDirect256x16: launch_direct<float, 256, 16>(grid, ga, s); break;
-            case kKindTiled128x32: launch_tiled<float, 128, 32, 16>(grid, ga, s); break;
-            default: launch_tiled<float, 64, 64, 16>(grid, ga, s); break;
+            case kKindSmall: launch_pdl(gett_small_kernel<float>, grid, 256, 0, s, pdl, ga); break;
+            case kKindWarpK: launch_pdl(gett_warpk_kernel<float>, grid, 256, 0, s, pdl, ga); break;
+            case kKindReduce: launch_pdl(gett_reduce_kernel<float>, grid, 256, 0, s, pdl, ga); break;
+            case kKindZero: launch_pdl(gett_zero_kernel<float>, grid, 256, 0, s, pdl, ga); break;
+            case kKindDot: launch_pdl(gett_dot_kernel<float>, grid, 256, 0, s, pdl, ga); break;
+            case kKindTiledWide: launch_tiled<float, 128, 64, 16>(grid, ga, s, pdl); break;
+            case kKindTiled256x16: launch_tiled<float, 256, 16, 16>(grid, ga, s, pdl); break;
+            case kKindDirect: launch_direct<float, 64, 64>(grid, ga, s, pdl); break;
+            case kKindDirect256x16: launch_direct<float, 256, 16>(grid, ga, s, pdl); break;
+            case kKindTiled128x32: launch_tiled<float, 128, 32, 16>(grid, ga, s, pdl); break;
+            default: launch_tiled<float, 64, 64, 16>(grid, ga, s, pdl); break;
         }
     } else {
         switch (kind) {
-            case kKindSmall: launch_pdl(gett_small_kernel<double>, grid, 256, 0, s, ga); break;
-            case kKindWarpK: launch_pdl(gett_warpk_kernel<double>, grid, 256, 0, s, ga); break;
-            case kKindReduce: launch_pdl(gett_reduce_kernel<double>, grid, 256, 0, s, ga); break;
-            case kKindZero: launch_pdl(gett_zero_kernel<double>, grid, 256, 0, s, ga); break;
-            case kKindDot: launch_pdl(gett_dot_kernel<double>, grid, 256, 0, s, ga); break;
-            case kKindDirect: launch_direct<double, 64, 64>(grid, ga, s); break;
-            default: launch_tiled<double, 64, 64, 8>(grid, ga, s); break;
+            case kKindSmall: launch_pdl(gett_small_kernel<double>, grid, 256, 0, s, pdl, ga); break;
+            case kKindWarpK: launch_pdl(gett_warpk_kernel<double>, grid, 256, 0, s, pdl, ga); break;
+            case kKindReduce: launch_pdl(gett_reduce_kernel<double>, grid, 256, 0, s, pdl, ga); break;
+            case kKindZero: launch_pdl(gett_zero_kernel<double>, grid, 256, 0, s, pdl, ga); break;
+            case kKindDot: launch_pdl(gett_dot_kernel<double>, grid, 256, 0, s, pdl, ga); break;
+            case kKindDirect: launch_direct<double, 64, 64>(grid, ga, s, pdl); break;
+            default: launch_tiled<double, 64, 64, 8>(grid, ga, s, pdl); break;
         }
     }
     g_launches++;
@@ -1094,14 +1102,15 @@ void launch_gett_group(int kind, int dtype, const GettDesc *descs, int ndesc, in
     launch_group_args(kind, dtype, ga, total_ctas, s);
 }
 
-static void launch_gett_single(const GettDesc &d, int kind, int64_t ctas, int dtype, cudaStream_t s) {
+static void launch_gett_single(const GettDesc &d, int kind, int64_t ctas, int dtype, cudaStream_t s,
+                               bool pdl = true) {
     GroupArgs ga;
     memset(&ga, 0, sizeof(ga));
     ga.descs = nullptr;
     ga.ndesc = 1;
     ga.single = d;
     ga.single.tile_begin = 0;
-    launch_group_args(kind, dtype, ga, ctas, s);
+    launch_group_args(kind, dtype, ga, ctas, s, pdl);
 }
 
 // ---------------------------------------------------------------------------
@@ -1168,6 +1177,7 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
         }
     }
     const int BK = dtype == ROSNET_C64 ? 16 : 8;
+    const int64_t kSMs = num_sms();
     std::vector<GettDesc> cands;
     // the split the heuristic would pick for a 64x64 tiling
     int64_t auto_split = (d.kind == kKindPackF32 || is_direct_kind(d.kind)) ? 1 : d.ksplit;
@@ -1299,6 +1309,17 @@ int64_t reduce_ctas(const GettDesc &d) { return (d.M * d.N + 31) / 32; }
 // ---------------------------------------------------------------------------
 // one pairwise contraction
 // ---------------------------------------------------------------------------
+// The launches of one CUDA-core problem: C = 0 before an order-free split,
+// the GEMM, the fixed-order sum of a stored split.  pdl applies to the first.
+static void launch_sequence(const GettDesc &x, int dtype, cudaStream_t s, bool pdl) {
+    if (x.flags & kFlagAtomic) {
+        launch_gett_single(x, kKindZero, zero_ctas(x), dtype, s, pdl);
+        pdl = true;
+    }
+    launch_gett_single(x, x.kind, desc_ctas(x), dtype, s, pdl);
+    if (x.part) launch_gett_single(x, kKindReduce, reduce_ctas(x), dtype, s);
+}
+
 // A contraction planned once for fixed layouts (offset tables on the device,
 // kernel choice, split-K and tensor-core workspaces) and run for any operand
 // pointers with those layouts.
@@ -1327,10 +1348,16 @@ struct Prepared {
         d.part = part.p;
     }
     bool is_tc() const { return is_packed_kind(d.kind); }
+    // The first launch of the first run follows the kernel that built the
+    // offset tables it reads in its prologue: it is launched in plain stream
+    // order (see launch_pdl).
+    bool tables_fresh = true;
     void run(rosnet_btensor A, rosnet_btensor B, rosnet_btensor C, cudaStream_t s, bool pack_b = true) {
         if (empty) return;
         GettDesc x = d;
         bind_operands(x, A->data, B->data, C->data, A->pstride, B->pstride, C->pstride);
+        const bool pdl = !tables_fresh;
+        tables_fresh = false;
         if (is_tc()) {
             GroupArgs ga;
             memset(&ga, 0, sizeof(ga));
@@ -1338,12 +1365,11 @@ struct Prepared {
             ga.single = x;
             // after an operand swap the kernel's first operand is B
             const bool sw = x.flags & kFlagSwapped;
-            launch_tc_problem(packed_mode(x.kind), x, ga, tcws.p, s, sw ? pack_b : true, sw ? true : pack_b);
+            launch_tc_problem(packed_mode(x.kind), x, ga, tcws.p, s, sw ? pack_b : true, sw ? true : pack_b, {},
+                              pdl);
             return;
         }
-        if (x.flags & kFlagAtomic) launch_gett_single(x, kKindZero, zero_ctas(x), dtype, s);
-        launch_gett_single(x, x.kind, desc_ctas(x), dtype, s);
-        if (x.part) launch_gett_single(x, kKindReduce, reduce_ctas(x), dtype, s);
+        launch_sequence(x, dtype, s, pdl);
     }
 };
 
@@ -1368,11 +1394,14 @@ int check_reduce(const rosnet_opts *opts) {
 
 
 // The same contraction with caller-provided scratch instead of allocations:
-// the offset tables and any split-K partials are placed in `ws` (ws_bytes
-// long, 256-byte aligned).  Returns the scratch bytes the problem needs; if
-// that exceeds ws_bytes nothing is launched.
+// the offset tables and any split-K partials or packed operands are placed in
+// `ws` (ws_bytes long, 256-byte aligned).  Returns the scratch bytes the
+// problem needs; if that exceeds ws_bytes nothing is launched.  The kernel
+// that builds the tables overwrites the previous call's in stream order (it
+// starts only after all earlier work in the stream), and the launch after it
+// waits for it to complete (pdl = false).
 size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa,
-                         const int *axb, rosnet_btensor C, int precision, void *ws,
+                         const int *axb, rosnet_btensor C, int precision, int reduce_mode, void *ws,
                          size_t ws_bytes, cudaStream_t s) {
     GettView v = make_view(A->lay, B->lay, C->lay, naxes, axa, axb);
     if (v.Mtot * v.Ntot == 0) return 0;
@@ -1380,7 +1409,7 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
     memset(&d, 0, sizeof(d));
     const size_t tab_bytes = (table_entries(v) * sizeof(int64_t) + 255) & ~(size_t)255;
     fill_desc_tables(d, v, (const int64_t *)ws);
-    choose_kernel(d, A->dtype, precision);
+    choose_kernel(d, A->dtype, precision, reduce_mode);
     const bool tcp = is_packed_kind(d.kind);
     const size_t extra = tcp ? tc_workspace_bytes(d, packed_mode(d.kind)) : desc_part_bytes(d, A->dtype);
     const size_t need = tab_bytes + extra;
@@ -1392,12 +1421,11 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
         memset(&ga, 0, sizeof(ga));
         ga.ndesc = 1;
         ga.single = d;
-        launch_tc_problem(packed_mode(d.kind), d, ga, (char *)ws + tab_bytes, s, true, true);
+        launch_tc_problem(packed_mode(d.kind), d, ga, (char *)ws + tab_bytes, s, true, true, {}, false);
         return need;
     }
-    d.part = d.ksplit > 1 ? (char *)ws + tab_bytes : nullptr;
-    launch_gett_single(d, d.kind, desc_ctas(d), A->dtype, s);
-    if (d.part) launch_gett_single(d, kKindReduce, reduce_ctas(d), A->dtype, s);
+    d.part = desc_part_bytes(d, A->dtype) ? (char *)ws + tab_bytes : nullptr;
+    launch_sequence(d, A->dtype, s, false);
     return need;
 }
 

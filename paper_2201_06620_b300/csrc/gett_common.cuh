@@ -48,19 +48,28 @@ __device__ __forceinline__ void load_desc(const GroupArgs &g, GettDesc &sd) {
 // stream-serialization attribute may start while the previous kernel in the
 // stream is still running: grid_dep_launch() lets the next kernel begin its
 // prologue, and grid_dep_wait() blocks until the previous kernel has finished
-// and its writes are visible.  Before grid_dep_wait() a kernel reads only
-// data that no kernel writes (descriptors, offset tables), and every CTA
-// calls it before touching operands or results and before it exits, so the
-// completion of a grid still implies the completion of all earlier grids.
-// Without the attribute both are no-ops.
+// and its writes are visible.  Before grid_dep_wait() a kernel reads only its
+// descriptor and offset tables, and every CTA calls it before touching
+// operands or results and before it exits, so the completion of a grid still
+// implies the completion of all earlier grids.  Without the attribute both
+// are no-ops.
+//
+// The prologue's reads are safe only if the descriptor and tables were
+// complete before the previous kernel in the stream started.  Tables uploaded
+// by a copy are; tables written by a kernel (build_table_kernel) are not when
+// that kernel is the one immediately before: the launch that follows a table
+// build therefore passes pdl = false and starts only after the build has
+// completed and its writes are visible.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Launch a kernel with programmatic stream serialization, so that its
-// prologue overlaps the end of the previous kernel in the stream; the kernel
-// calls grid_dep_wait() before it touches operands, workspaces or results.
+// Launch a kernel, with programmatic stream serialization when pdl is set (its
+// prologue then overlaps the end of the previous kernel in the stream; the
+// kernel calls grid_dep_wait() before it touches operands, workspaces or
+// results), else in plain stream order.
 template <typename Kern, typename... Args>
-inline void launch_pdl(Kern kern, dim3 grid, unsigned threads, size_t smem, cudaStream_t s, const Args &...args) {
+inline void launch_pdl(Kern kern, dim3 grid, unsigned threads, size_t smem, cudaStream_t s, bool pdl,
+                       const Args &...args) {
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = grid;
@@ -71,7 +80,7 @@ inline void launch_pdl(Kern kern, dim3 grid, unsigned threads, size_t smem, cuda
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     RN_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
 }
 

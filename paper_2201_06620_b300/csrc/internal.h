@@ -52,6 +52,10 @@ const char *last_error_cstr();
 
 extern std::atomic<int64_t> g_launches;
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// queried once per device).  Grid sizes and the split heuristics scale with it.
+int num_sms();
+
 // Read and clear the device status word written by kernels whose bounded
 // waits gave up (0 = none).
 int32_t take_device_status();

@@ -6,9 +6,9 @@
 // memory and forbids foreign allocations, real-time or embedded callers with
 // a fixed, pre-committed memory budget, and callers on a path where an
 // allocation could block or fail unpredictably.  They pass inputs and an
-// already created output tensor; the scratch the kernels need (offset tables
-// and split-K partial sums) lives in one file-scope device array of fixed
-// size instead of coming from an allocator.
+// already created output tensor; the scratch the kernels need (offset tables,
+// split-K partial sums, packed operands) lives in one file-scope device array
+// of fixed size instead of coming from an allocator.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -21,7 +21,7 @@ void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *a
                      const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc);
 int check_precision(const rosnet_opts *opts, int dtype);
 size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const int *axa,
-                         const int *axb, rosnet_btensor C, int precision, void *ws,
+                         const int *axb, rosnet_btensor C, int precision, int reduce_mode, void *ws,
                          size_t ws_bytes, cudaStream_t s);
 
 namespace {
@@ -35,7 +35,8 @@ void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the
+// process (a device reset would invalidate it; the header says so).
 void *scratch_on_current_device() {
     int dev = 0;
     RN_CHECK_CUDA(cudaGetDevice(&dev));
@@ -47,6 +48,25 @@ void *scratch_on_current_device() {
         g_scratch_addr[dev] = p;
     }
     return g_scratch_addr[dev];
+}
+
+// Bytes [lo, hi) that a tensor's two planes can touch: from its data pointer
+// to one past the last element of its imaginary plane.
+void storage_range(rosnet_btensor t, uintptr_t *lo, uintptr_t *hi) {
+    int64_t last = 0;   // largest element offset within a plane
+    for (int i = 0; i < t->lay.rank; ++i) {
+        const int64_t b = t->lay.block[i], g = t->lay.shape[i] / b;
+        last += (g - 1) * t->lay.gstride[i] + (b - 1) * t->lay.lstride[i];
+    }
+    *lo = (uintptr_t)t->data;
+    *hi = *lo + (uintptr_t)((t->pstride + last + 1) * (int64_t)t->elsize);
+}
+
+bool storage_overlaps(rosnet_btensor x, rosnet_btensor y) {
+    uintptr_t xl, xh, yl, yh;
+    storage_range(x, &xl, &xh);
+    storage_range(y, &yl, &yh);
+    return xl < yh && yl < xh;
 }
 
 }  // namespace
@@ -64,8 +84,8 @@ extern "C" rosnet_status rosnet_tensordot_noalloc(rosnet_btensor A, rosnet_btens
     int axa[kMaxRank], axb[kMaxRank], rc = 0;
     int64_t shc[kMaxRank], blc[kMaxRank];
     check_tensordot(A, B, naxes, axes_a, axes_b, axa, axb, rc, shc, blc);
-    if (C == A || C == B || C->data == A->data || C->data == B->data)
-        RN_FAIL(ROSNET_ERR_INVALID_ARG, "the output may not alias an operand");
+    if (C->lay.numel > 0 && (storage_overlaps(C, A) || storage_overlaps(C, B)))
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "the output's storage overlaps an operand's");
     if (C->dtype != A->dtype) RN_FAIL(ROSNET_ERR_DTYPE, "output dtype differs from the operands'");
     if (C->lay.rank != rc) RN_FAIL(ROSNET_ERR_SHAPE, "output rank does not match the result");
     for (int i = 0; i < rc; ++i) {
@@ -74,8 +94,12 @@ extern "C" rosnet_status rosnet_tensordot_noalloc(rosnet_btensor A, rosnet_btens
             RN_FAIL(ROSNET_ERR_BLOCK_MISMATCH, "output block shape does not match the result");
     }
     const int prec = check_precision(opts, A->dtype);
+    const int red = check_reduce(opts);
+    if (opts && (opts->flags & ROSNET_OPT_AUTOTUNE))
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "autotuning times candidate kernels in buffers of their own; "
+                                        "rosnet_tensordot_noalloc allocates nothing");
     void *ws = scratch_on_current_device();
-    const size_t need = tensordot_into_ws(A, B, naxes, axa, axb, C, prec, ws,
+    const size_t need = tensordot_into_ws(A, B, naxes, axa, axb, C, prec, red, ws,
                                           ROSNET_NOALLOC_SCRATCH_BYTES, s);
     if (need > (size_t)ROSNET_NOALLOC_SCRATCH_BYTES)
         RN_FAIL(ROSNET_ERR_UNSUPPORTED,

@@ -873,7 +873,7 @@ void make_map_f32(CUtensorMap *m, void *base, int64_t rows, int64_t Kpad, int bo
 }
 
 void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, cudaStream_t s, bool pack_a,
-                bool pack_b, const std::function<void()> &before_gemm) {
+                bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
     static bool attr_set = false;
     if (!attr_set) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -891,7 +891,7 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     if (pack_a || pack_b) {
         const int64_t n = (pack_a ? ca : 0) + (pack_b ? cb : 0);
         if (n > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "operands too large to pack");
-        launch_pdl(f32p::f32_pack_kernel, dim3((unsigned)n), 256, 0, s, ga, pa, pb, g.Mpad, g.Npad, g.Kpad,
+        launch_pdl(f32p::f32_pack_kernel, dim3((unsigned)n), 256, 0, s, pdl, ga, pa, pb, g.Mpad, g.Npad, g.Kpad,
                    pack_a ? ca : (int64_t)0, pack_a ? 0 : 1);
         g_launches++;
     }
@@ -903,7 +903,10 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     args.nkt = (int)(g.Kpad / f32p::BK);
     args.kpad = (int)g.Kpad;
     if (before_gemm) before_gemm();
-    launch_pdl(f32p::f32_gemm_kernel, dim3((unsigned)ctas), f32p::NT, f32p::SMEM, s, args);
+    // after a pack the GEMM's prologue may overlap it (it reads only its
+    // descriptor before waiting); with no pack it is the first launch
+    launch_pdl(f32p::f32_gemm_kernel, dim3((unsigned)ctas), f32p::NT, f32p::SMEM, s, pdl || pack_a || pack_b,
+               args);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
 }
@@ -928,14 +931,16 @@ size_t tc_workspace_bytes(const GettDesc &d, int mode) {
 // tc_workspace_bytes(d, mode) bytes, 256-byte aligned.  pack_a / pack_b = false
 // reuse the packed operand already in ws (same operand as the previous call).
 // before_gemm, when set, is called after the pack launches and before the
-// GEMM launch (e.g. to record a timing event around the GEMM alone).
+// GEMM launch (e.g. to record a timing event around the GEMM alone).  pdl =
+// false: the first kernel starts only after everything before it in the
+// stream has completed (it follows a kernel that built its offset tables).
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
-                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm) {
+                       bool pack_a, bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
     const int64_t ctas = d.tiles_m * d.tiles_n;
     if (ctas <= 0) return;
     if (ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one launch");
     if (mode == kPackedModeF32) {
-        launch_f32(ga, d, ws, ctas, s, pack_a, pack_b, before_gemm);
+        launch_f32(ga, d, ws, ctas, s, pack_a, pack_b, before_gemm, pdl);
         return;
     }
     const TcGeom g = tc_geom(d, mode);

@@ -93,6 +93,37 @@ def test_rqc20_amplitude_full_size():
             assert amp_err(got, ref, 20) <= 1e-5
 
 
+# Tensor-core split products on the same workload, against the state vector.
+# 3xTF32 keeps about 22 significant bits per operand and reaches the FP32
+# bar.  3xBF16 keeps about 16 (hi + lo, each 8 bits; the lo*lo product and
+# the residual below lo are dropped, ~2^-18 of each operand per product), and
+# over the amplitude's chain of large steps its error reaches ~2e-5: it is
+# stated against a 1e-4 bound and not used where 1e-5 is required.
+@pytest.mark.parametrize("prec,kind,tol", [(R.PREC_TF32X3, 6, 1e-5), (R.PREC_BF16X3, 7, 1e-4)])
+def test_rqc20_amplitude_split_precisions(prec, kind, tol):
+    circ = W.rqc20_config()
+    psi = oracle.statevector(circ)
+    rng = np.random.default_rng(0)
+    bitstrings = [circ.bitstring] + [rng.integers(0, 2, 20) for _ in range(3)]
+    net0 = W.circuit_network(circ, bitstring=bitstrings[0])
+    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net0.tensors]
+    ngates = len(ts) - 20
+    path = R.path_greedy(ts, net0.labels, net0.out_labels)
+    net = R.Network(ts, net0.labels, net0.out_labels)
+    proj = [R.btensor(np.eye(2, dtype=np.complex64)[b]) for b in (0, 1)]
+    R.timing_drain()
+    for bits in bitstrings:
+        for q in range(20):
+            net.set_tensor(ngates + q, proj[int(bits[q])])
+        got = complex(R.contract(net, path=path, precision=prec, flags=R.OPT_GRAPH | R.OPT_TIMING,
+                                 max_block_entries=256).download())
+        ref = psi[oracle.bitstring_index(bits)]
+        assert amp_err(got, ref, 20) <= tol, (prec, amp_err(got, ref, 20))
+    # the heaviest launch of the plan ran on the tensor cores in this mode
+    kinds = {r[3] for r in R.timing_drain()}
+    assert kinds == {kind}, kinds
+
+
 def test_graph_replay_determinism_and_reuse():
     circ = W.random_circuit(12, 10, 8)
     net = W.circuit_network(circ)
@@ -154,9 +185,10 @@ def test_timing_records_heaviest_launch_under_graph():
         assert amp_err(got, ref, 20) <= 1e-5
     recs = R.timing_drain()
     assert len(recs) == 3
-    for ms, fl, by, kind in recs:
+    for ms, fl, by, kind, ms_whole in recs:
         assert ms > 0 and fl in (8.0 * 4096 * 256 * 256, 16.0 * 4096 * 256 * 256) and by > 0
         assert kind in (2, 3, 10)
+        assert ms_whole >= ms
     assert R.timing_drain() == []
 
 

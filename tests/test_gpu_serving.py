@@ -79,3 +79,78 @@ def test_admission_by_footprint():
     loose.step()
     assert len(loose.running) == 4
     loose.drain()
+
+
+def _tc_steps(circ, k, cid):
+    """Steps of the served (circuit, k) path (the server's path search, seeded
+    with the circuit's index) that are large enough for the
+    tensor-core kernels (max(M, N) >= 128, min(M, N) >= 64, K >= 32)."""
+    import math
+    labels = [(q,) for q in range(circ.n)]
+    ext = [(2,)] * circ.n
+    wire, nl = list(range(circ.n)), circ.n
+    for _, qs, mat in circ.gates:
+        outs = list(range(nl, nl + len(qs)))
+        nl += len(qs)
+        labels.append(tuple(outs + [wire[q] for q in qs]))
+        ext.append(np.asarray(mat).shape)
+        for q, o in zip(qs, outs):
+            wire[q] = o
+    closed = circ.n - k
+    labels += [(wire[q],) for q in range(closed)]
+    ext += [(2,)] * closed
+    out = [wire[q] for q in range(closed, circ.n)]
+    path, _ = R.path_search(labels, ext, out, ntrials=16, seed=cid)
+    e = {x: v for l, s in zip(labels, ext) for x, v in zip(l, s)}
+    live = {i: list(l) for i, l in enumerate(labels)}
+    nid, count = len(labels), 0
+    for a, b in path:
+        la, lb = live.pop(a), live.pop(b)
+        sh = set(la) & set(lb)
+        M = math.prod(e[x] for x in la if x not in sh)
+        N = math.prod(e[x] for x in lb if x not in sh)
+        K = math.prod(e[x] for x in sh)
+        count += max(M, N) >= 128 and min(M, N) >= 64 and K >= 32
+        live[nid] = [x for x in la if x not in sh] + [x for x in lb if x not in sh]
+        nid += 1
+    return count
+
+
+def test_server_tf32x3_vs_oracle():
+    """The served 3xTF32 form (the benchmark's serving default) against the
+    state vector at the FP32 bar, on circuits whose k = 10 queries contain
+    tensor-core-sized steps; alone and in a mix of concurrent queries."""
+    circs = [W.random_circuit(18, 10, 700), W.random_circuit(20, 8, 700), W.random_circuit(16, 8, 701)]
+    psi = [oracle.statevector(c) for c in circs]
+    assert _tc_steps(circs[0], 10, 0) + _tc_steps(circs[1], 10, 1) > 0
+    rng = np.random.default_rng(5)
+    queries = []
+    for i in range(12):
+        ci = i % len(circs)
+        n = circs[ci].n
+        k = 10 if i < 6 else int(rng.integers(0, 11))
+        prefix = tuple(int(b) for b in rng.integers(0, 2, n - k))
+        m = int(rng.integers(1, 2 ** k + 1))
+        suffixes = sorted(int(x) for x in rng.choice(2 ** k, size=m, replace=False))
+        queries.append(Query(circuit=ci, prefix=prefix, k=k, suffixes=suffixes))
+    alone_srv = AmplitudeServer(circs, slots=1, precision=R.PREC_TF32X3)
+    alone = []
+    for q in queries:
+        qq = _copy(q)
+        alone_srv.submit(qq)
+        alone_srv.drain()
+        alone.append(qq.result)
+    mix_srv = AmplitudeServer(circs, slots=3, precision=R.PREC_TF32X3)
+    mixed = [_copy(q) for q in queries]
+    for q in mixed:
+        mix_srv.submit(q)
+    mix_srv.drain()
+    for q, a, m in zip(queries, alone, mixed):
+        n = circs[q.circuit].n
+        base = 0
+        for b in q.prefix:
+            base = (base << 1) | b
+        ref = np.array([psi[q.circuit][(base << q.k) | s] for s in q.suffixes])
+        scale = max(np.abs(ref).max(), 2.0 ** (-n / 2))
+        assert np.abs(a - ref).max() / scale <= 1e-5
+        assert np.abs(m.result - ref).max() / scale <= 1e-5

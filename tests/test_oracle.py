@@ -228,9 +228,21 @@ def test_sqrt_gate_layer_uniform():
 def test_gate_matrices():
     for g in (W.SQRT_X, W.SQRT_Y, W.SQRT_W, W.FSIM):
         np.testing.assert_allclose(g @ g.conj().T, np.eye(len(g)), atol=1e-15)
+    # Pauli matrices written out here, independently of the generator: each
+    # gate is a square root of its rotation axis up to the phase -i
     X = np.array([[0, 1], [1, 0]])
+    Y = np.array([[0, -1j], [1j, 0]])
+    Wm = np.array([[0, (1 - 1j) / np.sqrt(2)], [(1 + 1j) / np.sqrt(2), 0]])   # (X + Y) / sqrt 2
+    np.testing.assert_allclose(Wm @ Wm, np.eye(2), atol=1e-15)
     np.testing.assert_allclose(W.SQRT_X @ W.SQRT_X, -1j * X, atol=1e-15)
-    assert W.FSIM[0, 0] == 1 and W.FSIM[1, 2] == -1j
+    np.testing.assert_allclose(W.SQRT_Y @ W.SQRT_Y, -1j * Y, atol=1e-15)
+    np.testing.assert_allclose(W.SQRT_W @ W.SQRT_W, -1j * Wm, atol=1e-15)
+    # fSim(pi/2, pi/6): |01> <-> -i|10>, phase e^(-i pi/6) on |11>
+    ref = np.zeros((4, 4), dtype=complex)
+    ref[0, 0] = 1
+    ref[1, 2] = ref[2, 1] = -1j
+    ref[3, 3] = np.exp(-1j * np.pi / 6)
+    np.testing.assert_allclose(W.FSIM, ref, atol=1e-15)
 
 
 def test_u_udagger_identity():
