@@ -735,7 +735,7 @@ def run_batch(args):
         outs = R.contract_batch(nets, paths, precision=prec, flags=fl_)
         torch.cuda.synchronize()
         plan_s = time.perf_counter() - t0
-        req, planned, launches = R.plan_stats(nets, paths, precision=prec, flags=fl_)
+        req, planned, launches, _ = R.plan_stats(nets, paths, precision=prec, flags=fl_)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
         for _ in range(args.steps):

@@ -284,9 +284,12 @@ rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes,
  * offset tables, split-K partial sums and packed operands of the tensor-core
  * and packed-FP32 kernels are placed in one fixed device array of
  * ROSNET_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
- * loads the library keeps until the process exits.  A problem needing more
- * scratch is rejected with ROSNET_ERR_UNSUPPORTED before anything is launched
- * (rosnet_last_error() gives the bytes needed).  opts as rosnet_tensordot:
+ * loads the library keeps until the process exits.  When the kernel choice
+ * of rosnet_tensordot would split the contracted range over CTAs with partial
+ * sums that do not fit (and no reduction flag asks for the split), the call
+ * runs unsplit instead; a problem that still needs more scratch is rejected
+ * with ROSNET_ERR_UNSUPPORTED before anything is launched (rosnet_last_error()
+ * gives the bytes needed).  opts as rosnet_tensordot:
  * the precision and the reduction flags are honoured; ROSNET_OPT_AUTOTUNE is
  * refused (UNSUPPORTED), because timing candidate kernels needs buffers of
  * their own.
@@ -492,10 +495,14 @@ rosnet_status rosnet_contract_batch(int32_t nnet, const rosnet_network *nets,
 
 /* For a batch already planned (same arguments as rosnet_contract_batch): the
  * number of path steps requested, of distinct steps planned after merging
- * identical ones, and of launches per call.  INVALID_ARG if not planned yet. */
+ * identical ones, of launches per call, and of operands that the plan's
+ * packed-FP32 and tensor-core steps gather into a packed workspace per call
+ * (an intermediate laid out as a dense K x rows matrix for a packed-FP32
+ * step is read in place and not counted).  Any output may be NULL.
+ * INVALID_ARG if not planned yet. */
 rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
                                 const rosnet_opts *opts, void *stream, int64_t *steps_requested,
-                                int64_t *steps_planned, int64_t *launches);
+                                int64_t *steps_planned, int64_t *launches, int64_t *packed_operands);
 
 /*
  * out = sum of the n tensors ts[0..n) in FP64, in that order (deterministic):

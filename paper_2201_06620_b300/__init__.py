@@ -138,7 +138,7 @@ def lib():
                                                 ctypes.POINTER(vp)]
             L.rosnet_plan_stats.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
                                             ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp, i64p,
-                                            i64p, i64p]
+                                            i64p, i64p, i64p]
             L.rosnet_tensordot_ooc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Opts),
@@ -686,13 +686,15 @@ def contract_batch(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_e
 
 
 def plan_stats(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_entries=0, stream=None):
-    """(steps requested, distinct steps planned, launches per call) of a planned batch."""
+    """(steps requested, distinct steps planned, launches per call, operands
+    gathered into a packed workspace per call) of a planned batch."""
     nets, arr, parr = _batch_args(networks, paths)
     o = _opts(precision, flags, max_block_entries)
-    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(lib().rosnet_plan_stats(len(nets), arr, parr, ctypes.byref(o), _stream(stream),
-                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "rosnet_plan_stats")
-    return a.value, b.value, c.value
+                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "rosnet_plan_stats")
+    return a.value, b.value, c.value, d.value
 
 
 def sync(stream=None):

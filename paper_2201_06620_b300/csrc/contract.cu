@@ -148,6 +148,38 @@ struct Plan {
     }
 };
 
+// A layout of `cur`'s shape whose storage order is `order` (logical axes,
+// outermost first): block-major over the axes in that order, each axis either
+// a whole grid axis or wholly inside the block, the slowest axes in `order`
+// made grid axes until a block holds at most maxblk entries (maxblk <= 0: one
+// block).  Element x then sits at the row-major position of x's coordinates
+// taken in `order`.
+Layout ordered_layout(const Layout &cur, const std::vector<int> &order, int64_t maxblk) {
+    const int r = cur.rank;
+    int64_t sh[kMaxRank], bl[kMaxRank];
+    int64_t bs = 1;
+    for (int j = 0; j < r; ++j) {
+        sh[j] = cur.shape[order[j]];
+        bl[j] = sh[j];
+        bs *= sh[j];
+    }
+    for (int j = 0; j < r && maxblk > 0 && bs > maxblk; ++j) {
+        bs /= sh[j] > 0 ? sh[j] : 1;
+        bl[j] = 1;
+    }
+    Layout P;
+    P.init(r, sh, bl);
+    Layout L = P;
+    for (int j = 0; j < r; ++j) {
+        const int x = order[j];
+        L.shape[x] = P.shape[j];
+        L.block[x] = P.block[j];
+        L.gstride[x] = P.gstride[j];
+        L.lstride[x] = P.lstride[j];
+    }
+    return L;
+}
+
 // Cached plans.  Deliberately never destroyed at process exit: by then the
 // CUDA runtime or an injected allocator (e.g. one implemented in Python) may
 // already be gone.  rosnet_release_plans() frees them explicitly.
@@ -453,6 +485,65 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             S.last_use = end_wave;   // copied into the output after the last wave
         }
     }
+    // Storage order of the intermediates read by the packed FP32 kernel.  That
+    // kernel loads its tiles of an operand viewed as a dense K x rows matrix
+    // straight from memory with TMA; an intermediate stored with its
+    // contracted axes outermost (in the order of the other operand's) and its
+    // free axes innermost is such a matrix, so no pack pass runs for it.  The
+    // step that produces it writes that order through its output offset
+    // tables at no cost: the permutation of a block pair (Sec. II-C step 3) is
+    // folded into the producer's stores and the consumer's tensor map.  An
+    // intermediate takes the order of its first packed consumer; its blocks
+    // become the innermost axes in that order (the slowest ones turned into
+    // grid axes until a block holds at most max_block_entries).
+    if (plan->dtype == ROSNET_C64) {
+        const int red0 = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
+                         : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
+                         : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
+        std::vector<char> laid(plan->steps.size(), 0);
+        auto axis_stride = [](const Layout &L, int x) { return L.block[x] == 1 ? L.gstride[x] : L.lstride[x]; };
+        for (size_t g = 0; g < plan->steps.size(); ++g) {
+            const Step &S = plan->steps[g];
+            const Layout &la = lay_of(S.ga), &lb = lay_of(S.gb);
+            int64_t K = 1;
+            for (int i = 0; i < S.naxes; ++i) K *= la.shape[S.axa[i]];
+            if (K == 0 || la.numel == 0 || lb.numel == 0) continue;
+            GettDesc t;
+            memset(&t, 0, sizeof(t));
+            t.M = la.numel / K;
+            t.N = lb.numel / K;
+            t.K = K;
+            choose_kernel(t, plan->dtype, prec, red0);
+            if (t.kind != kKindPackF32) continue;
+            // order of the contracted pairs: as given, or a leaf operand's own
+            // (outermost first), which the intermediate side then follows
+            std::vector<int> pairs(S.naxes);
+            for (int i = 0; i < S.naxes; ++i) pairs[i] = i;
+            if ((S.ga < 0) != (S.gb < 0)) {
+                const Layout &leaf = S.ga < 0 ? la : lb;
+                const std::vector<int> &ax = S.ga < 0 ? S.axa : S.axb;
+                std::stable_sort(pairs.begin(), pairs.end(), [&](int i, int j) {
+                    return axis_stride(leaf, ax[i]) > axis_stride(leaf, ax[j]);
+                });
+            }
+            for (int side = 0; side < 2; ++side) {
+                const int64_t op = side ? S.gb : S.ga;
+                if (op < 0 || laid[op] || plan->steps[op].arena_off == SIZE_MAX) continue;
+                const std::vector<int> &ax = side ? S.axb : S.axa;
+                Layout &L = plan->steps[op].lay;
+                std::vector<char> contracted(L.rank, 0);
+                std::vector<int> order;
+                for (int i : pairs) {
+                    order.push_back(ax[i]);
+                    contracted[ax[i]] = 1;
+                }
+                for (int x = 0; x < L.rank; ++x)
+                    if (!contracted[x]) order.push_back(x);
+                L = ordered_layout(L, order, maxblk);
+                laid[op] = 1;
+            }
+        }
+    }
     // arena: every step not written straight into an output, packed by
     // lifetime with a sweep over the waves: a step's bytes are reserved from
     // the wave that writes it to the last wave that reads it, then returned to
@@ -561,6 +652,10 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         memset(&S.desc, 0, sizeof(S.desc));
         fill_desc_tables(S.desc, views[g], dtab + S.table_off[0], dtab + S.table_off[1],
                          dtab + S.table_off[2]);
+        // leaves change address from call to call: never read in place by a
+        // tensor map that a captured graph would keep
+        if (S.ga < 0) S.desc.flags &= ~kFlagADense;
+        if (S.gb < 0) S.desc.flags &= ~kFlagBDense;
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
         const bool cuda_core_gemm =
@@ -768,8 +863,16 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
                 ga.ndesc = 1;
                 std::function<void()> hook;
                 if (th) hook = [&]() { rec(1); };
-                launch_tc_problem(packed_mode(L.kind), P.slot_desc[L.first], ga,
-                                  (char *)P.tcws.p + L.tc_ws_off, s, true, true, hook);
+                // the host copy carries the operand addresses that tensor maps
+                // over operands read in place are encoded with (only arena
+                // intermediates are flagged dense: their addresses are fixed
+                // for the life of the plan, so a captured graph stays valid)
+                const int st = P.desc_step[L.first];
+                const Step &S = P.steps[st];
+                GettDesc x = P.slot_desc[L.first];
+                bind_operands(x, ptr_of(S.ga), ptr_of(S.gb), ptr_of(st), pstride_of(S.ga), pstride_of(S.gb),
+                              pstride_of(st));
+                launch_tc_problem(packed_mode(L.kind), x, ga, (char *)P.tcws.p + L.tc_ws_off, s, true, true, hook);
             } else {
                 launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
             }
@@ -924,7 +1027,7 @@ rosnet_status rosnet_contract_batch(int32_t nnet, const rosnet_network *nets, co
 
 rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
                                 const rosnet_opts *opts, void *stream, int64_t *steps_requested,
-                                int64_t *steps_planned, int64_t *launches) {
+                                int64_t *steps_planned, int64_t *launches, int64_t *packed_operands) {
     RN_API_BEGIN
     if (nnet < 1 || !nets || !paths) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no networks");
     for (int i = 0; i < nnet; ++i) precheck_network(&nets[i], &paths[i]);
@@ -940,6 +1043,18 @@ rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const 
     if (steps_requested) *steps_requested = it->second->steps_requested;
     if (steps_planned) *steps_planned = (int64_t)it->second->steps.size();
     if (launches) *launches = (int64_t)it->second->launches.size();
+    if (packed_operands) {
+        int64_t n = 0;
+        const Plan &P = *it->second;
+        for (const auto &L : P.launches) {
+            if (!is_packed_kind(L.kind)) continue;
+            const int f = P.slot_desc[L.first].flags;
+            const bool f32 = L.kind == kKindPackF32;
+            n += (f32 && (f & kFlagADense)) ? 0 : 1;
+            n += (f32 && (f & kFlagBDense)) ? 0 : 1;
+        }
+        *packed_operands = n;
+    }
     return ROSNET_OK;
     RN_API_END
 }

@@ -182,8 +182,20 @@ void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tm, const i
     d.M = v.Mtot;
     d.N = v.Ntot;
     d.K = v.Ktot;
+    // digits whose strides in one tensor form a row-major sequence starting at
+    // `base` (the table of that class is then i -> i * base)
+    auto row_major = [](const ModeList &ml, int which, int64_t base) {
+        int64_t e = base;
+        for (int i = ml.n - 1; i >= 0; --i) {
+            if ((which ? ml.m[i].s1 : ml.m[i].s0) != e) return false;
+            e *= ml.m[i].ext;
+        }
+        return true;
+    };
+    const bool a_dense = row_major(v.M, 0, 1) && row_major(v.K, 0, v.Mtot);
+    const bool b_dense = row_major(v.N, 0, 1) && row_major(v.K, 1, v.Ntot);
     d.flags = (v.a_m_fast ? kFlagAMFast : 0) | (v.b_n_fast ? kFlagBNFast : 0) |
-              (v.c_n_fast ? kFlagCNFast : 0);
+              (v.c_n_fast ? kFlagCNFast : 0) | (a_dense ? kFlagADense : 0) | (b_dense ? kFlagBDense : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -925,7 +937,9 @@ static void swap_operands(GettDesc &d) {
     std::swap(d.M, d.N);
     int f = d.flags;
     d.flags = ((f & kFlagAMFast) ? kFlagBNFast : 0) | ((f & kFlagBNFast) ? kFlagAMFast : 0) |
-              ((f & kFlagCNFast) ? 0 : kFlagCNFast) | ((f & kFlagSwapped) ? 0 : kFlagSwapped);
+              ((f & kFlagCNFast) ? 0 : kFlagCNFast) | ((f & kFlagSwapped) ? 0 : kFlagSwapped) |
+              ((f & kFlagADense) ? kFlagBDense : 0) | ((f & kFlagBDense) ? kFlagADense : 0) |
+              (f & kFlagAtomic);
 }
 
 constexpr int kTiledStages = 3;
@@ -1406,14 +1420,20 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
     GettView v = make_view(A->lay, B->lay, C->lay, naxes, axa, axb);
     if (v.Mtot * v.Ntot == 0) return 0;
     GettDesc d;
-    memset(&d, 0, sizeof(d));
     const size_t tab_bytes = (table_entries(v) * sizeof(int64_t) + 255) & ~(size_t)255;
-    fill_desc_tables(d, v, (const int64_t *)ws);
-    choose_kernel(d, A->dtype, precision, reduce_mode);
-    const bool tcp = is_packed_kind(d.kind);
-    const size_t extra = tcp ? tc_workspace_bytes(d, packed_mode(d.kind)) : desc_part_bytes(d, A->dtype);
-    const size_t need = tab_bytes + extra;
+    auto plan = [&](int red) {
+        memset(&d, 0, sizeof(d));
+        fill_desc_tables(d, v, (const int64_t *)ws);
+        choose_kernel(d, A->dtype, precision, red);
+        return tab_bytes + (is_packed_kind(d.kind) ? tc_workspace_bytes(d, packed_mode(d.kind))
+                                                   : desc_part_bytes(d, A->dtype));
+    };
+    size_t need = plan(reduce_mode);
+    // an automatic split of the contracted range whose partial sums do not
+    // fit runs unsplit instead (one CTA per output tile over all pairs)
+    if (need > ws_bytes && reduce_mode == kReduceAuto && d.ksplit > 1) need = plan(kReduceSequential);
     if (need > ws_bytes) return need;
+    const bool tcp = is_packed_kind(d.kind);
     launch_build_tables(v, (int64_t *)ws, s);
     bind_operands(d, A->data, B->data, C->data, A->pstride, B->pstride, C->pstride);
     if (tcp) {

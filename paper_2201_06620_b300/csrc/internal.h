@@ -186,6 +186,11 @@ enum : int32_t {
     kFlagCNFast = 4,
     kFlagSwapped = 8,   // roles of A and B exchanged (the kernel computes C^T = B^T A^T)
     kFlagAtomic = 16,   // split-K ranges add into C with atomics (C zeroed first)
+    // A (B) is stored as a dense K x M (K x N) matrix in each plane: offAM[m]
+    // = m and offAK[k] = k * M (offBN[n] = n, offBK[k] = k * N), so the packed
+    // FP32 GEMM can load its tiles straight from it with TMA (no pack pass)
+    kFlagADense = 32,
+    kFlagBDense = 64,
 };
 
 // How the partial products of the matched block pairs of an output tile are

@@ -146,6 +146,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(su32(bar))
+        : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
 // 512 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -458,14 +467,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 // ---------------------------------------------------------------------------
 // 3. plain FP32 products on the CUDA cores from packed operands
 // ---------------------------------------------------------------------------
-// The same two-kernel scheme for the FP32 precision: f32_pack_kernel gathers
-// each operand once through its offset tables into [2 planes][Kpad][Rpad]
-// arrays (rows contiguous), and f32_gemm_kernel streams (BM or BN) x BK boxes
-// of them into a ring of shared-memory stages with TMA tensor copies, so the
-// inner loop is FFMAs and shared-memory loads only: no per-element address
-// arithmetic, no offset-table reads.  Each complex product is the four real
-// FP32 products of the definition, accumulated in FP32 registers over every
-// matched block pair of the tile (Sec. II-C steps 2-4) in a fixed order.
+// The FP32 precision: f32_gemm_kernel streams (BM or BN) x BK boxes of each
+// operand, viewed as a [2 planes][K][rows] array (rows contiguous), into a
+// ring of shared-memory stages with 3-D TMA tensor copies, so the inner loop
+// is FFMAs and shared-memory loads only: no per-element address arithmetic,
+// no offset-table reads.  An operand already stored that way (a dense K x rows
+// matrix in each plane, kFlagADense / kFlagBDense: the network executor lays
+// out the intermediates that feed this kernel so) is read in place, the
+// index permutation of the step folded into the tensor map; any other layout
+// is first gathered once through its offset tables by f32_pack_kernel into a
+// padded [2 planes][Kpad][Rpad] workspace.  Each complex product is the four
+// real FP32 products of the definition, accumulated in FP32 registers over
+// every matched block pair of the tile (Sec. II-C steps 2-4) in a fixed
+// order.
 namespace f32p {
 
 #ifndef ROSNET_F32P_BM
@@ -495,10 +509,9 @@ constexpr size_t RING_BYTES = (size_t)STAGES * STAGE_BYTES;
 constexpr size_t SMEM = (RING_BYTES > EPI_BYTES ? RING_BYTES : EPI_BYTES) + 128;
 
 struct Args {
-    CUtensorMap mapA, mapB;   // packed operands as 2-D {Rpad, 2 * Kpad} FP32 arrays
+    CUtensorMap mapA, mapB;   // operands as 3-D {rows, K, 2 planes} FP32 arrays
     GroupArgs g;              // the problem (C pointer, C offset tables, M, N, K, tiles)
     int32_t nkt;              // k-stages (Kpad / BK)
-    int32_t kpad;             // rows of one plane
 };
 
 // out[p][k][r] = operand(r, k) plane p (0 outside R x K), for A (the first
@@ -602,10 +615,10 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
         tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
         const uint32_t sa = tc::su32(stg + (size_t)s * 2 * (PA + PB));
         const uint32_t sb = sa + 2u * PA * 4u;
-        tc::tma_load_2d(sa, &p.mapA, m0, kt * BK, &full_bar[s]);
-        tc::tma_load_2d(sa + PA * 4u, &p.mapA, m0, p.kpad + kt * BK, &full_bar[s]);
-        tc::tma_load_2d(sb, &p.mapB, n0, kt * BK, &full_bar[s]);
-        tc::tma_load_2d(sb + PB * 4u, &p.mapB, n0, p.kpad + kt * BK, &full_bar[s]);
+        tc::tma_load_3d(sa, &p.mapA, m0, kt * BK, 0, &full_bar[s]);
+        tc::tma_load_3d(sa + PA * 4u, &p.mapA, m0, kt * BK, 1, &full_bar[s]);
+        tc::tma_load_3d(sb, &p.mapB, n0, kt * BK, 0, &full_bar[s]);
+        tc::tma_load_3d(sb + PB * 4u, &p.mapB, n0, kt * BK, 1, &full_bar[s]);
     };
     int issued = 0;
     if (tid == 0)
@@ -859,17 +872,28 @@ F32Geom f32_geom(const GettDesc &d) {
     return g;
 }
 
-// 2-D map over one packed [2 planes][Kpad][rows] FP32 operand: {rows, 2 Kpad},
-// boxes of `box_rows` rows x BK k (no swizzle: the GEMM reads rows as float4).
-void make_map_f32(CUtensorMap *m, void *base, int64_t rows, int64_t Kpad, int box_rows) {
-    cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)(2 * Kpad)};
-    cuuint64_t strides[1] = {(cuuint64_t)(rows * 4)};
-    cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)f32p::BK};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+// 3-D map over one FP32 operand viewed as [2 planes][K][rows]: {rows, K, 2}
+// with the given row and plane strides (elements), boxes of `box_rows` rows x
+// BK k x 1 plane (no swizzle: the GEMM reads rows as float4).  Boxes reaching
+// past rows or K are filled with zeros.
+void make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t K, int64_t row_stride,
+                  int64_t plane_stride, int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)rows, (cuuint64_t)K, 2};
+    cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 4), (cuuint64_t)(plane_stride * 4)};
+    cuuint32_t box[3] = {(cuuint32_t)box_rows, (cuuint32_t)f32p::BK, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) RN_FAIL(ROSNET_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
+// Whether an operand flagged dense can be read in place by a TMA map: its
+// planes start on 16-byte boundaries and its row and plane strides are
+// multiples of 16 bytes (every other limit is far above these sizes).
+bool tma_direct_ok(bool dense, const void *p, int64_t rows, int64_t K, int64_t plane) {
+    return dense && p != nullptr && ((uintptr_t)p & 15) == 0 && rows % 4 == 0 && plane % 4 == 0 &&
+           rows < (int64_t(1) << 31) && K < (int64_t(1) << 31) && plane < (int64_t(1) << 37);
 }
 
 void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, cudaStream_t s, bool pack_a,
@@ -883,6 +907,12 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     const F32Geom g = f32_geom(d);
     float *pa = (float *)ws;
     float *pb = pa + 2 * g.Mpad * g.Kpad;
+    // operands stored as dense K x rows matrices are read in place; the others
+    // are packed (unless the caller says the workspace already holds them)
+    const bool da = tma_direct_ok(d.flags & kFlagADense, d.a, d.M, d.K, d.a_plane);
+    const bool db = tma_direct_ok(d.flags & kFlagBDense, d.b, d.N, d.K, d.b_plane);
+    pack_a = pack_a && !da;
+    pack_b = pack_b && !db;
     const int64_t kt = (g.Kpad + f32p::PKT - 1) / f32p::PKT;
     const int64_t ca = (g.Mpad / 32) * kt, cb = (g.Npad / 32) * kt;
     if (ca > 0x7fffffffLL || cb > 0x7fffffffLL || 2 * g.Kpad > 0x7fffffffLL || g.Mpad > 0x7fffffffLL ||
@@ -897,11 +927,12 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     }
     f32p::Args args;
     memset(&args, 0, sizeof(args));
-    make_map_f32(&args.mapA, pa, g.Mpad, g.Kpad, f32p::BM);
-    make_map_f32(&args.mapB, pb, g.Npad, g.Kpad, f32p::BN);
+    if (da) make_map_f32(&args.mapA, d.a, d.M, d.K, d.M, d.a_plane, f32p::BM);
+    else make_map_f32(&args.mapA, pa, g.Mpad, g.Kpad, g.Mpad, g.Mpad * g.Kpad, f32p::BM);
+    if (db) make_map_f32(&args.mapB, d.b, d.N, d.K, d.N, d.b_plane, f32p::BN);
+    else make_map_f32(&args.mapB, pb, g.Npad, g.Kpad, g.Npad, g.Npad * g.Kpad, f32p::BN);
     args.g = ga;
     args.nkt = (int)(g.Kpad / f32p::BK);
-    args.kpad = (int)g.Kpad;
     if (before_gemm) before_gemm();
     // after a pack the GEMM's prologue may overlap it (it reads only its
     // descriptor before waiting); with no pack it is the first launch

@@ -35,7 +35,7 @@ def test_sliced_20_qubit_amplitude(dtype, tol):
     total = complex(R.sum_fp64(outs).download())
     ref = oracle.amplitude_sv(circ)
     assert abs(total - ref) / max(abs(ref), 2.0 ** -10) <= tol
-    req, planned, launches = R.plan_stats(nets, [path] * len(nets), flags=R.OPT_GRAPH)
+    req, planned, launches, _ = R.plan_stats(nets, [path] * len(nets), flags=R.OPT_GRAPH)
     assert req == 256 * (len(net.tensors) - 1)
     assert planned < req / 4          # slices share every step no cut bond reaches
     assert launches < 80              # grouped by dependency wave, not per step

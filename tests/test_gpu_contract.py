@@ -91,6 +91,15 @@ def test_rqc20_amplitude_full_size():
                                  max_block_entries=256, flags=flags)
             ref = psi[oracle.bitstring_index(bits)]
             assert amp_err(got, ref, 20) <= 1e-5
+    # the two 4096 x 256 x 256 steps run on the packed FP32 kernel with both
+    # operands (intermediates laid out for it) read in place: no pack pass
+    net = W.circuit_network(circ, bitstring=circ.bitstring)
+    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+    path = R.path_greedy(ts, net.labels, net.out_labels)
+    gn = R.Network(ts, net.labels, net.out_labels)
+    R.contract(gn, path=path, flags=R.OPT_GRAPH, max_block_entries=256)
+    _, _, _, packed = R.plan_stats([gn], [path], flags=R.OPT_GRAPH, max_block_entries=256)
+    assert packed == 0, packed
 
 
 # Tensor-core split products on the same workload, against the state vector.

@@ -1,5 +1,6 @@
-"""GPU parity of the packed FP32 path (operands gathered once into dense
-panels, then TMA-fed FFMA tiles) against the complex128 CPU oracle.
+"""GPU parity of the packed FP32 path (TMA-fed FFMA tiles; an operand stored
+as a dense K x rows matrix is read in place, any other is first gathered once
+into a dense panel) against the complex128 CPU oracle.
 
 Large complex64 contractions at the default (plain FP32) precision take this
 path; the bar is the FP32 one, relative Frobenius error <= 1e-5.  Shapes span
@@ -56,7 +57,7 @@ def test_blocked_permuted_qubit_tensors(trial):
     A = R.btensor(a, prob["block_a"])
     B = R.btensor(b, prob["block_b"])
     C, n = _launches(lambda: R.tensordot(A, B, prob["axes_a"], prob["axes_b"]))
-    assert n == _tiled_launches() + 1, n
+    assert n in (_tiled_launches(), _tiled_launches() + 1), n   # GEMM, after a pack unless both are dense
     ref = oracle.tensordot(a, b, prob["axes_a"], prob["axes_b"])
     assert oracle.rel_frobenius(C.download(), ref) <= 1e-5, trial
 
@@ -70,3 +71,32 @@ def test_deterministic_and_sequential_mode():
     c3 = R.tensordot(A, B, [1], [0], flags=R.REDUCE_SEQUENTIAL).download()
     assert np.array_equal(c1, c2) and np.array_equal(c1, c3)
     assert oracle.rel_frobenius(c1, oracle.tensordot(a, b, [1], [0])) <= 1e-5
+
+
+# Operands stored as dense K x rows matrices are read in place by the GEMM's
+# tensor maps (no pack launch); the others are packed.  (a layout, b layout,
+# axes, pack launches expected): "km" = (K, M) storage, "mk" = (M, K).
+@pytest.mark.parametrize("mnk", [(1000, 700, 200), (4096, 256, 256), (1024, 520, 131)])
+@pytest.mark.parametrize("la,lb,packs", [("km", "kn", 0), ("km", "nk", 1), ("mk", "kn", 1), ("mk", "nk", 1)])
+def test_dense_operands_read_in_place(mnk, la, lb, packs):
+    M, N, K = mnk
+    a = W.complex_normal((K, M) if la == "km" else (M, K), 61).astype(np.complex64)
+    b = W.complex_normal((K, N) if lb == "kn" else (N, K), 62).astype(np.complex64)
+    ax_a = [0] if la == "km" else [1]
+    ax_b = [0] if lb == "kn" else [1]
+    A, B = R.btensor(a), R.btensor(b)
+    C, n = _launches(lambda: R.tensordot(A, B, ax_a, ax_b))
+    assert n == _tiled_launches() + packs, (n, packs)
+    ref = oracle.tensordot(a, b, ax_a, ax_b)
+    assert oracle.rel_frobenius(C.download(), ref) <= 1e-5
+
+
+def test_dense_operand_unaligned_rows_is_packed():
+    """A dense K x 998 operand: rows of 998 floats are not a whole number of
+    16-byte units, which a tensor map cannot stride over; it is packed."""
+    a = W.complex_normal((256, 998), 63).astype(np.complex64)
+    b = W.complex_normal((256, 640), 64).astype(np.complex64)
+    A, B = R.btensor(a), R.btensor(b)
+    C, n = _launches(lambda: R.tensordot(A, B, [0], [0]))
+    assert n == _tiled_launches() + 1, n
+    assert oracle.rel_frobenius(C.download(), oracle.tensordot(a, b, [0], [0])) <= 1e-5
