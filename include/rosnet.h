@@ -443,12 +443,13 @@ rosnet_status rosnet_timing_drain(double *ms, double *ms_whole, double *flops, d
 /*
  * Autotuner decisions (ROSNET_OPT_AUTOTUNE) as text, so that a later process
  * can plan with the same kernels without timing them again.  One line per
- * tuned problem shape, seven integers separated by spaces:
- *     dtype key_flags M N K kind ksplit
+ * tuned problem shape, eight integers separated by spaces:
+ *     dtype key_flags M N K kind ksplit schedule
  * (kind: 2 = 64x64 tiles, 3 = 128x64, 11 = 256x16, 12 = 128x32, 13 / 14 =
  * direct 64x64 / 256x16 (one 32-long contracted range per CTA, so ksplit =
  * ceil(K / 32)), 10 = packed FP32; ksplit = number of contracted-index
- * ranges, 1 = none).
+ * ranges, 1 = none; schedule = 1 for the packed FP32 GEMM's stream-K
+ * schedule, else 0; a line without it is read with schedule 0).
  * rosnet_tune_export writes the text, NUL-terminated, into buf when cap is
  * large enough; *len always receives the bytes needed (terminator included).
  * rosnet_tune_import merges the lines of a NUL-terminated text into the

@@ -24,6 +24,7 @@
 #include <sstream>
 #include <string>
 #include <random>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -38,6 +39,7 @@ int check_precision(const rosnet_opts *opts, int dtype);
 int64_t reduce_ctas(const GettDesc &d);
 void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
+void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {},
                        bool pdl = true);
@@ -605,9 +607,14 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     // classes with equal digits -- the same step in every slice of a network,
     // repeated gate contractions -- share one copy.
     static_assert(sizeof(Mode) == 3 * sizeof(int64_t), "a digit list is compared as bytes");
+    // The large class of a low-arithmetic-intensity step (gate kernel) is
+    // kept as a mode record instead of a table as large as the tensor.
+    const int red = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
+                    : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
+                    : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
     std::vector<GettView> views(plan->steps.size());
     std::unordered_map<std::string, int64_t> table_at;   // digits -> first entry
-    std::vector<std::pair<size_t, int>> owners;          // (step, class) that fills each table
+    std::vector<std::tuple<size_t, int, bool>> owners;   // (step, class, record) that fills each table
     int64_t tab_entries = 0;
     auto class_of = [&](const GettView &v, int c) -> std::pair<const ModeList *, int64_t> {
         return c == 0 ? std::make_pair(&v.M, v.Mtot) : c == 1 ? std::make_pair(&v.N, v.Ntot)
@@ -616,23 +623,29 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     for (size_t g = 0; g < plan->steps.size(); ++g) {
         Step &S = plan->steps[g];
         views[g] = make_view(lay_of(S.ga), lay_of(S.gb), S.lay, S.naxes, S.axa.data(), S.axb.data());
+        const int rec = gate_record_class(views[g], plan->dtype, prec, red,
+                                          (S.ga < 0 ? kFlagADense | kFlagAMVec : 0) |
+                                              (S.gb < 0 ? kFlagBDense | kFlagBNVec : 0));
         for (int c = 0; c < 3; ++c) {
             const auto mt = class_of(views[g], c);
-            std::string key((const char *)&mt.second, sizeof(int64_t));
+            const bool is_rec = c == rec;
+            std::string key(is_rec ? "R" : "T");
+            key.append((const char *)&mt.second, sizeof(int64_t));
             key.append((const char *)mt.first->m, (size_t)mt.first->n * sizeof(Mode));
             auto ins = table_at.emplace(std::move(key), tab_entries);
             if (ins.second) {
-                owners.push_back({g, c});
-                tab_entries += 2 * mt.second;
+                owners.emplace_back(g, c, is_rec);
+                tab_entries += is_rec ? record_entries(*mt.first) : 2 * mt.second;
             }
             S.table_off[c] = ins.first->second;
         }
     }
     std::vector<int64_t> htab(std::max<int64_t>(tab_entries, 1));
     for (const auto &o : owners) {
-        const auto mt = class_of(views[o.first], o.second);
-        int64_t *t = htab.data() + plan->steps[o.first].table_off[o.second];
-        host_table(*mt.first, mt.second, t, t + mt.second);
+        const auto mt = class_of(views[std::get<0>(o)], std::get<1>(o));
+        int64_t *t = htab.data() + plan->steps[std::get<0>(o)].table_off[std::get<1>(o)];
+        if (std::get<2>(o)) host_mode_record(*mt.first, t);
+        else host_table(*mt.first, mt.second, t, t + mt.second);
     }
     plan->tables = DevBuf(htab.size() * sizeof(int64_t), s);
     plan->arena = DevBuf(std::max<size_t>(plan->arena_bytes, 256), s);
@@ -643,9 +656,6 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     const int64_t *dtab = (const int64_t *)plan->tables.p;
     std::map<std::pair<int, int>, std::vector<int>> groups;
     std::map<int, std::vector<int>> split_of_wave, atomic_of_wave;
-    const int red = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
-                    : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
-                    : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
     for (size_t g = 0; g < plan->steps.size(); ++g) {
         Step &S = plan->steps[g];
         const int st = (int)g;
@@ -654,8 +664,8 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
                          dtab + S.table_off[2]);
         // leaves change address from call to call: never read in place by a
         // tensor map that a captured graph would keep
-        if (S.ga < 0) S.desc.flags &= ~kFlagADense;
-        if (S.gb < 0) S.desc.flags &= ~kFlagBDense;
+        if (S.ga < 0) S.desc.flags &= ~(kFlagADense | kFlagAMVec);
+        if (S.gb < 0) S.desc.flags &= ~(kFlagBDense | kFlagBNVec);
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
         const bool cuda_core_gemm =
@@ -739,7 +749,10 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             add_launch(kKindReduce, split_of_wave[w], 1);
     }
     plan->slot_desc = std::move(slot_desc);
-    if (tc_bytes) plan->tcws = DevBuf(tc_bytes, s);
+    if (tc_bytes) {   // zeroed once: the stream-K tile counters start at zero
+        plan->tcws = DevBuf(tc_bytes, s);
+        RN_CHECK_CUDA(cudaMemsetAsync(plan->tcws.p, 0, tc_bytes, s));
+    }
     // the launch with the most algorithmic work (8 M N K per complex GEMM)
     {
         const double el2d = 2.0 * (plan->dtype == ROSNET_C64 ? 4 : 8);

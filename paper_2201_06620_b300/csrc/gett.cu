@@ -171,6 +171,54 @@ void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *t) {
     fill_desc_tables(d, v, t, t + 2 * v.Mtot, t + 2 * v.Mtot + 2 * v.Ntot);
 }
 
+void host_mode_record(const ModeList &ml, int64_t *out) {
+    out[0] = ml.n;
+    for (int j = 0; j < ml.n; ++j) {
+        out[1 + 3 * j] = ml.m[j].ext;
+        out[2 + 3 * j] = ml.m[j].s0;
+        out[3 + 3 * j] = ml.m[j].s1;
+    }
+}
+
+__global__ void write_record_kernel(ModeList ml, int64_t *__restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        out[0] = ml.n;
+        for (int j = 0; j < ml.n; ++j) {
+            out[1 + 3 * j] = ml.m[j].ext;
+            out[2 + 3 * j] = ml.m[j].s0;
+            out[3 + 3 * j] = ml.m[j].s1;
+        }
+    }
+}
+
+TableLayout table_layout(const GettView &v, int record_class) {
+    TableLayout L;
+    L.record_class = record_class;
+    const ModeList *ml[3] = {&v.M, &v.N, &v.K};
+    const int64_t tot[3] = {v.Mtot, v.Ntot, v.Ktot};
+    int64_t o = 0;
+    for (int c = 0; c < 3; ++c) {
+        L.off[c] = o;
+        o += c == record_class ? record_entries(*ml[c]) : 2 * tot[c];
+    }
+    L.entries = o;
+    return L;
+}
+
+void launch_build_tables(const GettView &v, const TableLayout &L, int64_t *t, cudaStream_t s) {
+    const ModeList *ml[3] = {&v.M, &v.N, &v.K};
+    const int64_t tot[3] = {v.Mtot, v.Ntot, v.Ktot};
+    for (int c = 0; c < 3; ++c) {
+        if (c == L.record_class) {
+            write_record_kernel<<<1, 32, 0, s>>>(*ml[c], t + L.off[c]);
+            g_launches++;
+            RN_CHECK_CUDA(cudaGetLastError());
+        } else {
+            launch_table(*ml[c], tot[c], t + L.off[c], t + L.off[c] + tot[c], s);
+        }
+    }
+}
+
 void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tm, const int64_t *tn,
                       const int64_t *tk) {
     d.offAM = tm;
@@ -194,8 +242,33 @@ void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tm, const i
     };
     const bool a_dense = row_major(v.M, 0, 1) && row_major(v.K, 0, v.Mtot);
     const bool b_dense = row_major(v.N, 0, 1) && row_major(v.K, 1, v.Ntot);
+    // vector access (gett_gate_kernel): the innermost mode of a class is a
+    // unit-stride run whose extent is a multiple of 8, and every other offset
+    // of the tensor involved is a multiple of 4 elements (16 bytes)
+    auto mult4 = [](const ModeList &ml, int which, int skip_inner) {
+        for (int i = 0; i < ml.n - skip_inner; ++i)
+            if ((which ? ml.m[i].s1 : ml.m[i].s0) % 4) return false;
+        return true;
+    };
+    auto run8 = [&](const ModeList &ml, int which, int64_t stride) {
+        return ml.n > 0 && (which ? ml.m[ml.n - 1].s1 : ml.m[ml.n - 1].s0) == stride &&
+               ml.m[ml.n - 1].ext % 8 == 0 && mult4(ml, which, 1);
+    };
+    // C with class `in` innermost and dense (offsets 0 .. tot - 1), the
+    // innermost mode of class `out` right above it in runs of 8
+    auto inner = [&](const ModeList &in, int64_t tot, const ModeList &out) {
+        const bool dense = in.n == 0 || (in.n == 1 && in.m[0].s1 == 1);
+        return dense && (tot == 1 || tot == 2 || tot == 4) && run8(out, 1, tot);
+    };
+    int vec = 0;
+    if (run8(v.M, 0, 1) && mult4(v.K, 0, 0)) vec |= kFlagAMVec;
+    if (run8(v.N, 0, 1) && mult4(v.K, 1, 0)) vec |= kFlagBNVec;
+    if (run8(v.M, 1, 1) && mult4(v.N, 1, 0)) vec |= kFlagCMVec;
+    if (run8(v.N, 1, 1) && mult4(v.M, 1, 0)) vec |= kFlagCNVec;
+    if (inner(v.N, v.Ntot, v.M)) vec |= kFlagCNInner;
+    if (inner(v.M, v.Mtot, v.N)) vec |= kFlagCMInner;
     d.flags = (v.a_m_fast ? kFlagAMFast : 0) | (v.b_n_fast ? kFlagBNFast : 0) |
-              (v.c_n_fast ? kFlagCNFast : 0) | (a_dense ? kFlagADense : 0) | (b_dense ? kFlagBDense : 0);
+              (v.c_n_fast ? kFlagCNFast : 0) | (a_dense ? kFlagADense : 0) | (b_dense ? kFlagBDense : 0) | vec;
 }
 
 // ---------------------------------------------------------------------------
@@ -379,6 +452,146 @@ __global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
         C[ic + sd.c_plane] = ti;
     }
     cluster.sync();   // no CTA leaves while CTA 0 may still read its sum
+}
+
+// Low arithmetic intensity: C[m, n] = sum_k A[m, k] B[k, n] for K, N <= 4
+// and M large -- a one- or two-qubit gate applied along some axes of a big
+// tensor, a projection, a vector-like block.  The work is streaming A and C
+// through HBM once.  Each thread takes V consecutive m (a unit-stride run in
+// A and in C, kFlagAMVec and kFlagCMVec / kFlagCNInner) and reads them with
+// 16-byte loads, two planes per contracted index; the whole small operand B
+// sits in registers; C leaves with 16-byte stores: V values per n along C's
+// m run, or the V x N block when C's n index is innermost.  The offsets of
+// the M index come from its mode record (a few shifts per thread, no table
+// as large as the tensor); the other tables hold at most 4 entries.  Planes
+// that do not start on 16-byte boundaries are read and written element by
+// element instead.
+template <int NK, int NN>
+__global__ void __launch_bounds__(256) gett_gate_kernel(const __grid_constant__ GroupArgs g) {
+    constexpr int V = NK * NN >= 8 ? 4 : 8;   // rows per thread
+    constexpr int NV = V / 4;                 // float4 per plane per row run
+    __shared__ GettDesc sd;
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
+    __syncthreads();
+    const int64_t m0 = (((int64_t)blockIdx.x - sd.tile_begin) * 256 + threadIdx.x) * V;
+    const bool live = m0 < sd.M;
+    // offsets of row m0 in A and C from the mode record of the M class
+    int64_t am = 0, cm = 0, ak[NK], cn[NN];
+    if (live) {
+        const int64_t *rec = sd.offAM;
+        int64_t r = m0;
+        for (int j = (int)__ldg(rec) - 1; j >= 0; --j) {
+            const int64_t ext = __ldg(rec + 1 + 3 * j);
+            int64_t dg;
+            if ((ext & (ext - 1)) == 0) {
+                dg = r & (ext - 1);
+                r >>= __popcll(ext - 1);
+            } else {
+                dg = r % ext;
+                r /= ext;
+            }
+            am += dg * __ldg(rec + 2 + 3 * j);
+            cm += dg * __ldg(rec + 3 + 3 * j);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) ak[k] = __ldg(sd.offAK + k);
+#pragma unroll
+    for (int n = 0; n < NN; ++n) cn[n] = __ldg(sd.offCN + n);
+    grid_dep_wait();   // A and B may be the previous kernel's results
+    if (!live) return;
+    const float *__restrict__ A = (const float *)sd.a;
+    const float *__restrict__ B = (const float *)sd.b;
+    float gr[NK][NN], gi[NK][NN];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            const int64_t o = __ldg(sd.offBK + k) + __ldg(sd.offBN + n);
+            gr[k][n] = B[o];
+            gi[k][n] = B[o + sd.b_plane];
+        }
+    float *C = (float *)sd.c;
+    const int64_t cp = sd.c_plane;
+    // every offset is a multiple of 4 elements (the vector flags); 16-byte
+    // accesses need the planes to start on 16-byte boundaries too
+    const bool vec = (((uintptr_t)A | (uintptr_t)C) & 15) == 0 && ((sd.a_plane | cp) & 3) == 0;
+    float xr[NK][V], xi[NK][V];
+    if (vec) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const float4 r = __ldcs(reinterpret_cast<const float4 *>(A + am + ak[k]) + q);
+                const float4 i = __ldcs(reinterpret_cast<const float4 *>(A + am + ak[k] + sd.a_plane) + q);
+                xr[k][4 * q] = r.x; xr[k][4 * q + 1] = r.y; xr[k][4 * q + 2] = r.z; xr[k][4 * q + 3] = r.w;
+                xi[k][4 * q] = i.x; xi[k][4 * q + 1] = i.y; xi[k][4 * q + 2] = i.z; xi[k][4 * q + 3] = i.w;
+            }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                xr[k][v] = A[am + ak[k] + v];
+                xi[k][v] = A[am + ak[k] + v + sd.a_plane];
+            }
+    }
+    float cr[NN][V], ci[NN][V];
+#pragma unroll
+    for (int n = 0; n < NN; ++n)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) cmac(sr, si, xr[k][v], xi[k][v], gr[k][n], gi[k][n]);
+            cr[n][v] = sr;
+            ci[n][v] = si;
+        }
+    if (sd.flags & kFlagCMVec) {   // each n: V consecutive outputs along m
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            float *o = C + cm + cn[n];
+            if (vec) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    __stcs(reinterpret_cast<float4 *>(o) + q,
+                           make_float4(cr[n][4 * q], cr[n][4 * q + 1], cr[n][4 * q + 2], cr[n][4 * q + 3]));
+                    __stcs(reinterpret_cast<float4 *>(o + cp) + q,
+                           make_float4(ci[n][4 * q], ci[n][4 * q + 1], ci[n][4 * q + 2], ci[n][4 * q + 3]));
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    o[v] = cr[n][v];
+                    o[v + cp] = ci[n][v];
+                }
+            }
+        }
+    } else {                       // n innermost: the V x NN block is contiguous
+        constexpr int E = V * NN;
+        float er[E], ei[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            er[e] = cr[e % NN][e / NN];
+            ei[e] = ci[e % NN][e / NN];
+        }
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < E / 4; ++q) {
+                __stcs(reinterpret_cast<float4 *>(C + cm) + q,
+                       make_float4(er[4 * q], er[4 * q + 1], er[4 * q + 2], er[4 * q + 3]));
+                __stcs(reinterpret_cast<float4 *>(C + cm + cp) + q,
+                       make_float4(ei[4 * q], ei[4 * q + 1], ei[4 * q + 2], ei[4 * q + 3]));
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                C[cm + e] = er[e];
+                C[cm + e + cp] = ei[e];
+            }
+        }
+    }
 }
 
 // Sum of the split-K partials into C, in a fixed order (deterministic).
@@ -939,6 +1152,9 @@ static void swap_operands(GettDesc &d) {
     d.flags = ((f & kFlagAMFast) ? kFlagBNFast : 0) | ((f & kFlagBNFast) ? kFlagAMFast : 0) |
               ((f & kFlagCNFast) ? 0 : kFlagCNFast) | ((f & kFlagSwapped) ? 0 : kFlagSwapped) |
               ((f & kFlagADense) ? kFlagBDense : 0) | ((f & kFlagBDense) ? kFlagADense : 0) |
+              ((f & kFlagAMVec) ? kFlagBNVec : 0) | ((f & kFlagBNVec) ? kFlagAMVec : 0) |
+              ((f & kFlagCMVec) ? kFlagCNVec : 0) | ((f & kFlagCNVec) ? kFlagCMVec : 0) |
+              ((f & kFlagCNInner) ? kFlagCMInner : 0) | ((f & kFlagCMInner) ? kFlagCNInner : 0) |
               (f & kFlagAtomic);
 }
 
@@ -950,6 +1166,8 @@ int tc_tile_n();
 int f32p_tile_m();
 int f32p_tile_n();
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
+void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s);
+bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {},
                        bool pdl = true);
@@ -969,6 +1187,21 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
         d.tiles_n = (d.N + tc_tile_n() - 1) / tc_tile_n();
         return;
     }
+    // low arithmetic intensity: a large operand against at most 4 x 4 entries
+    // (a gate on some axes of a big tensor, a projection): streamed once with
+    // vector accesses, when the layouts allow them
+    if (dtype == ROSNET_C64 && gate_log2(d.K) >= 0 && gate_log2(std::min(d.M, d.N)) >= 0 &&
+        std::max(d.M, d.N) >= 2048) {
+        GettDesc e = d;
+        if (e.N > e.M) swap_operands(e);
+        if ((e.flags & kFlagAMVec) && (e.flags & (kFlagCMVec | kFlagCNInner))) {
+            d = e;
+            d.kind = kKindGateBase + 3 * gate_log2(d.K) + gate_log2(d.N);
+            d.tiles_m = (d.M + 256 * gate_rows(d.kind) - 1) / (256 * gate_rows(d.kind));
+            d.tiles_n = 1;
+            return;
+        }
+    }
     // large FP32 contractions: pack once, then TMA-fed FFMA tiles (no split-K)
     if (dtype == ROSNET_C64 && reduce_mode != kReduceTree && reduce_mode != kReduceCommutative &&
         std::min(d.M, d.N) >= 64 && d.K >= 128 && 8.0 * (double)MN * (double)d.K >= 268435456.0) {
@@ -978,6 +1211,7 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
             d.kind = kKindPackF32;
             d.tiles_m = (d.M + f32p_tile_m() - 1) / f32p_tile_m();
             d.tiles_n = (d.N + f32p_tile_n() - 1) / f32p_tile_n();
+            if (f32p_stream_k_pays(d, reduce_mode)) d.flags |= kFlagStreamK;
             return;
         }
     }
@@ -1042,6 +1276,16 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
     }
 }
 
+int gate_record_class(const GettView &v, int dtype, int precision, int reduce_mode, int clear_flags) {
+    GettDesc t;
+    memset(&t, 0, sizeof(t));
+    fill_desc_tables(t, v, nullptr, nullptr, nullptr);
+    t.flags &= ~clear_flags;
+    choose_kernel(t, dtype, precision, reduce_mode);
+    if (!is_gate_kind(t.kind)) return -1;
+    return (t.flags & kFlagSwapped) ? 1 : 0;   // the kernel walks the larger class as its M
+}
+
 size_t desc_part_bytes(const GettDesc &d, int dtype) {
     if (d.ksplit <= 1 || (d.flags & kFlagAtomic)) return 0;
     return (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * (dtype == ROSNET_C64 ? 4 : 8);
@@ -1078,6 +1322,23 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
     dim3 grid((unsigned)total_ctas);
     if (is_packed_kind(kind))
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "tensor-core problems are launched with their workspace");
+    if (is_gate_kind(kind)) {
+        if (dtype != ROSNET_C64) RN_FAIL(ROSNET_ERR_INVALID_ARG, "the gate kernel is complex64 only");
+        switch (kind - kKindGateBase) {
+            case 0: launch_pdl(gett_gate_kernel<1, 1>, grid, 256, 0, s, pdl, ga); break;
+            case 1: launch_pdl(gett_gate_kernel<1, 2>, grid, 256, 0, s, pdl, ga); break;
+            case 2: launch_pdl(gett_gate_kernel<1, 4>, grid, 256, 0, s, pdl, ga); break;
+            case 3: launch_pdl(gett_gate_kernel<2, 1>, grid, 256, 0, s, pdl, ga); break;
+            case 4: launch_pdl(gett_gate_kernel<2, 2>, grid, 256, 0, s, pdl, ga); break;
+            case 5: launch_pdl(gett_gate_kernel<2, 4>, grid, 256, 0, s, pdl, ga); break;
+            case 6: launch_pdl(gett_gate_kernel<4, 1>, grid, 256, 0, s, pdl, ga); break;
+            case 7: launch_pdl(gett_gate_kernel<4, 2>, grid, 256, 0, s, pdl, ga); break;
+            default: launch_pdl(gett_gate_kernel<4, 4>, grid, 256, 0, s, pdl, ga); break;
+        }
+        g_launches++;
+        RN_CHECK_CUDA(cudaGetLastError());
+        return;
+    }
     if (dtype == ROSNET_C64) {
         switch (kind) {
             case kKindSmall: launch_pdl(gett_small_kernel<float>, grid, 256, 0, s, pdl, ga); break;
@@ -1187,6 +1448,7 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
             d.tiles_n = c.tiles_n;
             d.ksplit = c.ksplit;
             d.ktiles_per_split = c.kps;
+            d.flags = (d.flags & ~kFlagStreamK) | (d.kind == kKindPackF32 ? (c.flags & kFlagStreamK) : 0);
             return;
         }
     }
@@ -1232,8 +1494,13 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
         y.tiles_m = (d.M + f32p_tile_m() - 1) / f32p_tile_m();
         y.tiles_n = (d.N + f32p_tile_n() - 1) / f32p_tile_n();
         apply_split(y, BK, 1);
-        cands.push_back(y);
+        y.flags &= ~kFlagStreamK;
+        cands.push_back(y);   // one CTA per tile
+        y.flags |= kFlagStreamK;
+        if (f32p_stream_k_pays(y, kReduceAuto)) cands.push_back(y);   // and stream-K
     }
+    for (GettDesc &c : cands)
+        if (c.kind != kKindPackF32) c.flags &= ~kFlagStreamK;
     cudaEvent_t e0, e1;
     RN_CHECK_CUDA(cudaEventCreate(&e0));
     RN_CHECK_CUDA(cudaEventCreate(&e1));
@@ -1243,6 +1510,7 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
         const bool packed = c.kind == kKindPackF32;
         DevBuf part(packed ? 0 : desc_part_bytes(c, dtype), s);
         DevBuf ws(packed ? tc_workspace_bytes(c, kPackedModeF32) : 0, s);
+        if (packed) tc_workspace_clear(c, kPackedModeF32, ws.p, s);
         c.part = part.p;
         GroupArgs ga;
         memset(&ga, 0, sizeof(ga));
@@ -1276,8 +1544,9 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
     d.tiles_n = pick.tiles_n;
     d.ksplit = pick.ksplit;
     d.ktiles_per_split = pick.ktiles_per_split;
+    d.flags = (d.flags & ~kFlagStreamK) | (pick.flags & kFlagStreamK);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = TuneChoice{d.kind, d.tiles_m, d.tiles_n, d.ksplit, d.ktiles_per_split, d.flags};
+    g_tune[key] = TuneChoice{d.kind, d.tiles_m, d.tiles_n, d.ksplit, d.ktiles_per_split, d.flags & kFlagStreamK};
 }
 
 // Geometry of a tuned choice for a problem of shape (M, N, K): tile grid
@@ -1351,13 +1620,16 @@ struct Prepared {
             empty = true;
             return;
         }
-        tab = DevBuf(table_entries(v) * sizeof(int64_t), s);
-        launch_build_tables(v, (int64_t *)tab.p, s);
-        fill_desc_tables(d, v, (const int64_t *)tab.p);
+        const TableLayout L = table_layout(v, gate_record_class(v, dt, precision, reduce_mode, 0));
+        tab = DevBuf(L.entries * sizeof(int64_t), s);
+        launch_build_tables(v, L, (int64_t *)tab.p, s);
+        const int64_t *t = (const int64_t *)tab.p;
+        fill_desc_tables(d, v, t + L.off[0], t + L.off[1], t + L.off[2]);
         choose_kernel(d, dt, precision, reduce_mode);
-        if (is_tc())
+        if (is_tc()) {
             tcws = DevBuf(tc_workspace_bytes(d, packed_mode(d.kind)), s);
-        else
+            tc_workspace_clear(d, packed_mode(d.kind), tcws.p, s);
+        } else
             part = DevBuf(desc_part_bytes(d, dt), s);
         d.part = part.p;
     }
@@ -1420,27 +1692,34 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
     GettView v = make_view(A->lay, B->lay, C->lay, naxes, axa, axb);
     if (v.Mtot * v.Ntot == 0) return 0;
     GettDesc d;
-    const size_t tab_bytes = (table_entries(v) * sizeof(int64_t) + 255) & ~(size_t)255;
+    TableLayout L;
+    size_t tab_bytes = 0;
     auto plan = [&](int red) {
+        L = table_layout(v, gate_record_class(v, A->dtype, precision, red, 0));
+        tab_bytes = (L.entries * sizeof(int64_t) + 255) & ~(size_t)255;
+        const int64_t *t = (const int64_t *)ws;
         memset(&d, 0, sizeof(d));
-        fill_desc_tables(d, v, (const int64_t *)ws);
+        fill_desc_tables(d, v, t + L.off[0], t + L.off[1], t + L.off[2]);
         choose_kernel(d, A->dtype, precision, red);
         return tab_bytes + (is_packed_kind(d.kind) ? tc_workspace_bytes(d, packed_mode(d.kind))
                                                    : desc_part_bytes(d, A->dtype));
     };
     size_t need = plan(reduce_mode);
-    // an automatic split of the contracted range whose partial sums do not
-    // fit runs unsplit instead (one CTA per output tile over all pairs)
-    if (need > ws_bytes && reduce_mode == kReduceAuto && d.ksplit > 1) need = plan(kReduceSequential);
+    // an automatic split of the contracted range (or stream-K schedule) whose
+    // partial sums do not fit runs unsplit instead (one CTA per output tile
+    // over all pairs)
+    if (need > ws_bytes && reduce_mode == kReduceAuto && (d.ksplit > 1 || (d.flags & kFlagStreamK)))
+        need = plan(kReduceSequential);
     if (need > ws_bytes) return need;
     const bool tcp = is_packed_kind(d.kind);
-    launch_build_tables(v, (int64_t *)ws, s);
+    launch_build_tables(v, L, (int64_t *)ws, s);
     bind_operands(d, A->data, B->data, C->data, A->pstride, B->pstride, C->pstride);
     if (tcp) {
         GroupArgs ga;
         memset(&ga, 0, sizeof(ga));
         ga.ndesc = 1;
         ga.single = d;
+        tc_workspace_clear(d, packed_mode(d.kind), (char *)ws + tab_bytes, s);
         launch_tc_problem(packed_mode(d.kind), d, ga, (char *)ws + tab_bytes, s, true, true, {}, false);
         return need;
     }
@@ -1641,7 +1920,7 @@ extern "C" rosnet_status rosnet_tune_export(char *buf, size_t cap, size_t *len) 
             const TuneChoice &c = e.second;
             t += std::to_string(k.dtype) + " " + std::to_string(k.flags) + " " + std::to_string(k.M) + " " +
                  std::to_string(k.N) + " " + std::to_string(k.K) + " " + std::to_string(c.kind) + " " +
-                 std::to_string(c.ksplit) + "\n";
+                 std::to_string(c.ksplit) + " " + std::to_string((c.flags & kFlagStreamK) ? 1 : 0) + "\n";
         }
     }
     *len = t.size() + 1;
@@ -1660,10 +1939,17 @@ extern "C" rosnet_status rosnet_tune_import(const char *text) {
     while (std::getline(in, line)) {
         if (line.find_first_not_of(" \t\r") == std::string::npos) continue;
         std::istringstream ls(line);
-        long long v[7];
+        long long v[8] = {0};
         for (int i = 0; i < 7; ++i)
             if (!(ls >> v[i])) RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed tuning line: " + line);
+        if (ls >> v[7]) {   // optional: the packed FP32 GEMM's stream-K schedule (0 / 1)
+            if (v[7] != 0 && (v[7] != 1 || v[5] != kKindPackF32))
+                RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad schedule field: " + line);
+        } else if (!ls.eof()) {
+            RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed tuning line: " + line);
+        }
         std::string rest;
+        ls.clear();
         if (ls >> rest) RN_FAIL(ROSNET_ERR_INVALID_ARG, "malformed tuning line: " + line);
         if (v[0] != ROSNET_C64 && v[0] != ROSNET_C128) RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad dtype: " + line);
         if (v[1] < 0 || v[1] > 0x7fffffffLL)
@@ -1671,7 +1957,7 @@ extern "C" rosnet_status rosnet_tune_import(const char *text) {
         TuneChoice c;
         if (!tune_geometry((int)v[0], (int)v[5], v[2], v[3], v[4], v[6], &c))
             RN_FAIL(ROSNET_ERR_INVALID_ARG, "choice impossible for this shape: " + line);
-        c.flags = (int32_t)(v[1] & 0x3fffffff);
+        c.flags = v[7] ? kFlagStreamK : 0;
         add.push_back({TuneKey{(int)v[0], (int)v[1], v[2], v[3], v[4]}, c});
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -191,6 +191,22 @@ enum : int32_t {
     // FP32 GEMM can load its tiles straight from it with TMA (no pack pass)
     kFlagADense = 32,
     kFlagBDense = 64,
+    // packed FP32 GEMM: stream-K schedule (units of (tile, k-tile) split
+    // evenly over one CTA per slot, partial tiles summed in a fixed order)
+    kFlagStreamK = 128,
+    // vector access for the low-arithmetic-intensity kernel (gett_gate_kernel):
+    // A (B) along M (N) in runs of 8 contiguous elements whose offsets, and
+    // those of every contracted index, are multiples of 4 (16-byte loads)
+    kFlagAMVec = 256,
+    kFlagBNVec = 512,
+    // C along M (N) in runs of 8 contiguous elements, all offsets of the
+    // other class multiples of 4
+    kFlagCMVec = 1024,
+    kFlagCNVec = 2048,
+    // C with the N (M) index innermost and dense, and the innermost M (N)
+    // mode right above it in runs of 8: 8 x N (8 x M) outputs are contiguous
+    kFlagCNInner = 4096,
+    kFlagCMInner = 8192,
 };
 
 // How the partial products of the matched block pairs of an output tile are
@@ -218,6 +234,17 @@ enum KernelKind : int32_t {
 };
 
 constexpr int kDirectK = 32;   // longest contraction range of one direct-kernel CTA
+
+// Low-arithmetic-intensity kinds (gett_gate_kernel): K and N in {1, 2, 4},
+// M large; kind = kKindGateBase + 3 log2 K + log2 N.  Each thread takes
+// gate_rows(kind) consecutive m.
+constexpr int kKindGateBase = 16;
+inline bool is_gate_kind(int kind) { return kind >= kKindGateBase && kind < kKindGateBase + 9; }
+inline int gate_log2(int64_t x) { return x == 1 ? 0 : x == 2 ? 1 : x == 4 ? 2 : -1; }
+inline int gate_rows(int kind) {
+    const int lk = (kind - kKindGateBase) / 3, ln = (kind - kKindGateBase) % 3;
+    return lk + ln >= 3 ? 4 : 8;   // fewer rows per thread when K * N >= 8 (registers)
+}
 
 inline bool is_direct_kind(int kind) { return kind == kKindDirect || kind == kKindDirect256x16; }
 // CTA tile of a direct kind, and whether it applies to a problem
@@ -281,6 +308,26 @@ size_t desc_part_bytes(const GettDesc &d, int dtype);
 size_t table_entries(const GettView &v);
 void launch_build_tables(const GettView &v, int64_t *tables, cudaStream_t s);
 void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tables);
+
+// The large index class of a low-arithmetic-intensity problem (a gate kind)
+// needs no offset table: the kernel computes its offsets from a mode record
+// [n, (extent, stride in the first tensor, stride in the second) x n],
+// outermost mode first.  A table layout puts one class (record_class: 0 M,
+// 1 N; -1 none) as such a record and the others as tables.
+struct TableLayout {
+    int record_class = -1;
+    int64_t off[3] = {0, 0, 0};   // entry offset of the M, N and K parts
+    int64_t entries = 0;
+};
+inline int64_t record_entries(const ModeList &ml) { return 1 + 3 * (int64_t)ml.n; }
+void host_mode_record(const ModeList &ml, int64_t *out);
+TableLayout table_layout(const GettView &v, int record_class);
+void launch_build_tables(const GettView &v, const TableLayout &L, int64_t *tables, cudaStream_t s);
+// The class a problem keeps as a mode record: the one the gate kernel walks
+// when the kernel choice for the view (with `clear_flags` removed, e.g. the
+// vector flags of operands whose address changes between calls) is a gate
+// kind, else -1.
+int gate_record_class(const GettView &v, int dtype, int precision, int reduce_mode, int clear_flags);
 // The same with the M, N and K tables ([offsets in the first tensor | in the
 // second] of each class) at separate addresses.
 void fill_desc_tables(GettDesc &d, const GettView &v, const int64_t *tm, const int64_t *tn,

@@ -36,6 +36,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <functional>
 #include <mutex>
 
@@ -502,16 +503,21 @@ constexpr int PA = BK * BM, PB = BK * BN;                  // floats of one plan
 constexpr uint32_t STAGE_BYTES = 2u * (PA + PB) * 4u;
 constexpr int KQ = 32;                                     // k tile of the pack kernel
 static_assert(KQ % BK == 0 && TM % 4 == 0 && TN % 4 == 0, "tile shape");
-// the finished C tile is staged through the (then idle) stage ring as two
-// planes of [BN][BM + 1] (or [BM][BN + 1]) floats
-constexpr size_t EPI_BYTES = 2 * (size_t)(BM + 1) * (BN + 1) * 4;
+// a finished C tile is staged as planes of [BN][BM + 1] (or [BM][BN + 1])
+// floats: one at a time through the stage just consumed (mid-stream), or
+// both through the idle ring (after a CTA's last unit)
+static_assert((size_t)(BM + 1) * (BN + 1) * 4 <= STAGE_BYTES, "a staged plane must fit one stage");
+static_assert(2 * (size_t)(BM + 1) * (BN + 1) * 4 <= (size_t)STAGES * STAGE_BYTES, "both planes must fit the ring");
 constexpr size_t RING_BYTES = (size_t)STAGES * STAGE_BYTES;
-constexpr size_t SMEM = (RING_BYTES > EPI_BYTES ? RING_BYTES : EPI_BYTES) + 128;
+constexpr size_t SMEM = RING_BYTES + 128;
 
 struct Args {
     CUtensorMap mapA, mapB;   // operands as 3-D {rows, K, 2 planes} FP32 arrays
     GroupArgs g;              // the problem (C pointer, C offset tables, M, N, K, tiles)
+    float *sk_part;           // stream-K: partial tiles [tile][piece][2][BM * BN] (fragment order)
+    int32_t *sk_count;        // stream-K: pieces stored per tile (0 between launches)
     int32_t nkt;              // k-stages (Kpad / BK)
+    int32_t sk_maxpieces;     // stream-K: most pieces of any tile
 };
 
 // out[p][k][r] = operand(r, k) plane p (0 outside R x K), for A (the first
@@ -583,12 +589,28 @@ __device__ __forceinline__ void cmac4(float &cr, float &ci, float ar, float ai, 
     ci = fmaf(ai, br, ci);
 }
 
+// CTA index owning unit u when U units are split evenly over G CTAs (CTA c
+// takes units [c U / G, (c + 1) U / G)).
+__device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) { return ((u + 1) * G - 1) / U; }
+
+// Work is a sequence of units (output tile t, k-tile kt), k fastest.  Without
+// kFlagStreamK a CTA takes the units of one tile (data-parallel).  With it
+// (stream-K) the launch has G CTAs and CTA c takes units [c U / G,
+// (c + 1) U / G) of all U = tiles * nkt, so every SM slot gets the same work
+// however the tile count divides the slots.  A CTA holding only part of a
+// tile's k range writes that partial tile to the workspace and counts it in
+// the tile's counter; the CTA that brings the count to the number of pieces
+// sums the pieces in k order (a fixed order: results do not depend on
+// scheduling), writes C and resets the counter.  No CTA ever waits for
+// another.
+template <bool SK>
 __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __grid_constant__ Args p) {
     extern __shared__ unsigned char dsm_raw[];
     float *stg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~(uintptr_t)127);
     __shared__ GettDesc sd;
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ volatile int abort_flag;
+    __shared__ int last_piece;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     grid_dep_launch();
     if (warp == 0) load_desc(p.g, sd);
@@ -601,28 +623,52 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // raster: the operand with fewer tiles varies fastest (its tiles stay in L2)
-    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
-    const bool n_fast = sd.tiles_n < sd.tiles_m;
-    const int64_t tm = n_fast ? tile / sd.tiles_n : tile % sd.tiles_m;
-    const int64_t tn = n_fast ? tile % sd.tiles_n : tile / sd.tiles_m;
-    const int m0 = (int)(tm * BM), n0 = (int)(tn * BN);
     const int nkt = p.nkt;
-    grid_dep_wait();   // the packed operands are the previous kernel's output
+    // raster: the operand with fewer tiles varies fastest (its tiles stay in L2)
+    const bool n_fast = sd.tiles_n < sd.tiles_m;
+    auto tile_origin = [&](int64_t t, int &m0, int &n0) {
+        const int64_t tm = n_fast ? t / sd.tiles_n : t % sd.tiles_m;
+        const int64_t tn = n_fast ? t % sd.tiles_n : t / sd.tiles_m;
+        m0 = (int)(tm * BM);
+        n0 = (int)(tn * BN);
+    };
+    const int64_t U = sd.tiles_m * sd.tiles_n * (int64_t)nkt, G = gridDim.x;
+    int64_t u0, u1;
+    if (SK) {
+        u0 = (int64_t)blockIdx.x * U / G;
+        u1 = ((int64_t)blockIdx.x + 1) * U / G;
+    } else {
+        u0 = ((int64_t)blockIdx.x - sd.tile_begin) * nkt;
+        u1 = u0 + nkt;
+    }
+    const int nitems = (int)(u1 - u0);
+    grid_dep_wait();   // operands may be the previous kernel's output
 
-    auto issue = [&](int kt) {   // one thread: tile kt into its stage
-        const int s = kt % STAGES;
+    // units are issued (one thread) and consumed strictly in order: each side
+    // walks (tile, k-tile) with its own cursor instead of dividing per unit
+    int pt = (int)(u0 / nkt);   // producer cursor (stream-K): tile, k-tile, tile origin
+    int pkt = (int)(u0 % nkt), pm0 = 0, pn0 = 0;
+    tile_origin(pt, pm0, pn0);
+    auto issue = [&](int i) {   // one thread: the next unit (u0 + i) into its stage
+        const int s = i % STAGES;
+        const int kt = SK ? pkt : i;   // one tile per CTA: unit i is k-tile i
         tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
         const uint32_t sa = tc::su32(stg + (size_t)s * 2 * (PA + PB));
         const uint32_t sb = sa + 2u * PA * 4u;
-        tc::tma_load_3d(sa, &p.mapA, m0, kt * BK, 0, &full_bar[s]);
-        tc::tma_load_3d(sa + PA * 4u, &p.mapA, m0, kt * BK, 1, &full_bar[s]);
-        tc::tma_load_3d(sb, &p.mapB, n0, kt * BK, 0, &full_bar[s]);
-        tc::tma_load_3d(sb + PB * 4u, &p.mapB, n0, kt * BK, 1, &full_bar[s]);
+        tc::tma_load_3d(sa, &p.mapA, pm0, kt * BK, 0, &full_bar[s]);
+        tc::tma_load_3d(sa + PA * 4u, &p.mapA, pm0, kt * BK, 1, &full_bar[s]);
+        tc::tma_load_3d(sb, &p.mapB, pn0, kt * BK, 0, &full_bar[s]);
+        tc::tma_load_3d(sb + PB * 4u, &p.mapB, pn0, kt * BK, 1, &full_bar[s]);
+        if (SK && ++pkt == nkt) {
+            pkt = 0;
+            tile_origin(++pt, pm0, pn0);
+        }
     };
     int issued = 0;
     if (tid == 0)
-        for (; issued < min(STAGES, nkt); ++issued) issue(issued);
+        for (; issued < min(STAGES, nitems); ++issued) issue(issued);
+    int ct = (int)(u0 / nkt);   // consumer cursor
+    int ckt = (int)(u0 % nkt);
 
     const int ty = tid >> 4, tx = tid & 15;
     float cr[TM][TN], ci[TM][TN];
@@ -654,13 +700,84 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
             for (int j = 0; j < TN; ++j) cmac4(cr[i][j], ci[i][j], xr[i], xi[i], yr[j], yi[j]);
     };
 
-    int done0 = 0;   // tiles whose full barrier thread 0 has passed
-    for (int kt = 0; kt < nkt; ++kt) {
-        const int s = kt % STAGES;
+    // the finished tile at (m0, n0) to C, staged through shared memory and
+    // written with the lanes of a warp along C's unit-stride dimension (m
+    // unless kFlagCNFast).  `cs`: a consumed stage, which holds one plane of
+    // (BM + 1) x BN floats (two passes), or the whole idle ring after the
+    // CTA's last unit (both planes in one pass).
+    auto store_c = [&](float *cs, bool both, int m0, int n0) {
+        float *C = (float *)sd.c;
+        const int64_t cp = sd.c_plane;
+        const bool m_fast = !(sd.flags & kFlagCNFast);
+        const int ld = m_fast ? BM + 1 : BN + 1;   // row length of a staged plane
+        const int plane = (m_fast ? BN : BM) * ld;
+        const int64_t M = sd.M, N = sd.N;
+#pragma unroll 1
+        for (int pl = 0; pl < (both ? 1 : 2); ++pl) {
+            __syncthreads();   // the staging area is free
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    const int ml = ty * TM + i, nl = tx * TN + j;
+                    const int e = m_fast ? nl * ld + ml : ml * ld + nl;
+                    if (both) {
+                        cs[e] = cr[i][j];
+                        cs[plane + e] = ci[i][j];
+                    } else {
+                        cs[e] = pl ? ci[i][j] : cr[i][j];
+                    }
+                }
+            __syncthreads();
+            float *out = C + (pl ? cp : 0);
+            if (m_fast) {
+                int64_t cm[BM / 32];
+#pragma unroll
+                for (int u = 0; u < BM / 32; ++u) {
+                    const int64_t m = m0 + lane + 32 * u;
+                    cm[u] = m < M ? __ldg(sd.offCM + m) : -1;
+                }
+                for (int nl = warp; nl < BN; nl += NT / 32) {
+                    const int64_t n = n0 + nl;
+                    if (n >= N) break;
+                    const int64_t c0 = __ldg(sd.offCN + n);
+#pragma unroll
+                    for (int u = 0; u < BM / 32; ++u)
+                        if (cm[u] >= 0) {
+                            out[cm[u] + c0] = cs[nl * ld + lane + 32 * u];
+                            if (both) out[cm[u] + c0 + cp] = cs[plane + nl * ld + lane + 32 * u];
+                        }
+                }
+            } else {
+                int64_t cn[BN / 32];
+#pragma unroll
+                for (int u = 0; u < BN / 32; ++u) {
+                    const int64_t n = n0 + lane + 32 * u;
+                    cn[u] = n < N ? __ldg(sd.offCN + n) : -1;
+                }
+                for (int ml = warp; ml < BM; ml += NT / 32) {
+                    const int64_t m = m0 + ml;
+                    if (m >= M) break;
+                    const int64_t c0 = __ldg(sd.offCM + m);
+#pragma unroll
+                    for (int u = 0; u < BN / 32; ++u)
+                        if (cn[u] >= 0) {
+                            out[c0 + cn[u]] = cs[ml * ld + lane + 32 * u];
+                            if (both) out[c0 + cn[u] + cp] = cs[plane + ml * ld + lane + 32 * u];
+                        }
+                }
+            }
+        }
+        __syncthreads();   // the staging area may be refilled
+    };
+
+    int done0 = 0;   // units whose full barrier thread 0 has passed
+    for (int i = 0; i < nitems; ++i) {
+        const int s = i % STAGES;
         // every lane observes the phase itself; the warp leaves together
-        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_fast(&full_bar[s], (kt / STAGES) & 1, &abort_flag));
+        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_fast(&full_bar[s], (i / STAGES) & 1, &abort_flag));
         if (!ok) break;
-        if (tid == 0) done0 = kt + 1;
+        if (tid == 0) done0 = i + 1;
         const float *a0 = stg + (size_t)s * 2 * (PA + PB) + ty * TM;
         const float *b0 = stg + (size_t)s * 2 * (PA + PB) + 2 * PA + tx * TN;
         float xr0[TM], xi0[TM], yr0[TN], yi0[TN], xr1[TM], xi1[TM], yr1[TN], yi1[TN];
@@ -677,13 +794,13 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
         macs(xr1, xi1, yr1, yi1);
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&empty_bar[s]);
-        // warp 0 refills the stage consumed one iteration ago (all warps have
-        // normally released it by now), keeping STAGES - 1 tiles ahead; the
+        // warp 0 refills the stage consumed one unit ago (all warps have
+        // normally released it by now), keeping STAGES - 1 units ahead; the
         // whole warp takes the branch so that no lane computes alone
-        if (warp == 0 && kt >= 1 && kt - 1 + STAGES < nkt) {
+        if (warp == 0 && i >= 1 && i - 1 + STAGES < nitems) {
             bool ok2 = true;
             if (lane == 0) {
-                const int t = kt - 1;
+                const int t = i - 1;
                 ok2 = tc::mbar_wait_fast(&empty_bar[t % STAGES], (t / STAGES) & 1, &abort_flag);
                 if (ok2) {
                     issue(t + STAGES);
@@ -692,69 +809,83 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
             }
             if (!__shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0)) break;
         }
+        if (!SK) continue;   // one tile per CTA: its epilogue follows the loop
+        const int t = ct;
+        const bool tile_end = ckt == nkt - 1 || i == nitems - 1;
+        if (++ckt == nkt) {
+            ckt = 0;
+            ++ct;
+        }
+        if (!tile_end) continue;
+        // ---- this CTA's range of tile t ends here
+        int m0, n0;
+        tile_origin(t, m0, n0);
+        // stage s holds consumed data and is refilled only after this
+        // epilogue (by the next unit's refill): it serves as staging area
+        float *cs = stg + (size_t)s * 2 * (PA + PB);
+        bool write_c = true;
+        const int64_t tb = (int64_t)t * nkt;   // the tile's first unit
+        if (SK && (u0 > tb || u1 < tb + nkt)) {
+            // a piece of the tile: store it, count it, and sum all pieces if
+            // it is the last one to arrive
+            const int64_t cf = sk_owner(tb, U, G);
+            const int npieces = (int)(sk_owner(tb + nkt - 1, U, G) - cf + 1);
+            const int piece = (int)((int64_t)blockIdx.x - cf);
+            float *slot = p.sk_part + ((int64_t)t * p.sk_maxpieces + piece) * (2 * BM * BN);
+#pragma unroll
+            for (int i2 = 0; i2 < TM; ++i2)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    slot[(i2 * TN + j) * NT + tid] = cr[i2][j];
+                    slot[(TM * TN + i2 * TN + j) * NT + tid] = ci[i2][j];
+                }
+            // the barrier orders every thread's stores before thread 0's
+            // release; its acquire orders the other pieces' stores before the
+            // barrier after which all threads read them
+            __syncthreads();
+            if (tid == 0) {
+                int old;
+                asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], 1;" : "=r"(old) : "l"(p.sk_count + t)
+                             : "memory");
+                last_piece = old == npieces - 1;
+            }
+            __syncthreads();
+            write_c = last_piece;
+            if (write_c) {
+                const float *base = p.sk_part + (int64_t)t * p.sk_maxpieces * (2 * BM * BN);
+#pragma unroll
+                for (int i2 = 0; i2 < TM; ++i2)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) cr[i2][j] = ci[i2][j] = 0.f;
+                for (int q = 0; q < npieces; ++q) {   // pieces in k order
+                    const float *src = base + (int64_t)q * (2 * BM * BN);
+#pragma unroll
+                    for (int i2 = 0; i2 < TM; ++i2)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) {
+                            cr[i2][j] += __ldcg(src + (i2 * TN + j) * NT + tid);
+                            ci[i2][j] += __ldcg(src + (TM * TN + i2 * TN + j) * NT + tid);
+                        }
+                }
+                if (tid == 0) p.sk_count[t] = 0;   // ready for the next launch
+            }
+        }
+        if (write_c) {
+            // after the CTA's last unit no copy is in flight: the whole ring
+            // stages both planes at once
+            if (i == nitems - 1) store_c(stg, true, m0, n0);
+            else store_c(cs, false, m0, n0);
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < TM; ++i2)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) cr[i2][j] = ci[i2][j] = 0.f;
     }
     if (tid == 0)   // no copy may still be landing in shared memory when the CTA exits
         for (int t = done0; t < issued; ++t)
             tc::mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1, &abort_flag, false);
     __syncthreads();
-    if (abort_flag) return;
-
-    // epilogue: stage the tile in shared memory, then write C with the lanes
-    // of a warp running along C's unit-stride dimension (m unless kFlagCNFast)
-    float *C = (float *)sd.c;
-    const int64_t cp = sd.c_plane;
-    const bool m_fast = !(sd.flags & kFlagCNFast);
-    float *cs = stg;
-    const int ld = m_fast ? BM + 1 : BN + 1;             // row length of the staged tile
-    const int plane = (m_fast ? BN : BM) * ld;
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int ml = ty * TM + i, nl = tx * TN + j;
-            const int e = m_fast ? nl * ld + ml : ml * ld + nl;
-            cs[e] = cr[i][j];
-            cs[plane + e] = ci[i][j];
-        }
-    __syncthreads();
-    const int64_t M = sd.M, N = sd.N;
-    if (m_fast) {
-        int64_t cm[BM / 32];
-#pragma unroll
-        for (int u = 0; u < BM / 32; ++u) {
-            const int64_t m = m0 + lane + 32 * u;
-            cm[u] = m < M ? __ldg(sd.offCM + m) : -1;
-        }
-        for (int nl = warp; nl < BN; nl += NT / 32) {
-            const int64_t n = n0 + nl;
-            if (n >= N) break;
-            const int64_t cn = __ldg(sd.offCN + n);
-#pragma unroll
-            for (int u = 0; u < BM / 32; ++u)
-                if (cm[u] >= 0) {
-                    C[cm[u] + cn] = cs[nl * ld + lane + 32 * u];
-                    C[cm[u] + cn + cp] = cs[plane + nl * ld + lane + 32 * u];
-                }
-        }
-    } else {
-        int64_t cn[BN / 32];
-#pragma unroll
-        for (int u = 0; u < BN / 32; ++u) {
-            const int64_t n = n0 + lane + 32 * u;
-            cn[u] = n < N ? __ldg(sd.offCN + n) : -1;
-        }
-        for (int ml = warp; ml < BM; ml += NT / 32) {
-            const int64_t m = m0 + ml;
-            if (m >= M) break;
-            const int64_t cm = __ldg(sd.offCM + m);
-#pragma unroll
-            for (int u = 0; u < BN / 32; ++u)
-                if (cn[u] >= 0) {
-                    C[cm + cn[u]] = cs[ml * ld + lane + 32 * u];
-                    C[cm + cn[u] + cp] = cs[plane + ml * ld + lane + 32 * u];
-                }
-        }
-    }
+    if (!SK && !abort_flag) store_c(stg, true, pm0, pn0);   // the CTA's tile; the idle ring stages both planes
 }
 
 }  // namespace f32p
@@ -862,13 +993,31 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
 
 struct F32Geom {
     int64_t Mpad, Npad, Kpad;
+    size_t pack_bytes;             // packed A and B panels
+    // stream-K: CTAs, units, most pieces of a tile, and the workspace of the
+    // partial tiles and per-tile counters (after the packed panels)
+    int64_t G = 0, U = 0, maxpieces = 0;
+    size_t part_bytes = 0, count_bytes = 0;
 };
+
+int64_t sk_owner_host(int64_t u, int64_t U, int64_t G) { return ((u + 1) * G - 1) / U; }
 
 F32Geom f32_geom(const GettDesc &d) {
     F32Geom g;
     g.Mpad = (d.M + f32p::BM - 1) / f32p::BM * f32p::BM;
     g.Npad = (d.N + f32p::BN - 1) / f32p::BN * f32p::BN;
     g.Kpad = (d.K + f32p::KQ - 1) / f32p::KQ * f32p::KQ;   // KQ is a multiple of BK
+    g.pack_bytes = (size_t)2 * (g.Mpad + g.Npad) * g.Kpad * 4;
+    if (d.flags & kFlagStreamK) {
+        const int64_t tiles = d.tiles_m * d.tiles_n, nkt = g.Kpad / f32p::BK;
+        g.U = tiles * nkt;
+        g.G = std::min<int64_t>(2 * (int64_t)num_sms(), g.U);
+        for (int64_t t = 0; t < tiles; ++t)
+            g.maxpieces = std::max(g.maxpieces, sk_owner_host((t + 1) * nkt - 1, g.U, g.G) -
+                                                    sk_owner_host(t * nkt, g.U, g.G) + 1);
+        g.part_bytes = (size_t)tiles * g.maxpieces * 2 * f32p::BM * f32p::BN * 4;
+        g.count_bytes = ((size_t)tiles * 4 + 255) & ~(size_t)255;
+    }
     return g;
 }
 
@@ -900,8 +1049,8 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
                 bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
     static bool attr_set = false;
     if (!attr_set) {
-        RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)f32p::SMEM));
+        for (auto k : {f32p::f32_gemm_kernel<false>, f32p::f32_gemm_kernel<true>})
+            RN_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32p::SMEM));
         attr_set = true;
     }
     const F32Geom g = f32_geom(d);
@@ -933,11 +1082,17 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     else make_map_f32(&args.mapB, pb, g.Npad, g.Kpad, g.Npad, g.Npad * g.Kpad, f32p::BN);
     args.g = ga;
     args.nkt = (int)(g.Kpad / f32p::BK);
+    if (d.flags & kFlagStreamK) {
+        args.sk_part = (float *)((char *)ws + g.pack_bytes);
+        args.sk_count = (int32_t *)((char *)ws + g.pack_bytes + g.part_bytes);
+        args.sk_maxpieces = (int32_t)g.maxpieces;
+        ctas = g.G;
+    }
     if (before_gemm) before_gemm();
     // after a pack the GEMM's prologue may overlap it (it reads only its
     // descriptor before waiting); with no pack it is the first launch
-    launch_pdl(f32p::f32_gemm_kernel, dim3((unsigned)ctas), f32p::NT, f32p::SMEM, s, pdl || pack_a || pack_b,
-               args);
+    launch_pdl((d.flags & kFlagStreamK) ? f32p::f32_gemm_kernel<true> : f32p::f32_gemm_kernel<false>,
+               dim3((unsigned)ctas), f32p::NT, f32p::SMEM, s, pdl || pack_a || pack_b, args);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
 }
@@ -947,14 +1102,40 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
 int f32p_tile_m() { return f32p::BM; }
 int f32p_tile_n() { return f32p::BN; }
 
-// Workspace bytes of the packed operands of a packed-kind problem.
+// Whether the packed FP32 GEMM of a problem takes the stream-K schedule.
+// Measured on B300 against one CTA per tile (2 CTA slots per SM): stream-K
+// wins for deep contractions whose tiles fill the slots poorly (704 x 704 x
+// 1024, 121 tiles: 1.09x); with 8-16 k-tiles per tile the extra
+// piece stores and barriers cost what the balance gains (1024 x 512 x 512,
+// 4096 x 256 x 256: equal; 2048 x 1024 x 256: 0.98x), and below ~3 k-tiles per
+// CTA it loses (704 x 704 x 128: 0.75x).  Never with a sequential (one CTA per
+// tile) reduction; the autotuner times both schedules where this says yes.
+bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode) {
+    if (reduce_mode == kReduceSequential) return false;
+    const int64_t tiles = d.tiles_m * d.tiles_n, slots = 2 * (int64_t)num_sms();
+    const int64_t nkt = (d.K + f32p::BK - 1) / f32p::BK;
+    if (nkt < 32 || tiles >= 3 * slots) return false;
+    const int64_t waves = (tiles + slots - 1) / slots;
+    return (double)tiles < 0.92 * (double)(waves * slots);   // the slots are used poorly
+}
+
+// Workspace bytes of a packed-kind problem: its packed operands (and the
+// stream-K partial tiles and counters of the packed FP32 GEMM).
 size_t tc_workspace_bytes(const GettDesc &d, int mode) {
     if (mode == kPackedModeF32) {
         const F32Geom g = f32_geom(d);
-        return (size_t)2 * (g.Mpad + g.Npad) * g.Kpad * 4;
+        return g.pack_bytes + g.part_bytes + g.count_bytes;
     }
     TcGeom g = tc_geom(d, mode);
     return g.narr * (g.arrA + g.arrB);
+}
+
+// Zero what must start at zero in a fresh workspace of a packed-kind problem
+// (the stream-K tile counters; each launch leaves them at zero again).
+void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s) {
+    if (mode != kPackedModeF32 || !(d.flags & kFlagStreamK)) return;
+    const F32Geom g = f32_geom(d);
+    RN_CHECK_CUDA(cudaMemsetAsync((char *)ws + g.pack_bytes + g.part_bytes, 0, g.count_bytes, s));
 }
 
 // Enqueue pack + GEMM for one tensor-core problem.  `ga` locates the

@@ -241,14 +241,14 @@ def test_slice_search_rejects_malformed_paths():
 def test_tune_table_roundtrip_and_validation():
     """Autotuner decisions move between processes as text; every imported
     entry is checked against its shape (no device needed)."""
-    good = ("1 9 4096 256 256 10 1\n1 11 2048 512 32 3 1\n2 0 300 200 5000 2 16\n"
-            "1 1 300 13 4000 11 8\n1 1 200 30 300 12 1\n1 3 2048 512 32 13 1\n2 3 300 40 20 13 1\n"
-            "1 9 256 16 4096 14 128\n1 9 300 200 100 13 4\n")
+    good = ("1 9 4096 256 256 10 1 1\n1 11 2048 512 32 3 1 0\n2 0 300 200 5000 2 16 0\n"
+            "1 1 300 13 4000 11 8 0\n1 1 200 30 300 12 1 0\n1 3 2048 512 32 13 1 0\n2 3 300 40 20 13 1 0\n"
+            "1 9 256 16 4096 14 128 0\n1 9 300 200 100 13 4 0\n1 9 1000 700 200 10 1 0\n")
     R.tune_import(good)
     lines = set(R.tune_export().splitlines())
     assert set(good.splitlines()) <= lines
-    R.tune_import("1 9 4096 256 256 2 4\n")          # replaces the first entry
-    assert "1 9 4096 256 256 2 4" in R.tune_export().splitlines()
+    R.tune_import("1 9 4096 256 256 2 4\n")          # replaces the first entry; no schedule field = 0
+    assert "1 9 4096 256 256 2 4 0" in R.tune_export().splitlines()
     bad = ["1 9 4096 256 256 10 2",      # packed kind cannot split
            "1 9 100 40 256 3 1",         # 128x64 tiles need M >= 128, N >= 48
            "2 0 64 64 64 10 1",          # packed FP32 is complex64 only
@@ -256,7 +256,9 @@ def test_tune_table_roundtrip_and_validation():
            "1 0 64 64 64 7 1",           # not a CUDA-core GEMM kind
            "3 0 64 64 64 2 1",           # unknown dtype
            "1 0 64 64",                  # short line
-           "1 0 64 64 64 2 1 9",         # extra field
+           "1 0 64 64 64 2 1 9",         # schedule is 0 or 1
+           "1 0 64 64 64 2 1 1",         # stream-K is a schedule of the packed kind only
+           "1 0 64 64 64 10 1 0 0",      # extra field
            "2 0 300 13 200 11 1",        # 256x16 tiles are complex64 only
            "1 0 100 13 200 11 1",        # 256x16 tiles need M >= 128
            "1 0 300 300 33 13 1",        # direct tiles hold 32 contracted indices per CTA

@@ -50,10 +50,11 @@ def test_every_family_matches_oracle(dtype, mnk):
     assert key is not None, "the autotuner recorded no entry for this problem"
     tried = 0
     for kind, splits in FAMILIES.items():
-        for ks in splits:
+        for ks, sched in [(k, 0) for k in splits] + ([(1, 1)] if kind == 10 else []):
             if ks is None:   # direct kinds: one 32-long contracted range per CTA
                 ks = max(1, -(-K // 32))
-            line = " ".join(key[:5] + [str(kind), str(ks)])
+            # schedule 1: the packed FP32 GEMM's stream-K schedule
+            line = " ".join(key[:5] + [str(kind), str(ks), str(sched)])
             try:
                 R.tune_import(line + "\n")
             except R.RosnetError as e:   # not a choice this shape (or dtype) can have
@@ -67,6 +68,6 @@ def test_every_family_matches_oracle(dtype, mnk):
             err = oracle.rel_frobenius(got, ref)
             assert err <= TOL[dtype], (kind, ks, err)
             tried += 1
-    assert tried >= (2 if dtype == R.C128 else 5)
+    assert tried >= (2 if dtype == R.C128 else 6)
     R.tune_import(" ".join(key) + "\n")   # the autotuner's own choice back for later tests
     R.release_plans()
