@@ -345,19 +345,20 @@ def _net_labels(rank_a, rank_b, axes_a, axes_b):
     return [la, lb], out
 
 
-def _timed_contract(R, torch, ts, labels, out, precision, reps):
+def _timed_contract(R, torch, ts, labels, out, precision, reps, path=((0, 1),)):
     """Plan (graph, timing) once, then `reps` replays: (ms per call from
     events around the calls, [(gemm ms, flops, bytes, kind, whole ms)])."""
     fl = R.OPT_GRAPH | R.OPT_TIMING
+    path = [tuple(p) for p in path]
     for _ in range(2):
-        C = R.contract(ts, labels, out, [(0, 1)], precision=precision, flags=fl)
+        C = R.contract(ts, labels, out, path, precision=precision, flags=fl)
         del C
     torch.cuda.synchronize()
     R.timing_drain()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        C = R.contract(ts, labels, out, [(0, 1)], precision=precision, flags=fl)
+        C = R.contract(ts, labels, out, path, precision=precision, flags=fl)
         del C
     e1.record()
     torch.cuda.synchronize()
@@ -427,9 +428,55 @@ def run_extras(R, torch, dev, probed):
         out["sweep_chunk"] = {"shape": "M = 2^10, N = 2^20, K = 2^10 complex64 (2^12-entry blocks, B_k = 16)",
                               "flop": flop, "modes": rows}
         del As, B
+        R.release_plans()
     except Exception as e:
         out["sweep_chunk"] = {"error": str(e)[:200]}
+    try:
+        out["gates_hbm"] = run_gate_extras(R, torch, dev)
+    except Exception as e:
+        out["gates_hbm"] = {"error": str(e)[:200]}
     return out
+
+
+def run_gate_extras(R, torch, dev, rank=28):
+    """Memory-bound contractions: one- and two-qubit gates applied along axes
+    of a [2]^28 complex64 tensor (2 GiB; entries from a seeded device
+    generator), each a single planned step whose kernel time is the timed
+    heavy launch.  Algorithmic bytes: the tensor read once, the result written
+    once (the gate's 32 or 128 bytes aside), against the measured HBM copy
+    bandwidth."""
+    peak = float(_measured_peaks().get("hbm_gbs", 6465.2))
+    T = R.empty((2,) * rank, None, R.C64)
+    g = torch.Generator(device=dev)
+    g.manual_seed(28)
+    raw = torch.randn(2 * T.numel, device=dev, generator=g) * 0.5 ** 0.5
+    T.upload_raw(raw)
+    torch.cuda.synchronize()
+    del raw
+    rng = np.random.default_rng(5)
+    rows = {}
+    labels_t = list(range(rank))
+    for name, axes, first in (("1q_axis13_out_last", (13,), False), ("1q_axis13_out_first", (13,), True),
+                              ("2q_axes9_20_out_last", (9, 20), False)):
+        q = len(axes)
+        gm = (rng.standard_normal((2,) * (2 * q)) + 1j * rng.standard_normal((2,) * (2 * q))).astype(np.complex64)
+        G = R.btensor(gm)
+        outs = [200 + i for i in range(q)]
+        rest = [x for x in labels_t if x not in axes]
+        lab = [labels_t, outs + list(axes)]
+        out_l = outs + rest if first else rest + outs
+        ms, recs = _timed_contract(R, torch, [T, G], lab, out_l, R.PREC_DEFAULT, 5,
+                                   path=[(1, 0)] if first else [(0, 1)])
+        kern = statistics.mean(r[0] for r in recs)
+        nbytes = 2 * T.numel * 8 + gm.size * 8
+        gbs = nbytes / (kern * 1e-3) / 1e9
+        rows[name] = {"kernel_ms": kern, "call_ms": ms, "bytes": nbytes, "achieved_gbs": gbs,
+                      "peak_gbs": peak, "frac_of_measured_hbm": gbs / peak,
+                      "kernel_kind": recs[0][3] if recs else None}
+        del G
+        R.release_plans()
+    del T
+    return {"tensor": "[2]^28 complex64 (2 GiB)", "rows": rows}
 
 
 def run_precision_modes(args, R, torch, net, path, bind, amps_fp32, flush, stream, flags):

@@ -624,8 +624,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         Step &S = plan->steps[g];
         views[g] = make_view(lay_of(S.ga), lay_of(S.gb), S.lay, S.naxes, S.axa.data(), S.axb.data());
         const int rec = gate_record_class(views[g], plan->dtype, prec, red,
-                                          (S.ga < 0 ? kFlagADense | kFlagAMVec : 0) |
-                                              (S.gb < 0 ? kFlagBDense | kFlagBNVec : 0));
+                                          (S.ga < 0 ? kFlagADense : 0) | (S.gb < 0 ? kFlagBDense : 0));
         for (int c = 0; c < 3; ++c) {
             const auto mt = class_of(views[g], c);
             const bool is_rec = c == rec;
@@ -664,8 +663,8 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
                          dtab + S.table_off[2]);
         // leaves change address from call to call: never read in place by a
         // tensor map that a captured graph would keep
-        if (S.ga < 0) S.desc.flags &= ~(kFlagADense | kFlagAMVec);
-        if (S.gb < 0) S.desc.flags &= ~(kFlagBDense | kFlagBNVec);
+        if (S.ga < 0) S.desc.flags &= ~kFlagADense;
+        if (S.gb < 0) S.desc.flags &= ~kFlagBDense;
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
         const bool cuda_core_gemm =

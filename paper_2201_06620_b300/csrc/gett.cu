@@ -1526,13 +1526,24 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
             if (c.part) launch_gett_single(c, kKindReduce, reduce_ctas(c), dtype, s);
         };
         once();   // warm-up
-        RN_CHECK_CUDA(cudaEventRecord(e0, s));
-        for (int r = 0; r < 3; ++r) once();
-        RN_CHECK_CUDA(cudaEventRecord(e1, s));
-        RN_CHECK_CUDA(cudaEventSynchronize(e1));
-        float ms = 0;
-        RN_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
+        float ms = 1e30f;
+        for (int trial = 0; trial < 3; ++trial) {   // best of three trials of 3 launches
+            RN_CHECK_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) once();
+            RN_CHECK_CUDA(cudaEventRecord(e1, s));
+            RN_CHECK_CUDA(cudaEventSynchronize(e1));
+            float t = 0;
+            RN_CHECK_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            ms = std::min(ms, t);
+        }
+        // the TMA-fed packed GEMM keeps its place unless another kernel is
+        // clearly faster: timed back to back with its operands in L2, the
+        // offset-table gathers of the tiled kernels look better than they do
+        // inside a contraction (4096 x 256 x 256 in the 20-qubit amplitude:
+        // within 3% here, 17% slower in place)
+        const bool pick_packed = pick.kind == kKindPackF32;
+        const float bar = packed == pick_packed ? best : packed ? best * 1.03f : best / 1.03f;
+        if (ms < bar) {
             best = ms;
             pick = c;
         }

@@ -93,10 +93,11 @@ def test_noalloc_matches_tensordot_two_calls_in_a_row():
 
 def test_noalloc_rejects_oversized_and_mismatched():
     R._init()
-    # offset tables alone exceed the fixed scratch (2*(2^19+4+1) int64 > 4 MiB)
-    A = R.btensor(np.ones((1 << 19, 1), dtype=np.complex64))
-    B = R.btensor(np.ones((1, 4), dtype=np.complex64))
-    C = R.empty((1 << 19, 4), None, R.C64)
+    # offset tables alone exceed the fixed scratch (2*(2^19+5+3) int64 > 4 MiB;
+    # 3 contracted indices keep it off the table-free gate kernel)
+    A = R.btensor(np.ones((1 << 19, 3), dtype=np.complex64))
+    B = R.btensor(np.ones((3, 5), dtype=np.complex64))
+    C = R.empty((1 << 19, 5), None, R.C64)
     with pytest.raises(R.RosnetError) as e:
         R.tensordot_noalloc(A, B, [1], [0], C)
     assert e.value.name == "UNSUPPORTED"
