@@ -499,11 +499,22 @@ rosnet_status rosnet_contract_batch(int32_t nnet, const rosnet_network *nets,
  * identical ones, of launches per call, and of operands that the plan's
  * packed-FP32 and tensor-core steps gather into a packed workspace per call
  * (an intermediate laid out as a dense K x rows matrix for a packed-FP32
- * step is read in place and not counted).  Any output may be NULL.
+ * step is read in place and not counted), and the device bytes the plan
+ * keeps between calls (intermediate arena, offset tables, descriptors,
+ * split-K partials, packed-operand workspace).  Any output may be NULL.
  * INVALID_ARG if not planned yet. */
 rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
                                 const rosnet_opts *opts, void *stream, int64_t *steps_requested,
-                                int64_t *steps_planned, int64_t *launches, int64_t *packed_operands);
+                                int64_t *steps_planned, int64_t *launches, int64_t *packed_operands,
+                                int64_t *device_bytes);
+
+/* Free the cached plan of these arguments (as rosnet_plan_stats), e.g. for a
+ * server that bounds the device memory its resident plans hold.  Work the
+ * plan already enqueued completes normally (buffers are released in stream
+ * order); a later call with the same arguments plans again.  INVALID_ARG if
+ * no such plan is cached. */
+rosnet_status rosnet_plan_release(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                  const rosnet_opts *opts, void *stream);
 
 /*
  * out = sum of the n tensors ts[0..n) in FP64, in that order (deterministic):

@@ -36,7 +36,7 @@ __all__ = [
     "PREC_TF32X3",
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
     "REDUCE_SEQUENTIAL", "REDUCE_TREE", "REDUCE_COMMUTATIVE", "OPT_AUTOTUNE",
-    "probe_peak", "PROBE_FFMA", "PROBE_DFMA", "PROBE_TF32", "PROBE_BF16",
+    "probe_peak", "PROBE_FFMA", "PROBE_DFMA", "PROBE_TF32", "PROBE_BF16", "plan_info", "plan_release",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -64,6 +64,7 @@ EXPORTS = [
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
     "rosnet_btensor_download_async", "rosnet_alloc_stats", "rosnet_btensor_upload_raw",
     "rosnet_btensor_download_raw", "rosnet_plan_cache_limit", "rosnet_probe_peak",
+    "rosnet_plan_release",
 ]
 
 _lock = threading.Lock()
@@ -138,7 +139,9 @@ def lib():
                                                 ctypes.POINTER(vp)]
             L.rosnet_plan_stats.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
                                             ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp, i64p,
-                                            i64p, i64p, i64p]
+                                            i64p, i64p, i64p, i64p]
+            L.rosnet_plan_release.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
+                                              ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp]
             L.rosnet_tensordot_ooc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Opts),
@@ -190,7 +193,7 @@ def lib():
                         "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
                         "rosnet_btensor_download_async", "rosnet_alloc_stats",
                         "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw",
-                        "rosnet_plan_cache_limit", "rosnet_probe_peak"):
+                        "rosnet_plan_cache_limit", "rosnet_probe_peak", "rosnet_plan_release"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -688,13 +691,25 @@ def contract_batch(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_e
 def plan_stats(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_entries=0, stream=None):
     """(steps requested, distinct steps planned, launches per call, operands
     gathered into a packed workspace per call) of a planned batch."""
+    return plan_info(networks, paths, precision, flags, max_block_entries, stream)[:4]
+
+
+def plan_info(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_entries=0, stream=None):
+    """plan_stats plus the device bytes the cached plan holds between calls."""
     nets, arr, parr = _batch_args(networks, paths)
     o = _opts(precision, flags, max_block_entries)
-    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    v = [ctypes.c_int64() for _ in range(5)]
     _check(lib().rosnet_plan_stats(len(nets), arr, parr, ctypes.byref(o), _stream(stream),
-                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
-           "rosnet_plan_stats")
-    return a.value, b.value, c.value, d.value
+                                   *[ctypes.byref(x) for x in v]), "rosnet_plan_stats")
+    return tuple(x.value for x in v)
+
+
+def plan_release(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_entries=0, stream=None):
+    """Free the cached plan of these arguments (rosnet_plan_release)."""
+    nets, arr, parr = _batch_args(networks, paths)
+    o = _opts(precision, flags, max_block_entries)
+    _check(lib().rosnet_plan_release(len(nets), arr, parr, ctypes.byref(o), _stream(stream)),
+           "rosnet_plan_release")
 
 
 def sync(stream=None):

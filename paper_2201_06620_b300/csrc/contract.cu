@@ -1037,10 +1037,9 @@ rosnet_status rosnet_contract_batch(int32_t nnet, const rosnet_network *nets, co
     RN_API_END
 }
 
-rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
-                                const rosnet_opts *opts, void *stream, int64_t *steps_requested,
-                                int64_t *steps_planned, int64_t *launches, int64_t *packed_operands) {
-    RN_API_BEGIN
+// The cache key of the plan rosnet_contract_batch would use for these arguments.
+static Key128 cached_key(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                         const rosnet_opts *opts, void *stream) {
     if (nnet < 1 || !nets || !paths) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no networks");
     for (int i = 0; i < nnet; ++i) precheck_network(&nets[i], &paths[i]);
     const int prec = check_precision(opts, nets[0].tensors[0]->dtype);
@@ -1048,10 +1047,22 @@ rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const 
     const int64_t maxblk = opts ? opts->max_block_entries : 0;
     std::vector<Leaf> leaves;
     auto slot = leaf_slots(nnet, nets, &leaves);
-    Key128 key = plan_key(nnet, nets, paths, slot, prec, flags, maxblk, (cudaStream_t)stream);
+    return plan_key(nnet, nets, paths, slot, prec, flags, maxblk, (cudaStream_t)stream);
+}
+
+rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                const rosnet_opts *opts, void *stream, int64_t *steps_requested,
+                                int64_t *steps_planned, int64_t *launches, int64_t *packed_operands,
+                                int64_t *device_bytes) {
+    RN_API_BEGIN
+    Key128 key = cached_key(nnet, nets, paths, opts, stream);
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
     if (it == g_plans.end()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no cached plan for these networks");
+    if (device_bytes) {
+        const Plan &P = *it->second;
+        *device_bytes = (int64_t)(P.arena.bytes + P.tables.bytes + P.descs.bytes + P.partials.bytes + P.tcws.bytes);
+    }
     if (steps_requested) *steps_requested = it->second->steps_requested;
     if (steps_planned) *steps_planned = (int64_t)it->second->steps.size();
     if (launches) *launches = (int64_t)it->second->launches.size();
@@ -1109,6 +1120,22 @@ rosnet_status rosnet_plan_cache_limit(int32_t max_plans, int32_t *cached) {
         if (max_plans > 0) evict_plans_to((size_t)max_plans);
     }
     if (cached) *cached = (int32_t)g_plans.size();
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_plan_release(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                  const rosnet_opts *opts, void *stream) {
+    RN_API_BEGIN
+    Key128 key = cached_key(nnet, nets, paths, opts, stream);
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it == g_plans.end()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no cached plan for these networks");
+    Plan *vp = it->second.get();
+    g_timing_log.erase(std::remove_if(g_timing_log.begin(), g_timing_log.end(),
+                                      [vp](const std::pair<Plan *, int> &e) { return e.first == vp; }),
+                       g_timing_log.end());
+    g_plans.erase(it);
     return ROSNET_OK;
     RN_API_END
 }

@@ -8,17 +8,22 @@ and the requested ones are read from that result.  Everything that runs on
 the device is rosnet_contract (librosnet's kernels); this module schedules.
 
 Scheduling: queries wait in arrival order; a query is admitted as soon as a
-stream slot is free and its predicted device footprint (its input tensors
-plus the peak of live intermediates along its path -- the analogue of the
-paper's per-task memory, Eq. 1 / Eq. 2) fits the memory budget next to the
-queries already running.  Admitted queries run concurrently on separate
-streams, so a query that arrives while others are on the GPU starts as soon
-as a slot and memory free up, and its kernels overlap theirs.  Each stream
-keeps one plan per (circuit, k) (offset tables, intermediate arena, captured
-CUDA graph) and a device buffer of projectors, so a query costs one small
-host-to-device copy (its prefix), one graph launch and one device-to-host
-copy (its amplitudes).  Latency runs from a query's arrival to the moment its
-amplitudes are on the host.
+stream slot is free and the device memory it needs fits the budget next to
+what is already held.  Each stream keeps one plan per (circuit, k) (offset
+tables, intermediate arena, captured CUDA graph) and a device buffer of
+projectors, so a query costs one small host-to-device copy (its prefix), one
+graph launch and one device-to-host copy (its amplitudes).  The budget
+counts every resident plan (its device bytes as the library reports them;
+before a plan exists, its predicted footprint: input tensors plus the peak
+of live intermediates along the path -- the analogue of the paper's
+per-task memory, Eq. 1 / Eq. 2) and the outputs of running queries.  When a
+query needs a new plan that does not fit, resident plans that no running
+query uses are freed, least recently used first; if it still does not fit
+it waits for running queries to retire (a query alone is always admitted).
+Admitted queries run concurrently on separate streams, so a query that
+arrives while others are on the GPU starts as soon as a slot and memory free
+up, and its kernels overlap theirs.  Latency runs from a query's arrival to
+the moment its amplitudes are on the host.
 """
 from __future__ import annotations
 
@@ -29,7 +34,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import C64, OPT_GRAPH, PREC_DEFAULT, Network, btensor, contract, empty, path_search
+from . import (C64, OPT_GRAPH, PREC_DEFAULT, Network, btensor, contract, empty, path_search, plan_info,
+               plan_release)
 
 __all__ = ["Query", "AmplitudeServer", "predict_footprint"]
 
@@ -126,13 +132,22 @@ class AmplitudeServer:
         self.slots = [_Slot(torch, nmax) for _ in range(slots)]
         self.free = list(range(slots))
         self.budget = memory_budget
-        self.in_use = 0.0
+        # resident plans: (slot, circuit, k) -> device bytes, least recently used first
+        self.resident = collections.OrderedDict()
+        self.resident_bytes = 0.0
+        self.in_use = 0.0          # outputs of running queries
+        self.evictions = 0
         self.precision = precision
         self.flags = OPT_GRAPH if use_graph else 0
         self.waiting = collections.deque()
         self.running = []
         self.finished = []
         self._qid = 0
+
+    @property
+    def device_bytes(self):
+        """Device memory the server accounts for: resident plans and running outputs."""
+        return self.resident_bytes + self.in_use
 
     def submit(self, q: Query, now=None):
         q.arrival = time.perf_counter() if now is None else now
@@ -142,15 +157,24 @@ class AmplitudeServer:
 
     def step(self):
         """Retire finished queries, then admit waiting ones while a slot is
-        free and their predicted footprint fits the budget."""
+        free and the memory they need fits the budget (freeing idle resident
+        plans, least recently used first, to make room)."""
         self._retire()
         while self.waiting and self.free:
             q = self.waiting[0]
-            foot = self.circuits[q.circuit].plan_for(q.k)[4]
-            if self.running and self.in_use + foot > self.budget:
+            si = self.free[-1]
+            key = (si, q.circuit, q.k)
+            need = 8.0 * 2 ** q.k + (0.0 if key in self.resident else self.circuits[q.circuit].plan_for(q.k)[4])
+            if self.device_bytes + need > self.budget:
+                busy = {(r[1], r[0].circuit, r[0].k) for r in self.running}
+                for victim in [k for k in self.resident if k not in busy and k != key]:
+                    if self.device_bytes + need <= self.budget:
+                        break
+                    self._evict(victim)
+            if self.running and self.device_bytes + need > self.budget:
                 break
             self.waiting.popleft()
-            self._launch(q, foot)
+            self._launch(q, key)
 
     def drain(self):
         while self.waiting or self.running:
@@ -159,38 +183,62 @@ class AmplitudeServer:
                 self.running[0][2].synchronize()
         self._retire()
 
-    def _launch(self, q, foot):
+    def _evict(self, key):
+        si, ci, k = key
+        sl = self.slots[si]
+        c = self.circuits[ci]
+        net = sl.nets.pop((ci, k))
+        plan_release([net], [c.plan_for(k)[2]], precision=self.precision, flags=self.flags, stream=sl.stream)
+        self.resident_bytes -= self.resident.pop(key)
+        self.evictions += 1
+
+    def _launch(self, q, key):
         torch = self.torch
-        si = self.free.pop()
+        si = key[0]
+        self.free.remove(si)
         sl = self.slots[si]
         c = self.circuits[q.circuit]
         labels, out, path, _, _ = c.plan_for(q.k)
         closed = c.n - q.k
-        key = (q.circuit, q.k)
-        if key not in sl.nets:
-            sl.nets[key] = Network(c.tensors + sl.views[:closed], labels, out)
+        if (q.circuit, q.k) not in sl.nets:
+            sl.nets[(q.circuit, q.k)] = Network(c.tensors + sl.views[:closed], labels, out)
+        net = sl.nets[(q.circuit, q.k)]
         pre = np.asarray(q.prefix, dtype=np.float32)
         sl.host[:closed, 0] = 1.0 - pre
         sl.host[:closed, 1] = pre
         q.started = time.perf_counter()
         sl.buf.upload(sl.host, stream=sl.stream)
-        res = contract(sl.nets[key], path=path, precision=self.precision, flags=self.flags,
-                       stream=sl.stream)
+        res = contract(net, path=path, precision=self.precision, flags=self.flags, stream=sl.stream)
+        if key in self.resident:
+            self.resident.move_to_end(key)
+        else:   # the plan now exists: account for what it really holds
+            nbytes = float(plan_info([net], [path], precision=self.precision, flags=self.flags,
+                                     stream=sl.stream)[4])
+            self.resident[key] = nbytes
+            self.resident_bytes += nbytes
         ev = torch.cuda.Event()
         ev.record(sl.stream)
-        self.in_use += foot
-        self.running.append((q, si, ev, res, foot))
+        out_bytes = 8.0 * 2 ** q.k
+        self.in_use += out_bytes
+        self.running.append((q, si, ev, res, out_bytes))
+        # a plan larger than predicted: free idle plans until the budget holds
+        if self.device_bytes > self.budget:
+            busy = {(r[1], r[0].circuit, r[0].k) for r in self.running}
+            for victim in [k for k in self.resident if k not in busy]:
+                if self.device_bytes <= self.budget:
+                    break
+                self._evict(victim)
 
     def _retire(self):
         keep = []
-        for q, si, ev, res, foot in self.running:
+        for q, si, ev, res, out_bytes in self.running:
             if ev.query():
                 amps = res.download(stream=self.slots[si].stream).reshape(-1)
                 q.result = amps[np.asarray(q.suffixes, dtype=np.int64)]
                 q.done = time.perf_counter()
-                self.in_use -= foot
+                self.in_use -= out_bytes
                 self.free.append(si)
                 self.finished.append(q)
             else:
-                keep.append((q, si, ev, res, foot))
+                keep.append((q, si, ev, res, out_bytes))
         self.running = keep

@@ -154,3 +154,44 @@ def test_server_tf32x3_vs_oracle():
         scale = max(np.abs(ref).max(), 2.0 ** (-n / 2))
         assert np.abs(a - ref).max() / scale <= 1e-5
         assert np.abs(m.result - ref).max() / scale <= 1e-5
+
+
+def test_budget_holds_resident_plans_across_many_circuits():
+    """Each slot keeps a plan per (circuit, k); with a budget that holds only
+    a few of them, idle plans are freed (least recently used first) so that
+    resident plans plus running outputs stay within the budget whenever more
+    than one query runs; results still match the state vector, and plans
+    freed and built again give the same amplitudes."""
+    rng = np.random.default_rng(17)
+    circs = [W.random_circuit(int(rng.integers(10, 13)), 6, 1100 + i) for i in range(6)]
+    psi = [oracle.statevector(c) for c in circs]
+    probe = AmplitudeServer(circs, slots=1)
+    sizes = []
+    for ci in range(len(circs)):
+        q = Query(circuit=ci, prefix=(0,) * (circs[ci].n - 2), k=2, suffixes=[0, 3])
+        probe.submit(q)
+        probe.drain()
+        sizes.append(probe.resident[(0, ci, 2)])
+    budget = 2.5 * max(sizes)
+    srv = AmplitudeServer(circs, slots=2, memory_budget=budget)
+    queries = _queries(circs, rng, 40)
+    for q in queries:
+        srv.submit(q)
+    while srv.waiting or srv.running:
+        srv.step()
+        busy = {(r[1], r[0].circuit, r[0].k) for r in srv.running}
+        idle = [k for k in srv.resident if k not in busy]
+        assert srv.device_bytes <= budget or len(srv.running) <= 1 or not idle, (srv.device_bytes, budget)
+        if srv.running:
+            srv.running[0][2].synchronize()
+    srv.drain()
+    assert len(srv.finished) == len(queries)
+    assert srv.evictions > 0
+    for q in srv.finished:
+        n = circs[q.circuit].n
+        base = 0
+        for b in q.prefix:
+            base = (base << 1) | b
+        ref = np.array([psi[q.circuit][(base << q.k) | s] for s in q.suffixes])
+        scale = max(np.abs(ref).max(), 2.0 ** (-n / 2))
+        assert np.abs(q.result - ref).max() / scale <= 1e-5
