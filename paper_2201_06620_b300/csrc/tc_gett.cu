@@ -20,8 +20,8 @@
 //      (cp.async.bulk.tensor, 64-byte swizzle = the MMA's K-major layout);
 //      one thread issues the MMAs; eight warps own the output tile.  The
 //      contracted loop (every matched block pair of the tile, Sec. II-C steps
-//      2-4) is accumulated in chunks (256 k for TF32, 64 k for the split
-//      modes) in two alternating TMEM accumulators; the eight warps add each
+//      2-4) is accumulated in chunks (256 k for TF32, 16 k for 3xTF32, 64 k
+//      for 3xBF16) in two alternating TMEM accumulators; the eight warps add each
 //      finished chunk into FP32 registers while the tensor core fills the
 //      other one.  The tensor core's accumulator adds carry a small one-sided
 //      error that grows with the number of terms; chunking caps it.  The sum
