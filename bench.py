@@ -895,6 +895,62 @@ def run_reduction(args):
                       "rows": rows}), flush=True)
 
 
+def run_tensordot(args):
+    """One pairwise contraction C = A^T B with A stored (K, M) and B (K, N)
+    (dense complex64 in the layout the TMA-fed GEMMs read in place; entries
+    from a seeded device generator), planned once and replayed: per-call
+    kernel time of the GEMM launch and algorithmic TFLOP/s.  For profiling
+    one kernel on a chosen shape (--mnk M,N,K --precision ...)."""
+    import torch
+    import paper_2201_06620_b300 as R
+    M, N, K = (int(x) for x in args.mnk.split(","))
+    prec = {"fp32": R.PREC_FP32, "tf32": R.PREC_TF32, "tf32x3": R.PREC_TF32X3,
+            "bf16x3": R.PREC_BF16X3}[args.precision]
+    dev = torch.device("cuda", 0)
+    A, B = R.empty((K, M), None, R.C64), R.empty((K, N), None, R.C64)
+    g = torch.Generator(device=dev)
+    for t, seed in ((A, 1), (B, 2)):
+        g.manual_seed(seed)
+        raw = torch.randn(2 * t.numel, device=dev, generator=g) * 0.5 ** 0.5
+        t.upload_raw(raw)
+        torch.cuda.synchronize()
+        del raw
+    ms, recs = _timed_contract(R, torch, [A, B], [(0, 1), (0, 2)], [1, 2], prec, max(args.steps, 1))
+    kern = statistics.mean(r[0] for r in recs)
+    flop = 8.0 * M * N * K
+    print(json.dumps({"metric": "tensordot TFLOP/s", "workload": f"tensordot {M}x{N}x{K} complex64",
+                      "precision": args.precision, "gemm_kernel_ms": kern, "call_ms": ms,
+                      "tflops": flop / (kern * 1e-3) / 1e12, "kernel_kind": recs[0][3] if recs else None}),
+          flush=True)
+
+
+def run_gate(args):
+    """A one-qubit gate on axis --axis of a [2]^--rank complex64 tensor (a
+    single planned step on the gate kernel, the gate's output axis last):
+    kernel time and HBM GB/s of the algorithmic bytes (tensor read once,
+    result written once).  For profiling the memory-bound kernel."""
+    import torch
+    import paper_2201_06620_b300 as R
+    dev = torch.device("cuda", 0)
+    T = R.empty((2,) * args.rank, None, R.C64)
+    g = torch.Generator(device=dev)
+    g.manual_seed(args.rank)
+    raw = torch.randn(2 * T.numel, device=dev, generator=g) * 0.5 ** 0.5
+    T.upload_raw(raw)
+    torch.cuda.synchronize()
+    del raw
+    G = R.btensor(W.SQRT_X.astype(np.complex64))
+    lt = list(range(args.rank))
+    out = [x for x in lt if x != args.axis] + [100]
+    ms, recs = _timed_contract(R, torch, [T, G], [lt, [100, args.axis]], out, R.PREC_DEFAULT, max(args.steps, 1))
+    kern = statistics.mean(r[0] for r in recs)
+    nbytes = 2 * T.numel * 8 + 32
+    print(json.dumps({"metric": "HBM GB/s", "workload": f"1q gate on axis {args.axis} of [2]^{args.rank} complex64",
+                      "kernel_ms": kern, "call_ms": ms, "bytes": nbytes,
+                      "gbs": nbytes / (kern * 1e-3) / 1e9, "kernel_kind": recs[0][3] if recs else None}),
+          flush=True)
+
+
 def run_sweep(args):
     """Precision sweep: [2]^30 x [2]^30 -> [2]^40 in 2^30-entry chunks."""
     import torch
@@ -957,7 +1013,13 @@ def main():
     ap.add_argument("--no-probes", action="store_true", help="skip the peak-rate probes")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the extra measurements (FP64 blocked tensordot, large tensor-core contractions)")
-    ap.add_argument("--workload", choices=["rqc20", "serve", "batch", "sweep", "reduction"], default="rqc20")
+    ap.add_argument("--workload", choices=["rqc20", "serve", "batch", "sweep", "reduction", "tensordot", "gate"],
+                    default="rqc20")
+    ap.add_argument("--mnk", default="1024,32768,1024", help="tensordot workload: M,N,K")
+    ap.add_argument("--precision", choices=["fp32", "tf32", "tf32x3", "bf16x3"], default="fp32",
+                    help="tensordot workload: arithmetic")
+    ap.add_argument("--rank", type=int, default=25, help="gate workload: tensor rank")
+    ap.add_argument("--axis", type=int, default=12, help="gate workload: gate axis")
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=20.0)
@@ -980,6 +1042,10 @@ def main():
         run_sweep(args)
     elif args.workload == "reduction":
         run_reduction(args)
+    elif args.workload == "tensordot":
+        run_tensordot(args)
+    elif args.workload == "gate":
+        run_gate(args)
     else:
         run_rosnet(args)
 

@@ -289,6 +289,12 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(const __grid_constant__ Gr
 // ---------------------------------------------------------------------------
 // 2. TMA + tcgen05 GEMM with chunked TMEM accumulation
 // ---------------------------------------------------------------------------
+// Persistent: one CTA per SM walks the output tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; stages and TMEM chunks are numbered across
+// the CTA's tiles, so the TMA ring and the two accumulators run on from one
+// tile into the next: the tensor core starts the next tile's first chunk
+// while the accumulator warps add the last chunk of the previous one and
+// store it, and the CTA's setup (barriers, TMEM allocation) happens once.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ TcArgs p) {
     using C_ = Cfg<MODE>;
@@ -328,88 +334,108 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     const uint32_t tmem = tmem_base;
     // raster: the operand with fewer tiles varies fastest, so its tiles stay
     // resident in L2 while the other operand streams through once
-    const int64_t tile = (int64_t)blockIdx.x - sd.tile_begin;
     const bool n_fast = sd.tiles_n < sd.tiles_m;
-    const int64_t tm = n_fast ? tile / sd.tiles_n : tile % sd.tiles_m;
-    const int64_t tn = n_fast ? tile % sd.tiles_n : tile / sd.tiles_m;
-    const int64_t m0 = tm * BM, n0 = tn * BN;
+    auto tile_origin = [&](int64_t tile, int64_t &m0, int64_t &n0) {
+        const int64_t tm = n_fast ? tile / sd.tiles_n : tile % sd.tiles_m;
+        const int64_t tn = n_fast ? tile % sd.tiles_n : tile / sd.tiles_m;
+        m0 = tm * BM;
+        n0 = tn * BN;
+    };
+    const int64_t ntiles = sd.tiles_m * sd.tiles_n;
+    const int64_t first = (int64_t)blockIdx.x - sd.tile_begin, G = gridDim.x;
+    const int mytiles = first < ntiles ? (int)((ntiles - first + G - 1) / G) : 0;
     const int nkt = p.nkt;
     const int nchunks = (nkt + C_::CH_STAGES - 1) / C_::CH_STAGES;
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
-            int issued = 0;
-            for (int kt = 0; kt < nkt; ++kt) {
-                const int s = kt % STAGES;
-                if (!mbar_wait(&empty_bar[s], ((kt / STAGES) & 1) ^ 1, &abort_flag)) break;
-                mbar_expect_tx(&full_bar[s], C_::STAGE);
-                const uint32_t sa = su32(dsm + (size_t)s * C_::STAGE);
-                const uint32_t sb = sa + NARR * C_::ARR_A;
+            int issued = 0;   // stages issued over all tiles
+            bool go = true;
+            for (int i = 0; i < mytiles && go; ++i) {
+                int64_t m0, n0;
+                tile_origin(first + (int64_t)i * G, m0, n0);
+                for (int kt = 0; kt < nkt; ++kt) {
+                    const int g = issued, s = g % STAGES;
+                    if (!mbar_wait(&empty_bar[s], ((g / STAGES) & 1) ^ 1, &abort_flag)) {
+                        go = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full_bar[s], C_::STAGE);
+                    const uint32_t sa = su32(dsm + (size_t)s * C_::STAGE);
+                    const uint32_t sb = sa + NARR * C_::ARR_A;
 #pragma unroll
-                for (int a = 0; a < NARR; ++a) {
-                    tma_load_2d(sa + a * C_::ARR_A, &p.mapA[a], kt * BK, (int)m0, &full_bar[s]);
-                    tma_load_2d(sb + a * C_::ARR_B, &p.mapB[a], kt * BK, (int)n0, &full_bar[s]);
+                    for (int a = 0; a < NARR; ++a) {
+                        tma_load_2d(sa + a * C_::ARR_A, &p.mapA[a], kt * BK, (int)m0, &full_bar[s]);
+                        tma_load_2d(sb + a * C_::ARR_B, &p.mapB[a], kt * BK, (int)n0, &full_bar[s]);
+                    }
+                    issued = g + 1;
                 }
-                issued = kt + 1;
             }
             // copies still in flight must land before this CTA can exit
-            for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
-                mbar_wait(&full_bar[kt % STAGES], (kt / STAGES) & 1, &abort_flag, false);
+            for (int g = (issued > STAGES ? issued - STAGES : 0); g < issued; ++g)
+                mbar_wait(&full_bar[g % STAGES], (g / STAGES) & 1, &abort_flag, false);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issue
         if (lane == 0) {
-            int kt = 0;
+            int g = 0;    // stage counter over all tiles
+            int gc = 0;   // chunk counter over all tiles
             bool go = true;
-            for (int c = 0; c < nchunks && go; ++c) {
-                const int b = c & 1;
-                if (c >= 2 && !mbar_wait(&acce[b], ((c >> 1) - 1) & 1, &abort_flag)) break;
-                tc_fence_after();
-                const uint32_t dr = tmem + b * 2 * BN, di = dr + BN;
-                const int kend = min(nkt, (c + 1) * C_::CH_STAGES);
-                for (; kt < kend; ++kt) {
-                    const int s = kt % STAGES;
-                    if (!mbar_wait(&full_bar[s], (kt / STAGES) & 1, &abort_flag)) {
+            for (int i = 0; i < mytiles && go; ++i) {
+                int kt = 0;
+                for (int c = 0; c < nchunks && go; ++c, ++gc) {
+                    const int b = gc & 1;
+                    if (gc >= 2 && !mbar_wait(&acce[b], ((gc >> 1) - 1) & 1, &abort_flag)) {
                         go = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = su32(dsm + (size_t)s * C_::STAGE);
-                    const uint32_t sb = sa + NARR * C_::ARR_A;
-#pragma unroll
-                    for (int ks = 0; ks < C_::KSTEPS; ++ks) {
-                        const uint32_t kb = ks * 32;   // byte offset of this MMA's K slice
-                        auto A_ = [&](int arr) { return sdesc(sa + arr * C_::ARR_A + kb); };
-                        auto B_ = [&](int arr) { return sdesc(sb + arr * C_::ARR_B + kb); };
-                        const uint32_t acc = (kt == c * C_::CH_STAGES && ks == 0) ? 0u : 1u;
-                        if (MODE == kTF32) {
-                            // arrays: 0 = re, 1 = im
-                            mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), acc);
-                            mma<MODE>(dr, A_(1), B_(1), idesc<MODE>(true), 1u);
-                            mma<MODE>(di, A_(0), B_(1), idesc<MODE>(false), acc);
-                            mma<MODE>(di, A_(1), B_(0), idesc<MODE>(false), 1u);
-                        } else {
-                            // arrays: 0 = re big/hi, 1 = re small/lo, 2 = im big/hi, 3 = im small/lo
-                            mma<MODE>(dr, A_(0), B_(1), idesc<MODE>(false), acc);
-                            mma<MODE>(dr, A_(1), B_(0), idesc<MODE>(false), 1u);
-                            mma<MODE>(dr, A_(2), B_(3), idesc<MODE>(true), 1u);
-                            mma<MODE>(dr, A_(3), B_(2), idesc<MODE>(true), 1u);
-                            mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), 1u);
-                            mma<MODE>(dr, A_(2), B_(2), idesc<MODE>(true), 1u);
-                            mma<MODE>(di, A_(0), B_(3), idesc<MODE>(false), acc);
-                            mma<MODE>(di, A_(1), B_(2), idesc<MODE>(false), 1u);
-                            mma<MODE>(di, A_(2), B_(1), idesc<MODE>(false), 1u);
-                            mma<MODE>(di, A_(3), B_(0), idesc<MODE>(false), 1u);
-                            mma<MODE>(di, A_(0), B_(2), idesc<MODE>(false), 1u);
-                            mma<MODE>(di, A_(2), B_(0), idesc<MODE>(false), 1u);
+                    const uint32_t dr = tmem + b * 2 * BN, di = dr + BN;
+                    const int kend = min(nkt, (c + 1) * C_::CH_STAGES);
+                    for (; kt < kend; ++kt, ++g) {
+                        const int s = g % STAGES;
+                        if (!mbar_wait(&full_bar[s], (g / STAGES) & 1, &abort_flag)) {
+                            go = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t sa = su32(dsm + (size_t)s * C_::STAGE);
+                        const uint32_t sb = sa + NARR * C_::ARR_A;
+#pragma unroll
+                        for (int ks = 0; ks < C_::KSTEPS; ++ks) {
+                            const uint32_t kb = ks * 32;   // byte offset of this MMA's K slice
+                            auto A_ = [&](int arr) { return sdesc(sa + arr * C_::ARR_A + kb); };
+                            auto B_ = [&](int arr) { return sdesc(sb + arr * C_::ARR_B + kb); };
+                            const uint32_t acc = (kt == c * C_::CH_STAGES && ks == 0) ? 0u : 1u;
+                            if (MODE == kTF32) {
+                                // arrays: 0 = re, 1 = im
+                                mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), acc);
+                                mma<MODE>(dr, A_(1), B_(1), idesc<MODE>(true), 1u);
+                                mma<MODE>(di, A_(0), B_(1), idesc<MODE>(false), acc);
+                                mma<MODE>(di, A_(1), B_(0), idesc<MODE>(false), 1u);
+                            } else {
+                                // arrays: 0 = re big/hi, 1 = re small/lo, 2 = im big/hi, 3 = im small/lo
+                                mma<MODE>(dr, A_(0), B_(1), idesc<MODE>(false), acc);
+                                mma<MODE>(dr, A_(1), B_(0), idesc<MODE>(false), 1u);
+                                mma<MODE>(dr, A_(2), B_(3), idesc<MODE>(true), 1u);
+                                mma<MODE>(dr, A_(3), B_(2), idesc<MODE>(true), 1u);
+                                mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), 1u);
+                                mma<MODE>(dr, A_(2), B_(2), idesc<MODE>(true), 1u);
+                                mma<MODE>(di, A_(0), B_(3), idesc<MODE>(false), acc);
+                                mma<MODE>(di, A_(1), B_(2), idesc<MODE>(false), 1u);
+                                mma<MODE>(di, A_(2), B_(1), idesc<MODE>(false), 1u);
+                                mma<MODE>(di, A_(3), B_(0), idesc<MODE>(false), 1u);
+                                mma<MODE>(di, A_(0), B_(2), idesc<MODE>(false), 1u);
+                                mma<MODE>(di, A_(2), B_(0), idesc<MODE>(false), 1u);
+                            }
+                        }
+                        mma_commit(&empty_bar[s]);   // frees the stage once these MMAs are done
                     }
-                    mma_commit(&empty_bar[s]);   // frees the stage once these MMAs are done
+                    if (go) mma_commit(&accf[b]);    // chunk gc is complete in accumulator b
                 }
-                if (go) mma_commit(&accf[b]);    // chunk c is complete in accumulator b
             }
-            mma_commit(&fin_bar);                // every MMA of this thread has completed
+            mma_commit(&fin_bar);                    // every MMA of this thread has completed
             mbar_wait(&fin_bar, 0, &abort_flag, false);
         }
     } else {
@@ -418,45 +444,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int h = e >> 2;                   // column half of the tile
         const int r = q * 32 + lane;            // output row of this thread
-        float sr[64], si[64];
-#pragma unroll
-        for (int j = 0; j < 64; ++j) sr[j] = si[j] = 0.f;
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c & 1;
-            ok = mbar_wait(&accf[b], (c >> 1) & 1, &abort_flag);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 2 * BN + h * 64;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                uint32_t vr[16], vi[16];
-                tmem_ld16(base + j * 16, vr);
-                tmem_ld16(base + BN + j * 16, vi);
-                tmem_wait_ld();
-#pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    sr[j * 16 + t] += __uint_as_float(vr[t]);
-                    si[j * 16 + t] += __uint_as_float(vi[t]);
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[b]);   // accumulator b may be overwritten
-        }
         const int64_t M = sd.M, N = sd.N;
-        if (ok && !abort_flag && m0 + r < M) {
-            float *__restrict__ C = (float *)sd.c;
-            const int64_t cp = sd.c_plane;
-            const int64_t cm = sd.offCM[m0 + r];
+        bool ok = true;
+        int gc = 0;
+        for (int i = 0; i < mytiles && ok; ++i) {
+            float sr[64], si[64];
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int64_t n = n0 + h * 64 + j;
-                if (n < N) {
-                    const int64_t o = cm + __ldg(sd.offCN + n);
-                    C[o] = sr[j];
-                    C[o + cp] = si[j];
+            for (int j = 0; j < 64; ++j) sr[j] = si[j] = 0.f;
+            for (int c = 0; c < nchunks; ++c, ++gc) {
+                const int b = gc & 1;
+                ok = mbar_wait(&accf[b], (gc >> 1) & 1, &abort_flag);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + b * 2 * BN + h * 64;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t vr[16], vi[16];
+                    tmem_ld16(base + j * 16, vr);
+                    tmem_ld16(base + BN + j * 16, vi);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        sr[j * 16 + t] += __uint_as_float(vr[t]);
+                        si[j * 16 + t] += __uint_as_float(vi[t]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[b]);   // accumulator b may be overwritten
+            }
+            if (!ok || abort_flag) break;
+            // the tile's sum to C, while the tensor core runs on into the next tile
+            int64_t m0, n0;
+            tile_origin(first + (int64_t)i * G, m0, n0);
+            if (m0 + r < M) {
+                float *C = (float *)sd.c;
+                const int64_t cp = sd.c_plane;
+                const int64_t cm = sd.offCM[m0 + r];
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const int64_t n = n0 + h * 64 + j;
+                    if (n < N) {
+                        const int64_t o = cm + __ldg(sd.offCN + n);
+                        C[o] = sr[j];
+                        C[o + cp] = si[j];
+                    }
                 }
             }
         }
@@ -992,7 +1025,9 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
     args.g = ga;
     args.nkt = (int)(g.Kpad / g.bk);
     if (before_gemm) before_gemm();
-    tc::tc_gemm_kernel<MODE><<<(unsigned)ctas, tc::NTHREADS, C_::SMEM, s>>>(args);
+    // persistent: one CTA per SM (its shared memory allows no second one)
+    const int64_t grid = std::min<int64_t>(ctas, (int64_t)num_sms());
+    tc::tc_gemm_kernel<MODE><<<(unsigned)grid, tc::NTHREADS, C_::SMEM, s>>>(args);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
 }
