@@ -525,6 +525,15 @@ rosnet_status rosnet_plan_release(int32_t nnet, const rosnet_network *nets, cons
  */
 rosnet_status rosnet_sum(int32_t n, const rosnet_btensor *ts, void *stream, rosnet_btensor *out);
 
+/*
+ * *out = sum over all elements x of t of |x|^2, accumulated in FP64 on the
+ * GPU in a fixed order (reproducible on a given device): the normalisation
+ * check of a state or of a batch of amplitudes (sum over all bitstrings of
+ * |<x|C|0>|^2 = 1, Sec. II-A).  Works on views.  Enqueued on `stream` and
+ * waited for (synchronous).  INVALID_ARG for NULL arguments.
+ */
+rosnet_status rosnet_norm2(rosnet_btensor t, void *stream, double *out);
+
 /* ----------------------------------------------------------------------- */
 /* misc                                                                     */
 /* ----------------------------------------------------------------------- */

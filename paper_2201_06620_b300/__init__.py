@@ -37,6 +37,7 @@ __all__ = [
     "OPT_GRAPH", "OPT_NOGROUP", "OPT_TIMING", "STATUS", "Network", "timing_drain",
     "REDUCE_SEQUENTIAL", "REDUCE_TREE", "REDUCE_COMMUTATIVE", "OPT_AUTOTUNE",
     "probe_peak", "PROBE_FFMA", "PROBE_DFMA", "PROBE_TF32", "PROBE_BF16", "plan_info", "plan_release",
+    "norm2",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -64,7 +65,7 @@ EXPORTS = [
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
     "rosnet_btensor_download_async", "rosnet_alloc_stats", "rosnet_btensor_upload_raw",
     "rosnet_btensor_download_raw", "rosnet_plan_cache_limit", "rosnet_probe_peak",
-    "rosnet_plan_release",
+    "rosnet_plan_release", "rosnet_norm2",
 ]
 
 _lock = threading.Lock()
@@ -142,6 +143,7 @@ def lib():
                                             i64p, i64p, i64p, i64p]
             L.rosnet_plan_release.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
                                               ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp]
+            L.rosnet_norm2.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
             L.rosnet_tensordot_ooc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Opts),
@@ -193,7 +195,8 @@ def lib():
                         "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
                         "rosnet_btensor_download_async", "rosnet_alloc_stats",
                         "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw",
-                        "rosnet_plan_cache_limit", "rosnet_probe_peak", "rosnet_plan_release"):
+                        "rosnet_plan_cache_limit", "rosnet_probe_peak", "rosnet_plan_release",
+                        "rosnet_norm2"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -710,6 +713,14 @@ def plan_release(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_ent
     o = _opts(precision, flags, max_block_entries)
     _check(lib().rosnet_plan_release(len(nets), arr, parr, ctypes.byref(o), _stream(stream)),
            "rosnet_plan_release")
+
+
+def norm2(t, stream=None):
+    """Sum of |x|^2 over the tensor, accumulated in FP64 on the GPU."""
+    _init()
+    out = ctypes.c_double()
+    _check(lib().rosnet_norm2(t.handle, _stream(stream), ctypes.byref(out)), "rosnet_norm2")
+    return out.value
 
 
 def sync(stream=None):

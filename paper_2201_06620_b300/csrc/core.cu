@@ -308,6 +308,44 @@ void launch_relayout(const Layout &src, const Layout &dst, const int *perm, int 
     launch_copy<2>(cm, dst.numel, dtype, sp, spstride, dp, dpstride, s);
 }
 
+// Sum of |x|^2 over a tensor in FP64: every thread of a fixed grid adds the
+// elements i = tid, tid + grid, ... (logical row-major index, offsets from
+// the layout, so views work), the block's threads are summed in a fixed
+// tree, and one block adds the per-block partials in block order: a fixed
+// order for a given grid, so the result is reproducible.
+template <typename T>
+__global__ void __launch_bounds__(256) norm2_partial_kernel(Layout lay, const T *__restrict__ re, int64_t pstride,
+                                                             double *__restrict__ part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < lay.numel; i += (int64_t)gridDim.x * 256) {
+        int64_t r = i, off = 0;
+        for (int a = lay.rank - 1; a >= 0; --a) {
+            const int64_t x = r % lay.shape[a];
+            r /= lay.shape[a];
+            off += (x / lay.block[a]) * lay.gstride[a] + (x % lay.block[a]) * lay.lstride[a];
+        }
+        const double xr = (double)re[off], xi = (double)re[off + pstride];
+        acc = fma(xr, xr, acc);
+        acc = fma(xi, xi, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void norm2_final_kernel(const double *__restrict__ part, int nparts, double *__restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int j = 0; j < nparts; ++j) s += part[j];
+        *out = s;
+    }
+}
+
 // out[i] = sum_j in_j[i] in FP64, j in order (deterministic); inputs complex64
 // or complex128 planar with plane strides ps[j], output complex128 planar.
 template <typename T>
@@ -425,6 +463,32 @@ rosnet_status rosnet_btensor_upload_range(rosnet_btensor t, const void *host, in
     RN_CHECK_CUDA(cudaMemcpyAsync(stage.p, host, bytes, cudaMemcpyHostToDevice, s));
     launch_pack(t->lay, t->dtype, stage.p, t->data, t->pstride, start, count, s);
     if (t->owned) t->stream = s;
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_norm2(rosnet_btensor t, void *stream, double *out) {
+    if (!t || !out) return ROSNET_ERR_INVALID_ARG;
+    RN_API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nparts = num_sms() * 4;
+    DevBuf buf((size_t)(nparts + 1) * sizeof(double), s);
+    double *part = (double *)buf.p, *res = part + nparts;
+    if (t->lay.numel == 0) {
+        *out = 0.0;
+        return ROSNET_OK;
+    }
+    if (t->dtype == ROSNET_C64)
+        rosnet::norm2_partial_kernel<float><<<nparts, 256, 0, s>>>(t->lay, (const float *)t->data, t->pstride, part);
+    else
+        rosnet::norm2_partial_kernel<double><<<nparts, 256, 0, s>>>(t->lay, (const double *)t->data, t->pstride, part);
+    rosnet::norm2_final_kernel<<<1, 32, 0, s>>>(part, nparts, res);
+    g_launches += 2;
+    RN_CHECK_CUDA(cudaGetLastError());
+    double h = 0.0;
+    RN_CHECK_CUDA(cudaMemcpyAsync(&h, res, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RN_CHECK_CUDA(cudaStreamSynchronize(s));
+    *out = h;
     return ROSNET_OK;
     RN_API_END
 }

@@ -372,17 +372,20 @@ __global__ void __launch_bounds__(256) gett_warpk_kernel(const __grid_constant__
 }
 
 // One cluster of kDotCTAs CTAs per output entry for very long contractions
-// with few outputs (e.g. the final scalar of a network): the cluster's
-// threads stride over K with four independent loads in flight each, every
-// CTA reduces its threads' sums in a fixed order, and CTA 0 of the cluster
-// adds the CTAs' sums in rank order through distributed shared memory.  One
-// launch, no workspace, deterministic.
+// with few outputs (e.g. the final scalar of a network: an amplitude): the
+// cluster's threads stride over K with four independent loads in flight
+// each, every CTA reduces its threads' sums in a fixed order, and CTA 0 of
+// the cluster adds the CTAs' sums in rank order through distributed shared
+// memory.  Products and sums are taken in FP64 whatever the operands' type
+// (a product of two floats is exact in double), so the final reduction of an
+// amplitude adds no FP32 rounding; the result is rounded once to C's type.
+// One launch, no workspace, deterministic.
 template <typename T>
 __global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
     gett_dot_kernel(const __grid_constant__ GroupArgs g) {
     __shared__ GettDesc sd;
-    __shared__ T red[2][8];
-    __shared__ T cta_sum[2];
+    __shared__ double red[2][8];
+    __shared__ double cta_sum[2];
     grid_dep_launch();
     if (threadIdx.x < 32) load_desc(g, sd);
     __syncthreads();
@@ -401,7 +404,10 @@ __global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
     const int64_t ap = sd.a_plane, bp = sd.b_plane;
     constexpr int64_t stride = 256 * kDotCTAs;
     grid_dep_wait();
-    T sr = 0, si = 0;
+    double sr = 0, si = 0;
+    auto mac = [&](T ar, T ai, T br, T bi) {
+        cmac<double>(sr, si, (double)ar, (double)ai, (double)br, (double)bi);
+    };
     int64_t k = (int64_t)rank * 256 + threadIdx.x;
     for (; k + 3 * stride < K; k += 4 * stride) {
         int64_t ia[4], ib[4];
@@ -411,12 +417,11 @@ __global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
             ib[u] = bn + __ldg(offBK + k + stride * u);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) cmac(sr, si, __ldg(A + ia[u]), __ldg(A + ia[u] + ap), __ldg(B + ib[u]),
-                                         __ldg(B + ib[u] + bp));
+        for (int u = 0; u < 4; ++u) mac(__ldg(A + ia[u]), __ldg(A + ia[u] + ap), __ldg(B + ib[u]), __ldg(B + ib[u] + bp));
     }
     for (; k < K; k += stride) {
         const int64_t ia = am + offAK[k], ib = bn + offBK[k];
-        cmac(sr, si, A[ia], A[ia + ap], B[ib], B[ib + bp]);
+        mac(A[ia], A[ia + ap], B[ib], B[ib + bp]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -430,7 +435,7 @@ __global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        T tr = 0, ti = 0;
+        double tr = 0, ti = 0;
         for (int j = 0; j < 8; ++j) {
             tr += red[0][j];
             ti += red[1][j];
@@ -440,16 +445,16 @@ __global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
     }
     cluster.sync();   // every CTA's sum is visible to the cluster
     if (rank == 0 && threadIdx.x == 0) {
-        T tr = 0, ti = 0;
+        double tr = 0, ti = 0;
         for (int r = 0; r < kDotCTAs; ++r) {
-            const T *p = cluster.map_shared_rank(cta_sum, r);
+            const double *p = cluster.map_shared_rank(cta_sum, r);
             tr += p[0];
             ti += p[1];
         }
         T *C = (T *)sd.c;
         const int64_t ic = sd.offCM[m] + sd.offCN[n];
-        C[ic] = tr;
-        C[ic + sd.c_plane] = ti;
+        C[ic] = (T)tr;
+        C[ic + sd.c_plane] = (T)ti;
     }
     cluster.sync();   // no CTA leaves while CTA 0 may still read its sum
 }

@@ -67,6 +67,31 @@ def test_open_output_state_and_norm():
         assert abs(np.sum(np.abs(got.astype(np.complex128)) ** 2) - 1) <= 10 * TOL[dtype]
 
 
+def test_norm2_on_gpu_in_fp64():
+    """The normalisation check on the GPU (rosnet_norm2, FP64 sums): a
+    16-qubit state from an open-output network has norm 1 within the FP32
+    bar, the GPU's FP64 sum equals the host's FP64 sum of the same
+    downloaded entries, and on views (a fixed qubit, blocked layouts) it sums
+    exactly the viewed entries."""
+    circ = W.random_circuit(16, 10, 12)
+    net = W.circuit_network(circ, open_output=True)
+    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+    path = R.path_greedy(ts, net.labels, net.out_labels)
+    S = R.contract(ts, net.labels, net.out_labels, path, max_block_entries=256)
+    psi = S.download().astype(np.complex128)
+    host = float(np.sum(np.abs(psi) ** 2))
+    gpu = R.norm2(S)
+    assert abs(gpu - 1.0) <= 1e-5
+    assert abs(gpu - host) <= 1e-12 * host
+    for axis, val in ((0, 1), (7, 0), (15, 1)):
+        V = S.fix([axis], [val])
+        part = float(np.sum(np.abs(np.take(psi, val, axis=axis)) ** 2))
+        assert abs(R.norm2(V) - part) <= 1e-12 * part
+    X = R.btensor(W.complex_normal((6, 10, 4), 3), (2, 5, 2), R.C128)
+    x = X.download()
+    assert abs(R.norm2(X) - float(np.sum(np.abs(x) ** 2))) <= 1e-12 * float(np.sum(np.abs(x) ** 2))
+
+
 def test_out_label_permutation():
     circ = W.random_circuit(6, 4, 9)
     net = W.circuit_network(circ, open_output=True)
