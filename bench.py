@@ -251,7 +251,7 @@ def run_rosnet(args):
     if not args.no_precision_modes:
         others = run_precision_modes(args, R, torch, net, path, bind, amps, flush, stream, flags)
     e2e = run_e2e(args, R, torch, circ, net, path, ngates, stream) if not args.no_e2e else None
-    extras = None if args.no_extras else run_extras(R, torch, dev, probed)
+    extras = None if args.no_extras else run_extras(R, torch, dev, probed, args)
     cpu, ref_amps = None, []
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, ref_amps = cpu_baseline(circ, bits[args.warmup:], args.cpu_seconds)
@@ -365,14 +365,16 @@ def _timed_contract(R, torch, ts, labels, out, precision, reps, path=((0, 1),)):
     return e0.elapsed_time(e1) / reps, R.timing_drain()
 
 
-def run_extras(R, torch, dev, probed):
+def run_extras(R, torch, dev, probed, args=None):
     """Measurements beside the headline, each against the probed peak of its
     arithmetic: (1) the single blocked FP64 tensordot ([2]^14 x [2]^14 in
     2^10-entry blocks, 6 contracted axes, complex128); (2) the precision
     sweep's chunk contraction ([2]^20 x [2]^30 -> [2]^30: M = 2^10, N = 2^20,
     K = 2^10, complex64, 2^12-entry blocks, entries ~ 2^-15 complex normal from
     a seeded device generator) in every precision mode, GEMM kernel alone and
-    with its operand packs."""
+    with its operand packs; (3) gates on a [2]^28 state against the HBM rate;
+    (4) the serving stream (16 circuits, 10 s) and (5) the batched plan (256
+    slices of a 30-qubit circuit + 64 circuits), in short form."""
     probed = probed or {}
     out = {}
     try:
@@ -435,6 +437,28 @@ def run_extras(R, torch, dev, probed):
         out["gates_hbm"] = run_gate_extras(R, torch, dev)
     except Exception as e:
         out["gates_hbm"] = {"error": str(e)[:200]}
+    if args is None:
+        return out
+    # the serving and batch workloads in short form, so that every run of the
+    # default line carries them (their own workloads print the full lines)
+    try:
+        sa = argparse.Namespace(**vars(args))
+        sa.pool, sa.duration, sa.plain_sample, sa.no_cpu_baseline = 16, 10.0, 8, True
+        line = run_serve(sa, emit=False)
+        out["serve"] = {k: line[k] for k in ("value", "unit", "config", "queries", "amplitudes", "wall_s",
+                                             "warmup_s", "latency_ms", "plain_fp32_per_query",
+                                             "max_rel_err_vs_plain_fp32", "evictions")}
+        R.release_plans()
+    except Exception as e:
+        out["serve"] = {"error": str(e)[:200]}
+    try:
+        ba = argparse.Namespace(**vars(args))
+        ba.steps = 3
+        line = run_batch(ba, emit=False)
+        out["batch"] = {k: line[k] for k in ("workload", "path_gflop", "sliced_gflop", "modes")}
+        R.release_plans()
+    except Exception as e:
+        out["batch"] = {"error": str(e)[:200]}
     return out
 
 
@@ -697,7 +721,7 @@ def serving_pool(count, seed, max_flops=1e11):
     return pool
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     """Poisson stream of amplitude-batch queries served with continuous
     batching; p50/p99 latency and amplitudes/s, against the plain per-query
     FP32 form (one amplitude per contraction, one at a time)."""
@@ -798,10 +822,12 @@ def run_serve(args):
                              "what": "served amplitudes of the pool's circuits with n <= 20 against the "
                                      "oracle's state vector (the CPU baseline's results)"},
             "evictions": srv.evictions, "resident_plan_bytes": srv.resident_bytes}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Sliced 30-qubit circuit (256 slices) + 64 circuits of 16-24 qubits in
     one batched plan per precision mode."""
     import torch
@@ -845,7 +871,9 @@ def run_batch(args):
         R.release_plans()
     line = {"metric": "batch amplitudes/s", "workload": "sliced 30q (256 slices) + 64 circuits",
             "path_gflop": fl / 1e9, "sliced_gflop": ft / 1e9, "max_slice_entries": mx, "modes": res}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_reduction(args):

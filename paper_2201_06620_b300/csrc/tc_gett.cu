@@ -130,6 +130,22 @@ __device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile in
     return true;
 }
 
+// The same bounded wait without sleeping between tests: for the one thread
+// whose wake-up latency stalls the tensor core (the MMA issuer).
+__device__ __noinline__ bool mbar_wait_spin(uint64_t *b, uint32_t parity, volatile int *abort) {
+    if (mbar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitBudget) {
+            atomicExch(&g_dev_status, kDevErrTimeout);
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
 // The same wait with the uncontended case inline (one try_wait, no call):
 // for hot loops that usually find the phase already complete.
 __device__ __forceinline__ bool mbar_wait_fast(uint64_t *b, uint32_t parity, volatile int *abort) {
@@ -381,12 +397,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         if (lane == 0) {
             int g = 0;    // stage counter over all tiles
             int gc = 0;   // chunk counter over all tiles
+            // the full barrier of stage g was already seen complete: each
+            // stage's test is issued while the previous stage's MMAs go out,
+            // so its latency is not paid between them
+            bool ready = false;
             bool go = true;
             for (int i = 0; i < mytiles && go; ++i) {
                 int kt = 0;
                 for (int c = 0; c < nchunks && go; ++c, ++gc) {
                     const int b = gc & 1;
-                    if (gc >= 2 && !mbar_wait(&acce[b], ((gc >> 1) - 1) & 1, &abort_flag)) {
+                    if (gc >= 2 && !mbar_wait_spin(&acce[b], ((gc >> 1) - 1) & 1, &abort_flag)) {
                         go = false;
                         break;
                     }
@@ -395,7 +415,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                     const int kend = min(nkt, (c + 1) * C_::CH_STAGES);
                     for (; kt < kend; ++kt, ++g) {
                         const int s = g % STAGES;
-                        if (!mbar_wait(&full_bar[s], (g / STAGES) & 1, &abort_flag)) {
+                        if (!ready && !mbar_wait_fast(&full_bar[s], (g / STAGES) & 1, &abort_flag)) {
                             go = false;
                             break;
                         }
@@ -408,6 +428,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                             auto A_ = [&](int arr) { return sdesc(sa + arr * C_::ARR_A + kb); };
                             auto B_ = [&](int arr) { return sdesc(sb + arr * C_::ARR_B + kb); };
                             const uint32_t acc = (kt == c * C_::CH_STAGES && ks == 0) ? 0u : 1u;
+                            if (ks == C_::KSTEPS - 1)
+                                ready = mbar_try(&full_bar[(g + 1) % STAGES], ((g + 1) / STAGES) & 1);
                             if (MODE == kTF32) {
                                 // arrays: 0 = re, 1 = im
                                 mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), acc);
@@ -445,6 +467,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         const int h = e >> 2;                   // column half of the tile
         const int r = q * 32 + lane;            // output row of this thread
         const int64_t M = sd.M, N = sd.N;
+        // C along n in unit-stride runs of 8 whose offsets (and every offset
+        // along m, and the imaginary plane's) are multiples of 4 floats, on a
+        // 16-byte boundary: a thread's 64 outputs of its row go out as float4s
+        const bool cvec = (sd.flags & kFlagCNVec) && ((uintptr_t)sd.c & 15) == 0 && sd.c_plane % 4 == 0;
         bool ok = true;
         int gc = 0;
         for (int i = 0; i < mytiles && ok; ++i) {
@@ -478,17 +504,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             // the tile's sum to C, while the tensor core runs on into the next tile
             int64_t m0, n0;
             tile_origin(first + (int64_t)i * G, m0, n0);
-            if (m0 + r < M) {
+            {
                 float *C = (float *)sd.c;
                 const int64_t cp = sd.c_plane;
-                const int64_t cm = sd.offCM[m0 + r];
+                const bool rok = m0 + r < M;
+                const int64_t cm = rok ? sd.offCM[m0 + r] : 0;
+                // the warp's 64 column offsets: two coalesced loads, then
+                // shuffled to every lane (all lanes take part)
+                const int64_t nb = n0 + h * 64;
+                const int64_t olo = nb + lane < N ? __ldg(sd.offCN + nb + lane) : 0;
+                const int64_t ohi = nb + 32 + lane < N ? __ldg(sd.offCN + nb + 32 + lane) : 0;
+                if (cvec) {   // runs of 4 along n: 16-byte stores
 #pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    const int64_t n = n0 + h * 64 + j;
-                    if (n < N) {
-                        const int64_t o = cm + __ldg(sd.offCN + n);
-                        C[o] = sr[j];
-                        C[o + cp] = si[j];
+                    for (int j = 0; j < 64; j += 4) {
+                        const int64_t o = cm + __shfl_sync(0xffffffffu, j < 32 ? olo : ohi, j & 31);
+                        if (rok && nb + j < N) {
+                            *reinterpret_cast<float4 *>(C + o) = make_float4(sr[j], sr[j + 1], sr[j + 2], sr[j + 3]);
+                            *reinterpret_cast<float4 *>(C + o + cp) =
+                                make_float4(si[j], si[j + 1], si[j + 2], si[j + 3]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 64; ++j) {
+                        const int64_t o = cm + __shfl_sync(0xffffffffu, j < 32 ? olo : ohi, j & 31);
+                        if (rok && nb + j < N) {
+                            C[o] = sr[j];
+                            C[o + cp] = si[j];
+                        }
                     }
                 }
             }
@@ -522,22 +565,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 // order.
 namespace f32p {
 
-#ifndef ROSNET_F32P_BM
-#define ROSNET_F32P_BM 64
-#endif
-#ifndef ROSNET_F32P_BK
-#define ROSNET_F32P_BK 32
-#endif
-#ifndef ROSNET_F32P_STAGES
-#define ROSNET_F32P_STAGES 3
-#endif
-#ifndef ROSNET_F32P_KU
-#define ROSNET_F32P_KU 2
-#endif
 constexpr int NT = 256;   // 16 x 16 threads, TM x TN complex outputs each
-constexpr int BM = ROSNET_F32P_BM, BN = 64, BK = ROSNET_F32P_BK, STAGES = ROSNET_F32P_STAGES;
+constexpr int BM = 64, BN = 64, BK = 32, STAGES = 3;
 constexpr int TM = BM / 16, TN = BN / 16;
-constexpr int KU = ROSNET_F32P_KU;                         // unroll of the two-row inner loop
+constexpr int KU = 2;                                      // unroll of the two-row inner loop
 constexpr int PA = BK * BM, PB = BK * BN;                  // floats of one plane of one stage
 constexpr uint32_t STAGE_BYTES = 2u * (PA + PB) * 4u;
 constexpr int KQ = 32;                                     // k tile of the pack kernel
@@ -628,6 +659,56 @@ __device__ __forceinline__ void cmac4(float &cr, float &ci, float ar, float ai, 
     ci = fmaf(ai, br, ci);
 }
 
+// Write a finished C tile staged in shared memory to C with the lanes of a
+// warp along C's unit-stride dimension (m if m_fast, else n).  The staged
+// plane holds (BM + 1) x BN (m_fast) or BM x (BN + 1) floats, row length ld;
+// `both`: the imaginary plane follows at cs + plane, otherwise cs holds plane
+// `pl` alone.
+__device__ __forceinline__ void emit_tile(const float *cs, int plane, int ld, bool m_fast, bool both, int pl,
+                                          int m0, int n0, const GettDesc &sd, int warp, int lane) {
+    float *C = (float *)sd.c;
+    const int64_t cp = sd.c_plane;
+    const int64_t M = sd.M, N = sd.N;
+    float *out = C + (pl ? cp : 0);
+    if (m_fast) {
+        int64_t cm[BM / 32];
+#pragma unroll
+        for (int u = 0; u < BM / 32; ++u) {
+            const int64_t m = m0 + lane + 32 * u;
+            cm[u] = m < M ? __ldg(sd.offCM + m) : -1;
+        }
+        for (int nl = warp; nl < BN; nl += NT / 32) {
+            const int64_t n = n0 + nl;
+            if (n >= N) break;
+            const int64_t c0 = __ldg(sd.offCN + n);
+#pragma unroll
+            for (int u = 0; u < BM / 32; ++u)
+                if (cm[u] >= 0) {
+                    out[cm[u] + c0] = cs[nl * ld + lane + 32 * u];
+                    if (both) out[cm[u] + c0 + cp] = cs[plane + nl * ld + lane + 32 * u];
+                }
+        }
+    } else {
+        int64_t cn[BN / 32];
+#pragma unroll
+        for (int u = 0; u < BN / 32; ++u) {
+            const int64_t n = n0 + lane + 32 * u;
+            cn[u] = n < N ? __ldg(sd.offCN + n) : -1;
+        }
+        for (int ml = warp; ml < BM; ml += NT / 32) {
+            const int64_t m = m0 + ml;
+            if (m >= M) break;
+            const int64_t c0 = __ldg(sd.offCM + m);
+#pragma unroll
+            for (int u = 0; u < BN / 32; ++u)
+                if (cn[u] >= 0) {
+                    out[c0 + cn[u]] = cs[ml * ld + lane + 32 * u];
+                    if (both) out[c0 + cn[u] + cp] = cs[plane + ml * ld + lane + 32 * u];
+                }
+        }
+    }
+}
+
 // CTA index owning unit u when U units are split evenly over G CTAs (CTA c
 // takes units [c U / G, (c + 1) U / G)).
 __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) { return ((u + 1) * G - 1) / U; }
@@ -643,7 +724,7 @@ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) { r
 // scheduling), writes C and resets the counter.  No CTA ever waits for
 // another.
 template <bool SK>
-__global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __grid_constant__ Args p) {
+__global__ void __launch_bounds__(NT, 2) f32_gemm_kernel(const __grid_constant__ Args p) {
     extern __shared__ unsigned char dsm_raw[];
     float *stg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~(uintptr_t)127);
     __shared__ GettDesc sd;
@@ -745,12 +826,9 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
     // (BM + 1) x BN floats (two passes), or the whole idle ring after the
     // CTA's last unit (both planes in one pass).
     auto store_c = [&](float *cs, bool both, int m0, int n0) {
-        float *C = (float *)sd.c;
-        const int64_t cp = sd.c_plane;
         const bool m_fast = !(sd.flags & kFlagCNFast);
         const int ld = m_fast ? BM + 1 : BN + 1;   // row length of a staged plane
         const int plane = (m_fast ? BN : BM) * ld;
-        const int64_t M = sd.M, N = sd.N;
 #pragma unroll 1
         for (int pl = 0; pl < (both ? 1 : 2); ++pl) {
             __syncthreads();   // the staging area is free
@@ -768,44 +846,7 @@ __global__ void __launch_bounds__(NT, BM == 64 ? 2 : 1) f32_gemm_kernel(const __
                     }
                 }
             __syncthreads();
-            float *out = C + (pl ? cp : 0);
-            if (m_fast) {
-                int64_t cm[BM / 32];
-#pragma unroll
-                for (int u = 0; u < BM / 32; ++u) {
-                    const int64_t m = m0 + lane + 32 * u;
-                    cm[u] = m < M ? __ldg(sd.offCM + m) : -1;
-                }
-                for (int nl = warp; nl < BN; nl += NT / 32) {
-                    const int64_t n = n0 + nl;
-                    if (n >= N) break;
-                    const int64_t c0 = __ldg(sd.offCN + n);
-#pragma unroll
-                    for (int u = 0; u < BM / 32; ++u)
-                        if (cm[u] >= 0) {
-                            out[cm[u] + c0] = cs[nl * ld + lane + 32 * u];
-                            if (both) out[cm[u] + c0 + cp] = cs[plane + nl * ld + lane + 32 * u];
-                        }
-                }
-            } else {
-                int64_t cn[BN / 32];
-#pragma unroll
-                for (int u = 0; u < BN / 32; ++u) {
-                    const int64_t n = n0 + lane + 32 * u;
-                    cn[u] = n < N ? __ldg(sd.offCN + n) : -1;
-                }
-                for (int ml = warp; ml < BM; ml += NT / 32) {
-                    const int64_t m = m0 + ml;
-                    if (m >= M) break;
-                    const int64_t c0 = __ldg(sd.offCM + m);
-#pragma unroll
-                    for (int u = 0; u < BN / 32; ++u)
-                        if (cn[u] >= 0) {
-                            out[c0 + cn[u]] = cs[ml * ld + lane + 32 * u];
-                            if (both) out[c0 + cn[u] + cp] = cs[plane + ml * ld + lane + 32 * u];
-                        }
-                }
-            }
+            emit_tile(cs, plane, ld, m_fast, both, pl, m0, n0, sd, warp, lane);
         }
         __syncthreads();   // the staging area may be refilled
     };
