@@ -373,7 +373,8 @@ def run_extras(R, torch, dev, probed, args=None):
     K = 2^10, complex64, 2^12-entry blocks, entries ~ 2^-15 complex normal from
     a seeded device generator) in every precision mode, GEMM kernel alone and
     with its operand packs; (3) gates on a [2]^28 state against the HBM rate;
-    (4) the serving stream (16 circuits, 10 s) and (5) the batched plan (256
+    (4) the out-of-core tier with the large operand streamed from host memory;
+    (5) the serving stream (16 circuits, 10 s) and (6) the batched plan (256
     slices of a 30-qubit circuit + 64 circuits), in short form."""
     probed = probed or {}
     out = {}
@@ -437,6 +438,10 @@ def run_extras(R, torch, dev, probed, args=None):
         out["gates_hbm"] = run_gate_extras(R, torch, dev)
     except Exception as e:
         out["gates_hbm"] = {"error": str(e)[:200]}
+    try:
+        out["ooc_operand"] = run_ooc_extras(R, torch, dev)
+    except Exception as e:
+        out["ooc_operand"] = {"error": str(e)[:200]}
     if args is None:
         return out
     # the serving and batch workloads in short form, so that every run of the
@@ -460,6 +465,57 @@ def run_extras(R, torch, dev, probed, args=None):
     except Exception as e:
         out["batch"] = {"error": str(e)[:200]}
     return out
+
+
+def run_ooc_extras(R, torch, dev, chunks=3):
+    """The out-of-core tier with the large operand in host memory, on the
+    weak-scaling contraction U_mk V_nk of Sec. V-A scaled down 4x per block
+    dimension (m_b = n_b = 2^12, k_b = 2^11; B_m = 8, B_n = 6, B_k = 16): U
+    (8 GiB, complex64) stays in pinned host memory and each output chunk (one
+    m-block row, 4096 x 24576) streams its 1 GiB slice of U in on a side
+    stream while the previous chunk computes; chunks go out to pinned host
+    memory.  Timed against the same chunks with U resident on the device:
+    equal times mean the copies are hidden."""
+    mb, nb, kb, Bm, Bn, Bk = 4096, 4096, 2048, 8, 6, 16
+    shape_u, block_u = (Bm, mb, Bk * kb), (1, mb, kb)
+    V = R.empty((Bn * nb, Bk * kb), (nb, kb), R.C64)
+    U = R.empty(shape_u, block_u, R.C64)
+    g = torch.Generator(device=dev)
+    for t, seed in ((U, 31), (V, 32)):
+        g.manual_seed(seed)
+        raw = torch.randn(2 * t.numel, device=dev, generator=g) * 0.5 ** 0.5
+        t.upload_raw(raw)
+        torch.cuda.synchronize()
+        del raw
+    u_host = torch.empty(2 * U.numel * 4, dtype=torch.uint8).pin_memory()
+    U.download_raw(u_host)
+    torch.cuda.synchronize()
+    chunk_bytes = 2 * mb * Bn * nb * 4
+    host = torch.empty(2 * chunk_bytes, dtype=torch.uint8).pin_memory()
+    flop = 8.0 * mb * (Bn * nb) * (Bk * kb) * chunks
+    R.tensordot_ooc(U, V, [2], [1], 1, 0, 1, host)            # warm-up (plans, packs)
+    R.tensordot_ooc_host(u_host, shape_u, block_u, V, [2], [1], 1, 0, 1, host)
+    torch.cuda.synchronize()
+    res = {}
+    for name in ("device", "host"):
+        t0 = time.perf_counter()
+        if name == "device":
+            R.tensordot_ooc(U, V, [2], [1], 1, 1, chunks, host)
+        else:
+            R.tensordot_ooc_host(u_host, shape_u, block_u, V, [2], [1], 1, 1, chunks, host)
+        torch.cuda.synchronize()
+        res[name] = time.perf_counter() - t0
+    slice_bytes = 2 * mb * Bk * kb * 4
+    del U, V, u_host, host
+    R.release_plans()
+    return {"shape": "U (8 x 4096, 16 x 2048) x V (6 x 4096, 16 x 2048) complex64, blocks (4096, 2048)",
+            "chunks": chunks, "chunk": "4096 x 24576 (768 MiB out), U slice 1 GiB in",
+            "s_u_on_device": res["device"], "s_u_in_host": res["host"],
+            "tflops_u_in_host": flop / res["host"] / 1e12, "tflops_u_on_device": flop / res["device"] / 1e12,
+            "copy_hidden_frac": res["device"] / res["host"],
+            "h2d_gbs_needed": slice_bytes * chunks / res["host"] / 1e9,
+            "what": "wall time of rosnet_tensordot_ooc (U resident) and rosnet_tensordot_ooc_host (U streamed "
+                    "from pinned host) over the same chunks, output chunks to pinned host in both"}
 
 
 def run_gate_extras(R, torch, dev, rank=28):

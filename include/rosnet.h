@@ -331,6 +331,29 @@ rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B, int naxes
                                    int64_t first_chunk, int64_t nchunks, const rosnet_opts *opts,
                                    void *host_out, size_t host_bytes, void *stream);
 
+/*
+ * The same with A left in host memory (the out-of-core tier for an operand
+ * larger than the device memory, Sec. I and III): A is described by its rank,
+ * shape and block shape (NULL block_a: one block), has B's dtype, and lives at
+ * a_host in the raw block-major planar layout (the real plane, then the
+ * imaginary plane, numel elements each: what rosnet_btensor_download_raw
+ * writes).  Chunk c needs only its slice of A (the split axes fixed: one
+ * contiguous run of blocks per plane), which is copied into one of two
+ * device buffers on an input stream while the previous chunk is computed;
+ * output chunks stream out as in rosnet_tensordot_ooc.  B stays on the
+ * device.  a_host and host_out should be pinned for the copies to run
+ * asynchronously; the caller keeps a_host unchanged until the call returns.
+ * Device memory used: two slices of A, two output chunks and B.  Errors as
+ * rosnet_tensordot_ooc, plus INVALID_ARG for a NULL a_host (unless A is
+ * empty or nchunks is 0) and the layout errors of rosnet_btensor_create.
+ */
+rosnet_status rosnet_tensordot_ooc_host(int rank_a, const int64_t *shape_a, const int64_t *block_a,
+                                        const void *a_host, rosnet_btensor B, int naxes,
+                                        const int *axes_a, const int *axes_b, int nsplit,
+                                        int64_t first_chunk, int64_t nchunks,
+                                        const rosnet_opts *opts, void *host_out, size_t host_bytes,
+                                        void *stream);
+
 /* ----------------------------------------------------------------------- */
 /* networks (Sec. II-A)                                                     */
 /* ----------------------------------------------------------------------- */

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
-    "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc", "contract_batch",
+    "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc", "tensordot_ooc_host", "contract_batch",
     "plan_stats", "path_search", "slice_search", "sliced_networks", "sum_fp64",
     "sync", "kernel_launches", "release_plans", "plan_cache_limit", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
@@ -60,7 +60,8 @@ EXPORTS = [
     "rosnet_release_plans", "rosnet_sync", "rosnet_status_string", "rosnet_last_error",
     "rosnet_kernel_launches", "rosnet_path_greedy_extents", "rosnet_timing_drain",
     "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range", "rosnet_btensor_slice",
-    "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_contract_batch", "rosnet_plan_stats",
+    "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_tensordot_ooc_host", "rosnet_contract_batch",
+    "rosnet_plan_stats",
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
     "rosnet_btensor_download_async", "rosnet_alloc_stats", "rosnet_btensor_upload_raw",
@@ -148,6 +149,10 @@ def lib():
                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Opts),
                                                vp, ctypes.c_size_t, vp]
+            L.rosnet_tensordot_ooc_host.argtypes = [ctypes.c_int, i64p, i64p, vp, vp, ctypes.c_int,
+                                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                    ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                                    ctypes.POINTER(_Opts), vp, ctypes.c_size_t, vp]
             L.rosnet_btensor_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i64p, i64p,
                                               ctypes.POINTER(ctypes.c_int)]
             L.rosnet_btensor_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -196,7 +201,7 @@ def lib():
                         "rosnet_btensor_download_async", "rosnet_alloc_stats",
                         "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw",
                         "rosnet_plan_cache_limit", "rosnet_probe_peak", "rosnet_plan_release",
-                        "rosnet_norm2"):
+                        "rosnet_norm2", "rosnet_tensordot_ooc_host"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -518,6 +523,29 @@ def tensordot_ooc(A, B, axes_a, axes_b, nsplit, first_chunk, nchunks, host_out,
                                       _i32arr(axes_b), int(nsplit), int(first_chunk), int(nchunks),
                                       ctypes.byref(o), ctypes.c_void_p(ptr), int(nbytes),
                                       _stream(stream)), "rosnet_tensordot_ooc")
+
+
+def tensordot_ooc_host(a_host, shape_a, block_a, B, axes_a, axes_b, nsplit, first_chunk, nchunks, host_out,
+                       precision=PREC_DEFAULT, stream=None):
+    """Out-of-core tensordot with A in host memory: ``a_host`` (a pinned torch
+    CPU tensor or a numpy array) holds A raw block-major planar (real plane,
+    then imaginary plane) with the given shape and block shape; each chunk's
+    slice of A is copied in on a side stream while the previous chunk is
+    computed, and output chunks go to ``host_out`` as in tensordot_ooc."""
+    _init()
+    o = _opts(precision)
+
+    def ptr_bytes(x):
+        if hasattr(x, "data_ptr"):
+            return x.data_ptr(), x.numel() * x.element_size()
+        return x.ctypes.data, x.nbytes
+    aptr, _ = ptr_bytes(a_host)
+    optr, obytes = ptr_bytes(host_out)
+    blk = None if block_a is None else _i64arr(block_a)
+    _check(lib().rosnet_tensordot_ooc_host(len(shape_a), _i64arr(shape_a), blk, ctypes.c_void_p(aptr), B.handle,
+                                           len(axes_a), _i32arr(axes_a), _i32arr(axes_b), int(nsplit),
+                                           int(first_chunk), int(nchunks), ctypes.byref(o), ctypes.c_void_p(optr),
+                                           int(obytes), _stream(stream)), "rosnet_tensordot_ooc_host")
 
 
 class Network:

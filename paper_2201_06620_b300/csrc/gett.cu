@@ -1824,15 +1824,22 @@ extern "C" rosnet_status rosnet_tensordot(rosnet_btensor A, rosnet_btensor B, in
 }
 
 // ---------------------------------------------------------------------------
-// out-of-core: output chunks streamed to pinned host memory
+// out-of-core: output chunks streamed to pinned host memory; A either on the
+// device or, slice by slice, streamed in from host memory
 // ---------------------------------------------------------------------------
-extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B, int naxes,
-                                              const int *axes_a, const int *axes_b, int nsplit,
-                                              int64_t first_chunk, int64_t nchunks,
-                                              const rosnet_opts *opts, void *host_out,
-                                              size_t host_bytes, void *stream) {
-    RN_API_BEGIN
-    cudaStream_t s = (cudaStream_t)stream;
+namespace rosnet {
+namespace {
+
+// The chunk loop shared by both entry points.  A describes A's layout and
+// dtype; with from_host set its data pointer is unused and chunk c's slice of
+// A (a contiguous run of blocks in each plane, planes numel apart in the
+// host array) is copied into one of two device buffers on an input stream,
+// one chunk ahead of the computation; output chunk c goes out on a second
+// side stream while chunk c + 1 is computed.
+void ooc_run(rosnet_btensor A, bool from_host, const void *a_host, rosnet_btensor B, int naxes,
+             const int *axes_a,
+             const int *axes_b, int nsplit, int64_t first_chunk, int64_t nchunks, const rosnet_opts *opts,
+             void *host_out, size_t host_bytes, cudaStream_t s) {
     if (!A || !B || nsplit < 0 || nsplit > A->lay.rank || first_chunk < 0 || nchunks < 0)
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad operands or chunk range");
     int axa[kMaxRank], axb[kMaxRank], rc = 0;
@@ -1857,7 +1864,7 @@ extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B
     const int64_t nslots = chunk_bytes ? (int64_t)(host_bytes / chunk_bytes) : 1;
     if (nchunks > 0 && (!host_out || nslots < 1))
         RN_FAIL(ROSNET_ERR_INVALID_ARG, "the host buffer cannot hold one output chunk");
-    if (nchunks == 0) return ROSNET_OK;
+    if (nchunks == 0) return;
     rosnet_btensor_s av;   // slice view of A (A's strides), re-pointed per chunk
     av.lay.rank = A->lay.rank - nsplit;
     av.lay.numel = 1;
@@ -1870,25 +1877,39 @@ extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B
     }
     av.dtype = A->dtype;
     av.elsize = A->elsize;
-    av.pstride = A->pstride;
+    av.pstride = from_host ? av.lay.numel : A->pstride;   // staged slices: planes back to back
     av.owned = false;
+    const size_t slice_plane = (size_t)av.lay.numel * A->elsize;
+    auto slice_offset = [&](int64_t c) {   // elements from A's start to chunk c's slice (one plane)
+        int64_t rem = c, off = 0;
+        for (int i = nsplit - 1; i >= 0; --i) {
+            off += (rem % A->lay.shape[i]) * A->lay.gstride[i];
+            rem /= A->lay.shape[i];
+        }
+        return off;
+    };
     rosnet_btensor_s cv[2];
-    DevBuf cbuf[2];
-    cudaStream_t side = nullptr;
-    cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    DevBuf cbuf[2], abuf[2];
+    cudaStream_t side = nullptr, ins = nullptr;
+    cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr}, loaded[2] = {nullptr, nullptr};
     auto cleanup = [&]() {
         if (side) { cudaStreamSynchronize(side); cudaStreamDestroy(side); }
+        if (ins) { cudaStreamSynchronize(ins); cudaStreamDestroy(ins); }
         for (int i = 0; i < 2; ++i) {
             if (computed[i]) cudaEventDestroy(computed[i]);
             if (copied[i]) cudaEventDestroy(copied[i]);
+            if (loaded[i]) cudaEventDestroy(loaded[i]);
         }
     };
     try {
         RN_CHECK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        if (from_host) RN_CHECK_CUDA(cudaStreamCreateWithFlags(&ins, cudaStreamNonBlocking));
         for (int i = 0; i < 2; ++i) {
             RN_CHECK_CUDA(cudaEventCreateWithFlags(&computed[i], cudaEventDisableTiming));
             RN_CHECK_CUDA(cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming));
+            RN_CHECK_CUDA(cudaEventCreateWithFlags(&loaded[i], cudaEventDisableTiming));
             cbuf[i] = DevBuf(chunk_bytes, s);
+            if (from_host) abuf[i] = DevBuf(2 * slice_plane, s);
             cv[i].lay = lc;
             cv[i].dtype = A->dtype;
             cv[i].elsize = A->elsize;
@@ -1896,15 +1917,37 @@ extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B
             cv[i].pstride = lc.numel;
             cv[i].owned = false;
         }
+        // the staging buffers come from the caller's stream: the input stream
+        // starts after their allocation
+        if (from_host) {
+            RN_CHECK_CUDA(cudaEventRecord(loaded[0], s));
+            RN_CHECK_CUDA(cudaStreamWaitEvent(ins, loaded[0], 0));
+        }
+        // chunk c's slice of A into buffer (c - first_chunk) % 2, once the
+        // chunk that used that buffer before (c - 2) has been computed
+        auto load = [&](int64_t c) {
+            const int b = (int)((c - first_chunk) & 1);
+            if (c - first_chunk >= 2) RN_CHECK_CUDA(cudaStreamWaitEvent(ins, computed[b], 0));
+            if (slice_plane > 0) {
+                const char *src = (const char *)a_host + (size_t)slice_offset(c) * A->elsize;
+                const size_t host_plane = (size_t)A->lay.numel * A->elsize;
+                RN_CHECK_CUDA(cudaMemcpyAsync(abuf[b].p, src, slice_plane, cudaMemcpyHostToDevice, ins));
+                RN_CHECK_CUDA(cudaMemcpyAsync((char *)abuf[b].p + slice_plane, src + host_plane, slice_plane,
+                                              cudaMemcpyHostToDevice, ins));
+            }
+            RN_CHECK_CUDA(cudaEventRecord(loaded[b], ins));
+        };
+        if (from_host) load(first_chunk);
         Prepared prep(av.lay, B->lay, lc, naxes, axa_s, axb, A->dtype, prec, s, check_reduce(opts));
         for (int64_t c = first_chunk; c < first_chunk + nchunks; ++c) {
             const int b = (int)((c - first_chunk) & 1);
-            int64_t rem = c, off = 0;
-            for (int i = nsplit - 1; i >= 0; --i) {
-                off += (rem % A->lay.shape[i]) * A->lay.gstride[i];
-                rem /= A->lay.shape[i];
+            if (from_host) {
+                if (c + 1 < first_chunk + nchunks) load(c + 1);   // the next slice streams in meanwhile
+                RN_CHECK_CUDA(cudaStreamWaitEvent(s, loaded[b], 0));
+                av.data = abuf[b].p;
+            } else {
+                av.data = (char *)A->data + slice_offset(c) * A->elsize;
             }
-            av.data = (char *)A->data + off * A->elsize;
             if (c - first_chunk >= 2) RN_CHECK_CUDA(cudaStreamWaitEvent(s, copied[b], 0));
             prep.run(&av, B, &cv[b], s, c == first_chunk);   // B is packed once
             RN_CHECK_CUDA(cudaEventRecord(computed[b], s));
@@ -1913,13 +1956,49 @@ extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B
             RN_CHECK_CUDA(cudaMemcpyAsync(dst, cv[b].data, chunk_bytes, cudaMemcpyDeviceToHost, side));
             RN_CHECK_CUDA(cudaEventRecord(copied[b], side));
         }
-        // the caller's stream waits for the last copies
+        // the caller's stream waits for the last copies (and the staging
+        // buffers are released on it after the last computation)
         for (int i = 0; i < 2; ++i) RN_CHECK_CUDA(cudaStreamWaitEvent(s, copied[i], 0));
     } catch (...) {
         cleanup();
         throw;
     }
-    cleanup();   // synchronises the side stream (the copies are complete on return)
+    cleanup();   // synchronises the side streams (the copies are complete on return)
+}
+
+}  // namespace
+}  // namespace rosnet
+
+extern "C" rosnet_status rosnet_tensordot_ooc(rosnet_btensor A, rosnet_btensor B, int naxes,
+                                              const int *axes_a, const int *axes_b, int nsplit,
+                                              int64_t first_chunk, int64_t nchunks,
+                                              const rosnet_opts *opts, void *host_out,
+                                              size_t host_bytes, void *stream) {
+    RN_API_BEGIN
+    ooc_run(A, false, nullptr, B, naxes, axes_a, axes_b, nsplit, first_chunk, nchunks, opts, host_out, host_bytes,
+            (cudaStream_t)stream);
+    return ROSNET_OK;
+    RN_API_END
+}
+
+extern "C" rosnet_status rosnet_tensordot_ooc_host(int rank_a, const int64_t *shape_a, const int64_t *block_a,
+                                                   const void *a_host, rosnet_btensor B, int naxes,
+                                                   const int *axes_a, const int *axes_b, int nsplit,
+                                                   int64_t first_chunk, int64_t nchunks,
+                                                   const rosnet_opts *opts, void *host_out,
+                                                   size_t host_bytes, void *stream) {
+    RN_API_BEGIN
+    if (!B || rank_a < 0 || rank_a > kMaxRank || (rank_a > 0 && !shape_a))
+        RN_FAIL(ROSNET_ERR_INVALID_ARG, "bad operand description");
+    rosnet_btensor_s a;   // A's layout and dtype only: its data stay in host memory
+    a.lay.init(rank_a, shape_a, block_a);
+    a.dtype = B->dtype;
+    a.elsize = B->elsize;
+    a.pstride = a.lay.numel;
+    a.owned = false;
+    if (!a_host && a.lay.numel > 0 && nchunks > 0) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no host array for A");
+    ooc_run(&a, true, a_host, B, naxes, axes_a, axes_b, nsplit, first_chunk, nchunks, opts, host_out, host_bytes,
+            (cudaStream_t)stream);
     return ROSNET_OK;
     RN_API_END
 }

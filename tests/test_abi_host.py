@@ -44,6 +44,11 @@ def L():
     lib.rosnet_tensordot_ooc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int64,
                                          ctypes.c_int64, ctypes.POINTER(R._Opts), vp, ctypes.c_size_t, vp]
+    lib.rosnet_tensordot_ooc_host.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.POINTER(R._Opts), vp, ctypes.c_size_t, vp]
     lib.rosnet_path_greedy.argtypes = [ctypes.POINTER(R._Network), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32)]
     lib._held = held
@@ -208,6 +213,21 @@ def test_tensordot_argument_checks(L):
         assert ooc(2, 0, 1) == "BLOCK_MISMATCH"                 # axis 1 has block extent 3
         assert ooc(1, 0, 1, (0,), (1,)) == "SHAPE"                # extents 2 and 3
         assert ooc(1, 0, 0) == "OK"                             # empty range: nothing to do
+        # the same checks with A in host memory (described by shape and blocks)
+        a_host = ctypes.create_string_buffer(2 * 24 * 8)
+
+        def ooch(nsplit, first, n, shape=(2, 3, 4), block=(1, 3, 2), ax_a=(2,), ax_b=(0,), src=a_host):
+            sh = (ctypes.c_int64 * len(shape))(*shape)
+            bl = (ctypes.c_int64 * len(block))(*block)
+            return STATUS[L.rosnet_tensordot_ooc_host(len(shape), sh, bl, src, B.handle, len(ax_a), _i32(ax_a),
+                                                      _i32(ax_b), nsplit, first, n, None, host, len(host), None)]
+        assert ooch(1, 0, 3) == "INVALID_ARG"                   # only 2 chunks along axis 0
+        assert ooch(2, 0, 1) == "BLOCK_MISMATCH"                # axis 1 has block extent 3
+        assert ooch(1, 0, 1, block=(1, 3, 3)) == "BLOCK_MISMATCH"   # 3 does not divide 4
+        assert ooch(1, 0, 1, ax_a=(0,), ax_b=(1,)) == "SHAPE"
+        assert ooch(1, 0, 1, src=None) == "INVALID_ARG"          # no host array
+        assert ooch(1, 0, 1, block=(1, 3, 4)) == "BLOCK_MISMATCH"   # contracted blocks 4 and 2
+        assert ooch(1, 0, 0) == "OK"
     finally:
         for t in (A, B, Bc, Bb, W1, W2):
             t.destroy()
