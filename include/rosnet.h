@@ -384,6 +384,36 @@ typedef struct {
 } rosnet_path;
 
 /*
+ * Rank reduction before path search (the paper builds and simplifies its
+ * circuit networks with a front end before choosing a path, Sec. V): while
+ * some tensor of rank <= max_rank (0, 1 or 2) not marked in keep shares a
+ * label with a tensor not marked in keep, it is absorbed into such a
+ * neighbour -- the one of highest rank, then lowest index -- by one
+ * rosnet_tensordot on `stream` with `opts` (precision as that call).  Only
+ * labels carried by exactly these two tensors are summed (a label in
+ * out_labels never is); the merged tensor's labels are the neighbour's
+ * remaining labels, then the absorbed tensor's, and it takes the
+ * neighbour's position.  Tensors marked in keep (e.g. output projectors that
+ * change from query to query) are neither absorbed nor absorbed into.
+ *
+ * Output, survivors in input order: tensors_out[0 .. *ntensors_out), their
+ * ranks, their labels concatenated in labels_out, and origin_out[i] = the
+ * input index whose position survivor i holds.  tensors_out, ranks_out and
+ * origin_out must hold ntensors entries and labels_out the total rank of the
+ * input (the total never grows).  A survivor that absorbed nothing is the
+ * caller's own handle; every other one is a new tensor owned by the caller
+ * (release it with rosnet_btensor_destroy).  The absorbed input tensors are
+ * not modified.  keep may be NULL (nothing kept).  Errors: INVALID_ARG
+ * (NULL outputs, max_rank outside 0..2, a rank that does not match its
+ * tensor), and the errors of rosnet_tensordot, after which no new tensor is
+ * left alive.
+ */
+rosnet_status rosnet_simplify(const rosnet_network *net, const uint8_t *keep, int32_t max_rank,
+                              const rosnet_opts *opts, void *stream, rosnet_btensor *tensors_out,
+                              int32_t *ranks_out, int64_t *labels_out, int32_t *origin_out,
+                              int32_t *ntensors_out);
+
+/*
  * A greedy min-size path (the paper takes its paths from an external path
  * optimiser, Sec. V; this one is the library's own): at each step join the
  * pair of tensors sharing at least one label whose result is smallest; ties go

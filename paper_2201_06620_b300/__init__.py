@@ -30,6 +30,7 @@ import numpy as np
 __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
     "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc", "tensordot_ooc_host", "contract_batch",
+    "simplify",
     "plan_stats", "path_search", "slice_search", "sliced_networks", "sum_fp64",
     "sync", "kernel_launches", "release_plans", "plan_cache_limit", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
@@ -60,7 +61,8 @@ EXPORTS = [
     "rosnet_release_plans", "rosnet_sync", "rosnet_status_string", "rosnet_last_error",
     "rosnet_kernel_launches", "rosnet_path_greedy_extents", "rosnet_timing_drain",
     "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range", "rosnet_btensor_slice",
-    "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_tensordot_ooc_host", "rosnet_contract_batch",
+    "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_tensordot_ooc_host", "rosnet_simplify",
+    "rosnet_contract_batch",
     "rosnet_plan_stats",
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
     "rosnet_selftest_timeout", "rosnet_tune_export", "rosnet_tune_import",
@@ -153,6 +155,10 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                     ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                                     ctypes.POINTER(_Opts), vp, ctypes.c_size_t, vp]
+            L.rosnet_simplify.argtypes = [ctypes.POINTER(_Network), ctypes.POINTER(ctypes.c_uint8), ctypes.c_int32,
+                                          ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp),
+                                          ctypes.POINTER(ctypes.c_int32), i64p, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]
             L.rosnet_btensor_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i64p, i64p,
                                               ctypes.POINTER(ctypes.c_int)]
             L.rosnet_btensor_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -201,7 +207,7 @@ def lib():
                         "rosnet_btensor_download_async", "rosnet_alloc_stats",
                         "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw",
                         "rosnet_plan_cache_limit", "rosnet_probe_peak", "rosnet_plan_release",
-                        "rosnet_norm2", "rosnet_tensordot_ooc_host"):
+                        "rosnet_norm2", "rosnet_tensordot_ooc_host", "rosnet_simplify"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -678,6 +684,36 @@ def sum_fp64(tensors, stream=None):
     h = ctypes.c_void_p()
     _check(lib().rosnet_sum(len(tensors), arr, _stream(stream), ctypes.byref(h)), "rosnet_sum")
     return BTensor(h.value)
+
+
+def simplify(tensors, labels, out_labels=(), keep=(), max_rank=2, precision=PREC_DEFAULT, stream=None):
+    """Rank reduction before path search (rosnet_simplify): tensors of rank
+    <= max_rank not in ``keep`` (indices) are absorbed into neighbours by
+    tensordots on the device.  Returns (tensors, labels, origin): the
+    survivors in input order (the caller's own BTensor where nothing was
+    absorbed, a new one otherwise), their labels, and for each the input
+    index whose position it holds."""
+    _init()
+    net = Network(tensors, labels, out_labels)
+    n = len(tensors)
+    kp = (ctypes.c_uint8 * max(1, n))(*[1 if i in set(keep) else 0 for i in range(n)])
+    tout = (ctypes.c_void_p * max(1, n))()
+    rout = (ctypes.c_int32 * max(1, n))()
+    lout = (ctypes.c_int64 * max(1, sum(len(l) for l in net.labels)))()
+    oout = (ctypes.c_int32 * max(1, n))()
+    nout = ctypes.c_int32()
+    o = _opts(precision)
+    _check(lib().rosnet_simplify(ctypes.byref(net.net), kp, int(max_rank), ctypes.byref(o), _stream(stream), tout,
+                                 rout, lout, oout, ctypes.byref(nout)), "rosnet_simplify")
+    res_t, res_l, origin, pos = [], [], [], 0
+    for i in range(nout.value):
+        j = oout[i]
+        h = tout[i]
+        res_t.append(tensors[j] if h == tensors[j].handle.value else BTensor(h))
+        res_l.append(tuple(lout[pos:pos + rout[i]]))
+        origin.append(j)
+        pos += rout[i]
+    return res_t, res_l, origin
 
 
 def contract(tensors, labels=None, out_labels=None, path=None, precision=PREC_DEFAULT, flags=0,

@@ -35,7 +35,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import (C64, OPT_GRAPH, PREC_DEFAULT, Network, btensor, contract, empty, path_search, plan_info,
-               plan_release)
+               plan_release, simplify)
 
 __all__ = ["Query", "AmplitudeServer", "predict_footprint"]
 
@@ -81,7 +81,11 @@ def predict_footprint(labels, extents, out_labels, path, elem_bytes=8):
 
 
 class _Circuit:
-    """Device-resident gate tensors of one circuit and its per-k paths."""
+    """Device-resident tensors of one circuit and its per-k paths.  The
+    circuit part (|0> vectors and gates, final wires open) is simplified once
+    on registration: every rank-1 and rank-2 tensor is absorbed into a
+    neighbour on the device (rosnet_simplify), which leaves about one tensor
+    per two-qubit gate; the projectors of a query attach to the open wires."""
 
     def __init__(self, cid, circ):
         self.cid, self.n = cid, circ.n
@@ -97,6 +101,7 @@ class _Circuit:
             for q, o in zip(qs, outs):
                 wire[q] = o
         self.wire = wire
+        self.tensors, self.labels, _ = simplify(self.tensors, self.labels, out_labels=wire)
         self.per_k = {}
 
     def plan_for(self, k):

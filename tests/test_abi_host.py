@@ -306,3 +306,47 @@ def test_network_checks_and_greedy_path(L):
     finally:
         for t in (a, b, c, d, z):
             t.destroy()
+
+
+def test_simplify_without_merges_does_no_device_work(L):
+    """rosnet_simplify on networks where nothing may be absorbed (every small
+    tensor kept, or only rank-3 tensors) returns the caller's handles, labels
+    and positions unchanged without touching the device; bad arguments are
+    refused."""
+    L.rosnet_simplify.argtypes = [ctypes.POINTER(R._Network), ctypes.POINTER(ctypes.c_uint8), ctypes.c_int32,
+                                  ctypes.POINTER(R._Opts), vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32)]
+    a = T(L, (2, 3))
+    b = T(L, (3, 4))
+    c = T(L, (4, 2, 2))
+    d = T(L, (2, 2, 5))
+    try:
+        def run(tensors, labels, out, keep, max_rank=2):
+            net = _network(L, tensors, labels, out)
+            n = len(tensors)
+            kp = (ctypes.c_uint8 * n)(*keep) if keep is not None else None
+            tout = (vp * n)()
+            rout = (ctypes.c_int32 * n)()
+            lout = (ctypes.c_int64 * sum(len(x) for x in labels))()
+            oout = (ctypes.c_int32 * n)()
+            nn = ctypes.c_int32()
+            rc = L.rosnet_simplify(ctypes.byref(net.net), kp, max_rank, None, None, tout, rout, lout, oout,
+                                   ctypes.byref(nn))
+            return STATUS[rc], [tout[i] for i in range(nn.value)], [rout[i] for i in range(nn.value)], \
+                list(lout[:sum(rout[i] for i in range(nn.value))]), [oout[i] for i in range(nn.value)]
+        labels = [(0, 1), (1, 2), (2, 3, 4)]
+        st, ts, rk, lb, og = run([a, b, c], labels, [0, 3, 4], [1, 1, 0])
+        assert st == "OK" and ts == [a.handle.value, b.handle.value, c.handle.value]
+        assert rk == [2, 2, 3] and lb == [0, 1, 1, 2, 2, 3, 4] and og == [0, 1, 2]
+        st, ts, rk, lb, og = run([c, d], [(0, 1, 2), (1, 2, 3)], [0, 3], None)   # rank 3 only
+        assert st == "OK" and og == [0, 1] and lb == [0, 1, 2, 1, 2, 3]
+        st, ts, rk, lb, og = run([a, b], [(0, 1), (1, 2)], [0, 2], [0, 0], max_rank=3)
+        assert st == "INVALID_ARG" and ts == []
+        st, *_ = run([a, b], [(0, 1), (1, 2)], [0, 2], [0, 0], max_rank=-1)
+        assert st == "INVALID_ARG"
+        st, *_ = run([a, b], [(0, 1), (1, 2)], [0, 2], [0, 0], max_rank=0)       # rank-0 tensors only
+        assert st == "OK"
+    finally:
+        for t in (a, b, c, d):
+            t.destroy()
