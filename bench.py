@@ -460,7 +460,8 @@ def run_extras(R, torch, dev, probed, args=None):
         ba = argparse.Namespace(**vars(args))
         ba.steps = 3
         line = run_batch(ba, emit=False)
-        out["batch"] = {k: line[k] for k in ("workload", "path_gflop", "sliced_gflop", "modes")}
+        out["batch"] = {k: line[k] for k in ("workload", "tensors_30q_given_used", "small_circuits_simplified",
+                                             "path_gflop", "sliced_gflop", "modes")}
         R.release_plans()
     except Exception as e:
         out["batch"] = {"error": str(e)[:200]}
@@ -885,24 +886,31 @@ def run_serve(args, emit=True):
 
 def run_batch(args, emit=True):
     """Sliced 30-qubit circuit (256 slices) + 64 circuits of 16-24 qubits in
-    one batched plan per precision mode."""
+    one batched plan per precision mode (each network as given or simplified,
+    whichever has the cheaper searched path)."""
     import torch
     import paper_2201_06620_b300 as R
+    # each network as given or simplified (rank-1 and rank-2 tensors absorbed
+    # into neighbours on the device), whichever has the cheaper searched path;
+    # the 30-qubit one is then sliced
     circ = W.random_circuit(30, 14, 2022, 5, 6)
     net = W.circuit_network(circ)
-    ext = [t.shape for t in net.tensors]
-    path, fl = R.path_search(net.labels, ext, net.out_labels, ntrials=64, seed=0)
-    cut, mx, ft = R.slice_search(net.labels, ext, net.out_labels, path, 8)
-    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
-    nets = [n for _, n in R.sliced_networks(ts, net.labels, net.out_labels, cut)]
+    raw = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+    ts, labels, path, fl = R.cheaper_network(raw, net.labels, net.out_labels, ntrials=64, seed=0)
+    ntens = (len(raw), len(ts))
+    ext = [t.shape for t in ts]
+    cut, mx, ft = R.slice_search(labels, ext, net.out_labels, path, 8)
+    nets = [n for _, n in R.sliced_networks(ts, labels, net.out_labels, cut)]
     paths = [path] * len(nets)
     rng = np.random.default_rng(7)
+    nsimp = 0
     for i in range(64):
         c = W.random_circuit(int(rng.integers(16, 25)), int(rng.integers(8, 13)), 500 + i)
         nw = W.circuit_network(c)
-        tt = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in nw.tensors]
-        p, _ = R.path_search(nw.labels, [t.shape for t in nw.tensors], nw.out_labels, ntrials=16, seed=i)
-        nets.append(R.Network(tt, nw.labels, nw.out_labels))
+        tr = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in nw.tensors]
+        tt, ll, p, _ = R.cheaper_network(tr, nw.labels, nw.out_labels, ntrials=16, seed=i)
+        nsimp += len(tt) < len(tr)
+        nets.append(R.Network(tt, ll, nw.out_labels))
         paths.append(p)
     res = {}
     for name, prec in (("fp32", R.PREC_DEFAULT), ("bf16x3", R.PREC_BF16X3), ("tf32x3", R.PREC_TF32X3)):
@@ -926,6 +934,7 @@ def run_batch(args, emit=True):
         del outs
         R.release_plans()
     line = {"metric": "batch amplitudes/s", "workload": "sliced 30q (256 slices) + 64 circuits",
+            "tensors_30q_given_used": list(ntens), "small_circuits_simplified": nsimp,
             "path_gflop": fl / 1e9, "sliced_gflop": ft / 1e9, "max_slice_entries": mx, "modes": res}
     if emit:
         print(json.dumps(line), flush=True)

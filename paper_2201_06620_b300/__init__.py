@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
     "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc", "tensordot_ooc_host", "contract_batch",
-    "simplify",
+    "simplify", "cheaper_network",
     "plan_stats", "path_search", "slice_search", "sliced_networks", "sum_fp64",
     "sync", "kernel_launches", "release_plans", "plan_cache_limit", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
@@ -714,6 +714,23 @@ def simplify(tensors, labels, out_labels=(), keep=(), max_rank=2, precision=PREC
         origin.append(j)
         pos += rout[i]
     return res_t, res_l, origin
+
+
+def cheaper_network(tensors, labels, out_labels=(), keep=(), ntrials=16, seed=0, max_rank=2, stream=None):
+    """The network as given or simplified (``simplify``), whichever has the
+    cheaper path found by ``path_search`` with the same trials and seed:
+    (tensors, labels, path, flops).  Simplification leaves fewer, larger
+    tensors, on which the randomised greedy search can find better or worse
+    paths than on the raw network, so both are searched."""
+    ext = [t.shape for t in tensors]
+    path, fl = path_search(labels, ext, out_labels, ntrials=ntrials, seed=seed)
+    st, sl, _ = simplify(tensors, labels, out_labels, keep=keep, max_rank=max_rank, stream=stream)
+    if len(st) == len(tensors):
+        return list(tensors), [tuple(l) for l in labels], path, fl
+    p2, f2 = path_search(sl, [t.shape for t in st], out_labels, ntrials=ntrials, seed=seed)
+    if f2 < fl:
+        return st, sl, p2, f2
+    return list(tensors), [tuple(l) for l in labels], path, fl
 
 
 def contract(tensors, labels=None, out_labels=None, path=None, precision=PREC_DEFAULT, flags=0,

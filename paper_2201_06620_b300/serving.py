@@ -37,6 +37,16 @@ import numpy as np
 from . import (C64, OPT_GRAPH, PREC_DEFAULT, Network, btensor, contract, empty, path_search, plan_info,
                plan_release, simplify)
 
+
+@dataclass
+class _Plan:
+    tensors: list      # circuit tensors (as given or simplified); projectors follow
+    labels: list
+    out: list
+    path: list
+    flops: float
+    footprint: float
+
 __all__ = ["Query", "AmplitudeServer", "predict_footprint"]
 
 
@@ -82,10 +92,11 @@ def predict_footprint(labels, extents, out_labels, path, elem_bytes=8):
 
 class _Circuit:
     """Device-resident tensors of one circuit and its per-k paths.  The
-    circuit part (|0> vectors and gates, final wires open) is simplified once
-    on registration: every rank-1 and rank-2 tensor is absorbed into a
-    neighbour on the device (rosnet_simplify), which leaves about one tensor
-    per two-qubit gate; the projectors of a query attach to the open wires."""
+    circuit part (|0> vectors and gates, final wires open) is also simplified
+    once on registration: every rank-1 and rank-2 tensor absorbed into a
+    neighbour on the device (rosnet_simplify), about one tensor per two-qubit
+    gate.  For each k the path is searched on both forms, with the query's
+    projectors on the closed wires, and the cheaper one is used."""
 
     def __init__(self, cid, circ):
         self.cid, self.n = cid, circ.n
@@ -101,17 +112,22 @@ class _Circuit:
             for q, o in zip(qs, outs):
                 wire[q] = o
         self.wire = wire
-        self.tensors, self.labels, _ = simplify(self.tensors, self.labels, out_labels=wire)
+        st, sl, _ = simplify(self.tensors, self.labels, out_labels=wire)
+        self.forms = [(self.tensors, self.labels)] + ([(st, sl)] if len(st) < len(self.tensors) else [])
         self.per_k = {}
 
     def plan_for(self, k):
         if k not in self.per_k:
             closed = self.n - k
-            labels = self.labels + [(self.wire[q],) for q in range(closed)]
-            ext = [t.shape for t in self.tensors] + [(2,)] * closed
             out = [self.wire[q] for q in range(closed, self.n)]
-            path, flops = path_search(labels, ext, out, ntrials=16, seed=self.cid)
-            self.per_k[k] = (labels, out, path, flops, predict_footprint(labels, ext, out, path))
+            best = None
+            for tensors, labels in self.forms:
+                labels = list(labels) + [(self.wire[q],) for q in range(closed)]
+                ext = [t.shape for t in tensors] + [(2,)] * closed
+                path, flops = path_search(labels, ext, out, ntrials=16, seed=self.cid)
+                if best is None or flops < best.flops:
+                    best = _Plan(tensors, labels, out, path, flops, predict_footprint(labels, ext, out, path))
+            self.per_k[k] = best
         return self.per_k[k]
 
 
@@ -169,7 +185,7 @@ class AmplitudeServer:
             q = self.waiting[0]
             si = self.free[-1]
             key = (si, q.circuit, q.k)
-            need = 8.0 * 2 ** q.k + (0.0 if key in self.resident else self.circuits[q.circuit].plan_for(q.k)[4])
+            need = 8.0 * 2 ** q.k + (0.0 if key in self.resident else self.circuits[q.circuit].plan_for(q.k).footprint)
             if self.device_bytes + need > self.budget:
                 busy = {(r[1], r[0].circuit, r[0].k) for r in self.running}
                 for victim in [k for k in self.resident if k not in busy and k != key]:
@@ -193,7 +209,7 @@ class AmplitudeServer:
         sl = self.slots[si]
         c = self.circuits[ci]
         net = sl.nets.pop((ci, k))
-        plan_release([net], [c.plan_for(k)[2]], precision=self.precision, flags=self.flags, stream=sl.stream)
+        plan_release([net], [c.plan_for(k).path], precision=self.precision, flags=self.flags, stream=sl.stream)
         self.resident_bytes -= self.resident.pop(key)
         self.evictions += 1
 
@@ -203,10 +219,11 @@ class AmplitudeServer:
         self.free.remove(si)
         sl = self.slots[si]
         c = self.circuits[q.circuit]
-        labels, out, path, _, _ = c.plan_for(q.k)
+        pl = c.plan_for(q.k)
+        path = pl.path
         closed = c.n - q.k
         if (q.circuit, q.k) not in sl.nets:
-            sl.nets[(q.circuit, q.k)] = Network(c.tensors + sl.views[:closed], labels, out)
+            sl.nets[(q.circuit, q.k)] = Network(list(pl.tensors) + sl.views[:closed], pl.labels, pl.out)
         net = sl.nets[(q.circuit, q.k)]
         pre = np.asarray(q.prefix, dtype=np.float32)
         sl.host[:closed, 0] = 1.0 - pre

@@ -44,6 +44,25 @@ def test_sliced_20_qubit_amplitude(dtype, tol):
     assert complex(R.sum_fp64(outs2).download()) == total
 
 
+def test_sliced_simplified_20_qubit_amplitude():
+    """The batch workload's recipe: the network simplified on the device
+    first, then sliced over 8 bonds of the simplified network (256
+    subnetworks in one batch), slice results summed in FP64."""
+    circ = W.rqc20_config()
+    net = W.circuit_network(circ)
+    raw = _device_network(net, R.C128)
+    ts, labels, _ = R.simplify(raw, net.labels, net.out_labels)
+    assert len(ts) < len(raw) // 3
+    ext = [t.shape for t in ts]
+    path, _ = R.path_search(labels, ext, net.out_labels, ntrials=32, seed=1)
+    cut, _, _ = R.slice_search(labels, ext, net.out_labels, path, 8)
+    nets = [n for _, n in R.sliced_networks(ts, labels, net.out_labels, cut)]
+    assert len(nets) == 256
+    total = complex(R.sum_fp64(R.contract_batch(nets, [path] * len(nets), flags=R.OPT_GRAPH)).download())
+    ref = oracle.amplitude_sv(circ)
+    assert abs(total - ref) / max(abs(ref), 2.0 ** -10) <= 1e-12
+
+
 def test_sliced_matches_oracle_sliced_per_slice():
     """Each slice's result equals the oracle's projection of the same network."""
     circ = W.random_circuit(12, 8, 31)

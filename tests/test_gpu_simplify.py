@@ -105,3 +105,15 @@ def test_searched_paths_on_simplified_grid_circuits():
         path, _ = R.path_search(sl, [t.shape for t in st], [], ntrials=16, seed=seed)
         got = complex(R.contract(st, sl, [], path).download())
         assert _rel(got, oracle.amplitude_sv(circ), circ.n) <= 1e-5
+
+
+def test_cheaper_network_never_costs_more_than_the_raw_one():
+    for seed in (21, 22, 23):
+        circ = W.random_circuit(14, 10, seed)
+        net = W.circuit_network(circ)
+        ts = _leaves(net)
+        _, raw_flops = R.path_search(net.labels, [t.shape for t in ts], [], ntrials=8, seed=seed)
+        st, sl, path, flops = R.cheaper_network(ts, net.labels, [], ntrials=8, seed=seed)
+        assert flops <= raw_flops
+        got = complex(R.contract(st, sl, [], path).download())
+        assert _rel(got, oracle.amplitude_sv(circ), circ.n) <= 1e-5
