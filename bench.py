@@ -171,16 +171,25 @@ def run_rosnet(args):
     path = net.greedy_path()
     steps = args.warmup + args.steps
     bits = _bitstrings(1000 + rank, steps)
-    # |0> and |1> for every output qubit, resident; a step binds its bitstring's
-    proj = [[R.btensor(np.eye(2, dtype=np.complex64)[b]) for b in (0, 1)] for _ in range(N_QUBITS)]
+    # the output projectors are the rows of one device buffer (fixed
+    # addresses: the plan's descriptors never change); every step's projector
+    # values (real plane one-hot per qubit, imaginary plane zero) are resident
+    # in HBM before the timed region, and a step copies its row of that table
+    # into the buffer (one 320-byte device-to-device copy) before contracting
+    pbuf = R.empty((N_QUBITS, 2), None, R.C64)
+    prow = [pbuf.fix([0], [q]) for q in range(N_QUBITS)]
+    for q in range(N_QUBITS):
+        net.set_tensor(ngates + q, prow[q])
+    ptab_h = np.zeros((steps, 2, N_QUBITS, 2), dtype=np.float32)
+    ptab_h[np.arange(steps)[:, None], 0, np.arange(N_QUBITS)[None, :], np.asarray(bits)] = 1.0
+    ptab = torch.from_numpy(ptab_h.reshape(steps, -1)).to(dev)
     flags = R.OPT_GRAPH | R.OPT_TIMING | (0 if args.no_autotune else R.OPT_AUTOTUNE)
     if args.tune_file and os.path.exists(args.tune_file):
         with open(args.tune_file) as f:
             R.tune_import(f.read())          # kernel choices of an earlier run
 
     def bind(i):
-        for q in range(N_QUBITS):
-            net.set_tensor(ngates + q, proj[q][int(bits[i][q])])
+        pbuf.upload_raw(ptab[i], stream=stream)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -283,7 +292,10 @@ def run_rosnet(args):
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32)",
             "data": "synthetic (seeded random circuit and bitstrings)",
-            "config": _config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+            "config": _config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                               "step_input": "every step's 20 projector vectors resident in HBM; a step "
+                                             "copies its own (320 B, device to device) into the "
+                                             "network's projector rows, then contracts"}),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                            "p99": float(np.percentile(step_ms, 99))},
             "tensordot_tflops": achieved,
