@@ -69,6 +69,7 @@ struct Step {
     Layout lay;          // layout of the result
     int wave;
     int last_use = -1;   // last wave that reads it
+    bool forest = false; // computed in the plan's fused small-step launch (before every wave)
     int64_t table_off[3];   // M, N and K offset tables, in int64 entries
     size_t arena_off;    // SIZE_MAX: written straight into output out_net
     int out_net = -1;
@@ -98,7 +99,14 @@ struct Plan {
     size_t arena_bytes = 0;
     DevBuf arena, tables, descs, partials, tcws;
     // launch list: (kind, first desc, count, total CTAs)
-    struct Launch { int kind; int first; int count; int64_t tiles; size_t tc_ws_off; };
+    struct Launch {
+        int kind;
+        int first;
+        int count;
+        int64_t tiles;
+        size_t tc_ws_off;
+        int64_t prog_off = 0;   // fused small steps: program, in int64 entries of `tables`
+    };
     std::vector<Launch> launches;
     std::vector<int> desc_step;       // desc slot -> step index
     std::vector<GettDesc> slot_desc;  // desc slot -> static descriptor fields
@@ -546,17 +554,89 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             }
         }
     }
+    // the GEMM view of every step, and the fused small steps: a step whose
+    // kernel would be gett_small_kernel, with at most kForestMacs complex
+    // multiply-adds, and whose operands are leaves or other such steps is
+    // eligible; when the first W waves hold eligible steps only, those steps
+    // are computed in one launch ahead of every other (gett_forest_kernel),
+    // which replaces W launches by one of at most W dependent levels.  The
+    // groups they form (connected through producer -> consumer) go one per
+    // CTA; a group above kForestGroupMacs in total or kForestMaxSteps steps
+    // stays in the waves
+    const int red = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
+                    : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
+                    : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
+    std::vector<GettView> views(plan->steps.size());
+    for (size_t g = 0; g < plan->steps.size(); ++g) {
+        Step &S = plan->steps[g];
+        views[g] = make_view(lay_of(S.ga), lay_of(S.gb), S.lay, S.naxes, S.axa.data(), S.axb.data());
+    }
+    // kernel of step g as the descriptor pass below chooses it (table
+    // addresses do not enter the choice; the autotuner never changes a small step)
+    auto chosen_kind = [&](size_t g) {
+        const Step &S = plan->steps[g];
+        GettDesc t;
+        memset(&t, 0, sizeof(t));
+        fill_desc_tables(t, views[g], nullptr, nullptr, nullptr);
+        if (S.ga < 0) t.flags &= ~kFlagADense;
+        if (S.gb < 0) t.flags &= ~kFlagBDense;
+        choose_kernel(t, plan->dtype, prec, red);
+        return std::make_tuple(t.kind, (double)t.M * (double)t.N * (double)t.K, t.M * t.N);
+    };
+    std::vector<int> comp(plan->steps.size(), -1);   // fused group of each fused step (its root's index)
+    if (!(flags & ROSNET_OPT_NOGROUP)) {
+        constexpr double kForestMacs = 65536.0, kForestGroupMacs = 262144.0;
+        constexpr int64_t kForestEntries = kForestThreads / 2;   // a level's entries stay about one per thread
+        std::vector<double> macs(plan->steps.size(), 0.0);
+        int wmax = 1 << 30;   // the first waves that hold eligible steps only
+        for (size_t g = 0; g < plan->steps.size(); ++g) {   // producers come before their consumers
+            Step &S = plan->steps[g];
+            const auto km = chosen_kind(g);
+            S.forest = std::get<0>(km) == kKindSmall && std::get<1>(km) > 0 && std::get<1>(km) <= kForestMacs &&
+                       std::get<2>(km) <= kForestEntries && (S.ga < 0 || plan->steps[S.ga].forest) &&
+                       (S.gb < 0 || plan->steps[S.gb].forest);
+            macs[g] = std::get<1>(km);
+            if (!S.forest) wmax = std::min(wmax, S.wave - 1);
+        }
+        for (Step &S : plan->steps) S.forest = S.forest && S.wave <= wmax;
+        // groups: union-find over producer -> consumer edges between fused steps
+        std::vector<int> up(plan->steps.size());
+        for (size_t g = 0; g < up.size(); ++g) up[g] = (int)g;
+        std::function<int(int)> find = [&](int x) { return up[x] == x ? x : (up[x] = find(up[x])); };
+        for (size_t g = 0; g < plan->steps.size(); ++g) {
+            const Step &S = plan->steps[g];
+            if (!S.forest) continue;
+            for (int64_t op : {S.ga, S.gb})
+                if (op >= 0 && plan->steps[op].forest) up[find((int)op)] = find((int)g);
+        }
+        std::unordered_map<int, double> gmacs;
+        std::unordered_map<int, int> gsteps;
+        for (size_t g = 0; g < plan->steps.size(); ++g)
+            if (plan->steps[g].forest) {
+                gmacs[find((int)g)] += macs[g];
+                ++gsteps[find((int)g)];
+            }
+        for (size_t g = 0; g < plan->steps.size(); ++g) {
+            Step &S = plan->steps[g];
+            if (!S.forest) continue;
+            const int r = find((int)g);
+            if (gmacs[r] > kForestGroupMacs || gsteps[r] > kForestMaxSteps) S.forest = false;
+            else comp[g] = r;
+        }
+    }
     // arena: every step not written straight into an output, packed by
     // lifetime with a sweep over the waves: a step's bytes are reserved from
     // the wave that writes it to the last wave that reads it, then returned to
-    // a first-fit free list (coalescing neighbours)
+    // a first-fit free list (coalescing neighbours).  Fused small steps run
+    // before every wave, concurrently in their groups: they are written at
+    // wave 0, so no two of them share bytes
     {
         const size_t el2 = 2 * (plan->dtype == ROSNET_C64 ? 4 : 8);
         std::vector<int> order;
         for (size_t g = 0; g < plan->steps.size(); ++g)
             if (plan->steps[g].arena_off != SIZE_MAX) order.push_back((int)g);
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int x, int y) { return plan->steps[x].wave < plan->steps[y].wave; });
+        auto written = [&](int x) { return plan->steps[x].forest ? 0 : plan->steps[x].wave; };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return written(x) < written(y); });
         std::map<size_t, size_t> freel;                       // offset -> size
         std::multimap<int, std::pair<size_t, size_t>> ends;   // release wave -> (off, size)
         size_t top = 0;
@@ -577,7 +657,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         };
         for (int g : order) {
             Step &S = plan->steps[g];
-            while (!ends.empty() && ends.begin()->first < S.wave) {   // free slots dead before this wave
+            while (!ends.empty() && ends.begin()->first < written(g)) {   // free slots dead before this wave
                 release(ends.begin()->second.first, ends.begin()->second.second);
                 ends.erase(ends.begin());
             }
@@ -597,7 +677,7 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
                 top += bytes;
             }
             S.arena_off = off;
-            const int to = S.last_use < 0 ? S.wave : S.last_use;
+            const int to = S.last_use < 0 ? std::max(S.wave, 0) : S.last_use;
             ends.emplace(to, std::make_pair(off, bytes));
         }
         plan->arena_bytes = top;
@@ -609,10 +689,6 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     static_assert(sizeof(Mode) == 3 * sizeof(int64_t), "a digit list is compared as bytes");
     // The large class of a low-arithmetic-intensity step (gate kernel) is
     // kept as a mode record instead of a table as large as the tensor.
-    const int red = (flags & ROSNET_OPT_REDUCE_SEQUENTIAL) ? kReduceSequential
-                    : (flags & ROSNET_OPT_REDUCE_TREE) ? kReduceTree
-                    : (flags & ROSNET_OPT_REDUCE_COMMUTATIVE) ? kReduceCommutative : kReduceAuto;
-    std::vector<GettView> views(plan->steps.size());
     std::unordered_map<std::string, int64_t> table_at;   // digits -> first entry
     std::vector<std::tuple<size_t, int, bool>> owners;   // (step, class, record) that fills each table
     int64_t tab_entries = 0;
@@ -622,7 +698,6 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     };
     for (size_t g = 0; g < plan->steps.size(); ++g) {
         Step &S = plan->steps[g];
-        views[g] = make_view(lay_of(S.ga), lay_of(S.gb), S.lay, S.naxes, S.axa.data(), S.axb.data());
         const int rec = gate_record_class(views[g], plan->dtype, prec, red,
                                           (S.ga < 0 ? kFlagADense : 0) | (S.gb < 0 ? kFlagBDense : 0));
         for (int c = 0; c < 3; ++c) {
@@ -639,7 +714,46 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             S.table_off[c] = ins.first->second;
         }
     }
+    // the fused launch's program: its steps ordered by (group, level, index),
+    // a step's level one more than its fused producers' (0 on leaves); per
+    // group its run of levels, per level its run of descriptors
+    std::vector<int> forest_order;
+    std::vector<int64_t> prog;
+    {
+        std::vector<int> level(plan->steps.size(), 0);
+        for (size_t g = 0; g < plan->steps.size(); ++g) {
+            const Step &S = plan->steps[g];
+            if (!S.forest) continue;
+            for (int64_t op : {S.ga, S.gb})
+                if (op >= 0 && plan->steps[op].forest) level[g] = std::max(level[g], level[op] + 1);
+            forest_order.push_back((int)g);
+        }
+        std::stable_sort(forest_order.begin(), forest_order.end(), [&](int x, int y) {
+            return comp[x] != comp[y] ? comp[x] < comp[y] : level[x] < level[y];
+        });
+        std::vector<int64_t> cta_groups, groups;   // groups: (first, count) pairs
+        for (size_t i = 0; i < forest_order.size(); ++i) {
+            const int g = forest_order[i];
+            const bool new_cta = i == 0 || comp[forest_order[i - 1]] != comp[g];
+            if (new_cta) cta_groups.push_back((int64_t)groups.size() / 2);
+            if (new_cta || level[forest_order[i - 1]] != level[g]) {
+                groups.push_back((int64_t)i);
+                groups.push_back(0);
+            }
+            ++groups.back();
+        }
+        if (!forest_order.empty()) {
+            const int64_t ncta = (int64_t)cta_groups.size();
+            cta_groups.push_back((int64_t)groups.size() / 2);
+            prog.push_back(ncta);
+            prog.insert(prog.end(), cta_groups.begin(), cta_groups.end());
+            prog.insert(prog.end(), groups.begin(), groups.end());
+        }
+    }
+    const int64_t prog_off = tab_entries;
+    tab_entries += (int64_t)prog.size();
     std::vector<int64_t> htab(std::max<int64_t>(tab_entries, 1));
+    std::copy(prog.begin(), prog.end(), htab.begin() + prog_off);
     for (const auto &o : owners) {
         const auto mt = class_of(views[std::get<0>(o)], std::get<1>(o));
         int64_t *t = htab.data() + plan->steps[std::get<0>(o)].table_off[std::get<1>(o)];
@@ -667,6 +781,10 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         if (S.gb < 0) S.desc.flags &= ~kFlagBDense;
         choose_kernel(S.desc, plan->dtype, prec, red);
         if (S.desc.M * S.desc.N == 0) continue;  // empty result: nothing to launch
+        if (S.forest) {   // computed in the fused launch
+            if (S.desc.kind != kKindSmall) RN_FAIL(ROSNET_ERR_CUDA, "internal: fused step changed kernel");
+            continue;
+        }
         const bool cuda_core_gemm =
             is_tiled_kind(S.desc.kind) || S.desc.kind == kKindPackF32 || is_direct_kind(S.desc.kind);
         if ((flags & ROSNET_OPT_AUTOTUNE) && cuda_core_gemm &&
@@ -738,6 +856,11 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         L.tiles = ctas;
         plan->launches.push_back(L);
     };
+    if (!forest_order.empty()) {   // before every wave
+        add_launch(kKindForest, forest_order, 0);
+        plan->launches.back().tiles = prog[0];
+        plan->launches.back().prog_off = prog_off;
+    }
     for (auto it = groups.begin(); it != groups.end(); ++it) {
         const int w = it->first.first;
         if ((it == groups.begin() || std::prev(it)->first.first != w) && atomic_of_wave.count(w))
@@ -885,6 +1008,8 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
                 bind_operands(x, ptr_of(S.ga), ptr_of(S.gb), ptr_of(st), pstride_of(S.ga), pstride_of(S.gb),
                               pstride_of(st));
                 launch_tc_problem(packed_mode(L.kind), x, ga, (char *)P.tcws.p + L.tc_ws_off, s, true, true, hook);
+            } else if (L.kind == kKindForest) {
+                launch_forest(P.dtype, dd + L.first, (const int64_t *)P.tables.p + L.prog_off, L.tiles, s);
             } else {
                 launch_gett_group(L.kind, P.dtype, dd + L.first, L.count, L.tiles, s);
             }

@@ -330,6 +330,95 @@ __global__ void __launch_bounds__(256) gett_small_kernel(const __grid_constant__
     C[ic + sd.c_plane] = si;
 }
 
+// The leaf-side small steps of a plan in one launch.  CTA c runs one
+// connected group of them -- steps whose operands are leaves or earlier steps
+// of the same group, a subtree of the contraction -- level by level: the
+// steps of a level are independent of one another, their output entries are
+// spread over all the CTA's threads (one thread per entry, the K loop in
+// registers, as gett_small_kernel), and a barrier separates levels, so every
+// step reads only outputs its own CTA wrote before the barrier (operands are
+// read with coherent loads, not the read-only path).  No CTA waits for
+// another.  The group's descriptors are staged in shared memory once.
+// prog: [G, then G + 1 level offsets (CTA c owns levels [prog[1 + c],
+// prog[2 + c])), then per level (first descriptor, descriptor count)]; a
+// CTA's descriptors are contiguous, at most kForestMaxSteps of them.
+struct ForestDesc {
+    const void *a, *b;
+    void *c;
+    int64_t a_plane, b_plane, c_plane;
+    const int64_t *offAM, *offBN, *offAK, *offBK, *offCM, *offCN;
+    int64_t M, N, K;
+    int64_t pre;     // output entries of the level's earlier steps
+    int64_t flags;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kForestThreads) gett_forest_kernel(const GettDesc *descs, const int64_t *prog) {
+    __shared__ ForestDesc fd[kForestMaxSteps];
+    grid_dep_launch();
+    grid_dep_wait();   // leaves and descriptors may come from earlier work on the stream
+    const int64_t G = prog[0];
+    const int64_t *lv = prog + G + 2;
+    const int64_t l0 = prog[1 + blockIdx.x], l1 = prog[2 + blockIdx.x];
+    const int64_t d0 = lv[2 * l0], nd = lv[2 * (l1 - 1)] + lv[2 * (l1 - 1) + 1] - d0;
+    for (int64_t j = threadIdx.x; j < nd; j += kForestThreads) {
+        const GettDesc &d = descs[d0 + j];
+        ForestDesc &f = fd[j];
+        f.a = d.a; f.b = d.b; f.c = d.c;
+        f.a_plane = d.a_plane; f.b_plane = d.b_plane; f.c_plane = d.c_plane;
+        f.offAM = d.offAM; f.offBN = d.offBN; f.offAK = d.offAK; f.offBK = d.offBK;
+        f.offCM = d.offCM; f.offCN = d.offCN;
+        f.M = d.M; f.N = d.N; f.K = d.K;
+        f.flags = d.flags;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)   // per level, the running count of output entries
+        for (int64_t l = l0; l < l1; ++l) {
+            int64_t run = 0;
+            for (int64_t j = lv[2 * l] - d0; j < lv[2 * l] - d0 + lv[2 * l + 1]; ++j) {
+                fd[j].pre = run;
+                run += fd[j].M * fd[j].N;
+            }
+        }
+    __syncthreads();
+    for (int64_t l = l0; l < l1; ++l) {
+        const int jb = (int)(lv[2 * l] - d0), je = jb + (int)lv[2 * l + 1];
+        const int64_t total = fd[je - 1].pre + fd[je - 1].M * fd[je - 1].N;
+        for (int64_t i = threadIdx.x; i < total; i += kForestThreads) {
+            int lo = jb, hi = je - 1;   // the last step whose entries start at or before i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (fd[mid].pre <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            const ForestDesc &f = fd[lo];
+            const int64_t o = i - f.pre;
+            int64_t m, n;
+            if (f.flags & (kFlagBNFast | kFlagCNFast)) {
+                n = o % f.N;
+                m = o / f.N;
+            } else {
+                m = o % f.M;
+                n = o / f.M;
+            }
+            const T *A = (const T *)f.a;
+            const T *B = (const T *)f.b;
+            const int64_t am = __ldg(f.offAM + m), bn = __ldg(f.offBN + n);
+            T sr = 0, si = 0;
+#pragma unroll 4
+            for (int64_t k = 0; k < f.K; ++k) {
+                const int64_t ia = am + __ldg(f.offAK + k), ib = bn + __ldg(f.offBK + k);
+                cmac(sr, si, A[ia], A[ia + f.a_plane], B[ib], B[ib + f.b_plane]);
+            }
+            T *C = (T *)f.c;
+            const int64_t ic = __ldg(f.offCM + m) + __ldg(f.offCN + n);
+            C[ic] = sr;
+            C[ic + f.c_plane] = si;
+        }
+        __syncthreads();   // this level's outputs are visible to the next level
+    }
+}
+
 // One warp per output entry; lanes split the K loop, shuffle reduction.
 template <typename T>
 __global__ void __launch_bounds__(256) gett_warpk_kernel(const __grid_constant__ GroupArgs g) {
@@ -1369,6 +1458,17 @@ static void launch_group_args(int kind, int dtype, const GroupArgs &ga, int64_t 
             default: launch_tiled<double, 64, 64, 8>(grid, ga, s, pdl); break;
         }
     }
+    g_launches++;
+    RN_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_forest(int dtype, const GettDesc *descs, const int64_t *prog, int64_t ctas, cudaStream_t s) {
+    if (ctas <= 0) return;
+    if (ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "too many groups in one launch");
+    if (dtype == ROSNET_C64)
+        launch_pdl(gett_forest_kernel<float>, dim3((unsigned)ctas), kForestThreads, 0, s, true, descs, prog);
+    else
+        launch_pdl(gett_forest_kernel<double>, dim3((unsigned)ctas), kForestThreads, 0, s, true, descs, prog);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
 }

@@ -231,7 +231,11 @@ enum KernelKind : int32_t {
     kKindTiled128x32 = 12,  // 128x32 tiles (complex64 only)
     kKindDirect = 13,       // 64x64 tiles, each CTA's K range (<= kDirectK) gathered in one pass
     kKindDirect256x16 = 14, // 256x16 tiles of the same kernel (complex64 only)
+    kKindForest = 15,       // a plan's leaf-side small steps, one connected group per CTA
 };
+
+constexpr int kForestThreads = 512;    // threads of a gett_forest_kernel CTA
+constexpr int kForestMaxSteps = 192;   // most steps of one fused group (its descriptors in shared memory)
 
 constexpr int kDirectK = 32;   // longest contraction range of one direct-kernel CTA
 
@@ -342,6 +346,9 @@ inline int64_t zero_ctas(const GettDesc &d) { return (d.M * d.N + 1023) / 1024; 
 // Launch one group of problems of the same kind and dtype.  `descs` is in
 // device memory (ndesc entries, with tile_begin prefix sums); total_tiles is
 // the sum of tiles_m*tiles_n.
+// The fused leaf-side small steps of a plan (gett_forest_kernel): `ctas`
+// groups, program `prog` in device memory.
+void launch_forest(int dtype, const GettDesc *descs, const int64_t *prog, int64_t ctas, cudaStream_t s);
 void launch_gett_group(int kind, int dtype, const GettDesc *descs, int ndesc,
                        int64_t total_tiles, cudaStream_t s);
 

@@ -46,6 +46,8 @@ class _Plan:
     path: list
     flops: float
     footprint: float
+    sig: tuple = ()    # what the library keys its cached plan by (with the slot's stream):
+                       # equal signatures share one plan
 
 __all__ = ["Query", "AmplitudeServer", "predict_footprint"]
 
@@ -127,6 +129,9 @@ class _Circuit:
                 path, flops = path_search(labels, ext, out, ntrials=16, seed=self.cid)
                 if best is None or flops < best.flops:
                     best = _Plan(tensors, labels, out, path, flops, predict_footprint(labels, ext, out, path))
+            best.sig = (tuple(map(tuple, best.labels)), tuple(tuple(t.shape) for t in best.tensors),
+                        tuple(tuple(t.block_shape) for t in best.tensors), tuple(best.out),
+                        tuple(map(tuple, best.path)))
             self.per_k[k] = best
         return self.per_k[k]
 
@@ -153,7 +158,9 @@ class AmplitudeServer:
         self.slots = [_Slot(torch, nmax) for _ in range(slots)]
         self.free = list(range(slots))
         self.budget = memory_budget
-        # resident plans: (slot, circuit, k) -> device bytes, least recently used first
+        # resident plans: (slot, plan signature) -> device bytes, least recently
+        # used first.  Circuits of equal structure and path share one plan in
+        # the library's cache, so it is counted and released once
         self.resident = collections.OrderedDict()
         self.resident_bytes = 0.0
         self.in_use = 0.0          # outputs of running queries
@@ -184,10 +191,10 @@ class AmplitudeServer:
         while self.waiting and self.free:
             q = self.waiting[0]
             si = self.free[-1]
-            key = (si, q.circuit, q.k)
+            key = self._key(si, q)
             need = 8.0 * 2 ** q.k + (0.0 if key in self.resident else self.circuits[q.circuit].plan_for(q.k).footprint)
             if self.device_bytes + need > self.budget:
-                busy = {(r[1], r[0].circuit, r[0].k) for r in self.running}
+                busy = {self._key(r[1], r[0]) for r in self.running}
                 for victim in [k for k in self.resident if k not in busy and k != key]:
                     if self.device_bytes + need <= self.budget:
                         break
@@ -204,12 +211,17 @@ class AmplitudeServer:
                 self.running[0][2].synchronize()
         self._retire()
 
+    def _key(self, si, q):
+        return (si, self.circuits[q.circuit].plan_for(q.k).sig)
+
     def _evict(self, key):
-        si, ci, k = key
+        si, sig = key
         sl = self.slots[si]
-        c = self.circuits[ci]
-        net = sl.nets.pop((ci, k))
-        plan_release([net], [c.plan_for(k).path], precision=self.precision, flags=self.flags, stream=sl.stream)
+        users = [ck for ck in sl.nets if self.circuits[ck[0]].plan_for(ck[1]).sig == sig]
+        nets = [sl.nets.pop(ck) for ck in users]
+        ci, k = users[0]
+        plan_release([nets[0]], [self.circuits[ci].plan_for(k).path], precision=self.precision, flags=self.flags,
+                     stream=sl.stream)
         self.resident_bytes -= self.resident.pop(key)
         self.evictions += 1
 
@@ -245,7 +257,7 @@ class AmplitudeServer:
         self.running.append((q, si, ev, res, out_bytes))
         # a plan larger than predicted: free idle plans until the budget holds
         if self.device_bytes > self.budget:
-            busy = {(r[1], r[0].circuit, r[0].k) for r in self.running}
+            busy = {self._key(r[1], r[0]) for r in self.running}
             for victim in [k for k in self.resident if k not in busy]:
                 if self.device_bytes <= self.budget:
                     break

@@ -127,6 +127,26 @@ def test_rqc20_amplitude_full_size():
     assert packed == 0, packed
 
 
+def test_fused_small_steps_match_wave_launches():
+    """The leaf-side gate-sized steps of the 20-qubit amplitude run in one
+    fused launch (one CTA per connected group, level by level); each step is
+    computed as in its own launch, so the amplitude is bitwise equal to the
+    ungrouped plan (one launch per step), and the plan has fewer launches."""
+    circ = W.rqc20_config()
+    net = W.circuit_network(circ, bitstring=circ.bitstring)
+    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+    path = R.path_greedy(ts, net.labels, net.out_labels)
+    gn = R.Network(ts, net.labels, net.out_labels)
+    amps, launches = [], []
+    for flags in (R.OPT_GRAPH, R.OPT_GRAPH | R.OPT_NOGROUP):
+        amps.append(complex(R.contract(gn, path=path, flags=flags, max_block_entries=256).download()))
+        launches.append(R.plan_stats([gn], [path], flags=flags, max_block_entries=256)[2])
+    assert amps[0] == amps[1]
+    assert launches[0] <= 13 < launches[1], launches
+    ref = oracle.statevector(circ)[oracle.bitstring_index(circ.bitstring)]
+    assert amp_err(amps[0], ref, 20) <= 1e-5
+
+
 # Tensor-core split products on the same workload, against the state vector.
 # 3xTF32 keeps about 22 significant bits per operand and reaches the FP32
 # bar.  3xBF16 keeps about 16 (hi + lo, each 8 bits; the lo*lo product and

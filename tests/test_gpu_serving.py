@@ -171,7 +171,7 @@ def test_budget_holds_resident_plans_across_many_circuits():
         q = Query(circuit=ci, prefix=(0,) * (circs[ci].n - 2), k=2, suffixes=[0, 3])
         probe.submit(q)
         probe.drain()
-        sizes.append(probe.resident[(0, ci, 2)])
+        sizes.append(probe.resident[probe._key(0, q)])
     budget = 2.5 * max(sizes)
     srv = AmplitudeServer(circs, slots=2, memory_budget=budget)
     queries = _queries(circs, rng, 40)
