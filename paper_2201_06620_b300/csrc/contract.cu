@@ -523,6 +523,8 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             t.M = la.numel / K;
             t.N = lb.numel / K;
             t.K = K;
+            // intermediates will be laid out dense for this consumer (leaves never are)
+            t.flags = (S.ga >= 0 ? kFlagADense : 0) | (S.gb >= 0 ? kFlagBDense : 0);
             choose_kernel(t, plan->dtype, prec, red0);
             if (t.kind != kKindPackF32) continue;
             // order of the contracted pairs: as given, or a leaf operand's own

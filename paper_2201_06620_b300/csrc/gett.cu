@@ -1296,9 +1296,13 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
             return;
         }
     }
-    // large FP32 contractions: pack once, then TMA-fed FFMA tiles (no split-K)
+    // large FP32 contractions: pack once, then TMA-fed FFMA tiles (no split-K).
+    // Short contractions (32 <= K < 128) only when both operands are read in
+    // place: a pack pass would cost more than the one or few k-tiles it feeds
+    const bool in_place = (d.flags & kFlagADense) && (d.flags & kFlagBDense);
     if (dtype == ROSNET_C64 && reduce_mode != kReduceTree && reduce_mode != kReduceCommutative &&
-        std::min(d.M, d.N) >= 64 && d.K >= 128 && 8.0 * (double)MN * (double)d.K >= 268435456.0) {
+        std::min(d.M, d.N) >= 64 && (d.K >= 128 || (d.K >= 32 && in_place)) &&
+        8.0 * (double)MN * (double)d.K >= 268435456.0) {
         const int64_t t = ((d.M + f32p_tile_m() - 1) / f32p_tile_m()) * ((d.N + f32p_tile_n() - 1) / f32p_tile_n());
         if (t >= 120) {
             if (d.N > d.M) swap_operands(d);
