@@ -604,7 +604,13 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         // groups: union-find over producer -> consumer edges between fused steps
         std::vector<int> up(plan->steps.size());
         for (size_t g = 0; g < up.size(); ++g) up[g] = (int)g;
-        std::function<int(int)> find = [&](int x) { return up[x] == x ? x : (up[x] = find(up[x])); };
+        auto find = [&](int x) {   // root of x's group, with path halving (no recursion)
+            while (up[x] != x) {
+                up[x] = up[up[x]];
+                x = up[x];
+            }
+            return x;
+        };
         for (size_t g = 0; g < plan->steps.size(); ++g) {
             const Step &S = plan->steps[g];
             if (!S.forest) continue;
