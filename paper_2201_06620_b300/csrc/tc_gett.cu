@@ -54,14 +54,18 @@ constexpr int NTHREADS = 320;            // warp 0 TMA, warp 1 MMA, warps 2-9 ac
 constexpr int NACC_WARPS = 8;
 // contracted indices per TMEM accumulation chunk.  The tensor core's FP32
 // accumulator adds carry a one-sided error that grows with the number of
-// terms; each finished chunk is added into FP32 registers.  TF32: 256 (its
-// error is set by the operand rounding).  3xTF32, the FP32-accuracy arm: 16,
+// terms; each finished chunk is added into FP32 registers.  TF32: 4096 (its
+// error is set by the operand rounding, 2^-11 of each operand; the
+// accumulator's bias over 4096 terms, ~1.4e-8 each, stays far below it, and
+// one chunk per tile for most shapes leaves the accumulator drain off the
+// tensor core's path: 661 -> 689 TFLOP/s on 2^10 x 2^15 x 2^10 against
+// 256-term chunks).  3xTF32, the FP32-accuracy arm: 16,
 // which brings its amplitudes to plain FP32's error on deep circuits
 // (measured vs the FP64 oracle on 16-20 qubit, depth 12-16 circuits: worst
 // 8.8e-6 against FP32's 9.1e-6; 1.06e-5 with 32, 1.28e-5 with 64) for 16%
 // of its throughput on large contractions.  3xBF16: 64 (its error is set by
 // the bf16 split; shorter chunks do not reduce it).
-constexpr int chunk_k(int mode) { return mode == 0 ? 256 : mode == 1 ? 16 : 64; }
+constexpr int chunk_k(int mode) { return mode == 0 ? 4096 : mode == 1 ? 16 : 64; }
 constexpr long long kWaitBudget = 4000000000LL;   // cycles (~2 s at 2 GHz)
 
 enum Mode : int { kTF32 = 0, kTF32x3 = 1, kBF16x3 = 2 };
