@@ -63,9 +63,11 @@ constexpr int NACC_WARPS = 8;
 // which brings its amplitudes to plain FP32's error on deep circuits
 // (measured vs the FP64 oracle on 16-20 qubit, depth 12-16 circuits: worst
 // 8.8e-6 against FP32's 9.1e-6; 1.06e-5 with 32, 1.28e-5 with 64) for 16%
-// of its throughput on large contractions.  3xBF16: 64 (its error is set by
-// the bf16 split; shorter chunks do not reduce it).
-constexpr int chunk_k(int mode) { return mode == 0 ? 4096 : mode == 1 ? 16 : 64; }
+// of its throughput on large contractions.  3xBF16: 128 (its error is set by
+// the bf16 split: the 20-qubit amplitude's error against plain FP32 is
+// 1.71e-5 with 16-, 64- or 128-term chunks, 1.94e-5 with 256; 128 against 64
+// gives 501 -> 542 TFLOP/s on 2^10 x 2^15 x 2^10).
+constexpr int chunk_k(int mode) { return mode == 0 ? 4096 : mode == 1 ? 16 : 128; }
 constexpr long long kWaitBudget = 4000000000LL;   // cycles (~2 s at 2 GHz)
 
 enum Mode : int { kTF32 = 0, kTF32x3 = 1, kBF16x3 = 2 };
