@@ -561,6 +561,21 @@ rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const 
                                 int64_t *steps_planned, int64_t *launches, int64_t *packed_operands,
                                 int64_t *device_bytes);
 
+/* Spill the cached plan of these arguments (as rosnet_plan_stats) to pinned
+ * host memory, the out-of-core tier applied to a plan (Sec. I and III): once
+ * the work enqueued on `stream` and the plan's own work have finished (the
+ * call waits for them), its offset tables are copied to page-locked host
+ * memory and all its device memory (tables, descriptors, intermediate arena,
+ * split-K and packed-operand workspaces) and its captured graph are released;
+ * rosnet_plan_stats then reports 0 device bytes.  The next contraction with
+ * the same arguments restores it -- the buffers allocated again, the tables
+ * copied back, the graph captured again -- instead of planning anew, with
+ * the same results.  *host_bytes (may be NULL) receives the page-locked bytes
+ * held while spilled.  Spilling a spilled plan does nothing.  INVALID_ARG if
+ * no such plan is cached. */
+rosnet_status rosnet_plan_spill(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                const rosnet_opts *opts, void *stream, int64_t *host_bytes);
+
 /* Free the cached plan of these arguments (as rosnet_plan_stats), e.g. for a
  * server that bounds the device memory its resident plans hold.  Work the
  * plan already enqueued completes normally (buffers are released in stream

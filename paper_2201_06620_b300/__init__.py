@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "RosnetError", "BTensor", "Network", "btensor", "empty", "tensordot", "path_greedy",
     "path_greedy_extents", "contract", "tensordot_noalloc", "tensordot_ooc", "tensordot_ooc_host", "contract_batch",
-    "simplify", "cheaper_network",
+    "simplify", "cheaper_network", "plan_spill",
     "plan_stats", "path_search", "slice_search", "sliced_networks", "sum_fp64",
     "sync", "kernel_launches", "release_plans", "plan_cache_limit", "lib", "use_torch_allocator",
     "C64", "C128", "PREC_DEFAULT", "PREC_FP32", "PREC_TF32", "PREC_BF16X3", "PREC_FP64",
@@ -62,6 +62,7 @@ EXPORTS = [
     "rosnet_kernel_launches", "rosnet_path_greedy_extents", "rosnet_timing_drain",
     "rosnet_tensordot_noalloc", "rosnet_btensor_upload_range", "rosnet_btensor_slice",
     "rosnet_btensor_block", "rosnet_tensordot_ooc", "rosnet_tensordot_ooc_host", "rosnet_simplify",
+    "rosnet_plan_spill",
     "rosnet_contract_batch",
     "rosnet_plan_stats",
     "rosnet_btensor_fix", "rosnet_path_search", "rosnet_slice_search", "rosnet_sum",
@@ -146,6 +147,8 @@ def lib():
                                             i64p, i64p, i64p, i64p]
             L.rosnet_plan_release.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network),
                                               ctypes.POINTER(_Path), ctypes.POINTER(_Opts), vp]
+            L.rosnet_plan_spill.argtypes = [ctypes.c_int32, ctypes.POINTER(_Network), ctypes.POINTER(_Path),
+                                            ctypes.POINTER(_Opts), vp, i64p]
             L.rosnet_norm2.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
             L.rosnet_tensordot_ooc.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -207,7 +210,8 @@ def lib():
                         "rosnet_btensor_download_async", "rosnet_alloc_stats",
                         "rosnet_btensor_upload_raw", "rosnet_btensor_download_raw",
                         "rosnet_plan_cache_limit", "rosnet_probe_peak", "rosnet_plan_release",
-                        "rosnet_norm2", "rosnet_tensordot_ooc_host", "rosnet_simplify"):
+                        "rosnet_norm2", "rosnet_tensordot_ooc_host", "rosnet_simplify",
+                        "rosnet_plan_spill"):
                     f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -794,6 +798,18 @@ def plan_release(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_ent
     o = _opts(precision, flags, max_block_entries)
     _check(lib().rosnet_plan_release(len(nets), arr, parr, ctypes.byref(o), _stream(stream)),
            "rosnet_plan_release")
+
+
+def plan_spill(networks, paths, precision=PREC_DEFAULT, flags=0, max_block_entries=0, stream=None):
+    """Move the cached plan of these arguments to pinned host memory
+    (rosnet_plan_spill); the next contraction restores it.  Returns the
+    page-locked bytes it holds."""
+    nets, arr, parr = _batch_args(networks, paths)
+    o = _opts(precision, flags, max_block_entries)
+    hb = ctypes.c_int64()
+    _check(lib().rosnet_plan_spill(len(nets), arr, parr, ctypes.byref(o), _stream(stream), ctypes.byref(hb)),
+           "rosnet_plan_spill")
+    return hb.value
 
 
 def norm2(t, stream=None):

@@ -25,6 +25,7 @@
 #include <string>
 #include <random>
 #include <tuple>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -137,6 +138,14 @@ struct Plan {
     int tpos = 0;
     int64_t steps_requested = 0;               // path steps before common steps were merged
     uint64_t last_used = 0;                    // cache clock of the latest call
+    // pinned-host spill: while spilled the offset tables (the one part of the
+    // device state that is not scratch or rebuilt per call) live in
+    // page-locked host memory and every device buffer and the graph are
+    // released; the device addresses they had are kept to re-point the
+    // descriptors when the plan is restored
+    bool spilled = false;
+    void *host_tables = nullptr;
+    const char *old_tables = nullptr, *old_partials = nullptr;
     ~Plan() {
         // device buffers go first, while every stream they were allocated or
         // last used on still exists (the side stream is destroyed below)
@@ -152,6 +161,7 @@ struct Plan {
         }
         if (graph) cudaGraphExecDestroy(graph);
         if (graph_src) cudaGraphDestroy(graph_src);
+        if (host_tables) cudaFreeHost(host_tables);
         if (side) { cudaStreamSynchronize(side); cudaStreamDestroy(side); }
         for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : tev) if (e) cudaEventDestroy(e);
@@ -914,6 +924,74 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
     return plan;
 }
 
+// Device bytes a plan holds (0 while spilled).
+size_t plan_device_bytes(const Plan &P) {
+    if (P.spilled) return 0;
+    return P.arena.bytes + P.tables.bytes + P.descs.bytes + P.partials.bytes + P.tcws.bytes;
+}
+
+// Spill: wait for the plan's work, copy its tables to page-locked host
+// memory, release its device buffers and graph.  Returns the host bytes held.
+size_t spill_plan(Plan &P, cudaStream_t s) {
+    if (P.spilled) return P.tables.bytes;
+    RN_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (P.side) RN_CHECK_CUDA(cudaStreamSynchronize(P.side));
+    for (int i = 0; i < Plan::kRing; ++i)
+        if (P.ev[i]) RN_CHECK_CUDA(cudaEventSynchronize(P.ev[i]));
+    if (P.tables.bytes) {
+        if (!P.host_tables) RN_CHECK_CUDA(cudaMallocHost(&P.host_tables, P.tables.bytes));
+        RN_CHECK_CUDA(cudaMemcpy(P.host_tables, P.tables.p, P.tables.bytes, cudaMemcpyDeviceToHost));
+    }
+    P.old_tables = (const char *)P.tables.p;
+    P.old_partials = (const char *)P.partials.p;
+    if (P.graph) RN_CHECK_CUDA(cudaGraphExecDestroy(P.graph));
+    if (P.graph_src) RN_CHECK_CUDA(cudaGraphDestroy(P.graph_src));
+    P.graph = nullptr;
+    P.graph_src = nullptr;
+    for (auto &nd : P.ev_node) nd = nullptr;
+    P.arena.reset();
+    P.tables.reset();
+    P.descs.reset();
+    P.partials.reset();
+    P.tcws.reset();
+    P.mirror_valid = false;
+    P.spilled = true;
+    return P.tables.bytes;
+}
+
+// Restore a spilled plan on stream s: the same buffer sizes again, the tables
+// copied back, the descriptors' table and partial-sum pointers moved to the
+// new addresses (everything else they hold is bound per call), the graph
+// captured again on its next replay.
+void restore_plan(Plan &P, cudaStream_t s) {
+    if (!P.spilled) return;
+    const size_t ab = P.arena.bytes, tb = P.tables.bytes, db = P.descs.bytes, pb = P.partials.bytes,
+                 wb = P.tcws.bytes;
+    P.arena = DevBuf(ab, s);
+    P.tables = DevBuf(tb, s);
+    P.descs = DevBuf(db, s);
+    P.partials = DevBuf(pb, s);
+    P.tcws = DevBuf(wb, s);
+    if (tb) RN_CHECK_CUDA(cudaMemcpyAsync(P.tables.p, P.host_tables, tb, cudaMemcpyHostToDevice, s));
+    if (wb) RN_CHECK_CUDA(cudaMemsetAsync(P.tcws.p, 0, wb, s));   // stream-K tile counters start at zero
+    auto move = [](auto &ptr, const char *from, size_t bytes, void *to) {
+        const char *q = (const char *)ptr;
+        if (q && from && q >= from && q < from + bytes)
+            ptr = (std::remove_reference_t<decltype(ptr)>)((char *)to + (q - from));
+    };
+    for (GettDesc &d : P.slot_desc) {
+        move(d.offAM, P.old_tables, tb, P.tables.p);
+        move(d.offCM, P.old_tables, tb, P.tables.p);
+        move(d.offBN, P.old_tables, tb, P.tables.p);
+        move(d.offCN, P.old_tables, tb, P.tables.p);
+        move(d.offAK, P.old_tables, tb, P.tables.p);
+        move(d.offBK, P.old_tables, tb, P.tables.p);
+        move(d.part, P.old_partials, pb, P.partials.p);
+    }
+    P.mirror_valid = false;
+    P.spilled = false;
+}
+
 void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStream_t s) {
     char *arena = (char *)P.arena.p;
     auto leaf_of = [&](int64_t g) -> rosnet_btensor {
@@ -1134,6 +1212,7 @@ static void contract_batch(int nnet, const rosnet_network *nets, const rosnet_pa
     } else {
         P = it->second.get();
         P->leaves = std::move(leaves);   // same sharing pattern; refresh the representatives
+        restore_plan(*P, s);
     }
     P->last_used = ++g_plan_clock;
     std::vector<rosnet_btensor> made;
@@ -1192,10 +1271,7 @@ rosnet_status rosnet_plan_stats(int32_t nnet, const rosnet_network *nets, const 
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
     if (it == g_plans.end()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no cached plan for these networks");
-    if (device_bytes) {
-        const Plan &P = *it->second;
-        *device_bytes = (int64_t)(P.arena.bytes + P.tables.bytes + P.descs.bytes + P.partials.bytes + P.tcws.bytes);
-    }
+    if (device_bytes) *device_bytes = (int64_t)plan_device_bytes(*it->second);
     if (steps_requested) *steps_requested = it->second->steps_requested;
     if (steps_planned) *steps_planned = (int64_t)it->second->steps.size();
     if (launches) *launches = (int64_t)it->second->launches.size();
@@ -1269,6 +1345,19 @@ rosnet_status rosnet_plan_release(int32_t nnet, const rosnet_network *nets, cons
                                       [vp](const std::pair<Plan *, int> &e) { return e.first == vp; }),
                        g_timing_log.end());
     g_plans.erase(it);
+    return ROSNET_OK;
+    RN_API_END
+}
+
+rosnet_status rosnet_plan_spill(int32_t nnet, const rosnet_network *nets, const rosnet_path *paths,
+                                const rosnet_opts *opts, void *stream, int64_t *host_bytes) {
+    RN_API_BEGIN
+    Key128 key = cached_key(nnet, nets, paths, opts, stream);
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it == g_plans.end()) RN_FAIL(ROSNET_ERR_INVALID_ARG, "no cached plan for these networks");
+    const size_t hb = spill_plan(*it->second, (cudaStream_t)stream);
+    if (host_bytes) *host_bytes = (int64_t)hb;
     return ROSNET_OK;
     RN_API_END
 }

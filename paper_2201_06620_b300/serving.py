@@ -18,8 +18,12 @@ before a plan exists, its predicted footprint: input tensors plus the peak
 of live intermediates along the path -- the analogue of the paper's
 per-task memory, Eq. 1 / Eq. 2) and the outputs of running queries.  When a
 query needs a new plan that does not fit, resident plans that no running
-query uses are freed, least recently used first; if it still does not fit
-it waits for running queries to retire (a query alone is always admitted).
+query uses are spilled to pinned host memory, least recently used first
+(rosnet_plan_spill: their device memory is released and their offset tables
+kept in page-locked host memory, so a later query restores the plan instead
+of planning it anew; spilled plans beyond a host budget are freed, oldest
+first); if it still does not fit it waits for running queries to retire (a
+query alone is always admitted).
 Admitted queries run concurrently on separate streams, so a query that
 arrives while others are on the GPU starts as soon as a slot and memory free
 up, and its kernels overlap theirs.  Latency runs from a query's arrival to
@@ -35,7 +39,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import (C64, OPT_GRAPH, PREC_DEFAULT, Network, btensor, contract, empty, path_search, plan_info,
-               plan_release, simplify)
+               plan_release, plan_spill, simplify)
 
 
 @dataclass
@@ -150,7 +154,8 @@ class _Slot:
 class AmplitudeServer:
     """Continuous-batching amplitude server over a pool of stream slots."""
 
-    def __init__(self, circuits, slots=4, memory_budget=160e9, precision=PREC_DEFAULT, use_graph=True):
+    def __init__(self, circuits, slots=4, memory_budget=160e9, precision=PREC_DEFAULT, use_graph=True,
+                 spill=True, host_budget=64e9):
         import torch
         self.torch = torch
         self.circuits = [_Circuit(i, c) for i, c in enumerate(circuits)]
@@ -165,6 +170,11 @@ class AmplitudeServer:
         self.resident_bytes = 0.0
         self.in_use = 0.0          # outputs of running queries
         self.evictions = 0
+        # plans spilled to pinned host memory: (slot, signature) -> host bytes, oldest first
+        self.spill, self.host_budget = spill, host_budget
+        self.spilled = collections.OrderedDict()
+        self.spilled_bytes = 0.0
+        self.restores = 0
         self.precision = precision
         self.flags = OPT_GRAPH if use_graph else 0
         self.waiting = collections.deque()
@@ -214,16 +224,38 @@ class AmplitudeServer:
     def _key(self, si, q):
         return (si, self.circuits[q.circuit].plan_for(q.k).sig)
 
-    def _evict(self, key):
+    def _users(self, key):
         si, sig = key
+        return [ck for ck in self.slots[si].nets if self.circuits[ck[0]].plan_for(ck[1]).sig == sig]
+
+    def _evict(self, key):
+        """Free the device memory of an idle resident plan: spill it to
+        pinned host memory (or release it when spilling is off)."""
+        si, _ = key
         sl = self.slots[si]
-        users = [ck for ck in sl.nets if self.circuits[ck[0]].plan_for(ck[1]).sig == sig]
+        ci, k = self._users(key)[0]
+        self.resident_bytes -= self.resident.pop(key)
+        self.evictions += 1
+        if not self.spill:
+            self._release(key)
+            return
+        hb = plan_spill([sl.nets[(ci, k)]], [self.circuits[ci].plan_for(k).path], precision=self.precision,
+                        flags=self.flags, stream=sl.stream)
+        self.spilled[key] = float(hb)
+        self.spilled_bytes += float(hb)
+        while self.spilled_bytes > self.host_budget and self.spilled:
+            old = next(iter(self.spilled))
+            self.spilled_bytes -= self.spilled.pop(old)
+            self._release(old)
+
+    def _release(self, key):
+        si, _ = key
+        sl = self.slots[si]
+        users = self._users(key)
         nets = [sl.nets.pop(ck) for ck in users]
         ci, k = users[0]
         plan_release([nets[0]], [self.circuits[ci].plan_for(k).path], precision=self.precision, flags=self.flags,
                      stream=sl.stream)
-        self.resident_bytes -= self.resident.pop(key)
-        self.evictions += 1
 
     def _launch(self, q, key):
         torch = self.torch
@@ -245,7 +277,10 @@ class AmplitudeServer:
         res = contract(net, path=path, precision=self.precision, flags=self.flags, stream=sl.stream)
         if key in self.resident:
             self.resident.move_to_end(key)
-        else:   # the plan now exists: account for what it really holds
+        else:   # the plan now exists (built, or restored from host memory): account for it
+            if key in self.spilled:
+                self.spilled_bytes -= self.spilled.pop(key)
+                self.restores += 1
             nbytes = float(plan_info([net], [path], precision=self.precision, flags=self.flags,
                                      stream=sl.stream)[4])
             self.resident[key] = nbytes

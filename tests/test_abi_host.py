@@ -299,6 +299,15 @@ def test_network_checks_and_greedy_path(L):
         bad_rank = _network(L, [a, b], [(0, 1), (1, 2)], [0, 2])
         bad_rank.ranks[0] = 3
         assert _contract(L, bad_rank, [(0, 1)]) == "INVALID_ARG"
+        # spilling a plan that was never built is refused before any device work
+        ring_path = (ctypes.c_int32 * 4)(pairs[0], pairs[1], pairs[2], pairs[3])
+        rp = R._Path(2, ctypes.cast(ring_path, ctypes.POINTER(ctypes.c_int32)))
+        L.rosnet_plan_spill.argtypes = [ctypes.c_int32, ctypes.POINTER(R._Network), ctypes.POINTER(R._Path),
+                                        ctypes.POINTER(R._Opts), vp, ctypes.POINTER(ctypes.c_int64)]
+        hb = ctypes.c_int64(-1)
+        assert STATUS[L.rosnet_plan_spill(1, ctypes.byref(ring.net), ctypes.byref(rp), None, None,
+                                          ctypes.byref(hb))] == "INVALID_ARG"
+        assert hb.value == -1
         # a label on three tensors is not a pairwise bond
         tri = _network(L, [a, T.wrap(L, a.handle), T.wrap(L, a.handle)],
                        [(0, 1), (0, 2), (0, 3)], [1, 2, 3])

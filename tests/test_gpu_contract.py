@@ -287,3 +287,30 @@ def test_plan_cache_limit_evicts_least_recently_used():
     finally:
         R.plan_cache_limit(0)
         R.release_plans()
+
+
+@pytest.mark.parametrize("prec", [R.PREC_DEFAULT, R.PREC_TF32X3])
+def test_plan_spill_and_restore(prec):
+    """A cached plan spilled to pinned host memory (its device buffers and
+    graph released, its offset tables kept on the host) and restored by the
+    next contraction gives bitwise the same amplitude; the 20-qubit plan has
+    a fused launch, split-K partial sums and packed (FP32) or tensor-core
+    workspaces, all re-pointed on restore."""
+    circ = W.rqc20_config()
+    net = W.circuit_network(circ, bitstring=circ.bitstring)
+    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+    path = R.path_greedy(ts, net.labels, net.out_labels)
+    gn = R.Network(ts, net.labels, net.out_labels)
+    kw = dict(precision=prec, flags=R.OPT_GRAPH, max_block_entries=256)
+    a1 = complex(R.contract(gn, path=path, **kw).download())
+    dev1 = R.plan_info([gn], [path], **kw)[4]
+    assert dev1 > 0
+    hb = R.plan_spill([gn], [path], **kw)
+    assert hb > 0 and R.plan_info([gn], [path], **kw)[4] == 0
+    assert R.plan_spill([gn], [path], **kw) == hb      # already spilled: nothing to do
+    for _ in range(2):
+        assert complex(R.contract(gn, path=path, **kw).download()) == a1
+    assert R.plan_info([gn], [path], **kw)[4] == dev1
+    ref = oracle.statevector(circ)[oracle.bitstring_index(circ.bitstring)]
+    assert amp_err(a1, ref, 20) <= 1e-5
+    R.plan_release([gn], [path], **kw)

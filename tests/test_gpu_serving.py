@@ -156,9 +156,11 @@ def test_server_tf32x3_vs_oracle():
         assert np.abs(m.result - ref).max() / scale <= 1e-5
 
 
-def test_budget_holds_resident_plans_across_many_circuits():
+@pytest.mark.parametrize("spill", [True, False])
+def test_budget_holds_resident_plans_across_many_circuits(spill):
     """Each slot keeps a plan per (circuit, k); with a budget that holds only
-    a few of them, idle plans are freed (least recently used first) so that
+    a few of them, idle plans are spilled to pinned host memory (or freed,
+    with spilling off), least recently used first, so that
     resident plans plus running outputs stay within the budget whenever more
     than one query runs; results still match the state vector, and plans
     freed and built again give the same amplitudes."""
@@ -173,7 +175,7 @@ def test_budget_holds_resident_plans_across_many_circuits():
         probe.drain()
         sizes.append(probe.resident[probe._key(0, q)])
     budget = 2.5 * max(sizes)
-    srv = AmplitudeServer(circs, slots=2, memory_budget=budget)
+    srv = AmplitudeServer(circs, slots=2, memory_budget=budget, spill=spill)
     queries = _queries(circs, rng, 40)
     for q in queries:
         srv.submit(q)
@@ -187,6 +189,8 @@ def test_budget_holds_resident_plans_across_many_circuits():
     srv.drain()
     assert len(srv.finished) == len(queries)
     assert srv.evictions > 0
+    if spill:   # idle plans went to pinned host memory and came back for later queries
+        assert srv.restores > 0 and srv.spilled_bytes >= 0
     for q in srv.finished:
         n = circs[q.circuit].n
         base = 0
