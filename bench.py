@@ -757,13 +757,20 @@ def run_reference(args):
 def _profiled_traffic(kind):
     """DRAM bytes per launch of the heaviest kernel from the committed ncu
     summary (profiles/traffic.json), or None when that summary is for another
-    kernel family or the kernel's source file changed since the capture."""
+    kernel family or the kernel's source changed since the capture (the
+    summary names the block of its source file that holds the kernel, else
+    the whole file is compared)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+            text = f.read()
+        if "source_block" in rec:
+            start, end = (x.encode() for x in rec["source_block"])
+            i = text.index(start)
+            text = text[i:text.index(end, i) + len(end)]
+        sha = hashlib.sha256(text).hexdigest()
     except (OSError, ValueError, KeyError):
         return None
     if rec.get("kind") != kind or not sha.startswith(rec.get("source_sha256_prefix", "-")):
