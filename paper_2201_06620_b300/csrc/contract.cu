@@ -38,7 +38,7 @@ void check_tensordot(rosnet_btensor A, rosnet_btensor B, int naxes, const int *a
                      const int *axes_b, int *axa, int *axb, int &rc, int64_t *shc, int64_t *blc);
 int check_precision(const rosnet_opts *opts, int dtype);
 int64_t reduce_ctas(const GettDesc &d);
-void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s);
+void autotune_problem(GettDesc &d, int dtype, bool packed_ok, int reduce_mode, cudaStream_t s);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
@@ -823,12 +823,13 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
             bind_operands(x, pa.first, pb.first, cs.p, pa.second, pb.second, S.lay.numel);
             const bool fp32_class = prec != ROSNET_PREC_TF32 && prec != ROSNET_PREC_TF32X3 &&
                                     prec != ROSNET_PREC_BF16X3;
-            autotune_problem(x, plan->dtype, fp32_class && (red == kReduceAuto || red == kReduceSequential), s);
+            autotune_problem(x, plan->dtype, fp32_class && (red == kReduceAuto || red == kReduceSequential), red, s);
             S.desc.kind = x.kind;
             S.desc.tiles_m = x.tiles_m;
             S.desc.tiles_n = x.tiles_n;
             S.desc.ksplit = x.ksplit;
             S.desc.ktiles_per_split = x.ktiles_per_split;
+            S.desc.flags = (S.desc.flags & ~kFlagStreamK) | (x.flags & kFlagStreamK);   // the tuned schedule
         }
         // tensor-core problems carry their own tensor maps: one launch each
         int key_kind = ((flags & ROSNET_OPT_NOGROUP) || is_packed_kind(S.desc.kind)) ? 1000 + st : S.desc.kind;

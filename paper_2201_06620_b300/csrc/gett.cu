@@ -1262,6 +1262,7 @@ int f32p_tile_n();
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s);
 bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode);
+bool f32p_stream_k_worth_timing(const GettDesc &d, int reduce_mode);
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {},
                        bool pdl = true);
@@ -1542,11 +1543,12 @@ int64_t reduce_ctas(const GettDesc &d);
 // each with several contracted-range splits, and -- for plain FP32 when no
 // reduction mode is forced -- the packed path.  Results are cached by
 // (dtype, M, N, K, layout flags).
-void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
+void autotune_problem(GettDesc &d, int dtype, bool packed_ok, int reduce_mode, cudaStream_t s) {
     if (!is_tiled_kind(d.kind) && d.kind != kKindPackF32 && !is_direct_kind(d.kind)) return;
     if (d.flags & kFlagAtomic) return;
     packed_ok = packed_ok && dtype == ROSNET_C64;
-    const TuneKey key{dtype, d.flags | (packed_ok ? 1 << 30 : 0), d.M, d.N, d.K};
+    const bool sk_ok = reduce_mode != kReduceSequential;   // one CTA per tile when asked for
+    const TuneKey key{dtype, d.flags | (packed_ok ? 1 << 30 : 0) | (sk_ok ? 0 : 1 << 29), d.M, d.N, d.K};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -1557,7 +1559,7 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
             d.tiles_n = c.tiles_n;
             d.ksplit = c.ksplit;
             d.ktiles_per_split = c.kps;
-            d.flags = (d.flags & ~kFlagStreamK) | (d.kind == kKindPackF32 ? (c.flags & kFlagStreamK) : 0);
+            d.flags = (d.flags & ~kFlagStreamK) | (d.kind == kKindPackF32 && sk_ok ? (c.flags & kFlagStreamK) : 0);
             return;
         }
     }
@@ -1606,7 +1608,10 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, cudaStream_t s) {
         y.flags &= ~kFlagStreamK;
         cands.push_back(y);   // one CTA per tile
         y.flags |= kFlagStreamK;
-        if (f32p_stream_k_pays(y, kReduceAuto)) cands.push_back(y);   // and stream-K
+        // and stream-K wherever the tiles are few enough for its balance to
+        // matter (timed: the heuristic's rule misses cases such as 2000 x 300
+        // x 333, 160 tiles of 11 k-tiles: 1.36x)
+        if (f32p_stream_k_worth_timing(y, reduce_mode)) cands.push_back(y);
     }
     for (GettDesc &c : cands)
         if (c.kind != kKindPackF32) c.flags &= ~kFlagStreamK;

@@ -571,21 +571,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 // order.
 namespace f32p {
 
-constexpr int NT = 256;   // 16 x 16 threads, TM x TN complex outputs each
-constexpr int BM = 64, BN = 64, BK = 32, STAGES = 3;
-constexpr int TM = BM / 16, TN = BN / 16;
-constexpr int KU = 2;                                      // unroll of the two-row inner loop
-constexpr int PA = BK * BM, PB = BK * BN;                  // floats of one plane of one stage
-constexpr uint32_t STAGE_BYTES = 2u * (PA + PB) * 4u;
-constexpr int KQ = 32;                                     // k tile of the pack kernel
-static_assert(KQ % BK == 0 && TM % 4 == 0 && TN % 4 == 0, "tile shape");
-// a finished C tile is staged as planes of [BN][BM + 1] (or [BM][BN + 1])
-// floats: one at a time through the stage just consumed (mid-stream), or
-// both through the idle ring (after a CTA's last unit)
-static_assert((size_t)(BM + 1) * (BN + 1) * 4 <= STAGE_BYTES, "a staged plane must fit one stage");
-static_assert(2 * (size_t)(BM + 1) * (BN + 1) * 4 <= (size_t)STAGES * STAGE_BYTES, "both planes must fit the ring");
-constexpr size_t RING_BYTES = (size_t)STAGES * STAGE_BYTES;
-constexpr size_t SMEM = RING_BYTES + 128;
+constexpr int BK = 32;   // k rows of a stage (the tensor maps' box depth)
+constexpr int KQ = 32;   // k tile of the pack kernel
+constexpr int KU = 2;    // unroll of the two-row inner loop
+static_assert(KQ % BK == 0, "k tiles");
+
+// Tile configurations of the GEMM.  A CTA computes a BM x 64 complex tile;
+// its threads form GY x GX groups (GX = 16 column groups of 4 adjacent
+// columns) of TM x 4 outputs, and KG such sets split the k rows of every
+// stage between them, their partial tiles summed in set order at the end.
+template <int BM_, int TM_, int KG_>
+struct Cfg {
+    static constexpr int BM = BM_, BN = 64, TM = TM_, TN = 4, KG = KG_;
+    static constexpr int GX = BN / TN, GY = BM / TM;
+    static constexpr int NT = GX * GY * KG;
+    static constexpr int STAGES = 3, KR = BK / KG;        // k rows of a stage per set
+    static constexpr int PA = BK * BM, PB = BK * BN;      // floats of one plane of one stage
+    static constexpr uint32_t STAGE_BYTES = 2u * (PA + PB) * 4u;
+    static constexpr size_t RING_BYTES = (size_t)STAGES * STAGE_BYTES;
+    static constexpr size_t SMEM = RING_BYTES + 128;
+    // a thread's TM rows are consecutive (read as float4), as are its columns
+    static_assert(GY * TM == BM && TM % 4 == 0 && KR * KG == BK && KR % 2 == 0 && (GX * GY) % 32 == 0 && KG <= 2,
+                  "tile shape");
+    static_assert((PA * 4) % 128 == 0 && (PB * 4) % 128 == 0, "stage planes 128-byte aligned (TMA destinations)");
+    // a finished C tile is staged as planes of [BN][BM + 1] (or [BM][BN + 1])
+    // floats: one at a time through the stage just consumed (mid-stream), or
+    // both through the idle ring (after a CTA's last unit)
+    static_assert((size_t)(BM + 1) * (BN + 1) * 4 <= STAGE_BYTES, "a staged plane must fit one stage");
+    static_assert(2 * (size_t)(BM + 1) * (BN + 1) * 4 <= RING_BYTES, "both planes must fit the ring");
+};
+// One CTA per tile: two sets of 8 x 16 threads of 8 x 4 outputs, each set
+// half of every stage's k rows.  A thread reads 96 bytes of fragments from
+// shared memory per 128 FMAs, where 4 x 4 outputs read 64 per 64 and keep
+// shared memory as busy as the FMA pipe: 61.0 against 57.5 TFLOP/s on
+// 1024 x 32768 x 1024, 49.3 against 51.2 us on 4096 x 256 x 256.
+using Tile8x4 = Cfg<64, 8, 2>;
+// Stream-K (a CTA's run of units crosses tiles, and a piece of a tile is
+// stored from the registers that hold it): one set of 16 x 16 threads of
+// 4 x 4 outputs.
+using Tile4x4 = Cfg<64, 4, 1>;
+constexpr int BM = 64, BN = 64;   // the tile of both
+static_assert(Tile8x4::BM == BM && Tile4x4::BM == BM && Tile8x4::BN == BN && Tile4x4::BN == BN, "tiles");
 
 struct Args {
     CUtensorMap mapA, mapB;   // operands as 3-D {rows, K, 2 planes} FP32 arrays
@@ -662,44 +688,38 @@ __global__ void __launch_bounds__(256) f32_pack_kernel(const __grid_constant__ G
 // warp along C's unit-stride dimension (m if m_fast, else n).  The staged
 // plane holds (BM + 1) x BN (m_fast) or BM x (BN + 1) floats, row length ld;
 // `both`: the imaginary plane follows at cs + plane, otherwise cs holds plane
-// `pl` alone.
+// `pl` alone.  om / on: the tile's C offsets of its rows and columns (-1 past
+// M or N), already in shared memory, so no store waits on a table load.
+template <class Tile>
 __device__ __forceinline__ void emit_tile(const float *cs, int plane, int ld, bool m_fast, bool both, int pl,
-                                          int m0, int n0, const GettDesc &sd, int warp, int lane) {
-    float *C = (float *)sd.c;
+                                          const int64_t *om, const int64_t *on, const GettDesc &sd, int warp,
+                                          int lane) {
+    constexpr int BM = Tile::BM, BN = Tile::BN, NT = Tile::NT;
     const int64_t cp = sd.c_plane;
-    const int64_t M = sd.M, N = sd.N;
-    float *out = C + (pl ? cp : 0);
+    float *out = (float *)sd.c + (pl ? cp : 0);
     if (m_fast) {
-        int64_t cm[BM / 32];
+        int64_t cm[(BM + 31) / 32];
 #pragma unroll
-        for (int u = 0; u < BM / 32; ++u) {
-            const int64_t m = m0 + lane + 32 * u;
-            cm[u] = m < M ? __ldg(sd.offCM + m) : -1;
-        }
+        for (int u = 0; u < (BM + 31) / 32; ++u) cm[u] = lane + 32 * u < BM ? om[lane + 32 * u] : -1;
         for (int nl = warp; nl < BN; nl += NT / 32) {
-            const int64_t n = n0 + nl;
-            if (n >= N) break;
-            const int64_t c0 = __ldg(sd.offCN + n);
+            const int64_t c0 = on[nl];
+            if (c0 < 0) break;
 #pragma unroll
-            for (int u = 0; u < BM / 32; ++u)
+            for (int u = 0; u < (BM + 31) / 32; ++u)
                 if (cm[u] >= 0) {
                     out[cm[u] + c0] = cs[nl * ld + lane + 32 * u];
                     if (both) out[cm[u] + c0 + cp] = cs[plane + nl * ld + lane + 32 * u];
                 }
         }
     } else {
-        int64_t cn[BN / 32];
+        int64_t cn[(BN + 31) / 32];
 #pragma unroll
-        for (int u = 0; u < BN / 32; ++u) {
-            const int64_t n = n0 + lane + 32 * u;
-            cn[u] = n < N ? __ldg(sd.offCN + n) : -1;
-        }
+        for (int u = 0; u < (BN + 31) / 32; ++u) cn[u] = lane + 32 * u < BN ? on[lane + 32 * u] : -1;
         for (int ml = warp; ml < BM; ml += NT / 32) {
-            const int64_t m = m0 + ml;
-            if (m >= M) break;
-            const int64_t c0 = __ldg(sd.offCM + m);
+            const int64_t c0 = om[ml];
+            if (c0 < 0) break;
 #pragma unroll
-            for (int u = 0; u < BN / 32; ++u)
+            for (int u = 0; u < (BN + 31) / 32; ++u)
                 if (cn[u] >= 0) {
                     out[c0 + cn[u]] = cs[ml * ld + lane + 32 * u];
                     if (both) out[c0 + cn[u] + cp] = cs[plane + ml * ld + lane + 32 * u];
@@ -722,14 +742,20 @@ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) { r
 // sums the pieces in k order (a fixed order: results do not depend on
 // scheduling), writes C and resets the counter.  No CTA ever waits for
 // another.
-template <bool SK>
-__global__ void __launch_bounds__(NT, 2) f32_gemm_kernel(const __grid_constant__ Args p) {
+template <class C, bool SK>
+__global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constant__ Args p) {
+    constexpr int NT = C::NT, BM = C::BM, BN = C::BN, TM = C::TM, TN = C::TN, STAGES = C::STAGES;
+    constexpr int PA = C::PA, PB = C::PB, GX = C::GX, GY = C::GY, KR = C::KR;
+    constexpr uint32_t STAGE_BYTES = C::STAGE_BYTES;
+    static_assert(!SK || C::KG == 1, "stream-K takes one set of threads");
     extern __shared__ unsigned char dsm_raw[];
     float *stg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~(uintptr_t)127);
     __shared__ GettDesc sd;
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ volatile int abort_flag;
     __shared__ int last_piece;
+    __shared__ int64_t c_om[BM], c_on[BN];   // C offsets of the current tile's rows and columns
+    static_assert(BM + BN <= NT, "one offset per thread");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     grid_dep_launch();
     if (warp == 0) load_desc(p.g, sd);
@@ -762,6 +788,12 @@ __global__ void __launch_bounds__(NT, 2) f32_gemm_kernel(const __grid_constant__
     }
     const int nitems = (int)(u1 - u0);
     grid_dep_wait();   // operands may be the previous kernel's output
+    // the C offsets of a tile's rows and columns into shared memory, one per
+    // thread (-1 past M or N)
+    auto load_offsets = [&](int m0, int n0) {
+        if (tid < BM) c_om[tid] = m0 + tid < sd.M ? __ldg(sd.offCM + m0 + tid) : -1;
+        else if (tid < BM + BN) c_on[tid - BM] = n0 + tid - BM < sd.N ? __ldg(sd.offCN + n0 + tid - BM) : -1;
+    };
 
     // units are issued (one thread) and consumed strictly in order: each side
     // walks (tile, k-tile) with its own cursor instead of dividing per unit
@@ -786,10 +818,13 @@ __global__ void __launch_bounds__(NT, 2) f32_gemm_kernel(const __grid_constant__
     int issued = 0;
     if (tid == 0)
         for (; issued < min(STAGES, nitems); ++issued) issue(issued);
+    // one tile per CTA: its offsets load while the first stages land (the
+    // barriers before the epilogue's stores publish them)
+    if (!SK) load_offsets(pm0, pn0);
     int ct = (int)(u0 / nkt);   // consumer cursor
     int ckt = (int)(u0 % nkt);
 
-    const int ty = tid >> 4, tx = tid & 15;
+    const int tx = tid % GX, ty = (tid / GX) % GY, kg = tid / (GX * GY);   // column group, row group, k set
     float cr[TM][TN], ci[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -846,14 +881,18 @@ __global__ void __launch_bounds__(NT, 2) f32_gemm_kernel(const __grid_constant__
     // written with the lanes of a warp along C's unit-stride dimension (m
     // unless kFlagCNFast).  `cs`: a consumed stage, which holds one plane of
     // (BM + 1) x BN floats (two passes), or the whole idle ring after the
-    // CTA's last unit (both planes in one pass).
+    // CTA's last unit (both planes in one pass).  With two k sets the second
+    // stages its partial tile and the first adds its own to it: C = first +
+    // second, the same order in every CTA.
     auto store_c = [&](float *cs, bool both, int m0, int n0) {
+        if (SK) {   // this tile's offsets (the previous tile's stores are done)
+            __syncthreads();
+            load_offsets(m0, n0);
+        }
         const bool m_fast = !(sd.flags & kFlagCNFast);
         const int ld = m_fast ? BM + 1 : BN + 1;   // row length of a staged plane
         const int plane = (m_fast ? BN : BM) * ld;
-#pragma unroll 1
-        for (int pl = 0; pl < (both ? 1 : 2); ++pl) {
-            __syncthreads();   // the staging area is free
+        auto put = [&](int pl, bool add) {
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -861,14 +900,24 @@ __global__ void __launch_bounds__(NT, 2) f32_gemm_kernel(const __grid_constant__
                     const int ml = ty * TM + i, nl = tx * TN + j;
                     const int e = m_fast ? nl * ld + ml : ml * ld + nl;
                     if (both) {
-                        cs[e] = cr[i][j];
-                        cs[plane + e] = ci[i][j];
+                        cs[e] = add ? cr[i][j] + cs[e] : cr[i][j];
+                        cs[plane + e] = add ? ci[i][j] + cs[plane + e] : ci[i][j];
                     } else {
-                        cs[e] = pl ? ci[i][j] : cr[i][j];
+                        const float v = pl ? ci[i][j] : cr[i][j];
+                        cs[e] = add ? v + cs[e] : v;
                     }
                 }
+        };
+#pragma unroll 1
+        for (int pl = 0; pl < (both ? 1 : 2); ++pl) {
+            __syncthreads();   // the staging area is free
+            if (kg == C::KG - 1) put(pl, false);
+            if (C::KG == 2) {
+                __syncthreads();
+                if (kg == 0) put(pl, true);
+            }
             __syncthreads();
-            emit_tile(cs, plane, ld, m_fast, both, pl, m0, n0, sd, warp, lane);
+            emit_tile<C>(cs, plane, ld, m_fast, both, pl, c_om, c_on, sd, warp, lane);
         }
         __syncthreads();   // the staging area may be refilled
     };
@@ -880,20 +929,30 @@ __global__ void __launch_bounds__(NT, 2) f32_gemm_kernel(const __grid_constant__
         const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_fast(&full_bar[s], (i / STAGES) & 1, &abort_flag));
         if (!ok) break;
         if (tid == 0) done0 = i + 1;
-        const float *a0 = stg + (size_t)s * 2 * (PA + PB) + ty * TM;
-        const float *b0 = stg + (size_t)s * 2 * (PA + PB) + 2 * PA + tx * TN;
-        float xr0[TM], xi0[TM], yr0[TN], yi0[TN], xr1[TM], xi1[TM], yr1[TN], yi1[TN];
-        frag(a0, b0, 0, xr0, xi0, yr0, yi0);
+        // this thread's rows and columns in the stage, from its set's first k row
+        const float *a0 = stg + (size_t)s * 2 * (PA + PB) + kg * KR * BM + ty * TM;
+        const float *b0 = stg + (size_t)s * 2 * (PA + PB) + 2 * PA + kg * KR * BN + tx * TN;
+        float xr0[TM], xi0[TM], yr0[TN], yi0[TN];
+        if constexpr (C::TM * C::TN <= 16) {   // the next row's fragments load while this row's FMAs run
+            float xr1[TM], xi1[TM], yr1[TN], yi1[TN];
+            frag(a0, b0, 0, xr0, xi0, yr0, yi0);
 #pragma unroll(KU)
-        for (int kk = 0; kk < BK - 2; kk += 2) {
-            frag(a0, b0, kk + 1, xr1, xi1, yr1, yi1);
+            for (int kk = 0; kk < KR - 2; kk += 2) {
+                frag(a0, b0, kk + 1, xr1, xi1, yr1, yi1);
+                macs(xr0, xi0, yr0, yi0);
+                frag(a0, b0, kk + 2, xr0, xi0, yr0, yi0);
+                macs(xr1, xi1, yr1, yi1);
+            }
+            frag(a0, b0, KR - 1, xr1, xi1, yr1, yi1);   // last two rows: no prefetch
             macs(xr0, xi0, yr0, yi0);
-            frag(a0, b0, kk + 2, xr0, xi0, yr0, yi0);
             macs(xr1, xi1, yr1, yi1);
+        } else {   // more outputs a thread: no registers for a second set of fragments
+#pragma unroll 4
+            for (int kk = 0; kk < KR; ++kk) {
+                frag(a0, b0, kk, xr0, xi0, yr0, yi0);
+                macs(xr0, xi0, yr0, yi0);
+            }
         }
-        frag(a0, b0, BK - 1, xr1, xi1, yr1, yi1);   // last two rows: no prefetch
-        macs(xr0, xi0, yr0, yi0);
-        macs(xr1, xi1, yr1, yi1);
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&empty_bar[s]);
         // warp 0 refills the stage consumed one unit ago (all warps have
@@ -1151,10 +1210,14 @@ bool tma_direct_ok(bool dense, const void *p, int64_t rows, int64_t K, int64_t p
 
 void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, cudaStream_t s, bool pack_a,
                 bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
+    using f32p::Tile4x4;
+    using f32p::Tile8x4;
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto k : {f32p::f32_gemm_kernel<false>, f32p::f32_gemm_kernel<true>})
-            RN_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32p::SMEM));
+        RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile8x4, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile8x4::SMEM));
+        RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile4x4, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile4x4::SMEM));
         attr_set = true;
     }
     const F32Geom g = f32_geom(d);
@@ -1195,8 +1258,13 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     if (before_gemm) before_gemm();
     // after a pack the GEMM's prologue may overlap it (it reads only its
     // descriptor before waiting); with no pack it is the first launch
-    launch_pdl((d.flags & kFlagStreamK) ? f32p::f32_gemm_kernel<true> : f32p::f32_gemm_kernel<false>,
-               dim3((unsigned)ctas), f32p::NT, f32p::SMEM, s, pdl || pack_a || pack_b, args);
+    const bool pdl_gemm = pdl || pack_a || pack_b;
+    if (d.flags & kFlagStreamK)
+        launch_pdl(f32p::f32_gemm_kernel<Tile4x4, true>, dim3((unsigned)ctas), Tile4x4::NT, Tile4x4::SMEM, s,
+                   pdl_gemm, args);
+    else
+        launch_pdl(f32p::f32_gemm_kernel<Tile8x4, false>, dim3((unsigned)ctas), Tile8x4::NT, Tile8x4::SMEM, s,
+                   pdl_gemm, args);
     g_launches++;
     RN_CHECK_CUDA(cudaGetLastError());
 }
@@ -1221,6 +1289,15 @@ bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode) {
     if (nkt < 32 || tiles >= 3 * slots) return false;
     const int64_t waves = (tiles + slots - 1) / slots;
     return (double)tiles < 0.92 * (double)(waves * slots);   // the slots are used poorly
+}
+
+// Whether the autotuner times the stream-K schedule of a problem: any
+// problem with fewer than three rounds of tiles over the CTA slots and at
+// least 4 k-tiles a tile (the cases where balance can pay for the pieces).
+bool f32p_stream_k_worth_timing(const GettDesc &d, int reduce_mode) {
+    if (reduce_mode == kReduceSequential) return false;
+    const int64_t tiles = d.tiles_m * d.tiles_n, slots = 2 * (int64_t)num_sms();
+    return tiles < 3 * slots && (d.K + f32p::BK - 1) / f32p::BK >= 4;
 }
 
 // Workspace bytes of a packed-kind problem: its packed operands (and the

@@ -71,3 +71,33 @@ def test_every_family_matches_oracle(dtype, mnk):
     assert tried >= (2 if dtype == R.C128 else 6)
     R.tune_import(" ".join(key) + "\n")   # the autotuner's own choice back for later tests
     R.release_plans()
+
+
+def test_tuned_stream_k_schedule_reaches_the_plan():
+    """A tuned choice of the FP32 GEMM's schedule is what the plan runs: with
+    the stream-K schedule imported for 2000 x 300 x 333 (160 output tiles of
+    11 k-tiles) the plan holds the partial-tile workspace, with one CTA per
+    tile it does not; both meet the bar against the oracle and each is
+    bitwise reproducible."""
+    M, N, K = 2000, 300, 333
+    a = W.complex_normal((M, K), 81).astype(np.complex64)
+    b = W.complex_normal((K, N), 82).astype(np.complex64)
+    A, B = R.btensor(a), R.btensor(b)
+    ref = oracle.tensordot(a, b, [1], [0])
+    net = ([A, B], [(0, 1), (1, 2)], [0, 2])
+    R.release_plans()
+    _run(A, B, R.OPT_AUTOTUNE).download()
+    key = _key(R.C64, M, N, K)
+    assert key is not None
+    dev, outs = {}, {}
+    for sched in (0, 1):
+        R.tune_import(" ".join(key[:5] + ["10", "1", str(sched)]) + "\n")
+        R.release_plans()
+        outs[sched] = _run(A, B, R.OPT_AUTOTUNE).download()
+        assert np.array_equal(outs[sched], _run(A, B, R.OPT_AUTOTUNE).download())
+        dev[sched] = R.plan_info([net], [[(0, 1)]], flags=R.OPT_AUTOTUNE)[4]
+        assert oracle.rel_frobenius(outs[sched], ref) <= 1e-5, sched
+    # stream-K's partial tiles: at least one 64 x 64 complex64 tile per CTA piece
+    assert dev[1] >= dev[0] + 160 * 2 * 64 * 64 * 4, dev
+    R.tune_import(" ".join(key) + "\n")
+    R.release_plans()
