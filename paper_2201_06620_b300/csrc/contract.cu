@@ -834,7 +834,9 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         // tensor-core problems carry their own tensor maps: one launch each
         int key_kind = ((flags & ROSNET_OPT_NOGROUP) || is_packed_kind(S.desc.kind)) ? 1000 + st : S.desc.kind;
         groups[{S.wave, key_kind}].push_back(st);
-        if (S.desc.ksplit > 1 && !(S.desc.flags & kFlagAtomic)) split_of_wave[S.wave].push_back(st);
+        // (a packed-operand problem sums its own split in its launch sequence)
+        if (S.desc.ksplit > 1 && !(S.desc.flags & kFlagAtomic) && !is_packed_kind(S.desc.kind))
+            split_of_wave[S.wave].push_back(st);
         if (S.desc.flags & kFlagAtomic) atomic_of_wave[S.wave].push_back(st);
     }
     // split-K partials: one workspace reused by every wave

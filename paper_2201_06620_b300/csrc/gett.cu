@@ -1257,8 +1257,9 @@ constexpr int kTiledStages = 3;
 bool tc_mode_of(int precision, int *mode);
 int tc_tile_m();
 int tc_tile_n();
-int f32p_tile_m();
-int f32p_tile_n();
+void f32p_tile(int64_t N, int *bm, int *bn);
+int64_t f32p_skinny_split(const GettDesc &d);
+void f32p_set_geometry(GettDesc &d);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
 void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s);
 bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode);
@@ -1304,15 +1305,26 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
     if (dtype == ROSNET_C64 && reduce_mode != kReduceTree && reduce_mode != kReduceCommutative &&
         std::min(d.M, d.N) >= 64 && (d.K >= 128 || (d.K >= 32 && in_place)) &&
         8.0 * (double)MN * (double)d.K >= 268435456.0) {
-        const int64_t t = ((d.M + f32p_tile_m() - 1) / f32p_tile_m()) * ((d.N + f32p_tile_n() - 1) / f32p_tile_n());
+        const int64_t t = ((d.M + 63) / 64) * ((d.N + 63) / 64);
         if (t >= 120) {
             if (d.N > d.M) swap_operands(d);
             d.kind = kKindPackF32;
-            d.tiles_m = (d.M + f32p_tile_m() - 1) / f32p_tile_m();
-            d.tiles_n = (d.N + f32p_tile_n() - 1) / f32p_tile_n();
+            d.tiles_m = (d.M + 63) / 64;
+            d.tiles_n = (d.N + 63) / 64;
             if (f32p_stream_k_pays(d, reduce_mode)) d.flags |= kFlagStreamK;
             return;
         }
+    }
+    // few columns and a long contraction (e.g. 256 x 16 x 4096): the same
+    // GEMM with 128 x 16 tiles and the contraction split over CTAs, its
+    // partial results summed in split order
+    if (dtype == ROSNET_C64 && (reduce_mode == kReduceAuto || reduce_mode == kReduceTree) &&
+        std::min(d.M, d.N) <= 16 && std::max(d.M, d.N) >= 128 && d.K >= 512 &&
+        8.0 * (double)MN * (double)d.K >= 67108864.0) {
+        if (d.N > d.M) swap_operands(d);
+        d.kind = kKindPackF32;
+        f32p_set_geometry(d);
+        return;
     }
     // short contractions: whole tiles in one pass
     if (d.K >= 8 && d.K <= kDirectK && std::min(d.M, d.N) >= 16 && MN >= 4096) {
@@ -1535,6 +1547,18 @@ bool direct_split(GettDesc &d) {
 }
 }  // namespace
 
+// Tile grid and contraction split of the TMA-fed FP32 GEMM for d's shape
+// (N <= M): 64 x 64 tiles, one CTA per tile; or for few columns 128 x 16
+// tiles with the contraction split (ktiles_per_split in 32-deep k-tiles).
+void f32p_set_geometry(GettDesc &d) {
+    int bm, bn;
+    f32p_tile(d.N, &bm, &bn);
+    d.tiles_m = (d.M + bm - 1) / bm;
+    d.tiles_n = (d.N + bn - 1) / bn;
+    const int64_t ks = f32p_skinny_split(d);
+    apply_split(d, 32, ks > 0 ? ks : 1);
+}
+
 int64_t reduce_ctas(const GettDesc &d);
 
 // Time the candidate kernels of a CUDA-core problem (operands a, b; output
@@ -1602,11 +1626,9 @@ void autotune_problem(GettDesc &d, int dtype, bool packed_ok, int reduce_mode, c
     if (packed_ok) {
         GettDesc y = d;
         y.kind = kKindPackF32;
-        y.tiles_m = (d.M + f32p_tile_m() - 1) / f32p_tile_m();
-        y.tiles_n = (d.N + f32p_tile_n() - 1) / f32p_tile_n();
-        apply_split(y, BK, 1);
         y.flags &= ~kFlagStreamK;
-        cands.push_back(y);   // one CTA per tile
+        f32p_set_geometry(y);
+        cands.push_back(y);   // one CTA per tile (a split contraction for few columns)
         y.flags |= kFlagStreamK;
         // and stream-K wherever the tiles are few enough for its balance to
         // matter (timed: the heuristic's rule misses cases such as 2000 x 300
@@ -1699,9 +1721,11 @@ static bool tune_geometry(int dtype, int kind, int64_t M, int64_t N, int64_t K, 
         if (!direct_split(y) || y.ksplit != ksplit) return false;
         *out = TuneChoice{kind, y.tiles_m, y.tiles_n, y.ksplit, y.ktiles_per_split, 0};
         return true;
-    } else if (kind == kKindPackF32 && dtype == ROSNET_C64 && ksplit == 1) {
-        y.tiles_m = (M + f32p_tile_m() - 1) / f32p_tile_m();
-        y.tiles_n = (N + f32p_tile_n() - 1) / f32p_tile_n();
+    } else if (kind == kKindPackF32 && dtype == ROSNET_C64) {
+        f32p_set_geometry(y);
+        if (y.ksplit != ksplit) return false;   // its split is fixed by the shape
+        *out = TuneChoice{kind, y.tiles_m, y.tiles_n, y.ksplit, y.ktiles_per_split, 0};
+        return true;
     } else {
         return false;
     }

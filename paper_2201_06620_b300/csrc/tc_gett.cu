@@ -576,48 +576,60 @@ constexpr int KQ = 32;   // k tile of the pack kernel
 constexpr int KU = 2;    // unroll of the two-row inner loop
 static_assert(KQ % BK == 0, "k tiles");
 
-// Tile configurations of the GEMM.  A CTA computes a BM x 64 complex tile;
-// its threads form GY x GX groups (GX = 16 column groups of 4 adjacent
-// columns) of TM x 4 outputs, and KG such sets split the k rows of every
-// stage between them, their partial tiles summed in set order at the end.
-template <int BM_, int TM_, int KG_>
+// Tile configurations of the GEMM.  A CTA computes a BM x BN complex tile;
+// its threads form GY x GX groups of TM x TN outputs (TN adjacent columns),
+// and KG such sets split the k rows of every stage between them, their
+// partial tiles summed in set order at the end.
+template <int BM_, int BN_, int TM_, int TN_, int KG_, int STAGES_>
 struct Cfg {
-    static constexpr int BM = BM_, BN = 64, TM = TM_, TN = 4, KG = KG_;
+    static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KG = KG_;
     static constexpr int GX = BN / TN, GY = BM / TM;
     static constexpr int NT = GX * GY * KG;
-    static constexpr int STAGES = 3, KR = BK / KG;        // k rows of a stage per set
+    static constexpr int STAGES = STAGES_, KR = BK / KG;  // k rows of a stage per set
     static constexpr int PA = BK * BM, PB = BK * BN;      // floats of one plane of one stage
     static constexpr uint32_t STAGE_BYTES = 2u * (PA + PB) * 4u;
     static constexpr size_t RING_BYTES = (size_t)STAGES * STAGE_BYTES;
     static constexpr size_t SMEM = RING_BYTES + 128;
     // a thread's TM rows are consecutive (read as float4), as are its columns
-    static_assert(GY * TM == BM && TM % 4 == 0 && KR * KG == BK && KR % 2 == 0 && (GX * GY) % 32 == 0 && KG <= 2,
+    static_assert(GY * TM == BM && GX * TN == BN && TM % 4 == 0 && TN % 4 == 0 && KR * KG == BK && KR % 2 == 0 &&
+                      (GX * GY) % 32 == 0 && BM + BN <= NT,
                   "tile shape");
     static_assert((PA * 4) % 128 == 0 && (PB * 4) % 128 == 0, "stage planes 128-byte aligned (TMA destinations)");
-    // a finished C tile is staged as planes of [BN][BM + 1] (or [BM][BN + 1])
-    // floats: one at a time through the stage just consumed (mid-stream), or
-    // both through the idle ring (after a CTA's last unit)
-    static_assert((size_t)(BM + 1) * (BN + 1) * 4 <= STAGE_BYTES, "a staged plane must fit one stage");
-    static_assert(2 * (size_t)(BM + 1) * (BN + 1) * 4 <= RING_BYTES, "both planes must fit the ring");
+    // a finished C tile is staged as planes of [BN][BM + 4] (or [BM][BN + 4])
+    // floats: one at a time through the stage just consumed (mid-stream, one
+    // set of threads), or both through the idle ring after a CTA's last unit,
+    // behind the other sets' partial tiles ([KG - 1][2 TM TN][GX GY] floats)
+    static constexpr size_t PLANE_MAX = (size_t)(BM + 4) * (BN + 4);
+    static_assert(KG > 1 || PLANE_MAX * 4 <= STAGE_BYTES, "a staged plane must fit one stage");
+    static_assert(((size_t)(KG - 1) * 2 * TM * TN * GX * GY + 2 * PLANE_MAX) * 4 <= RING_BYTES,
+                  "the sets' tiles and both staged planes must fit the ring");
 };
 // One CTA per tile: two sets of 8 x 16 threads of 8 x 4 outputs, each set
 // half of every stage's k rows.  A thread reads 96 bytes of fragments from
 // shared memory per 128 FMAs, where 4 x 4 outputs read 64 per 64 and keep
 // shared memory as busy as the FMA pipe: 61.0 against 57.5 TFLOP/s on
 // 1024 x 32768 x 1024, 49.3 against 51.2 us on 4096 x 256 x 256.
-using Tile8x4 = Cfg<64, 8, 2>;
+using Tile8x4 = Cfg<64, 64, 8, 4, 2, 3>;
 // Stream-K (a CTA's run of units crosses tiles, and a piece of a tile is
 // stored from the registers that hold it): one set of 16 x 16 threads of
 // 4 x 4 outputs.
-using Tile4x4 = Cfg<64, 4, 1>;
+using Tile4x4 = Cfg<64, 64, 4, 4, 1, 3>;
 constexpr int BM = 64, BN = 64;   // the tile of both
 static_assert(Tile8x4::BM == BM && Tile4x4::BM == BM && Tile8x4::BN == BN && Tile4x4::BN == BN, "tiles");
+// Few columns (N <= 16) and a long contraction, e.g. 256 x 16 x 4096: 128 x
+// 16 tiles, four sets of 32 x 2 threads of 4 x 8 outputs, the contraction
+// split over CTAs (each a run of k-tiles, its partial tile stored and the
+// partials summed in split order by f32_split_reduce_kernel): the work is
+// too small to fill the SMs with tiles, and each CTA streams its share of
+// the large operand once.
+using TileSkinny = Cfg<128, 16, 4, 8, 4, 2>;
 
 struct Args {
     CUtensorMap mapA, mapB;   // operands as 3-D {rows, K, 2 planes} FP32 arrays
     GroupArgs g;              // the problem (C pointer, C offset tables, M, N, K, tiles)
     float *sk_part;           // stream-K: partial tiles [tile][piece][2][BM * BN] (fragment order)
     int32_t *sk_count;        // stream-K: pieces stored per tile (0 between launches)
+    float *split_part;        // split contraction: partial results [split][2 planes][M x N], row-major (m, n)
     int32_t nkt;              // k-stages (Kpad / BK)
     int32_t sk_maxpieces;     // stream-K: most pieces of any tile
 };
@@ -684,19 +696,20 @@ __global__ void __launch_bounds__(256) f32_pack_kernel(const __grid_constant__ G
     }
 }
 
-// Write a finished C tile staged in shared memory to C with the lanes of a
-// warp along C's unit-stride dimension (m if m_fast, else n).  The staged
-// plane holds (BM + 1) x BN (m_fast) or BM x (BN + 1) floats, row length ld;
-// `both`: the imaginary plane follows at cs + plane, otherwise cs holds plane
-// `pl` alone.  om / on: the tile's C offsets of its rows and columns (-1 past
-// M or N), already in shared memory, so no store waits on a table load.
+// Write a finished tile staged in shared memory to the output (C, or a
+// split's partial result) with the lanes of a warp along its unit-stride
+// dimension (m if m_fast, else n).  The staged plane holds (BM + 1) x BN
+// (m_fast) or BM x (BN + 1) floats, row length ld; `both`: the imaginary
+// plane follows at cs + plane, otherwise cs holds plane `pl` alone.  om / on:
+// the output offsets of the tile's rows and columns (-1 past M or N), already
+// in shared memory, so no store waits on a table load; cp: the output's
+// plane stride.
 template <class Tile>
 __device__ __forceinline__ void emit_tile(const float *cs, int plane, int ld, bool m_fast, bool both, int pl,
-                                          const int64_t *om, const int64_t *on, const GettDesc &sd, int warp,
-                                          int lane) {
+                                          const int64_t *om, const int64_t *on, float *base, int64_t cp,
+                                          int warp, int lane) {
     constexpr int BM = Tile::BM, BN = Tile::BN, NT = Tile::NT;
-    const int64_t cp = sd.c_plane;
-    float *out = (float *)sd.c + (pl ? cp : 0);
+    float *out = base + (pl ? cp : 0);
     if (m_fast) {
         int64_t cm[(BM + 31) / 32];
 #pragma unroll
@@ -754,8 +767,7 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
     __shared__ volatile int abort_flag;
     __shared__ int last_piece;
-    __shared__ int64_t c_om[BM], c_on[BN];   // C offsets of the current tile's rows and columns
-    static_assert(BM + BN <= NT, "one offset per thread");
+    __shared__ int64_t c_om[BM], c_on[BN];   // output offsets of the current tile's rows and columns
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     grid_dep_launch();
     if (warp == 0) load_desc(p.g, sd);
@@ -778,21 +790,35 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         n0 = (int)(tn * BN);
     };
     const int64_t U = sd.tiles_m * sd.tiles_n * (int64_t)nkt, G = gridDim.x;
+    // one tile per CTA, or with a split contraction (ksplit > 1) CTA
+    // (tile, split) takes k-tiles [split kps, (split + 1) kps) of its tile and
+    // stores a partial result
+    const int ksplit = SK ? 1 : max(1, sd.ksplit);
+    int split = 0;
     int64_t u0, u1;
     if (SK) {
         u0 = (int64_t)blockIdx.x * U / G;
         u1 = ((int64_t)blockIdx.x + 1) * U / G;
     } else {
-        u0 = ((int64_t)blockIdx.x - sd.tile_begin) * nkt;
-        u1 = u0 + nkt;
+        const int64_t cta = (int64_t)blockIdx.x - sd.tile_begin;
+        split = (int)(cta % ksplit);
+        const int kt0 = ksplit > 1 ? split * sd.ktiles_per_split : 0;
+        const int kt1 = ksplit > 1 ? min(nkt, kt0 + sd.ktiles_per_split) : nkt;
+        u0 = (cta / ksplit) * nkt + kt0;
+        u1 = (cta / ksplit) * nkt + kt1;
     }
     const int nitems = (int)(u1 - u0);
     grid_dep_wait();   // operands may be the previous kernel's output
-    // the C offsets of a tile's rows and columns into shared memory, one per
-    // thread (-1 past M or N)
+    // the output offsets of a tile's rows and columns into shared memory, one
+    // per thread (-1 past M or N): C's, or the row-major (m, n) of a partial
     auto load_offsets = [&](int m0, int n0) {
-        if (tid < BM) c_om[tid] = m0 + tid < sd.M ? __ldg(sd.offCM + m0 + tid) : -1;
-        else if (tid < BM + BN) c_on[tid - BM] = n0 + tid - BM < sd.N ? __ldg(sd.offCN + n0 + tid - BM) : -1;
+        if (tid < BM) {
+            const int64_t m = m0 + tid;
+            c_om[tid] = m >= sd.M ? -1 : ksplit > 1 ? m * sd.N : __ldg(sd.offCM + m);
+        } else if (tid < BM + BN) {
+            const int64_t n = n0 + tid - BM;
+            c_on[tid - BM] = n >= sd.N ? -1 : ksplit > 1 ? n : __ldg(sd.offCN + n);
+        }
     };
 
     // units are issued (one thread) and consumed strictly in order: each side
@@ -802,7 +828,7 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
     tile_origin(pt, pm0, pn0);
     auto issue = [&](int i) {   // one thread: the next unit (u0 + i) into its stage
         const int s = i % STAGES;
-        const int kt = SK ? pkt : i;   // one tile per CTA: unit i is k-tile i
+        const int kt = SK ? pkt : pkt + i;   // one tile per CTA: unit i is k-tile pkt + i
         tc::mbar_expect_tx(&full_bar[s], STAGE_BYTES);
         const uint32_t sa = tc::su32(stg + (size_t)s * 2 * (PA + PB));
         const uint32_t sb = sa + 2u * PA * 4u;
@@ -877,47 +903,116 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         }
     };
 
-    // the finished tile at (m0, n0) to C, staged through shared memory and
-    // written with the lanes of a warp along C's unit-stride dimension (m
-    // unless kFlagCNFast).  `cs`: a consumed stage, which holds one plane of
-    // (BM + 1) x BN floats (two passes), or the whole idle ring after the
-    // CTA's last unit (both planes in one pass).  With two k sets the second
-    // stages its partial tile and the first adds its own to it: C = first +
-    // second, the same order in every CTA.
+    // the finished tile at (m0, n0).  `cs`: a consumed stage (mid-stream,
+    // one set of threads), which stages one plane at a time, or the whole
+    // idle ring after the CTA's last unit.  With several k sets, sets 1, 2,
+    // ... store their partial tiles in fragment order (consecutive threads,
+    // consecutive words: no bank conflicts) and set 0 adds them in set order:
+    // C = ((s0 + s1) + s2) + ..., the same in every CTA.  A split's partial
+    // result goes straight to global memory (row-major (m, n), n fastest);
+    // C is staged through shared memory as [BN][BM + 4] (or [BM][BN + 4])
+    // planes written as float4 and stored with the lanes of a warp along C's
+    // unit-stride dimension (m unless kFlagCNFast).
+    constexpr int GXY = GX * GY, FV = 2 * TM * TN;   // threads of a set, values a thread holds
     auto store_c = [&](float *cs, bool both, int m0, int n0) {
         if (SK) {   // this tile's offsets (the previous tile's stores are done)
             __syncthreads();
             load_offsets(m0, n0);
         }
-        const bool m_fast = !(sd.flags & kFlagCNFast);
-        const int ld = m_fast ? BM + 1 : BN + 1;   // row length of a staged plane
-        const int plane = (m_fast ? BN : BM) * ld;
-        auto put = [&](int pl, bool add) {
+        float *stage = cs;
+        if constexpr (C::KG > 1) {   // only after the CTA's last unit: the ring is idle
+            float *fr = cs;           // [KG - 1][FV][GXY]
+            stage = cs + (C::KG - 1) * FV * GXY;
+            const int tin = tid % GXY;
+            __syncthreads();
+            if (kg > 0) {
+                float *f = fr + (size_t)(kg - 1) * FV * GXY + tin;
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    const int ml = ty * TM + i, nl = tx * TN + j;
-                    const int e = m_fast ? nl * ld + ml : ml * ld + nl;
-                    if (both) {
-                        cs[e] = add ? cr[i][j] + cs[e] : cr[i][j];
-                        cs[plane + e] = add ? ci[i][j] + cs[plane + e] : ci[i][j];
+                    for (int j = 0; j < TN; ++j) {
+                        f[(i * TN + j) * GXY] = cr[i][j];
+                        f[(TM * TN + i * TN + j) * GXY] = ci[i][j];
+                    }
+            }
+            __syncthreads();
+            if (kg == 0) {
+#pragma unroll 1
+                for (int g = 1; g < C::KG; ++g) {
+                    const float *f = fr + (size_t)(g - 1) * FV * GXY + tin;
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) {
+                            cr[i][j] += f[(i * TN + j) * GXY];
+                            ci[i][j] += f[(TM * TN + i * TN + j) * GXY];
+                        }
+                }
+            }
+        }
+        if (ksplit > 1) {   // this split's partial result, from set 0's registers
+            if (kg != 0) return;
+            const int64_t M = sd.M, N = sd.N, MN = M * N;
+            float *out = p.split_part + 2 * (int64_t)split * MN;
+            const bool vec = (N & 3) == 0;
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                const int64_t m = m0 + ty * TM + i;
+                if (m >= M) break;
+#pragma unroll
+                for (int v = 0; v < TN / 4; ++v) {
+                    const int64_t n = n0 + tx * TN + 4 * v;
+                    float *o = out + m * N + n;
+                    if (vec && n + 3 < N) {
+                        *reinterpret_cast<float4 *>(o) =
+                            make_float4(cr[i][4 * v], cr[i][4 * v + 1], cr[i][4 * v + 2], cr[i][4 * v + 3]);
+                        *reinterpret_cast<float4 *>(o + MN) =
+                            make_float4(ci[i][4 * v], ci[i][4 * v + 1], ci[i][4 * v + 2], ci[i][4 * v + 3]);
                     } else {
-                        const float v = pl ? ci[i][j] : cr[i][j];
-                        cs[e] = add ? v + cs[e] : v;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (n + e < N) {
+                                o[e] = cr[i][4 * v + e];
+                                o[e + MN] = ci[i][4 * v + e];
+                            }
                     }
                 }
+            }
+            return;
+        }
+        const bool m_fast = !(sd.flags & kFlagCNFast);
+        const int ld = m_fast ? BM + 4 : BN + 4;   // row length of a staged plane (float4-aligned)
+        const int plane = (m_fast ? BN : BM) * ld;
+        auto put = [&](float *dst, const float (*x)[TN]) {
+            if (m_fast) {
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+#pragma unroll
+                    for (int v = 0; v < TM / 4; ++v)
+                        *reinterpret_cast<float4 *>(dst + (tx * TN + j) * ld + ty * TM + 4 * v) =
+                            make_float4(x[4 * v][j], x[4 * v + 1][j], x[4 * v + 2][j], x[4 * v + 3][j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int v = 0; v < TN / 4; ++v)
+                        *reinterpret_cast<float4 *>(dst + (ty * TM + i) * ld + tx * TN + 4 * v) =
+                            make_float4(x[i][4 * v], x[i][4 * v + 1], x[i][4 * v + 2], x[i][4 * v + 3]);
+            }
         };
 #pragma unroll 1
         for (int pl = 0; pl < (both ? 1 : 2); ++pl) {
             __syncthreads();   // the staging area is free
-            if (kg == C::KG - 1) put(pl, false);
-            if (C::KG == 2) {
-                __syncthreads();
-                if (kg == 0) put(pl, true);
+            if (kg == 0) {
+                if (both) {
+                    put(stage, cr);
+                    put(stage + plane, ci);
+                } else {
+                    put(stage, pl ? ci : cr);
+                }
             }
             __syncthreads();
-            emit_tile<C>(cs, plane, ld, m_fast, both, pl, c_om, c_on, sd, warp, lane);
+            emit_tile<C>(stage, plane, ld, m_fast, both, pl, c_om, c_on, (float *)sd.c, sd.c_plane, warp, lane);
         }
         __syncthreads();   // the staging area may be refilled
     };
@@ -1049,6 +1144,49 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
     if (!SK && !abort_flag) store_c(stg, true, pm0, pn0);   // the CTA's tile; the idle ring stages both planes
 }
 
+// Sum of the partial results of a split contraction into C, in split order
+// (deterministic): 32 outputs per CTA; warp w adds partials w, w + 8, ... of
+// its lane's output, then warp 0 adds the eight sums in warp order.  The
+// descriptor and C's offsets are read before the wait for the GEMM (planner
+// tables, complete before the GEMM started); the partials, which the GEMM
+// has just written, after it and through L2.
+__global__ void __launch_bounds__(256) f32_split_reduce_kernel(const __grid_constant__ GroupArgs g,
+                                                               const float *__restrict__ part, int nsplit) {
+    __shared__ GettDesc sd;
+    __shared__ float red[2][8][33];
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
+    __syncthreads();
+    const int64_t MN = sd.M * sd.N;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t o = ((int64_t)blockIdx.x - sd.tile_begin) * 32 + lane;
+    int64_t ic = -1;
+    if (w == 0 && o < MN) ic = __ldg(sd.offCM + o / sd.N) + __ldg(sd.offCN + o % sd.N);
+    grid_dep_wait();
+    float sr = 0.f, si = 0.f;
+    if (o < MN) {
+#pragma unroll 4
+        for (int sp = w; sp < nsplit; sp += 8) {
+            sr += __ldcg(part + (2 * (int64_t)sp) * MN + o);
+            si += __ldcg(part + (2 * (int64_t)sp + 1) * MN + o);
+        }
+    }
+    red[0][w][lane] = sr;
+    red[1][w][lane] = si;
+    __syncthreads();
+    if (w != 0 || o >= MN) return;
+    sr = red[0][0][lane];
+    si = red[1][0][lane];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) {
+        sr += red[0][j][lane];
+        si += red[1][j][lane];
+    }
+    float *C = (float *)sd.c;
+    C[ic] = sr;
+    C[ic + sd.c_plane] = si;
+}
+
 }  // namespace f32p
 
 // ---------------------------------------------------------------------------
@@ -1155,8 +1293,10 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
 }
 
 struct F32Geom {
+    int bm, bn;                    // the tile
     int64_t Mpad, Npad, Kpad;
     size_t pack_bytes;             // packed A and B panels
+    size_t split_bytes = 0;        // partial results of a split contraction (after the stream-K area)
     // stream-K: CTAs, units, most pieces of a tile, and the workspace of the
     // partial tiles and per-tile counters (after the packed panels)
     int64_t G = 0, U = 0, maxpieces = 0;
@@ -1165,10 +1305,18 @@ struct F32Geom {
 
 int64_t sk_owner_host(int64_t u, int64_t U, int64_t G) { return ((u + 1) * G - 1) / U; }
 
+// The GEMM's tile for an M x N output: 128 x 16 for N <= 16, else 64 x 64.
+bool f32p_skinny(int64_t N) { return N <= f32p::TileSkinny::BN; }
+
 F32Geom f32_geom(const GettDesc &d) {
     F32Geom g;
-    g.Mpad = (d.M + f32p::BM - 1) / f32p::BM * f32p::BM;
-    g.Npad = (d.N + f32p::BN - 1) / f32p::BN * f32p::BN;
+    const bool skinny = f32p_skinny(d.N);
+    g.bm = skinny ? f32p::TileSkinny::BM : f32p::BM;
+    g.bn = skinny ? f32p::TileSkinny::BN : f32p::BN;
+    // panels: rows padded to the tile and to the pack kernel's 32-row tile
+    const int64_t rn = std::max(g.bn, 32);
+    g.Mpad = (d.M + g.bm - 1) / g.bm * g.bm;
+    g.Npad = (d.N + rn - 1) / rn * rn;
     g.Kpad = (d.K + f32p::KQ - 1) / f32p::KQ * f32p::KQ;   // KQ is a multiple of BK
     g.pack_bytes = (size_t)2 * (g.Mpad + g.Npad) * g.Kpad * 4;
     if (d.flags & kFlagStreamK) {
@@ -1181,6 +1329,7 @@ F32Geom f32_geom(const GettDesc &d) {
         g.part_bytes = (size_t)tiles * g.maxpieces * 2 * f32p::BM * f32p::BN * 4;
         g.count_bytes = ((size_t)tiles * 4 + 255) & ~(size_t)255;
     }
+    if (d.ksplit > 1) g.split_bytes = (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * 4;
     return g;
 }
 
@@ -1212,15 +1361,22 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
                 bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
     using f32p::Tile4x4;
     using f32p::Tile8x4;
+    using f32p::TileSkinny;
     static bool attr_set = false;
     if (!attr_set) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile8x4, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile8x4::SMEM));
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile4x4, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile4x4::SMEM));
+        RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<TileSkinny, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileSkinny::SMEM));
         attr_set = true;
     }
     const F32Geom g = f32_geom(d);
+    const bool skinny = f32p_skinny(d.N), sk = d.flags & kFlagStreamK, split = d.ksplit > 1;
+    if (sk && (skinny || split)) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "stream-K takes 64 x 64 tiles and no split");
+    if (split && (d.ktiles_per_split < 1 || (int64_t)d.ksplit * d.ktiles_per_split < g.Kpad / f32p::BK))
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "split does not cover the contraction");
     float *pa = (float *)ws;
     float *pb = pa + 2 * g.Mpad * g.Kpad;
     // operands stored as dense K x rows matrices are read in place; the others
@@ -1243,10 +1399,10 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     }
     f32p::Args args;
     memset(&args, 0, sizeof(args));
-    if (da) make_map_f32(&args.mapA, d.a, d.M, d.K, d.M, d.a_plane, f32p::BM);
-    else make_map_f32(&args.mapA, pa, g.Mpad, g.Kpad, g.Mpad, g.Mpad * g.Kpad, f32p::BM);
-    if (db) make_map_f32(&args.mapB, d.b, d.N, d.K, d.N, d.b_plane, f32p::BN);
-    else make_map_f32(&args.mapB, pb, g.Npad, g.Kpad, g.Npad, g.Npad * g.Kpad, f32p::BN);
+    if (da) make_map_f32(&args.mapA, d.a, d.M, d.K, d.M, d.a_plane, g.bm);
+    else make_map_f32(&args.mapA, pa, g.Mpad, g.Kpad, g.Mpad, g.Mpad * g.Kpad, g.bm);
+    if (db) make_map_f32(&args.mapB, d.b, d.N, d.K, d.N, d.b_plane, g.bn);
+    else make_map_f32(&args.mapB, pb, g.Npad, g.Kpad, g.Npad, g.Npad * g.Kpad, g.bn);
     args.g = ga;
     args.nkt = (int)(g.Kpad / f32p::BK);
     if (d.flags & kFlagStreamK) {
@@ -1255,24 +1411,46 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
         args.sk_maxpieces = (int32_t)g.maxpieces;
         ctas = g.G;
     }
+    if (split) args.split_part = (float *)((char *)ws + g.pack_bytes + g.part_bytes + g.count_bytes);
     if (before_gemm) before_gemm();
     // after a pack the GEMM's prologue may overlap it (it reads only its
     // descriptor before waiting); with no pack it is the first launch
     const bool pdl_gemm = pdl || pack_a || pack_b;
-    if (d.flags & kFlagStreamK)
+    if (sk)
         launch_pdl(f32p::f32_gemm_kernel<Tile4x4, true>, dim3((unsigned)ctas), Tile4x4::NT, Tile4x4::SMEM, s,
                    pdl_gemm, args);
+    else if (skinny)
+        launch_pdl(f32p::f32_gemm_kernel<TileSkinny, false>, dim3((unsigned)ctas), TileSkinny::NT,
+                   TileSkinny::SMEM, s, pdl_gemm, args);
     else
         launch_pdl(f32p::f32_gemm_kernel<Tile8x4, false>, dim3((unsigned)ctas), Tile8x4::NT, Tile8x4::SMEM, s,
                    pdl_gemm, args);
     g_launches++;
+    if (split) {   // the partial results summed into C in split order
+        const int64_t rc = (d.M * d.N + 31) / 32;
+        if (rc > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "output too large for one launch");
+        launch_pdl(f32p::f32_split_reduce_kernel, dim3((unsigned)rc), 256, 0, s, true, ga,
+                   (const float *)args.split_part, (int)d.ksplit);
+        g_launches++;
+    }
     RN_CHECK_CUDA(cudaGetLastError());
 }
 
 }  // namespace
 
-int f32p_tile_m() { return f32p::BM; }
-int f32p_tile_n() { return f32p::BN; }
+// The FP32 GEMM's tile for an M x N output (N <= M after the operand swap).
+void f32p_tile(int64_t N, int *bm, int *bn) {
+    *bm = f32p_skinny(N) ? f32p::TileSkinny::BM : f32p::BM;
+    *bn = f32p_skinny(N) ? f32p::TileSkinny::BN : f32p::BN;
+}
+
+// The contraction split of a few-column problem for the FP32 GEMM (0 if it
+// is not one): enough CTAs to reach every SM, at least two k-tiles each.
+int64_t f32p_skinny_split(const GettDesc &d) {
+    if (!f32p_skinny(d.N)) return 0;
+    const int64_t nkt = (d.K + f32p::BK - 1) / f32p::BK, tiles = d.tiles_m * d.tiles_n;
+    return std::max<int64_t>(1, std::min<int64_t>((num_sms() + tiles - 1) / tiles, nkt / 2));
+}
 
 // Whether the packed FP32 GEMM of a problem takes the stream-K schedule.
 // Measured on B300 against one CTA per tile (2 CTA slots per SM): stream-K
@@ -1283,7 +1461,7 @@ int f32p_tile_n() { return f32p::BN; }
 // CTA it loses (704 x 704 x 128: 0.75x).  Never with a sequential (one CTA per
 // tile) reduction; the autotuner times both schedules where this says yes.
 bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode) {
-    if (reduce_mode == kReduceSequential) return false;
+    if (reduce_mode == kReduceSequential || f32p_skinny(d.N) || d.ksplit > 1) return false;
     const int64_t tiles = d.tiles_m * d.tiles_n, slots = 2 * (int64_t)num_sms();
     const int64_t nkt = (d.K + f32p::BK - 1) / f32p::BK;
     if (nkt < 32 || tiles >= 3 * slots) return false;
@@ -1295,7 +1473,7 @@ bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode) {
 // problem with fewer than three rounds of tiles over the CTA slots and at
 // least 4 k-tiles a tile (the cases where balance can pay for the pieces).
 bool f32p_stream_k_worth_timing(const GettDesc &d, int reduce_mode) {
-    if (reduce_mode == kReduceSequential) return false;
+    if (reduce_mode == kReduceSequential || f32p_skinny(d.N) || d.ksplit > 1) return false;
     const int64_t tiles = d.tiles_m * d.tiles_n, slots = 2 * (int64_t)num_sms();
     return tiles < 3 * slots && (d.K + f32p::BK - 1) / f32p::BK >= 4;
 }
@@ -1305,7 +1483,7 @@ bool f32p_stream_k_worth_timing(const GettDesc &d, int reduce_mode) {
 size_t tc_workspace_bytes(const GettDesc &d, int mode) {
     if (mode == kPackedModeF32) {
         const F32Geom g = f32_geom(d);
-        return g.pack_bytes + g.part_bytes + g.count_bytes;
+        return g.pack_bytes + g.part_bytes + g.count_bytes + g.split_bytes;
     }
     TcGeom g = tc_geom(d, mode);
     return g.narr * (g.arrA + g.arrB);
@@ -1329,7 +1507,7 @@ void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s) {
 // stream has completed (it follows a kernel that built its offset tables).
 void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *ws, cudaStream_t s,
                        bool pack_a, bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
-    const int64_t ctas = d.tiles_m * d.tiles_n;
+    const int64_t ctas = d.tiles_m * d.tiles_n * (mode == kPackedModeF32 ? std::max(1, d.ksplit) : 1);
     if (ctas <= 0) return;
     if (ctas > 0x7fffffffLL) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "problem too large for one launch");
     if (mode == kPackedModeF32) {

@@ -126,3 +126,47 @@ def test_dense_operand_unaligned_rows_is_packed():
     C, n = _launches(lambda: R.tensordot(A, B, [0], [0]))
     assert n == _tiled_launches() + 1, n
     assert oracle.rel_frobenius(C.download(), oracle.tensordot(a, b, [0], [0])) <= 1e-5
+
+
+# Few columns and a long contraction: 128 x 16 tiles with the contraction
+# split over CTAs, each storing a partial result that a second kernel sums in
+# split order.  (M, N, K): the amplitude's 256 x 16 x 4096 step, ragged rows
+# and contraction, 3 columns (a B panel of 3 rows is not 16-byte aligned:
+# packed), and several row tiles.
+@pytest.mark.parametrize("mnk", [(256, 16, 4096), (300, 12, 2500), (1000, 3, 3000), (2048, 16, 1024)])
+@pytest.mark.parametrize("la", ["km", "mk"])
+def test_few_columns_split_contraction(mnk, la):
+    M, N, K = mnk
+    a = W.complex_normal((K, M) if la == "km" else (M, K), 91).astype(np.complex64)
+    b = W.complex_normal((K, N), 92).astype(np.complex64)
+    ax_a = [0] if la == "km" else [1]
+    A, B = R.btensor(a), R.btensor(b)
+    R.timing_drain()
+    C = R.tensordot(A, B, ax_a, [0])
+    ref = oracle.tensordot(a, b, ax_a, [0])
+    got = C.download()
+    assert oracle.rel_frobenius(got, ref) <= 1e-5
+    for _ in range(2):   # fixed summation order: bitwise reproducible
+        assert np.array_equal(got, R.tensordot(A, B, ax_a, [0]).download())
+    # a plan replayed as a graph (the partials live in the plan's workspace)
+    outs = [R.contract([A, B], [(0, 1) if la == "km" else (1, 0), (0, 2)], [1, 2], [(0, 1)],
+                       flags=R.OPT_GRAPH | R.OPT_TIMING).download() for _ in range(3)]
+    recs = R.timing_drain()
+    assert recs and recs[-1][3] == 10, recs[-1:]
+    for o in outs:
+        assert np.array_equal(o, got)
+
+
+def test_few_columns_sequential_mode_is_not_split():
+    """REDUCE_SEQUENTIAL asks for one CTA per output tile over the whole
+    contraction: the split GEMM is not taken, the result meets the bar."""
+    a = W.complex_normal((4096, 256), 93).astype(np.complex64)
+    b = W.complex_normal((4096, 16), 94).astype(np.complex64)
+    A, B = R.btensor(a), R.btensor(b)
+    ref = oracle.tensordot(a, b, [0], [0])
+    R.timing_drain()
+    got = R.contract([A, B], [(0, 1), (0, 2)], [1, 2], [(0, 1)],
+                     flags=R.OPT_TIMING | R.REDUCE_SEQUENTIAL).download()
+    recs = R.timing_drain()
+    assert recs and recs[-1][3] != 10, recs[-1:]
+    assert oracle.rel_frobenius(got, ref) <= 1e-5
