@@ -37,6 +37,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <functional>
 #include <mutex>
 
@@ -610,12 +611,8 @@ struct Cfg {
 // shared memory as busy as the FMA pipe: 61.0 against 57.5 TFLOP/s on
 // 1024 x 32768 x 1024, 49.3 against 51.2 us on 4096 x 256 x 256.
 using Tile8x4 = Cfg<64, 64, 8, 4, 2, 3>;
-// Stream-K (a CTA's run of units crosses tiles, and a piece of a tile is
-// stored from the registers that hold it): one set of 16 x 16 threads of
-// 4 x 4 outputs.
-using Tile4x4 = Cfg<64, 64, 4, 4, 1, 3>;
-constexpr int BM = 64, BN = 64;   // the tile of both
-static_assert(Tile8x4::BM == BM && Tile4x4::BM == BM && Tile8x4::BN == BN && Tile4x4::BN == BN, "tiles");
+constexpr int BM = 64, BN = 64;   // its tile (also of the stream-K schedule)
+static_assert(Tile8x4::BM == BM && Tile8x4::BN == BN, "tiles");
 // Few columns (N <= 16) and a long contraction, e.g. 256 x 16 x 4096: 128 x
 // 16 tiles, four sets of 32 x 2 threads of 4 x 8 outputs, the contraction
 // split over CTAs (each a run of k-tiles, its partial tile stored and the
@@ -632,6 +629,7 @@ struct Args {
     float *split_part;        // split contraction: partial results [split][2 planes][M x N], row-major (m, n)
     int32_t nkt;              // k-stages (Kpad / BK)
     int32_t sk_maxpieces;     // stream-K: most pieces of any tile
+    int32_t sk_dp;            // stream-K: CTAs [0, sk_dp) take tiles [0, sk_dp) whole
 };
 
 // out[p][k][r] = operand(r, k) plane p (0 outside R x K), for A (the first
@@ -747,20 +745,25 @@ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) { r
 
 // Work is a sequence of units (output tile t, k-tile kt), k fastest.  Without
 // kFlagStreamK a CTA takes the units of one tile (data-parallel).  With it
-// (stream-K) the launch has G CTAs and CTA c takes units [c U / G,
-// (c + 1) U / G) of all U = tiles * nkt, so every SM slot gets the same work
-// however the tile count divides the slots.  A CTA holding only part of a
-// tile's k range writes that partial tile to the workspace and counts it in
-// the tile's counter; the CTA that brings the count to the number of pieces
-// sums the pieces in k order (a fixed order: results do not depend on
-// scheduling), writes C and resets the counter.  No CTA ever waits for
-// another.
+// (stream-K) the launch has G CTAs: the first D = sk_dp take tiles [0, D)
+// whole, and CTA D + c takes units [c U' / G', (c + 1) U' / G') of the U' =
+// (tiles - D) * nkt units of the other tiles, G' = G - D, so that every SM
+// gets the same work however the tile count divides the SMs (D = SMs when
+// the tiles number between one and two per SM: each SM holds one whole tile
+// and a share of the rest).  A CTA holding only part of a tile's k range
+// writes that partial tile to the workspace and counts it in the tile's
+// counter; the CTA that brings the count to the number of pieces sums the
+// pieces in k order (a fixed order: results do not depend on scheduling),
+// writes C and resets the counter.  No CTA ever waits for another.
 template <class C, bool SK>
 __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constant__ Args p) {
     constexpr int NT = C::NT, BM = C::BM, BN = C::BN, TM = C::TM, TN = C::TN, STAGES = C::STAGES;
     constexpr int PA = C::PA, PB = C::PB, GX = C::GX, GY = C::GY, KR = C::KR;
     constexpr uint32_t STAGE_BYTES = C::STAGE_BYTES;
-    static_assert(!SK || C::KG == 1, "stream-K takes one set of threads");
+    constexpr int GXY = GX * GY, FV = 2 * TM * TN;   // threads of a set, values a thread holds
+    // stream-K stages a tile's sets and then one C plane at a time through a
+    // single consumed stage
+    static_assert(!SK || ((size_t)FV * GXY * 4 <= STAGE_BYTES && C::PLANE_MAX * 4 <= STAGE_BYTES), "stage size");
     extern __shared__ unsigned char dsm_raw[];
     float *stg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~(uintptr_t)127);
     __shared__ GettDesc sd;
@@ -768,6 +771,7 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
     __shared__ volatile int abort_flag;
     __shared__ int last_piece;
     __shared__ int64_t c_om[BM], c_on[BN];   // output offsets of the current tile's rows and columns
+    __shared__ int64_t cta_u0, cta_u1;   // this CTA's unit range (stream-K; out of the k loop's registers)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     grid_dep_launch();
     if (warp == 0) load_desc(p.g, sd);
@@ -789,7 +793,13 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         m0 = (int)(tm * BM);
         n0 = (int)(tn * BN);
     };
-    const int64_t U = sd.tiles_m * sd.tiles_n * (int64_t)nkt, G = gridDim.x;
+    // stream-K: whole tiles for CTAs [0, D), the units of tiles [D, tiles)
+    // split evenly over the other Gs CTAs; owner(u): the CTA holding unit u
+    auto owner = [&](int64_t u) {
+        const int64_t D = p.sk_dp, ub = D * nkt;
+        const int64_t Us = sd.tiles_m * sd.tiles_n * (int64_t)nkt - ub, Gs = (int64_t)gridDim.x - D;
+        return u < ub ? u / nkt : D + sk_owner(u - ub, Us, Gs);
+    };
     // one tile per CTA, or with a split contraction (ksplit > 1) CTA
     // (tile, split) takes k-tiles [split kps, (split + 1) kps) of its tile and
     // stores a partial result
@@ -797,8 +807,11 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
     int split = 0;
     int64_t u0, u1;
     if (SK) {
-        u0 = (int64_t)blockIdx.x * U / G;
-        u1 = ((int64_t)blockIdx.x + 1) * U / G;
+        const int64_t D = p.sk_dp, ub = D * nkt;
+        const int64_t Us = sd.tiles_m * sd.tiles_n * (int64_t)nkt - ub, Gs = (int64_t)gridDim.x - D;
+        const int64_t c = (int64_t)blockIdx.x - D;
+        u0 = c < 0 ? (int64_t)blockIdx.x * nkt : ub + c * Us / Gs;
+        u1 = c < 0 ? u0 + nkt : ub + (c + 1) * Us / Gs;
     } else {
         const int64_t cta = (int64_t)blockIdx.x - sd.tile_begin;
         split = (int)(cta % ksplit);
@@ -842,8 +855,13 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         }
     };
     int issued = 0;
-    if (tid == 0)
+    if (tid == 0) {
+        if (SK) {
+            cta_u0 = u0;
+            cta_u1 = u1;
+        }
         for (; issued < min(STAGES, nitems); ++issued) issue(issued);
+    }
     // one tile per CTA: its offsets load while the first stages land (the
     // barriers before the epilogue's stores publish them)
     if (!SK) load_offsets(pm0, pn0);
@@ -903,30 +921,17 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         }
     };
 
-    // the finished tile at (m0, n0).  `cs`: a consumed stage (mid-stream,
-    // one set of threads), which stages one plane at a time, or the whole
-    // idle ring after the CTA's last unit.  With several k sets, sets 1, 2,
-    // ... store their partial tiles in fragment order (consecutive threads,
-    // consecutive words: no bank conflicts) and set 0 adds them in set order:
-    // C = ((s0 + s1) + s2) + ..., the same in every CTA.  A split's partial
-    // result goes straight to global memory (row-major (m, n), n fastest);
-    // C is staged through shared memory as [BN][BM + 4] (or [BM][BN + 4])
-    // planes written as float4 and stored with the lanes of a warp along C's
-    // unit-stride dimension (m unless kFlagCNFast).
-    constexpr int GXY = GX * GY, FV = 2 * TM * TN;   // threads of a set, values a thread holds
-    auto store_c = [&](float *cs, bool both, int m0, int n0) {
-        if (SK) {   // this tile's offsets (the previous tile's stores are done)
-            __syncthreads();
-            load_offsets(m0, n0);
-        }
-        float *stage = cs;
-        if constexpr (C::KG > 1) {   // only after the CTA's last unit: the ring is idle
-            float *fr = cs;           // [KG - 1][FV][GXY]
-            stage = cs + (C::KG - 1) * FV * GXY;
+    // Several k sets hold partial tiles of the same outputs: sets 1, 2, ...
+    // store theirs in fragment order through `scratch` (FV x GXY floats a set
+    // after the first; consecutive threads, consecutive words: no bank
+    // conflicts) and set 0 adds them in set order, ((s0 + s1) + s2) + ...,
+    // the same in every CTA.  Set 0 then holds the tile.
+    auto merge_sets = [&](float *scratch) {
+        if constexpr (C::KG > 1) {
             const int tin = tid % GXY;
-            __syncthreads();
+            __syncthreads();   // the scratch area is free
             if (kg > 0) {
-                float *f = fr + (size_t)(kg - 1) * FV * GXY + tin;
+                float *f = scratch + (size_t)(kg - 1) * FV * GXY + tin;
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -939,7 +944,7 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
             if (kg == 0) {
 #pragma unroll 1
                 for (int g = 1; g < C::KG; ++g) {
-                    const float *f = fr + (size_t)(g - 1) * FV * GXY + tin;
+                    const float *f = scratch + (size_t)(g - 1) * FV * GXY + tin;
 #pragma unroll
                     for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -950,6 +955,23 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
                 }
             }
         }
+    };
+
+    // the finished tile at (m0, n0), its sets merged first unless `merged`.
+    // `cs`: a consumed stage (mid-stream), which serves the merge and then
+    // stages one plane at a time, or the whole idle ring after the CTA's last
+    // unit (the merge, then both planes behind it).  A split's partial result
+    // goes straight to global memory (row-major (m, n), n fastest); C is
+    // staged through shared memory as [BN][BM + 4] (or [BM][BN + 4]) planes
+    // written as float4 by set 0 and stored with the lanes of a warp along
+    // C's unit-stride dimension (m unless kFlagCNFast).
+    auto store_c = [&](float *cs, bool both, int m0, int n0, bool merged) {
+        if (SK) {   // this tile's offsets (the previous tile's stores are done)
+            __syncthreads();
+            load_offsets(m0, n0);
+        }
+        if (!merged) merge_sets(cs);
+        float *stage = both ? cs + (C::KG - 1) * FV * GXY : cs;
         if (ksplit > 1) {   // this split's partial result, from set 0's registers
             if (kg != 0) return;
             const int64_t M = sd.M, N = sd.N, MN = M * N;
@@ -1079,25 +1101,31 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         // stage s holds consumed data and is refilled only after this
         // epilogue (by the next unit's refill): it serves as staging area
         float *cs = stg + (size_t)s * 2 * (PA + PB);
-        bool write_c = true;
+        bool write_c = true, merged = false;
         const int64_t tb = (int64_t)t * nkt;   // the tile's first unit
-        if (SK && (u0 > tb || u1 < tb + nkt)) {
-            // a piece of the tile: store it, count it, and sum all pieces if
-            // it is the last one to arrive
-            const int64_t cf = sk_owner(tb, U, G);
-            const int npieces = (int)(sk_owner(tb + nkt - 1, U, G) - cf + 1);
+        if (SK && (cta_u0 > tb || cta_u1 < tb + nkt)) {
+            // a piece of the tile: store it (set 0, after the sets are
+            // merged), count it, and sum all pieces if it is the last one to
+            // arrive
+            const int64_t cf = owner(tb);
+            const int npieces = (int)(owner(tb + nkt - 1) - cf + 1);
             const int piece = (int)((int64_t)blockIdx.x - cf);
+            const int tin = tid % GXY;
             float *slot = p.sk_part + ((int64_t)t * p.sk_maxpieces + piece) * (2 * BM * BN);
+            merge_sets(cs);
+            merged = true;
+            if (kg == 0) {
 #pragma unroll
-            for (int i2 = 0; i2 < TM; ++i2)
+                for (int i2 = 0; i2 < TM; ++i2)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    slot[(i2 * TN + j) * NT + tid] = cr[i2][j];
-                    slot[(TM * TN + i2 * TN + j) * NT + tid] = ci[i2][j];
-                }
+                    for (int j = 0; j < TN; ++j) {
+                        slot[(i2 * TN + j) * GXY + tin] = cr[i2][j];
+                        slot[(TM * TN + i2 * TN + j) * GXY + tin] = ci[i2][j];
+                    }
+            }
             // the barrier orders every thread's stores before thread 0's
             // release; its acquire orders the other pieces' stores before the
-            // barrier after which all threads read them
+            // barrier after which set 0 reads them
             __syncthreads();
             if (tid == 0) {
                 int old;
@@ -1108,20 +1136,22 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
             __syncthreads();
             write_c = last_piece;
             if (write_c) {
-                const float *base = p.sk_part + (int64_t)t * p.sk_maxpieces * (2 * BM * BN);
-#pragma unroll
-                for (int i2 = 0; i2 < TM; ++i2)
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) cr[i2][j] = ci[i2][j] = 0.f;
-                for (int q = 0; q < npieces; ++q) {   // pieces in k order
-                    const float *src = base + (int64_t)q * (2 * BM * BN);
+                if (kg == 0) {
+                    const float *base = p.sk_part + (int64_t)t * p.sk_maxpieces * (2 * BM * BN);
 #pragma unroll
                     for (int i2 = 0; i2 < TM; ++i2)
 #pragma unroll
-                        for (int j = 0; j < TN; ++j) {
-                            cr[i2][j] += __ldcg(src + (i2 * TN + j) * NT + tid);
-                            ci[i2][j] += __ldcg(src + (TM * TN + i2 * TN + j) * NT + tid);
-                        }
+                        for (int j = 0; j < TN; ++j) cr[i2][j] = ci[i2][j] = 0.f;
+                    for (int q = 0; q < npieces; ++q) {   // pieces in k order
+                        const float *src = base + (int64_t)q * (2 * BM * BN) + tin;
+#pragma unroll
+                        for (int i2 = 0; i2 < TM; ++i2)
+#pragma unroll
+                            for (int j = 0; j < TN; ++j) {
+                                cr[i2][j] += __ldcg(src + (i2 * TN + j) * GXY);
+                                ci[i2][j] += __ldcg(src + (TM * TN + i2 * TN + j) * GXY);
+                            }
+                    }
                 }
                 if (tid == 0) p.sk_count[t] = 0;   // ready for the next launch
             }
@@ -1129,8 +1159,8 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         if (write_c) {
             // after the CTA's last unit no copy is in flight: the whole ring
             // stages both planes at once
-            if (i == nitems - 1) store_c(stg, true, m0, n0);
-            else store_c(cs, false, m0, n0);
+            if (i == nitems - 1) store_c(stg, true, m0, n0, merged);
+            else store_c(cs, false, m0, n0, merged);
         }
 #pragma unroll
         for (int i2 = 0; i2 < TM; ++i2)
@@ -1141,7 +1171,7 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         for (int t = done0; t < issued; ++t)
             tc::mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1, &abort_flag, false);
     __syncthreads();
-    if (!SK && !abort_flag) store_c(stg, true, pm0, pn0);   // the CTA's tile; the idle ring stages both planes
+    if (!SK && !abort_flag) store_c(stg, true, pm0, pn0, false);   // the CTA's tile; the idle ring stages both planes
 }
 
 // Sum of the partial results of a split contraction into C, in split order
@@ -1297,9 +1327,10 @@ struct F32Geom {
     int64_t Mpad, Npad, Kpad;
     size_t pack_bytes;             // packed A and B panels
     size_t split_bytes = 0;        // partial results of a split contraction (after the stream-K area)
-    // stream-K: CTAs, units, most pieces of a tile, and the workspace of the
-    // partial tiles and per-tile counters (after the packed panels)
-    int64_t G = 0, U = 0, maxpieces = 0;
+    // stream-K: CTAs, whole-tile CTAs, split units, most pieces of a tile, and
+    // the workspace of the partial tiles and per-tile counters (after the
+    // packed panels)
+    int64_t G = 0, D = 0, U = 0, maxpieces = 0;
     size_t part_bytes = 0, count_bytes = 0;
 };
 
@@ -1320,12 +1351,16 @@ F32Geom f32_geom(const GettDesc &d) {
     g.Kpad = (d.K + f32p::KQ - 1) / f32p::KQ * f32p::KQ;   // KQ is a multiple of BK
     g.pack_bytes = (size_t)2 * (g.Mpad + g.Npad) * g.Kpad * 4;
     if (d.flags & kFlagStreamK) {
-        const int64_t tiles = d.tiles_m * d.tiles_n, nkt = g.Kpad / f32p::BK;
-        g.U = tiles * nkt;
-        g.G = std::min<int64_t>(2 * (int64_t)num_sms(), g.U);
-        for (int64_t t = 0; t < tiles; ++t)
-            g.maxpieces = std::max(g.maxpieces, sk_owner_host((t + 1) * nkt - 1, g.U, g.G) -
-                                                    sk_owner_host(t * nkt, g.U, g.G) + 1);
+        // between one and two tiles per SM: one whole tile per SM, the rest
+        // split evenly over a second CTA per SM; otherwise all tiles split
+        const int64_t tiles = d.tiles_m * d.tiles_n, nkt = g.Kpad / f32p::BK, sms = num_sms();
+        g.D = tiles > sms && tiles < 2 * sms ? sms : 0;
+        g.U = (tiles - g.D) * nkt;   // the split units
+        g.G = g.D + std::min<int64_t>(g.D ? sms : 2 * sms, g.U);
+        const int64_t gs = g.G - g.D;
+        for (int64_t t = g.D; t < tiles; ++t)
+            g.maxpieces = std::max(g.maxpieces, sk_owner_host((t + 1 - g.D) * nkt - 1, g.U, gs) -
+                                                    sk_owner_host((t - g.D) * nkt, g.U, gs) + 1);
         g.part_bytes = (size_t)tiles * g.maxpieces * 2 * f32p::BM * f32p::BN * 4;
         g.count_bytes = ((size_t)tiles * 4 + 255) & ~(size_t)255;
     }
@@ -1359,15 +1394,14 @@ bool tma_direct_ok(bool dense, const void *p, int64_t rows, int64_t K, int64_t p
 
 void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, cudaStream_t s, bool pack_a,
                 bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
-    using f32p::Tile4x4;
     using f32p::Tile8x4;
     using f32p::TileSkinny;
     static bool attr_set = false;
     if (!attr_set) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile8x4, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile8x4::SMEM));
-        RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile4x4, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile4x4::SMEM));
+        RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile8x4, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile8x4::SMEM));
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<TileSkinny, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileSkinny::SMEM));
         attr_set = true;
@@ -1409,6 +1443,7 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
         args.sk_part = (float *)((char *)ws + g.pack_bytes);
         args.sk_count = (int32_t *)((char *)ws + g.pack_bytes + g.part_bytes);
         args.sk_maxpieces = (int32_t)g.maxpieces;
+        args.sk_dp = (int32_t)g.D;
         ctas = g.G;
     }
     if (split) args.split_part = (float *)((char *)ws + g.pack_bytes + g.part_bytes + g.count_bytes);
@@ -1417,7 +1452,7 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     // descriptor before waiting); with no pack it is the first launch
     const bool pdl_gemm = pdl || pack_a || pack_b;
     if (sk)
-        launch_pdl(f32p::f32_gemm_kernel<Tile4x4, true>, dim3((unsigned)ctas), Tile4x4::NT, Tile4x4::SMEM, s,
+        launch_pdl(f32p::f32_gemm_kernel<Tile8x4, true>, dim3((unsigned)ctas), Tile8x4::NT, Tile8x4::SMEM, s,
                    pdl_gemm, args);
     else if (skinny)
         launch_pdl(f32p::f32_gemm_kernel<TileSkinny, false>, dim3((unsigned)ctas), TileSkinny::NT,
@@ -1453,20 +1488,25 @@ int64_t f32p_skinny_split(const GettDesc &d) {
 }
 
 // Whether the packed FP32 GEMM of a problem takes the stream-K schedule.
-// Measured on B300 against one CTA per tile (2 CTA slots per SM): stream-K
-// wins for deep contractions whose tiles fill the slots poorly (704 x 704 x
-// 1024, 121 tiles: 1.09x); with 8-16 k-tiles per tile the extra
-// piece stores and barriers cost what the balance gains (1024 x 512 x 512,
-// 4096 x 256 x 256: equal; 2048 x 1024 x 256: 0.98x), and below ~3 k-tiles per
-// CTA it loses (704 x 704 x 128: 0.75x).  Never with a sequential (one CTA per
-// tile) reduction; the autotuner times both schedules where this says yes.
+// Measured on B300 against one CTA per tile (8 x 4 outputs a thread in both,
+// operands in L2): stream-K pays where the tiles leave the SMs unevenly
+// loaded and a tile has enough k-tiles to split -- 2000 x 300 x 333 (160
+// tiles, 11 k-tiles; 148 SMs take one whole tile each and the other 12 are
+// split over a second CTA per SM): 49.4 against 65.7 us; 704 x 704 x 1024
+// (121 tiles, 32 k-tiles): 94.2 against 98.4 us.  It loses where the
+// imbalance is small or a tile has few k-tiles: 4096 x 256 x 256 (256 tiles
+// of 8 k-tiles) 53.3 against 49.2 us, 1000 x 700 x 200 (176 tiles of 7)
+// 47.2 against 43.0, and on large problems (1024 x 32768 x 1024: 4.91
+// against 4.52 ms).  Never with a sequential (one CTA per tile) reduction;
+// the autotuner times both schedules on more shapes than this selects.
 bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode) {
     if (reduce_mode == kReduceSequential || f32p_skinny(d.N) || d.ksplit > 1) return false;
-    const int64_t tiles = d.tiles_m * d.tiles_n, slots = 2 * (int64_t)num_sms();
+    const int64_t tiles = d.tiles_m * d.tiles_n, sms = num_sms();
     const int64_t nkt = (d.K + f32p::BK - 1) / f32p::BK;
-    if (nkt < 32 || tiles >= 3 * slots) return false;
-    const int64_t waves = (tiles + slots - 1) / slots;
-    return (double)tiles < 0.92 * (double)(waves * slots);   // the slots are used poorly
+    if (tiles >= 3 * sms) return false;
+    // the busiest SM's tiles over the average
+    const double per = (double)tiles / (double)sms, imbalance = std::ceil(per) / per;
+    return (nkt >= 8 && imbalance >= 1.5) || (nkt >= 32 && imbalance >= 1.15);
 }
 
 // Whether the autotuner times the stream-K schedule of a problem: any
