@@ -1261,6 +1261,7 @@ void f32p_tile(int64_t N, int *bm, int *bn);
 int64_t f32p_skinny_split(const GettDesc &d);
 void f32p_set_geometry(GettDesc &d);
 size_t tc_workspace_bytes(const GettDesc &d, int mode);
+size_t tc_workspace_bytes_bound(const GettDesc &d, int mode);
 void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s);
 bool f32p_stream_k_pays(const GettDesc &d, int reduce_mode);
 bool f32p_stream_k_worth_timing(const GettDesc &d, int reduce_mode);
@@ -1850,7 +1851,10 @@ size_t tensordot_into_ws(rosnet_btensor A, rosnet_btensor B, int naxes, const in
         memset(&d, 0, sizeof(d));
         fill_desc_tables(d, v, t + L.off[0], t + L.off[1], t + L.off[2]);
         choose_kernel(d, A->dtype, precision, red);
-        return tab_bytes + (is_packed_kind(d.kind) ? tc_workspace_bytes(d, packed_mode(d.kind))
+        // the workspace for these operand addresses (no packed panels for
+        // operands read in place)
+        bind_operands(d, A->data, B->data, C->data, A->pstride, B->pstride, C->pstride);
+        return tab_bytes + (is_packed_kind(d.kind) ? tc_workspace_bytes_bound(d, packed_mode(d.kind))
                                                    : desc_part_bytes(d, A->dtype));
     };
     size_t need = plan(reduce_mode);

@@ -1322,16 +1322,21 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
     RN_CHECK_CUDA(cudaGetLastError());
 }
 
+// The GEMM's workspace: [stream-K tile counters | stream-K partial tiles |
+// partial results of a split contraction | packed A and B panels], each part
+// 256-byte aligned.  The counters, pieces and partials sit at offsets that do
+// not depend on the panels, which are left out when both operands are read
+// in place.
 struct F32Geom {
     int bm, bn;                    // the tile
     int64_t Mpad, Npad, Kpad;
     size_t pack_bytes;             // packed A and B panels
-    size_t split_bytes = 0;        // partial results of a split contraction (after the stream-K area)
+    size_t split_bytes = 0;        // partial results of a split contraction
     // stream-K: CTAs, whole-tile CTAs, split units, most pieces of a tile, and
-    // the workspace of the partial tiles and per-tile counters (after the
-    // packed panels)
+    // the bytes of the partial tiles and per-tile counters
     int64_t G = 0, D = 0, U = 0, maxpieces = 0;
     size_t part_bytes = 0, count_bytes = 0;
+    size_t off_part = 0, off_split = 0, off_pack = 0, total = 0;
 };
 
 int64_t sk_owner_host(int64_t u, int64_t U, int64_t G) { return ((u + 1) * G - 1) / U; }
@@ -1339,7 +1344,7 @@ int64_t sk_owner_host(int64_t u, int64_t U, int64_t G) { return ((u + 1) * G - 1
 // The GEMM's tile for an M x N output: 128 x 16 for N <= 16, else 64 x 64.
 bool f32p_skinny(int64_t N) { return N <= f32p::TileSkinny::BN; }
 
-F32Geom f32_geom(const GettDesc &d) {
+F32Geom f32_geom(const GettDesc &d, bool both_in_place = false) {
     F32Geom g;
     const bool skinny = f32p_skinny(d.N);
     g.bm = skinny ? f32p::TileSkinny::BM : f32p::BM;
@@ -1349,7 +1354,7 @@ F32Geom f32_geom(const GettDesc &d) {
     g.Mpad = (d.M + g.bm - 1) / g.bm * g.bm;
     g.Npad = (d.N + rn - 1) / rn * rn;
     g.Kpad = (d.K + f32p::KQ - 1) / f32p::KQ * f32p::KQ;   // KQ is a multiple of BK
-    g.pack_bytes = (size_t)2 * (g.Mpad + g.Npad) * g.Kpad * 4;
+    g.pack_bytes = both_in_place ? 0 : (size_t)2 * (g.Mpad + g.Npad) * g.Kpad * 4;
     if (d.flags & kFlagStreamK) {
         // between one and two tiles per SM: one whole tile per SM, the rest
         // split evenly over a second CTA per SM; otherwise all tiles split
@@ -1364,7 +1369,11 @@ F32Geom f32_geom(const GettDesc &d) {
         g.part_bytes = (size_t)tiles * g.maxpieces * 2 * f32p::BM * f32p::BN * 4;
         g.count_bytes = ((size_t)tiles * 4 + 255) & ~(size_t)255;
     }
-    if (d.ksplit > 1) g.split_bytes = (size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * 4;
+    if (d.ksplit > 1) g.split_bytes = ((size_t)d.ksplit * 2 * (size_t)(d.M * d.N) * 4 + 255) & ~(size_t)255;
+    g.off_part = g.count_bytes;
+    g.off_split = g.off_part + g.part_bytes;
+    g.off_pack = g.off_split + g.split_bytes;
+    g.total = g.off_pack + g.pack_bytes;
     return g;
 }
 
@@ -1406,17 +1415,17 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileSkinny::SMEM));
         attr_set = true;
     }
-    const F32Geom g = f32_geom(d);
-    const bool skinny = f32p_skinny(d.N), sk = d.flags & kFlagStreamK, split = d.ksplit > 1;
-    if (sk && (skinny || split)) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "stream-K takes 64 x 64 tiles and no split");
-    if (split && (d.ktiles_per_split < 1 || (int64_t)d.ksplit * d.ktiles_per_split < g.Kpad / f32p::BK))
-        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "split does not cover the contraction");
-    float *pa = (float *)ws;
-    float *pb = pa + 2 * g.Mpad * g.Kpad;
     // operands stored as dense K x rows matrices are read in place; the others
     // are packed (unless the caller says the workspace already holds them)
     const bool da = tma_direct_ok(d.flags & kFlagADense, d.a, d.M, d.K, d.a_plane);
     const bool db = tma_direct_ok(d.flags & kFlagBDense, d.b, d.N, d.K, d.b_plane);
+    const F32Geom g = f32_geom(d, da && db);
+    const bool skinny = f32p_skinny(d.N), sk = d.flags & kFlagStreamK, split = d.ksplit > 1;
+    if (sk && (skinny || split)) RN_FAIL(ROSNET_ERR_UNSUPPORTED, "stream-K takes 64 x 64 tiles and no split");
+    if (split && (d.ktiles_per_split < 1 || (int64_t)d.ksplit * d.ktiles_per_split < g.Kpad / f32p::BK))
+        RN_FAIL(ROSNET_ERR_UNSUPPORTED, "split does not cover the contraction");
+    float *pa = (float *)((char *)ws + g.off_pack);
+    float *pb = pa + 2 * g.Mpad * g.Kpad;
     pack_a = pack_a && !da;
     pack_b = pack_b && !db;
     const int64_t kt = (g.Kpad + f32p::PKT - 1) / f32p::PKT;
@@ -1440,13 +1449,13 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
     args.g = ga;
     args.nkt = (int)(g.Kpad / f32p::BK);
     if (d.flags & kFlagStreamK) {
-        args.sk_part = (float *)((char *)ws + g.pack_bytes);
-        args.sk_count = (int32_t *)((char *)ws + g.pack_bytes + g.part_bytes);
+        args.sk_part = (float *)((char *)ws + g.off_part);
+        args.sk_count = (int32_t *)ws;
         args.sk_maxpieces = (int32_t)g.maxpieces;
         args.sk_dp = (int32_t)g.D;
         ctas = g.G;
     }
-    if (split) args.split_part = (float *)((char *)ws + g.pack_bytes + g.part_bytes + g.count_bytes);
+    if (split) args.split_part = (float *)((char *)ws + g.off_split);
     if (before_gemm) before_gemm();
     // after a pack the GEMM's prologue may overlap it (it reads only its
     // descriptor before waiting); with no pack it is the first launch
@@ -1519,22 +1528,30 @@ bool f32p_stream_k_worth_timing(const GettDesc &d, int reduce_mode) {
 }
 
 // Workspace bytes of a packed-kind problem: its packed operands (and the
-// stream-K partial tiles and counters of the packed FP32 GEMM).
+// stream-K partial tiles and counters, or a split contraction's partial
+// results, of the packed FP32 GEMM), for any operand addresses.
 size_t tc_workspace_bytes(const GettDesc &d, int mode) {
-    if (mode == kPackedModeF32) {
-        const F32Geom g = f32_geom(d);
-        return g.pack_bytes + g.part_bytes + g.count_bytes + g.split_bytes;
-    }
+    if (mode == kPackedModeF32) return f32_geom(d).total;
     TcGeom g = tc_geom(d, mode);
     return g.narr * (g.arrA + g.arrB);
 }
 
+// The same for the operand addresses bound in d: no packed panels when both
+// operands are read in place.
+size_t tc_workspace_bytes_bound(const GettDesc &d, int mode) {
+    if (mode != kPackedModeF32) return tc_workspace_bytes(d, mode);
+    const bool da = tma_direct_ok(d.flags & kFlagADense, d.a, d.M, d.K, d.a_plane);
+    const bool db = tma_direct_ok(d.flags & kFlagBDense, d.b, d.N, d.K, d.b_plane);
+    return f32_geom(d, da && db).total;
+}
+
 // Zero what must start at zero in a fresh workspace of a packed-kind problem
-// (the stream-K tile counters; each launch leaves them at zero again).
+// (the stream-K tile counters, at its start; each launch leaves them at zero
+// again).
 void tc_workspace_clear(const GettDesc &d, int mode, void *ws, cudaStream_t s) {
     if (mode != kPackedModeF32 || !(d.flags & kFlagStreamK)) return;
     const F32Geom g = f32_geom(d);
-    RN_CHECK_CUDA(cudaMemsetAsync((char *)ws + g.pack_bytes + g.part_bytes, 0, g.count_bytes, s));
+    RN_CHECK_CUDA(cudaMemsetAsync(ws, 0, g.count_bytes, s));
 }
 
 // Enqueue pack + GEMM for one tensor-core problem.  `ga` locates the

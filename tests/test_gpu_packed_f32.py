@@ -132,8 +132,11 @@ def test_dense_operand_unaligned_rows_is_packed():
 # split over CTAs, each storing a partial result that a second kernel sums in
 # split order.  (M, N, K): the amplitude's 256 x 16 x 4096 step, ragged rows
 # and contraction, 3 columns (a B panel of 3 rows is not 16-byte aligned:
-# packed), and several row tiles.
-@pytest.mark.parametrize("mnk", [(256, 16, 4096), (300, 12, 2500), (1000, 3, 3000), (2048, 16, 1024)])
+# packed), several row tiles, a single column, and 130 rows (a second row
+# tile of 2, rows not 16-byte aligned: A packed) over a 32768-long
+# contraction split 64 ways.
+@pytest.mark.parametrize("mnk", [(256, 16, 4096), (300, 12, 2500), (1000, 3, 3000), (2048, 16, 1024),
+                                 (4096, 1, 2048), (130, 16, 32768)])
 @pytest.mark.parametrize("la", ["km", "mk"])
 def test_few_columns_split_contraction(mnk, la):
     M, N, K = mnk

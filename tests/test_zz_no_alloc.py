@@ -51,6 +51,12 @@ def _cases():
     b = W.complex_normal((16, 8, 256), 50)
     yield a, None, b, None, [1, 2], [1, 0], R.C64, R.PREC_TF32X3, 0, 1e-5
     yield a, None, b, None, [1, 2], [1, 0], R.C64, R.PREC_BF16X3, 0, 1e-4
+    # few columns and a long contraction: 128 x 16 tiles with the contraction
+    # split over CTAs, the partial results (1 MB) in the scratch after the
+    # tensor-core panels
+    a = W.complex_normal((2048, 256), 53)
+    b = W.complex_normal((2048, 16), 54)
+    yield a, None, b, None, [0], [0], R.C64, R.PREC_DEFAULT, 0, 1e-5
     a = W.complex_normal((257, 130), 43)       # ragged 128x64 tiles
     b = W.complex_normal((130, 515), 44)
     yield a, None, b, None, [1], [0], R.C64, R.PREC_DEFAULT, 0, 1e-5
