@@ -307,3 +307,23 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     a = W.complex_normal((3, 4), 1)
     _, got = run(a, None, a.T.copy(), None, [1], [0], R.C128)
     np.testing.assert_allclose(got, a @ a.T, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [R.C64, R.C128])
+@pytest.mark.parametrize("mnk", [(1, 1, 1024), (1, 1, 4096), (16, 16, 2000), (2, 3, 4097), (1, 1, 70001)])
+def test_long_contractions_into_few_entries(dtype, mnk):
+    """Outputs of at most 256 entries over K >= 1024 (a network's final
+    scalar): a cluster of CTAs per entry, products and sums in FP64, the
+    result rounded once to C's type, the same bits on every call."""
+    M, N, K = mnk
+    npt = np.complex64 if dtype == R.C64 else np.complex128
+    a = W.complex_normal((M, K), 61).astype(npt)
+    b = W.complex_normal((K, N), 62).astype(npt)
+    A, B = R.btensor(a, None, dtype), R.btensor(b, None, dtype)
+    got = R.tensordot(A, B, [1], [0]).download()
+    ref = oracle.tensordot(a, b, [1], [0])
+    # FP64 accumulation: the error is the operands' own rounding (none) and
+    # the final rounding to C's type, far below the FP32 bar
+    tol = 1e-7 if dtype == R.C64 else 1e-12
+    assert oracle.rel_frobenius(got, ref) <= tol
+    assert np.array_equal(got, R.tensordot(A, B, [1], [0]).download())
