@@ -1027,11 +1027,11 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
         s = P.side;
     }
     // patch descriptors; stage and upload only the range whose operands
-    // changed since the last call
-    const int r = P.ring;
-    P.ring = (P.ring + 1) % Plan::kRing;
-    RN_CHECK_CUDA(cudaEventSynchronize(P.ev[r]));
-    GettDesc *h = P.pinned[r];
+    // changed since the last call.  Only an upload waits (for the copy that
+    // last read the pinned staging buffer it reuses): a call whose
+    // descriptors are unchanged does not hold the host back, so the host can
+    // run many calls ahead of the device and a brief host stall leaves the
+    // device busy
     const size_t nd = P.desc_step.size();
     if (P.mirror.size() != nd) P.mirror.resize(nd);
     size_t lo = nd, hi = 0;
@@ -1051,11 +1051,15 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
     }
     P.mirror_valid = true;
     if (lo < hi) {
+        const int r = P.ring;
+        P.ring = (P.ring + 1) % Plan::kRing;
+        RN_CHECK_CUDA(cudaEventSynchronize(P.ev[r]));
+        GettDesc *h = P.pinned[r];
         std::copy(P.mirror.begin() + lo, P.mirror.begin() + hi, h + lo);
         RN_CHECK_CUDA(cudaMemcpyAsync((GettDesc *)P.descs.p + lo, h + lo, (hi - lo) * sizeof(GettDesc),
                                       cudaMemcpyHostToDevice, s));
+        RN_CHECK_CUDA(cudaEventRecord(P.ev[r], s));
     }
-    RN_CHECK_CUDA(cudaEventRecord(P.ev[r], s));
 
     const bool timing = (P.flags & ROSNET_OPT_TIMING) && P.heavy >= 0;
     int slot = -1;
