@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <functional>
 #include <cstring>
 #include <mutex>
@@ -560,8 +561,14 @@ __global__ void __cluster_dims__(kDotCTAs, 1, 1) __launch_bounds__(256)
 // as large as the tensor); the other tables hold at most 4 entries.  Planes
 // that do not start on 16-byte boundaries are read and written element by
 // element instead.
+// Whether a gate kind's CTAs loop over runs of rows (the kinds with a side
+// of 4, whose 90-128 registers fit at most two CTAs per SM) rather than take
+// one run per thread.
+constexpr bool gate_loops(int nk, int nn) { return nk == 4 || nn == 4; }
+
 template <int NK, int NN>
 __global__ void __launch_bounds__(256) gett_gate_kernel(const __grid_constant__ GroupArgs g) {
+    if constexpr (!gate_loops(NK, NN)) {   // one run of rows per thread
     constexpr int V = NK * NN >= 8 ? 4 : 8;   // rows per thread
     constexpr int NV = V / 4;                 // float4 per plane per row run
     __shared__ GettDesc sd;
@@ -685,6 +692,146 @@ __global__ void __launch_bounds__(256) gett_gate_kernel(const __grid_constant__ 
                 C[cm + e + cp] = ei[e];
             }
         }
+    }
+    } else {   // the problem's resident CTAs loop over the runs
+    constexpr int V = NK * NN >= 8 ? 4 : 8;   // rows per thread
+    constexpr int NV = V / 4;                 // float4 per plane per row run
+    constexpr int kRecMax = 1 + 3 * 128;      // a mode record of up to 128 modes in shared memory
+    __shared__ GettDesc sd;
+    __shared__ int64_t rec[kRecMax];
+    grid_dep_launch();
+    if (threadIdx.x < 32) load_desc(g, sd);
+    __syncthreads();
+    // the M class's mode record into shared memory (read by every run; a
+    // longer one is read from global memory)
+    const int64_t nrec = 1 + 3 * __ldg(sd.offAM);
+    const int64_t *rp = nrec <= kRecMax ? rec : sd.offAM;
+    if (nrec <= kRecMax)
+        for (int e = threadIdx.x; e < nrec; e += 256) rec[e] = __ldg(sd.offAM + e);
+    int64_t ak[NK], cn[NN], bo[NK][NN];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) ak[k] = __ldg(sd.offAK + k);
+#pragma unroll
+    for (int n = 0; n < NN; ++n) cn[n] = __ldg(sd.offCN + n);
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int n = 0; n < NN; ++n) bo[k][n] = __ldg(sd.offBK + k) + __ldg(sd.offBN + n);
+    __syncthreads();
+    grid_dep_wait();   // A and B may be the previous kernel's results
+    const float *__restrict__ A = (const float *)sd.a;
+    const float *__restrict__ B = (const float *)sd.b;
+    float gr[NK][NN], gi[NK][NN];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            gr[k][n] = B[bo[k][n]];
+            gi[k][n] = B[bo[k][n] + sd.b_plane];
+        }
+    float *C = (float *)sd.c;
+    const int64_t cp = sd.c_plane;
+    // every offset is a multiple of 4 elements (the vector flags); 16-byte
+    // accesses need the planes to start on 16-byte boundaries too
+    const bool vec = (((uintptr_t)A | (uintptr_t)C) & 15) == 0 && ((sd.a_plane | cp) & 3) == 0;
+    // the problem's CTAs stay resident (as many as fit at once) and each
+    // thread takes runs t, t + stride, ... of V rows: the descriptor, the
+    // record and the gate are read once, and the loads of the next run
+    // follow the stores of the last without a CTA's prologue between them
+    const int64_t stride = sd.tiles_m * 256;
+    for (int64_t t = ((int64_t)blockIdx.x - sd.tile_begin) * 256 + threadIdx.x; t * V < sd.M; t += stride) {
+        const int64_t m0 = t * V;
+        // offsets of row m0 in A and C from the mode record of the M class
+        int64_t am = 0, cm = 0, r = m0;
+        for (int jm = (int)rp[0] - 1; jm >= 0; --jm) {
+            const int64_t ext = rp[1 + 3 * jm];
+            int64_t dg;
+            if ((ext & (ext - 1)) == 0) {
+                dg = r & (ext - 1);
+                r >>= __popcll(ext - 1);
+            } else {
+                dg = r % ext;
+                r /= ext;
+            }
+            am += dg * rp[2 + 3 * jm];
+            cm += dg * rp[3 + 3 * jm];
+        }
+        float xr[NK][V], xi[NK][V];
+        if (vec) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k)
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    const float4 rr = __ldcs(reinterpret_cast<const float4 *>(A + am + ak[k]) + q);
+                    const float4 ii = __ldcs(reinterpret_cast<const float4 *>(A + am + ak[k] + sd.a_plane) + q);
+                    xr[k][4 * q] = rr.x; xr[k][4 * q + 1] = rr.y; xr[k][4 * q + 2] = rr.z; xr[k][4 * q + 3] = rr.w;
+                    xi[k][4 * q] = ii.x; xi[k][4 * q + 1] = ii.y; xi[k][4 * q + 2] = ii.z; xi[k][4 * q + 3] = ii.w;
+                }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NK; ++k)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    xr[k][v] = A[am + ak[k] + v];
+                    xi[k][v] = A[am + ak[k] + v + sd.a_plane];
+                }
+        }
+        float cr[NN][V], ci[NN][V];
+#pragma unroll
+        for (int n = 0; n < NN; ++n)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int k = 0; k < NK; ++k) cmac(sr, si, xr[k][v], xi[k][v], gr[k][n], gi[k][n]);
+                cr[n][v] = sr;
+                ci[n][v] = si;
+            }
+        if (sd.flags & kFlagCMVec) {   // each n: V consecutive outputs along m
+#pragma unroll
+            for (int n = 0; n < NN; ++n) {
+                float *o = C + cm + cn[n];
+                if (vec) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        __stcs(reinterpret_cast<float4 *>(o) + q,
+                               make_float4(cr[n][4 * q], cr[n][4 * q + 1], cr[n][4 * q + 2], cr[n][4 * q + 3]));
+                        __stcs(reinterpret_cast<float4 *>(o + cp) + q,
+                               make_float4(ci[n][4 * q], ci[n][4 * q + 1], ci[n][4 * q + 2], ci[n][4 * q + 3]));
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        o[v] = cr[n][v];
+                        o[v + cp] = ci[n][v];
+                    }
+                }
+            }
+        } else {                       // n innermost: the V x NN block is contiguous
+            constexpr int E = V * NN;
+            float er[E], ei[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                er[e] = cr[e % NN][e / NN];
+                ei[e] = ci[e % NN][e / NN];
+            }
+            if (vec) {
+#pragma unroll
+                for (int q = 0; q < E / 4; ++q) {
+                    __stcs(reinterpret_cast<float4 *>(C + cm) + q,
+                           make_float4(er[4 * q], er[4 * q + 1], er[4 * q + 2], er[4 * q + 3]));
+                    __stcs(reinterpret_cast<float4 *>(C + cm + cp) + q,
+                           make_float4(ei[4 * q], ei[4 * q + 1], ei[4 * q + 2], ei[4 * q + 3]));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    C[cm + e] = er[e];
+                    C[cm + e + cp] = ei[e];
+                }
+            }
+        }
+    }
     }
 }
 
@@ -1269,6 +1416,41 @@ void launch_tc_problem(int mode, const GettDesc &d, const GroupArgs &ga, void *w
                        bool pack_a, bool pack_b, const std::function<void()> &before_gemm = {},
                        bool pdl = true);
 
+// The CTAs a gate problem launches at most.  For the looping kinds (a side
+// of 4: at most two CTAs fit on an SM), as many as are resident at once,
+// each looping over its runs of rows (measured on [2]^28: 0.72 -> 0.87 of the
+// HBM copy rate for a two-qubit gate); for the others one CTA per 256 runs,
+// which keeps more loads in flight for the one-qubit gates (0.87 / 0.94
+// against 0.79 / 0.85 looping).
+static int64_t gate_resident_ctas(int kind) {
+    static std::atomic<int64_t> cache[9];
+    const int i = kind - kKindGateBase;
+    const int64_t c = cache[i].load(std::memory_order_relaxed);
+    if (c) return c;
+    const void *fn = nullptr;
+    switch (i) {
+        case 0: fn = (const void *)gett_gate_kernel<1, 1>; break;
+        case 1: fn = (const void *)gett_gate_kernel<1, 2>; break;
+        case 2: fn = (const void *)gett_gate_kernel<1, 4>; break;
+        case 3: fn = (const void *)gett_gate_kernel<2, 1>; break;
+        case 4: fn = (const void *)gett_gate_kernel<2, 2>; break;
+        case 5: fn = (const void *)gett_gate_kernel<2, 4>; break;
+        case 6: fn = (const void *)gett_gate_kernel<4, 1>; break;
+        case 7: fn = (const void *)gett_gate_kernel<4, 2>; break;
+        default: fn = (const void *)gett_gate_kernel<4, 4>; break;
+    }
+    const int lk = i / 3, ln = i % 3;   // log2 K, log2 N
+    if (!gate_loops(1 << lk, 1 << ln)) {
+        cache[i].store(int64_t(1) << 40, std::memory_order_relaxed);
+        return int64_t(1) << 40;
+    }
+    int per = 0;
+    RN_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0));
+    const int64_t v = (int64_t)std::max(per, 1) * num_sms();
+    cache[i].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
     const int64_t kSMs = num_sms();
     d.ksplit = 1;
@@ -1294,7 +1476,8 @@ void choose_kernel(GettDesc &d, int dtype, int precision, int reduce_mode) {
         if ((e.flags & kFlagAMVec) && (e.flags & (kFlagCMVec | kFlagCNInner))) {
             d = e;
             d.kind = kKindGateBase + 3 * gate_log2(d.K) + gate_log2(d.N);
-            d.tiles_m = (d.M + 256 * gate_rows(d.kind) - 1) / (256 * gate_rows(d.kind));
+            d.tiles_m = std::min<int64_t>((d.M + 256 * gate_rows(d.kind) - 1) / (256 * gate_rows(d.kind)),
+                                          gate_resident_ctas(d.kind));
             d.tiles_n = 1;
             return;
         }
