@@ -173,3 +173,41 @@ def test_few_columns_sequential_mode_is_not_split():
     recs = R.timing_drain()
     assert recs and recs[-1][3] != 10, recs[-1:]
     assert oracle.rel_frobenius(got, ref) <= 1e-5
+
+
+def _random_gemm_shapes(seed, n):
+    """Seeded shapes that reach each FP32 GEMM schedule: one CTA per 64 x 64
+    tile, stream-K where 149-250 tiles load the SMs unevenly (one whole tile
+    per SM, the rest split), and the few-column split contraction."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        kind = i % 3
+        if kind == 0:      # many tiles
+            M, N, K = int(rng.integers(700, 2100)), int(rng.integers(300, 700)), int(rng.integers(128, 700))
+        elif kind == 1:    # 149-250 tiles of 64 x 64, deep enough to split
+            M = int(rng.integers(9, 13)) * 64 + int(rng.integers(0, 64))
+            N = int(rng.integers(15, 18)) * 64 - int(rng.integers(0, 64))
+            K = int(rng.integers(300, 1200))
+        else:              # few columns, long contraction
+            M, N, K = int(rng.integers(128, 1500)), int(rng.integers(1, 17)), int(rng.integers(2048, 9000))
+        out.append((M, N, K))
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_random_shapes_every_schedule(seed):
+    """Random ragged shapes through the heuristic's choice and through the
+    autotuner's (which also times the other schedules), both against the
+    oracle; the heuristic's result is bitwise repeatable."""
+    for M, N, K in _random_gemm_shapes(seed, 6):
+        a = W.complex_normal((K, M), 100 + M).astype(np.complex64)
+        b = W.complex_normal((K, N), 200 + N).astype(np.complex64)
+        A, B = R.btensor(a), R.btensor(b)
+        ref = oracle.tensordot(a, b, [0], [0])
+        got = R.tensordot(A, B, [0], [0]).download()
+        assert oracle.rel_frobenius(got, ref) <= 1e-5, (M, N, K)
+        assert np.array_equal(got, R.tensordot(A, B, [0], [0]).download()), (M, N, K)
+        tuned = R.contract([A, B], [(0, 1), (0, 2)], [1, 2], [(0, 1)], flags=R.OPT_AUTOTUNE).download()
+        assert oracle.rel_frobenius(tuned, ref) <= 1e-5, (M, N, K)
+    R.release_plans()
