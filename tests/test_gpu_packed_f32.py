@@ -132,11 +132,12 @@ def test_dense_operand_unaligned_rows_is_packed():
 # split over CTAs, each storing a partial result that a second kernel sums in
 # split order.  (M, N, K): the amplitude's 256 x 16 x 4096 step, ragged rows
 # and contraction, 3 columns (a B panel of 3 rows is not 16-byte aligned:
-# packed), several row tiles, a single column, and 130 rows (a second row
-# tile of 2, rows not 16-byte aligned: A packed) over a 32768-long
-# contraction split 64 ways.
+# packed), several row tiles, a single column, 130 rows (a second row tile
+# of 2, rows not 16-byte aligned: A packed) over a 32768-long contraction
+# split 64 ways, and 313 row tiles (enough CTAs unsplit: C staged through
+# shared memory by the four k sets).
 @pytest.mark.parametrize("mnk", [(256, 16, 4096), (300, 12, 2500), (1000, 3, 3000), (2048, 16, 1024),
-                                 (4096, 1, 2048), (130, 16, 32768)])
+                                 (4096, 1, 2048), (130, 16, 32768), (40000, 8, 600)])
 @pytest.mark.parametrize("la", ["km", "mk"])
 def test_few_columns_split_contraction(mnk, la):
     M, N, K = mnk
