@@ -821,6 +821,10 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
         u1 = (cta / ksplit) * nkt + kt1;
     }
     const int nitems = (int)(u1 - u0);
+    if (tid == 0) {   // the tensor maps into the TMA unit's cache while the previous kernel ends
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&p.mapB)) : "memory");
+    }
     grid_dep_wait();   // operands may be the previous kernel's output
     // the output offsets of a tile's rows and columns into shared memory, one
     // per thread (-1 past M or N): C's, or the row-major (m, n) of a partial
