@@ -77,10 +77,11 @@ template <int MODE>
 struct Cfg {
     static constexpr int ESZ = MODE == kBF16x3 ? 2 : 4;        // bytes per packed element
     static constexpr int BK = ROWB / ESZ;                      // k per stage (16 or 32)
-    static constexpr int NARR = MODE == kTF32 ? 2 : 4;         // arrays per operand
+    static constexpr int NARR = MODE == kTF32 ? 2 : 4;         // arrays of A
+    static constexpr int NARR_B = MODE == kTF32 ? 3 : 4;       // arrays of B (TF32: re, im, -re)
     static constexpr int ARR_A = BM * ROWB, ARR_B = BN * ROWB;   // bytes of one array's box
-    static constexpr int STAGE = NARR * (ARR_A + ARR_B);
-    static constexpr int STAGES = MODE == kTF32 ? 6 : 3;
+    static constexpr int STAGE = NARR * ARR_A + NARR_B * ARR_B;
+    static constexpr int STAGES = MODE == kTF32 ? 5 : 3;
     static constexpr int KSTEPS = BK / (32 / ESZ);             // MMAs per product per stage
     static constexpr int CH_STAGES = chunk_k(MODE) / BK;       // stages per chunk
     static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
@@ -197,14 +198,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, M=128, N=128, both K-major.
+// Instruction descriptor: FP32 accumulator, M=128, N=128 (or n), both K-major.
 template <int MODE>
-__host__ __device__ constexpr uint32_t idesc(bool negate_a) {
+__host__ __device__ constexpr uint32_t idesc(bool negate_a, int n = BN) {
     return (1u << 4)                                          // D: f32
            | ((MODE == kBF16x3 ? 1u : 2u) << 7)               // A: bf16 (kind::f16) / tf32
            | ((MODE == kBF16x3 ? 1u : 2u) << 10)              // B
            | ((negate_a ? 1u : 0u) << 13)                     // negate A
-           | ((uint32_t)(BN >> 3) << 17)                      // N
+           | ((uint32_t)(n >> 3) << 17)                       // N
            | ((uint32_t)(BM >> 4) << 24);                     // M
 }
 
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(const __grid_constant__ Gr
             const float x = tr[p][kk][rr];
             if (MODE == kTF32) {
                 reinterpret_cast<uint32_t *>(out + p * arr)[e] = to_tf32(x);
+                if (which == 1 && p == 0) reinterpret_cast<uint32_t *>(out + 2 * arr)[e] = to_tf32(-x);
             } else if (MODE == kTF32x3) {
                 const uint32_t big = to_tf32(x);
                 reinterpret_cast<uint32_t *>(out + (2 * p) * arr)[e] = big;
@@ -388,10 +390,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                     const uint32_t sa = su32(dsm + (size_t)s * C_::STAGE);
                     const uint32_t sb = sa + NARR * C_::ARR_A;
 #pragma unroll
-                    for (int a = 0; a < NARR; ++a) {
+                    for (int a = 0; a < NARR; ++a)
                         tma_load_2d(sa + a * C_::ARR_A, &p.mapA[a], kt * BK, (int)m0, &full_bar[s]);
+#pragma unroll
+                    for (int a = 0; a < C_::NARR_B; ++a)
                         tma_load_2d(sb + a * C_::ARR_B, &p.mapB[a], kt * BK, (int)n0, &full_bar[s]);
-                    }
                     issued = g + 1;
                 }
             }
@@ -438,11 +441,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                             if (ks == C_::KSTEPS - 1)
                                 ready = mbar_try(&full_bar[(g + 1) % STAGES], ((g + 1) / STAGES) & 1);
                             if (MODE == kTF32) {
-                                // arrays: 0 = re, 1 = im
-                                mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), acc);
-                                mma<MODE>(dr, A_(1), B_(1), idesc<MODE>(true), 1u);
-                                mma<MODE>(di, A_(0), B_(1), idesc<MODE>(false), acc);
-                                mma<MODE>(di, A_(1), B_(0), idesc<MODE>(false), 1u);
+                                // A arrays: 0 = re, 1 = im; B arrays: 0 = re, 1 = im, 2 = -re.
+                                // [dr | di] (256 columns) += A_re [B_re | B_im], then
+                                // (-A_im) [B_im | -B_re]
+                                mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false, 2 * BN), acc);
+                                mma<MODE>(dr, A_(1), B_(1), idesc<MODE>(true, 2 * BN), 1u);
                             } else {
                                 // arrays: 0 = re big/hi, 1 = re small/lo, 2 = im big/hi, 3 = im small/lo
                                 mma<MODE>(dr, A_(0), B_(1), idesc<MODE>(false), acc);
@@ -1241,7 +1244,7 @@ int tc_tile_n() { return tc::BN; }
 namespace {
 
 struct TcGeom {
-    int esz, bk, narr;
+    int esz, bk, narr, narr_b;
     int64_t Mpad, Npad, Kpad;
     size_t arrA, arrB;   // bytes of one packed array
 };
@@ -1251,6 +1254,7 @@ TcGeom tc_geom(const GettDesc &d, int mode) {
     g.esz = mode == tc::kBF16x3 ? 2 : 4;
     g.bk = tc::ROWB / g.esz;
     g.narr = mode == tc::kTF32 ? 2 : 4;
+    g.narr_b = mode == tc::kTF32 ? 3 : 4;
     g.Mpad = (d.M + tc::BM - 1) / tc::BM * tc::BM;
     g.Npad = (d.N + tc::BN - 1) / tc::BN * tc::BN;
     const int64_t kq = 32;   // the pack kernel's k tile; a multiple of bk
@@ -1312,10 +1316,8 @@ void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, c
     }
     tc::TcArgs args;
     memset(&args, 0, sizeof(args));
-    for (int a = 0; a < g.narr; ++a) {
-        make_map(&args.mapA[a], pa + a * g.arrA, g.Mpad, g.Kpad, g.esz);
-        make_map(&args.mapB[a], pb + a * g.arrB, g.Npad, g.Kpad, g.esz);
-    }
+    for (int a = 0; a < g.narr; ++a) make_map(&args.mapA[a], pa + a * g.arrA, g.Mpad, g.Kpad, g.esz);
+    for (int a = 0; a < g.narr_b; ++a) make_map(&args.mapB[a], pb + a * g.arrB, g.Npad, g.Kpad, g.esz);
     args.g = ga;
     args.nkt = (int)(g.Kpad / g.bk);
     if (before_gemm) before_gemm();
@@ -1537,7 +1539,7 @@ bool f32p_stream_k_worth_timing(const GettDesc &d, int reduce_mode) {
 size_t tc_workspace_bytes(const GettDesc &d, int mode) {
     if (mode == kPackedModeF32) return f32_geom(d).total;
     TcGeom g = tc_geom(d, mode);
-    return g.narr * (g.arrA + g.arrB);
+    return g.narr * g.arrA + g.narr_b * g.arrB;
 }
 
 // The same for the operand addresses bound in d: no packed panels when both
