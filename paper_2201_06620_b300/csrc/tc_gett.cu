@@ -79,6 +79,10 @@ struct Cfg {
     static constexpr int BK = ROWB / ESZ;                      // k per stage (16 or 32)
     static constexpr int NARR = MODE == kTF32 ? 2 : 4;         // arrays of A
     static constexpr int NARR_B = MODE == kTF32 ? 3 : 4;       // arrays of B (TF32: re, im, -re)
+    // stage position of B's array a: in the split modes (re hi, re lo, im hi,
+    // im lo) are staged as (re lo, im lo, re hi, im hi), so that [re lo | im
+    // lo] and [re hi | im hi] are contiguous N = 256 operand windows
+    static constexpr int bpos(int a) { return MODE == kTF32 ? a : (a == 0 ? 2 : a == 1 ? 0 : a == 2 ? 3 : 1); }
     static constexpr int ARR_A = BM * ROWB, ARR_B = BN * ROWB;   // bytes of one array's box
     static constexpr int STAGE = NARR * ARR_A + NARR_B * ARR_B;
     static constexpr int STAGES = MODE == kTF32 ? 5 : 3;
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                         tma_load_2d(sa + a * C_::ARR_A, &p.mapA[a], kt * BK, (int)m0, &full_bar[s]);
 #pragma unroll
                     for (int a = 0; a < C_::NARR_B; ++a)
-                        tma_load_2d(sb + a * C_::ARR_B, &p.mapB[a], kt * BK, (int)n0, &full_bar[s]);
+                        tma_load_2d(sb + C_::bpos(a) * C_::ARR_B, &p.mapB[a], kt * BK, (int)n0, &full_bar[s]);
                     issued = g + 1;
                 }
             }
@@ -447,19 +451,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                                 mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false, 2 * BN), acc);
                                 mma<MODE>(dr, A_(1), B_(1), idesc<MODE>(true, 2 * BN), 1u);
                             } else {
-                                // arrays: 0 = re big/hi, 1 = re small/lo, 2 = im big/hi, 3 = im small/lo
-                                mma<MODE>(dr, A_(0), B_(1), idesc<MODE>(false), acc);
-                                mma<MODE>(dr, A_(1), B_(0), idesc<MODE>(false), 1u);
-                                mma<MODE>(dr, A_(2), B_(3), idesc<MODE>(true), 1u);
-                                mma<MODE>(dr, A_(3), B_(2), idesc<MODE>(true), 1u);
-                                mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false), 1u);
-                                mma<MODE>(dr, A_(2), B_(2), idesc<MODE>(true), 1u);
-                                mma<MODE>(di, A_(0), B_(3), idesc<MODE>(false), acc);
-                                mma<MODE>(di, A_(1), B_(2), idesc<MODE>(false), 1u);
-                                mma<MODE>(di, A_(2), B_(1), idesc<MODE>(false), 1u);
-                                mma<MODE>(di, A_(3), B_(0), idesc<MODE>(false), 1u);
-                                mma<MODE>(di, A_(0), B_(2), idesc<MODE>(false), 1u);
-                                mma<MODE>(di, A_(2), B_(0), idesc<MODE>(false), 1u);
+                                // A arrays: 0 = re big/hi, 1 = re small/lo, 2 = im big/hi,
+                                // 3 = im small/lo; B the same arrays at stage positions
+                                // bpos: B_(0) = [B1 | B3], B_(2) = [B0 | B2] as N = 256
+                                // windows, B_(1) = B3, B_(3) = B2, B_(0) = B1, B_(2) = B0
+                                // as N = 128 ones.  The positive products of both parts
+                                // go out as N = 256 MMAs into [dr | di], each part's small
+                                // terms before its large ones (the order of the twelve
+                                // N = 128 products: dr A0B1, A1B0, -A2B3, -A3B2, A0B0,
+                                // -A2B2; di A0B3, A1B2, A2B1, A3B0, A0B2, A2B0)
+                                mma<MODE>(dr, A_(0), B_(0), idesc<MODE>(false, 2 * BN), acc);   // A0 [B1 | B3]
+                                mma<MODE>(dr, A_(1), B_(2), idesc<MODE>(false, 2 * BN), 1u);    // A1 [B0 | B2]
+                                mma<MODE>(dr, A_(2), B_(1), idesc<MODE>(true), 1u);             // -A2 B3
+                                mma<MODE>(di, A_(2), B_(0), idesc<MODE>(false), 1u);            // A2 B1
+                                mma<MODE>(dr, A_(3), B_(3), idesc<MODE>(true), 1u);             // -A3 B2
+                                mma<MODE>(di, A_(3), B_(2), idesc<MODE>(false), 1u);            // A3 B0
+                                mma<MODE>(dr, A_(0), B_(2), idesc<MODE>(false, 2 * BN), 1u);    // A0 [B0 | B2]
+                                mma<MODE>(dr, A_(2), B_(3), idesc<MODE>(true), 1u);             // -A2 B2
+                                mma<MODE>(di, A_(2), B_(2), idesc<MODE>(false), 1u);            // A2 B0
                             }
                         }
                         mma_commit(&empty_bar[s]);   // frees the stage once these MMAs are done
