@@ -911,7 +911,11 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
     // packed two-wide FMA: B's real and imaginary rows give the column pairs
     // as loaded, A's entries are duplicated into pairs.  The same FMAs in the
     // same order as four scalar FMAs per product (bitwise equal results) in
-    // half the issue slots (57.4 against 55.8 TFLOP/s on 1024 x 32768 x 1024)
+    // half the issue slots (57.4 against 55.8 TFLOP/s on 1024 x 32768 x 1024).
+    // A's real parts go out for every row before its imaginary parts, so the
+    // two FMAs into one accumulator pair are a row pass apart instead of
+    // adjacent (4096 x 256 x 256: 49.4 -> 47.5 us; each accumulator's order
+    // unchanged)
     auto macs = [&](const float *xr, const float *xi, const float *yr, const float *yi) {
         float2 br2[TN / 2], bi2[TN / 2], nbi2[TN / 2];
 #pragma unroll
@@ -921,15 +925,26 @@ __global__ void __launch_bounds__(C::NT, 2) f32_gemm_kernel(const __grid_constan
             nbi2[jp] = make_float2(-yi[2 * jp], -yi[2 * jp + 1]);
         }
 #pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            const float2 ar2 = make_float2(xr[i], xr[i]), ai2 = make_float2(xi[i], xi[i]);
+        for (int i = 0; i < TM; ++i) {   // the real parts of A first, for every row
+            const float2 ar2 = make_float2(xr[i], xr[i]);
 #pragma unroll
             for (int jp = 0; jp < TN / 2; ++jp) {
                 float2 r = make_float2(cr[i][2 * jp], cr[i][2 * jp + 1]);
                 float2 q = make_float2(ci[i][2 * jp], ci[i][2 * jp + 1]);
                 r = __ffma2_rn(ar2, br2[jp], r);
-                r = __ffma2_rn(ai2, nbi2[jp], r);
                 q = __ffma2_rn(ar2, bi2[jp], q);
+                cr[i][2 * jp] = r.x; cr[i][2 * jp + 1] = r.y;
+                ci[i][2 * jp] = q.x; ci[i][2 * jp + 1] = q.y;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {   // then the imaginary parts
+            const float2 ai2 = make_float2(xi[i], xi[i]);
+#pragma unroll
+            for (int jp = 0; jp < TN / 2; ++jp) {
+                float2 r = make_float2(cr[i][2 * jp], cr[i][2 * jp + 1]);
+                float2 q = make_float2(ci[i][2 * jp], ci[i][2 * jp + 1]);
+                r = __ffma2_rn(ai2, nbi2[jp], r);
                 q = __ffma2_rn(ai2, br2[jp], q);
                 cr[i][2 * jp] = r.x; cr[i][2 * jp + 1] = r.y;
                 ci[i][2 * jp] = q.x; ci[i][2 * jp + 1] = q.y;
