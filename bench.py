@@ -43,7 +43,8 @@ KERNEL_NAMES = {
     2: "gett_tiled_kernel 64x64 (offset-table gathers, FFMA)",
     3: "gett_tiled_kernel 128x64 (offset-table gathers, FFMA)",
     10: "f32_gemm_kernel (TMA-fed FFMA 64x64x32, two k sets of 8x4-output threads; dense operands read in "
-        "place; stream-K (4x4 outputs a thread) when tiles fill the slots poorly)",
+        "place; stream-K when tiles load the SMs unevenly; 128x16 tiles with a split contraction for few "
+        "columns)",
     5: "tc_gemm_kernel TF32 (tcgen05)", 6: "tc_gemm_kernel 3xTF32 (tcgen05)", 7: "tc_gemm_kernel 3xBF16 (tcgen05)",
 }
 METRIC = "amplitudes/s"

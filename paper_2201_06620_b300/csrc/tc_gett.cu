@@ -617,8 +617,8 @@ struct Cfg {
     static_assert(((size_t)(KG - 1) * 2 * TM * TN * GX * GY + 2 * PLANE_MAX) * 4 <= RING_BYTES,
                   "the sets' tiles and both staged planes must fit the ring");
 };
-// One CTA per tile: two sets of 8 x 16 threads of 8 x 4 outputs, each set
-// half of every stage's k rows.  A thread reads 96 bytes of fragments from
+// One CTA per tile, and stream-K: two sets of 8 x 16 threads of 8 x 4
+// outputs, each set half of every stage's k rows.  A thread reads 96 bytes of fragments from
 // shared memory per 128 FMAs, where 4 x 4 outputs read 64 per 64 and keep
 // shared memory as busy as the FMA pipe: 61.0 against 57.5 TFLOP/s on
 // 1024 x 32768 x 1024, 49.3 against 51.2 us on 4096 x 256 x 256.
