@@ -1589,11 +1589,12 @@ size_t desc_part_bytes(const GettDesc &d, int dtype) {
 template <typename T, int BM, int BN>
 static void launch_direct(dim3 grid, const GroupArgs &ga, cudaStream_t s, bool pdl) {
     using Cfg = DirectCfg<T, BM, BN>;
-    static bool attr_set = false;   // once per process (one device)
-    if (!attr_set) {
+    static std::atomic<uint64_t> done{0};   // once per device
+    uint64_t bit;
+    if (!attrs_set(done, &bit)) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(gett_direct_kernel<T, BM, BN>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
-        attr_set = true;
+        done.fetch_or(bit, std::memory_order_release);
     }
     launch_pdl(gett_direct_kernel<T, BM, BN>, grid, 256, Cfg::smem, s, pdl, ga);
 }
@@ -1601,11 +1602,12 @@ static void launch_direct(dim3 grid, const GroupArgs &ga, cudaStream_t s, bool p
 template <typename T, int BM, int BN, int BK>
 static void launch_tiled(dim3 grid, const GroupArgs &ga, cudaStream_t s, bool pdl) {
     using Cfg = TiledCfg<T, BM, BN, BK, kTiledStages>;
-    static bool attr_set = false;   // once per process (one device)
-    if (!attr_set) {
+    static std::atomic<uint64_t> done{0};   // once per device
+    uint64_t bit;
+    if (!attrs_set(done, &bit)) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem));
-        attr_set = true;
+        done.fetch_or(bit, std::memory_order_release);
     }
     launch_pdl(gett_tiled_kernel<T, BM, BN, BK, kTiledStages>, grid, 256, Cfg::smem, s, pdl, ga);
 }

@@ -56,6 +56,17 @@ extern std::atomic<int64_t> g_launches;
 // queried once per device).  Grid sizes and the split heuristics scale with it.
 int num_sms();
 
+// A kernel's function attributes (its dynamic shared-memory limit) are set
+// per device: `done` holds one bit per device index on which they are set.
+// Returns the current device's bit, 0 if it is not set yet (then set the
+// attributes and or the bit into `done`).  Setting them twice is harmless.
+inline uint64_t attrs_set(const std::atomic<uint64_t> &done, uint64_t *bit) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 63;
+    *bit = uint64_t(1) << dev;
+    return done.load(std::memory_order_acquire) & *bit;
+}
+
 // Read and clear the device status word written by kernels whose bounded
 // waits gave up (0 = none).
 int32_t take_device_status();

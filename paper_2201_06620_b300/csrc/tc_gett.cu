@@ -1323,11 +1323,12 @@ template <int MODE>
 void launch_mode(const GroupArgs &ga, const TcGeom &g, void *ws, int64_t ctas, cudaStream_t s,
                  bool pack_a, bool pack_b, const std::function<void()> &before_gemm) {
     using C_ = tc::Cfg<MODE>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<uint64_t> done{0};   // once per device
+    uint64_t bit;
+    if (!attrs_set(done, &bit)) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(tc::tc_gemm_kernel<MODE>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_::SMEM));
-        attr_set = true;
+        done.fetch_or(bit, std::memory_order_release);
     }
     unsigned char *pa = (unsigned char *)ws;
     unsigned char *pb = pa + g.narr * g.arrA;
@@ -1438,15 +1439,16 @@ void launch_f32(const GroupArgs &ga, const GettDesc &d, void *ws, int64_t ctas, 
                 bool pack_b, const std::function<void()> &before_gemm, bool pdl) {
     using f32p::Tile8x4;
     using f32p::TileSkinny;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<uint64_t> done{0};   // once per device
+    uint64_t bit;
+    if (!attrs_set(done, &bit)) {
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile8x4, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile8x4::SMEM));
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<Tile8x4, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile8x4::SMEM));
         RN_CHECK_CUDA(cudaFuncSetAttribute(f32p::f32_gemm_kernel<TileSkinny, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileSkinny::SMEM));
-        attr_set = true;
+        done.fetch_or(bit, std::memory_order_release);
     }
     // operands stored as dense K x rows matrices are read in place; the others
     // are packed (unless the caller says the workspace already holds them)
