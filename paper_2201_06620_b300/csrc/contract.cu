@@ -111,11 +111,18 @@ struct Plan {
     std::vector<Launch> launches;
     std::vector<int> desc_step;       // desc slot -> step index
     std::vector<GettDesc> slot_desc;  // desc slot -> static descriptor fields
-    // pinned staging ring for descriptor uploads
-    static constexpr int kRing = 4;
+    // pinned staging rings for descriptor uploads: kRing slots that hold any
+    // changed range, and kSmallRing slots of kSmall descriptors for the usual
+    // case of a few (a call's new output changes the final step's only), so
+    // that a call uploading those waits for the copy kSmallRing calls back:
+    // the host may run that far ahead of the device
+    static constexpr int kRing = 4, kSmallRing = 64, kSmall = 8;
     GettDesc *pinned[kRing] = {nullptr};
     cudaEvent_t ev[kRing] = {nullptr};
     int ring = 0;
+    GettDesc *pinned_small = nullptr;   // [kSmallRing][kSmall]
+    cudaEvent_t ev_small[kSmallRing] = {nullptr};
+    int ring_small = 0;
     cudaGraphExec_t graph = nullptr;
     cudaGraph_t graph_src = nullptr;           // kept for event-node updates
     // graphs cannot be captured on the legacy default stream: a plan called
@@ -159,6 +166,9 @@ struct Plan {
             if (ev[i]) { cudaEventSynchronize(ev[i]); cudaEventDestroy(ev[i]); }
             if (pinned[i]) cudaFreeHost(pinned[i]);
         }
+        for (cudaEvent_t &e : ev_small)
+            if (e) { cudaEventSynchronize(e); cudaEventDestroy(e); }
+        if (pinned_small) cudaFreeHost(pinned_small);
         if (graph) cudaGraphExecDestroy(graph);
         if (graph_src) cudaGraphDestroy(graph_src);
         if (host_tables) cudaFreeHost(host_tables);
@@ -924,6 +934,9 @@ std::unique_ptr<Plan> build_plan(int nnet, const rosnet_network *nets, const ros
         RN_CHECK_CUDA(cudaMallocHost((void **)&plan->pinned[r], nd * sizeof(GettDesc)));
         RN_CHECK_CUDA(cudaEventCreateWithFlags(&plan->ev[r], cudaEventDisableTiming));
     }
+    RN_CHECK_CUDA(cudaMallocHost((void **)&plan->pinned_small,
+                                 (size_t)Plan::kSmallRing * Plan::kSmall * sizeof(GettDesc)));
+    for (cudaEvent_t &e : plan->ev_small) RN_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return plan;
 }
 
@@ -941,6 +954,8 @@ size_t spill_plan(Plan &P, cudaStream_t s) {
     if (P.side) RN_CHECK_CUDA(cudaStreamSynchronize(P.side));
     for (int i = 0; i < Plan::kRing; ++i)
         if (P.ev[i]) RN_CHECK_CUDA(cudaEventSynchronize(P.ev[i]));
+    for (cudaEvent_t e : P.ev_small)
+        if (e) RN_CHECK_CUDA(cudaEventSynchronize(e));
     if (P.tables.bytes) {
         if (!P.host_tables) RN_CHECK_CUDA(cudaMallocHost(&P.host_tables, P.tables.bytes));
         RN_CHECK_CUDA(cudaMemcpy(P.host_tables, P.tables.p, P.tables.bytes, cudaMemcpyDeviceToHost));
@@ -1028,10 +1043,11 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
     }
     // patch descriptors; stage and upload only the range whose operands
     // changed since the last call.  Only an upload waits (for the copy that
-    // last read the pinned staging buffer it reuses): a call whose
-    // descriptors are unchanged does not hold the host back, so the host can
-    // run many calls ahead of the device and a brief host stall leaves the
-    // device busy
+    // last read the pinned staging slot it reuses): a call whose descriptors
+    // are unchanged does not hold the host back, and one that changes a few
+    // (a new output tensor each call) waits for the upload 64 calls back, so
+    // the host can run many calls ahead of the device and a brief host stall
+    // leaves the device busy
     const size_t nd = P.desc_step.size();
     if (P.mirror.size() != nd) P.mirror.resize(nd);
     size_t lo = nd, hi = 0;
@@ -1051,14 +1067,24 @@ void run_plan(Plan &P, const rosnet_network *nets, rosnet_btensor *outs, cudaStr
     }
     P.mirror_valid = true;
     if (lo < hi) {
-        const int r = P.ring;
-        P.ring = (P.ring + 1) % Plan::kRing;
-        RN_CHECK_CUDA(cudaEventSynchronize(P.ev[r]));
-        GettDesc *h = P.pinned[r];
-        std::copy(P.mirror.begin() + lo, P.mirror.begin() + hi, h + lo);
-        RN_CHECK_CUDA(cudaMemcpyAsync((GettDesc *)P.descs.p + lo, h + lo, (hi - lo) * sizeof(GettDesc),
+        GettDesc *h;   // the staging slot: the changed range goes to its start
+        cudaEvent_t e;
+        if (hi - lo <= Plan::kSmall) {
+            const int r = P.ring_small;
+            P.ring_small = (r + 1) % Plan::kSmallRing;
+            h = P.pinned_small + (size_t)r * Plan::kSmall;
+            e = P.ev_small[r];
+        } else {
+            const int r = P.ring;
+            P.ring = (r + 1) % Plan::kRing;
+            h = P.pinned[r];
+            e = P.ev[r];
+        }
+        RN_CHECK_CUDA(cudaEventSynchronize(e));   // the copy that last read the slot is done
+        std::copy(P.mirror.begin() + lo, P.mirror.begin() + hi, h);
+        RN_CHECK_CUDA(cudaMemcpyAsync((GettDesc *)P.descs.p + lo, h, (hi - lo) * sizeof(GettDesc),
                                       cudaMemcpyHostToDevice, s));
-        RN_CHECK_CUDA(cudaEventRecord(P.ev[r], s));
+        RN_CHECK_CUDA(cudaEventRecord(e, s));
     }
 
     const bool timing = (P.flags & ROSNET_OPT_TIMING) && P.heavy >= 0;
