@@ -147,6 +147,23 @@ def test_fused_small_steps_match_wave_launches():
     assert amp_err(amps[0], ref, 20) <= 1e-5
 
 
+def test_many_calls_each_into_a_new_output():
+    """Every call returns a new output tensor, which the final step writes
+    straight into, so every call uploads that step's descriptor through the
+    plan's ring of small staging slots (64 of them).  150 calls with every
+    earlier output still alive wrap the ring twice; each result is bitwise the
+    first one, and the first matches the state vector."""
+    circ = W.random_circuit(8, 8, 3)
+    net = W.circuit_network(circ)
+    ts = [R.btensor(np.asarray(t, dtype=np.complex64)) for t in net.tensors]
+    path = R.path_greedy(ts, net.labels, net.out_labels)
+    gn = R.Network(ts, net.labels, net.out_labels)
+    outs = [R.contract(gn, path=path, flags=R.OPT_GRAPH) for _ in range(150)]
+    vals = [complex(o.download()) for o in outs]
+    assert all(v == vals[0] for v in vals)
+    assert amp_err(vals[0], oracle.amplitude_sv(circ), 8) <= TOL[R.C64]
+
+
 # Tensor-core split products on the same workload, against the state vector.
 # 3xTF32 keeps about 22 significant bits per operand and reaches the FP32
 # bar.  3xBF16 keeps about 16 (hi + lo, each 8 bits; the lo*lo product and
